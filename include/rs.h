@@ -1,0 +1,184 @@
+/*
+ * rs.h -- C ABI of librs: exact bivariate resultants Res_y(f, g) in Z[x] on
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (paper, Section 2, Eq. (2.1)): f, g in Z[x, y],
+ *     f = sum_{i,j} f_ij x^i y^j = sum_{j=0}^{m_y} f_j^{(y)}(x) y^j,
+ * and likewise g with y-degree n_y.  Output (Section 3.1): the resultant
+ * R^{(y)} = res(f, g, y) in Z[x], the determinant of the (m_y+n_y)-square
+ * Sylvester matrix whose first n_y rows hold f_{m_y}^{(y)}, ..., f_0^{(y)}
+ * and whose last m_y rows hold g_{n_y}^{(y)}, ..., g_0^{(y)}, each row shifted
+ * one column right of the one above it.  deg R^{(y)} <= m * n (total degrees).
+ *
+ * Method (Section 4.1, Collins' modular algorithm): coefficients are mapped
+ * to Z_p for many 31-bit primes p and evaluated at many points x_i; one
+ * univariate resultant z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p is
+ * taken per (prime, point); R mod p is interpolated per prime; the integer
+ * coefficients are recovered by Chinese remaindering.  All of it runs on the
+ * GPU; the host only plans (degrees, bounds, prime count) and copies.
+ *
+ * Conventions where the paper is silent: f == 0 or g == 0 gives R = 0;
+ * m_y = n_y = 0 gives R = 1 (empty determinant).  Degrees are taken after
+ * trimming zero rows/columns; the y-degrees used are the actual y-degrees of
+ * f and g over Z[x].
+ *
+ * Memory: every pointer in this header is a HOST pointer.  Input arrays are
+ * owned by the caller and only read during the call.  Output arrays are owned
+ * by the caller and written only when the call returns RS_OK.  The context
+ * owns all device memory, its CUDA stream and its CUDA graphs.  A context is
+ * bound to the CUDA device that was current (or named in rs_config) when it
+ * was created and is not thread-safe: use one context per host thread.
+ *
+ * Errors: every int-returning call returns RS_OK (0), RS_PENDING (1) or a
+ * negative RS_ERR_* code; rs_last_error() gives a one-line description.
+ */
+#ifndef RS_H
+#define RS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RS_OK = 0,
+  RS_PENDING = 1,        /* serving: request not finished yet */
+  RS_ERR_ARG = -1,       /* NULL pointer, negative extent, limbs out of range */
+  RS_ERR_CAPACITY = -2,  /* output buffer too small; out->deg/limbs hold the need */
+  RS_ERR_NOMEM = -3,     /* device or host allocation failed / pool exhausted */
+  RS_ERR_CUDA = -4,      /* a CUDA runtime call failed (no device, launch error) */
+  RS_ERR_TIMEOUT = -5,   /* a bounded device-side wait ran out */
+  RS_ERR_LIMIT = -6,     /* input exceeds a library limit (see RS_MAX_*) */
+  RS_ERR_STATE = -7      /* call not valid in the object's current state */
+};
+
+/* Library limits. */
+#define RS_MAX_LIMBS 64        /* input coefficients up to 2048 bits */
+#define RS_MAX_DEG_Y 71        /* y-degree of f and of g */
+#define RS_MAX_POINTS 16384    /* degree bound D + 1 of the resultant */
+#define RS_MAX_PRIMES 16384    /* 31-bit primes available for the CRT */
+
+/* A bivariate polynomial f in Z[x, y] (Eq. (2.1)), dense, x-major:
+ * coefficient f_ij is coeffs[((i * (deg_y + 1)) + j) * limbs + k], k = 0..limbs-1,
+ * little-endian 32-bit limbs in two's complement.  deg_x, deg_y are the array
+ * extents minus one (>= 0); zero top rows/columns are allowed and trimmed. */
+typedef struct {
+  int32_t deg_x;
+  int32_t deg_y;
+  int32_t limbs;
+  const uint32_t *coeffs;
+} rs_bipoly;
+
+/* A univariate result R in Z[x]: coefficient of x^i is
+ * coeffs[i * limbs + k], k = 0..limbs-1, two's complement.  capacity_words is
+ * set by the caller (u32 words available); deg (-1 for R = 0) and limbs are
+ * written by the library.  On RS_ERR_CAPACITY, deg and limbs hold the bound
+ * that the caller must provide room for ((deg + 1) * limbs words). */
+typedef struct {
+  int32_t deg;
+  int32_t limbs;
+  int64_t capacity_words;
+  uint32_t *coeffs;
+} rs_upoly;
+
+typedef struct {
+  int32_t device;            /* CUDA device ordinal, -1 = the current device */
+  int32_t tile_points;       /* G1 points per block: 32, 64 or 128; 0 = autotuned/default */
+  int32_t use_graphs;        /* 1 = replay batch runs as CUDA graphs */
+  int32_t persistent;        /* 1 = persistent G1 over a cost-sorted tile list */
+  int32_t timing;            /* 1 = record per-stage CUDA events on each run */
+  int32_t reserved;
+  int64_t mem_limit_bytes;   /* serving: device bytes admitted requests may hold; 0 = auto */
+} rs_config;
+
+typedef struct rs_ctx rs_ctx;
+typedef struct rs_batch rs_batch;
+
+/* Fill *cfg with the defaults (device -1, tiles autotuned, graphs and
+ * persistent kernels on, timing off, memory limit auto). */
+int rs_config_default(rs_config *cfg);
+
+/* Create a context on the configured device: allocates the prime table and
+ * its CRT constants on the device and a non-blocking stream.  cfg may be
+ * NULL for the defaults.  Returns RS_ERR_CUDA when no usable GPU exists. */
+int rs_create(rs_ctx **ctx, const rs_config *cfg);
+
+/* Release every device resource of the context (batches included). */
+int rs_destroy(rs_ctx *ctx);
+
+/* The context's CUDA stream (a cudaStream_t) for callers that time or order
+ * work around the library's launches. */
+int rs_stream(rs_ctx *ctx, void **stream);
+
+/* Static description of an error code, and the last error of a context
+ * (ctx may be NULL for errors of calls that have no context). */
+const char *rs_error_string(int code);
+const char *rs_last_error(const rs_ctx *ctx);
+
+/* Host-only planning, no GPU needed: the degree bound D of R (Section 3.1:
+ * D = min(m_x n_y + n_x m_y, m n)), the limbs an output coefficient needs
+ * (from the Hadamard bound on the Sylvester rows, |coef R| < 2^bits), and
+ * the number of 31-bit primes the CRT uses.  Any output pointer may be NULL.
+ * *deg_bound is -1 when f or g is zero. */
+int rs_result_bound(const rs_bipoly *f, const rs_bipoly *g, int32_t *deg_bound,
+                    int32_t *limbs_bound, int32_t *primes, int32_t *bits);
+
+/* R = Res_y(f, g) (Section 3.1) through the modular method (Section 4.1). */
+int rs_resultant_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out);
+
+/* n independent resultants out[i] = Res_y(f[i], g[i]) in one batched run:
+ * one persistent G1 launch per register-capacity class over the flattened
+ * (pair, prime, point) work list, then batched interpolation and CRT.
+ * status (may be NULL) receives each pair's code; the call returns the
+ * first failure, RS_OK if none. */
+int rs_resultant_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
+                       rs_upoly *out, int32_t *status);
+
+/* Prepared batches: plan once and keep the inputs resident on the device,
+ * then run as often as wanted.  rs_batch_run only enqueues on the context's
+ * stream (a CUDA graph when enabled); rs_batch_sync waits for it;
+ * rs_batch_results copies the last run's results to the host. */
+int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
+                    rs_batch **batch);
+int rs_batch_upload(rs_batch *batch, int32_t n, const rs_bipoly *f, const rs_bipoly *g);
+int rs_batch_run(rs_batch *batch);
+int rs_batch_sync(rs_batch *batch);
+int rs_batch_results(rs_batch *batch, rs_upoly *out, int32_t *status);
+int rs_batch_destroy(rs_batch *batch);
+
+/* Work and timing of a prepared batch.  Counts are per run; stage times are
+ * those of the last run (only when rs_config.timing = 1, else -1). */
+typedef struct {
+  int64_t pairs;
+  int64_t images;             /* (pair, prime, point) univariate resultants */
+  int64_t primes_total;       /* sum over pairs of the prime count K */
+  int64_t coeffs_total;       /* sum over pairs of D + 1 */
+  double modmul_eval;         /* algorithmic modular products: evaluation (a3) */
+  double modmul_prs;          /* univariate resultants (a4) */
+  double modmul_interp;       /* interpolation (a5) */
+  double modmul_crt;          /* Garner CRT (a6) */
+  int64_t input_bytes;        /* host->device bytes of one upload */
+  int64_t output_bytes;       /* device->host bytes of one result fetch */
+  float ms_images;            /* G1 (reduce + evaluate + resultant) */
+  float ms_interp;            /* G2 */
+  float ms_crt;               /* G3 */
+  float ms_total;
+  int64_t unlucky_points;     /* images with lc_y f(x_i) lc_y g(x_i) = 0 mod p */
+  int64_t degenerate_images;  /* images whose remainder sequence hit a zero pivot */
+  int64_t unlucky_primes;     /* (pair, prime) with lc_y f or lc_y g = 0 mod p */
+} rs_batch_info;
+
+int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
+
+/* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
+ * (Section 4.1) for the first nprimes primes of the library's table and the
+ * points x_i = 0..npoints-1.  primes_out[nprimes] receives the primes,
+ * images_out[k * npoints + i] the image for prime k at x_i (0 <= z < p). */
+int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes,
+              int32_t npoints, uint32_t *primes_out, uint32_t *images_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RS_H */

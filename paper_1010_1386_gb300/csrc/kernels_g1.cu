@@ -1,0 +1,253 @@
+// G1: fused modular reduction + evaluation + univariate resultant, one
+// thread per modular image (pair, prime p, point x_i).  Paper, Section 4.1:
+// Collins' algorithm maps f, g to Z_p and evaluates them at points x_i
+// (steps 1-2), then takes z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p.
+//
+// The univariate resultant keeps the formal degrees (a, b) = (m_y, n_y) of
+// the Sylvester matrix of Section 3.1, so z_i^{(p)} = R^{(y)}(x_i) mod p for
+// every prime and point.  It is computed by a division-free remainder
+// sequence on the two coefficient vectors held in registers, top-aligned
+// (index 0 = leading coefficient), with one final inversion left to G2:
+//
+//   a >= b, l_B != 0:  A' = l_B A - l_A y^(a-b) B  (top term cancels, formal
+//                      degree a-1);  Res_{a,b}(A,B) l_B^{b-1} = (-1)^b Res_{a-1,b}(A',B)
+//   a <  b, l_A != 0:  B' = l_A B - l_B y^(b-a) A;  Res_{a,b}(A,B) l_A^{a-1} = Res_{a,b-1}(A,B')
+//   a >= b, l_B == 0:  Res_{a,b}(A,B) = l_A Res_{a,b-1}(A, B without its zero top)
+//   a <  b, l_A == 0:  Res_{a,b}(A,B) = (-1)^b l_B Res_{a-1,b}(A without its zero top, B)
+//   Res_{0,b}(A,B) = A_0^b,  Res_{a,0}(A,B) = B_0^a
+//
+// (each identity is a row operation on the Sylvester matrix followed by a
+// cofactor expansion along its first column).  The pivot powers
+// prod_t c_t^{e_t}, e_t = deg(pivot_t) - 1, are non-increasing in t, so they
+// are accumulated by Abel summation: with Q_t = c_1 ... c_t,
+// prod_t c_t^{e_t} = prod_t Q_t^{e_t - e_{t+1}}: one product per step into Q
+// and one into the denominator whenever e drops.
+//
+// Register arrays have a compile-time capacity C; once both degrees fit in
+// C - 8 entries the state moves to arrays of C - 8 (registers are renamed,
+// nothing is copied), so the unrolled update loops shrink with the degrees.
+#include "rs_internal.cuh"
+
+namespace {
+
+struct Prs {
+  int a, b;        // formal degrees of A and B
+  uint32_t num;    // numerator (Montgomery form)
+  uint32_t den;    // accumulated pivot powers (Montgomery form)
+  uint32_t Q;      // running product of pivots
+  int eprev;       // exponent of the previous pivot
+  uint32_t sign;   // parity of the accumulated (-1) factors
+  uint32_t degen;  // a zero pivot was met
+};
+
+__device__ __forceinline__ void settle(Prs &s, int e, uint32_t c, const ModP &m) {
+  while (s.eprev > e) {
+    s.den = mmul(s.den, s.Q, m);
+    --s.eprev;
+  }
+  s.Q = mmul(s.Q, c, m);
+  s.eprev = e;
+}
+
+// P[i] <- w1 P[i+1] + w2 V[i+1]; the top entry (which cancels) is dropped.
+template <int C>
+__device__ __forceinline__ void reduce_into(uint32_t (&P)[C], const uint32_t (&V)[C], uint32_t w1,
+                                            uint32_t w2, const ModP &m) {
+#pragma unroll
+  for (int i = 0; i < C - 1; ++i) P[i] = mmul2(P[i + 1], w1, V[i + 1], w2, m);
+  P[C - 1] = 0u;
+}
+
+template <int C>
+__device__ __forceinline__ void drop_top(uint32_t (&P)[C]) {
+#pragma unroll
+  for (int i = 0; i < C - 1; ++i) P[i] = P[i + 1];
+  P[C - 1] = 0u;
+}
+
+template <int C>
+__device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs &s, const ModP &m) {
+  // invariant: a, b <= C - 1
+  while (s.a > 0 && s.b > 0 && (C <= 8 || s.a > C - 9 || s.b > C - 9)) {
+    if (s.a >= s.b) {
+      const uint32_t lb = B[0];
+      if (lb != 0u) {
+        const uint32_t la = A[0];
+        settle(s, s.b - 1, lb, m);
+        reduce_into<C>(A, B, lb, mneg(la, m.p), m);
+        s.sign ^= (uint32_t)(s.b & 1);
+        --s.a;
+      } else {
+        s.num = mmul(s.num, A[0], m);
+        drop_top<C>(B);
+        --s.b;
+        s.degen = 1u;
+      }
+    } else {
+      const uint32_t la = A[0];
+      if (la != 0u) {
+        const uint32_t lb = B[0];
+        settle(s, s.a - 1, la, m);
+        reduce_into<C>(B, A, la, mneg(lb, m.p), m);
+        --s.b;
+      } else {
+        s.num = mmul(s.num, B[0], m);
+        s.sign ^= (uint32_t)(s.b & 1);
+        drop_top<C>(A);
+        --s.a;
+        s.degen = 1u;
+      }
+    }
+  }
+  if constexpr (C > 8) {
+    if (s.a > 0 && s.b > 0) {
+      uint32_t A2[C - 8], B2[C - 8];
+#pragma unroll
+      for (int i = 0; i < C - 8; ++i) {
+        A2[i] = A[i];
+        B2[i] = B[i];
+      }
+      prs_run<C - 8>(A2, B2, s, m);
+      return;
+    }
+  }
+  if (s.a == 0)
+    s.num = mmul(s.num, mpow(A[0], (uint32_t)s.b, m), m);
+  else
+    s.num = mmul(s.num, mpow(B[0], (uint32_t)s.a, m), m);
+}
+
+// P[r] = f_{deg - r}(x) (top-aligned), Horner over the staged residues.
+template <int C>
+__device__ __forceinline__ void eval_poly(uint32_t (&P)[C], const uint32_t *res, const int2 *meta,
+                                          int deg, uint32_t xm, const ModP &m) {
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    uint32_t v = 0u;
+    const int j = deg - r;
+    if (j >= 0) {
+      const int2 mt = meta[j];
+      if (mt.y >= 0) {
+        const uint32_t *c = res + mt.x;
+        v = c[mt.y];
+        for (int i = mt.y - 1; i >= 0; --i) v = madd(mmul(v, xm, m), c[i], m.p);
+      }
+    }
+    P[r] = v;
+  }
+}
+
+// Montgomery form of a two's-complement limb integer:
+// sum_l limb_l 2^(32 l) R - [negative] 2^(32 L) R, with V[l] = 2^(32 l) R^2.
+__device__ __forceinline__ uint32_t reduce_coef(const uint32_t *src, int L, const uint32_t *V,
+                                                const ModP &m) {
+  uint32_t acc = 0u;
+  for (int l = 0; l < L; ++l) acc = madd(acc, redc((uint64_t)src[l] * V[l], m.p, m.pinv), m.p);
+  if (src[L - 1] >> 31) acc = msub(acc, redc((uint64_t)V[L], m.p, m.pinv), m.p);
+  return acc;
+}
+
+__device__ __forceinline__ void stage_poly(uint32_t *sres, const int2 *smeta, int deg,
+                                           const uint32_t *limbs, int stride, int L,
+                                           const uint32_t *V, const ModP &m) {
+  for (int j = 0; j <= deg; ++j) {
+    const int2 mt = smeta[j];
+    for (int i = threadIdx.x; i <= mt.y; i += blockDim.x)
+      sres[mt.x + i] = reduce_coef(limbs + ((size_t)i * stride + j) * L, L, V, m);
+  }
+}
+
+template <int C>
+__global__ void __launch_bounds__(128) g1_kernel(G1Args a) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ int s_tile;
+  bool first = true;
+  for (;;) {
+    int t;
+    if (a.persistent) {
+      if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+      __syncthreads();
+      t = s_tile;
+    } else {
+      t = first ? (int)blockIdx.x : a.ntiles;
+    }
+    first = false;
+    if (t >= a.ntiles) return;
+
+    const Tile tl = a.tiles[t];
+    const PairDesc pd = a.pairs[tl.pair];
+    const ModP m = a.mods[tl.prime];
+    const uint32_t *V = a.vtab + (size_t)tl.prime * RS_VT_STRIDE;
+    const int nmeta = pd.my + pd.ny + 2;
+    int2 *smeta = reinterpret_cast<int2 *>(sm);
+    uint32_t *sres = sm + 2 * nmeta;
+
+    for (int i = threadIdx.x; i < nmeta; i += blockDim.x) smeta[i] = a.meta[pd.meta_off + i];
+    __syncthreads();
+    stage_poly(sres, smeta, pd.my, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, m);
+    stage_poly(sres, smeta + pd.my + 1, pd.ny, a.limbs + pd.g_off, pd.gstride, pd.Lg, V, m);
+    __syncthreads();
+
+    if (tl.x0 == 0 && threadIdx.x == 0) {  // unlucky prime: a leading coefficient vanishes mod p
+      bool zf = true, zg = true;
+      const int2 mf = smeta[pd.my], mg = smeta[pd.my + 1 + pd.ny];
+      for (int i = 0; i <= mf.y; ++i) zf = zf && sres[mf.x + i] == 0u;
+      for (int i = 0; i <= mg.y; ++i) zg = zg && sres[mg.x + i] == 0u;
+      if (zf || zg) atomicAdd(a.stats + ST_UNLUCKY_PRIMES, 1ull);
+    }
+
+    uint32_t unlucky = 0u, degen = 0u;
+    if ((int)threadIdx.x < tl.n) {
+      const int x = tl.x0 + (int)threadIdx.x;
+      const uint32_t xm = to_mont((uint32_t)x, m);
+      uint32_t A[C], B[C];
+      eval_poly<C>(A, sres, smeta, pd.my, xm, m);
+      eval_poly<C>(B, sres, smeta + pd.my + 1, pd.ny, xm, m);
+      unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
+      Prs s;
+      s.a = pd.my;
+      s.b = pd.ny;
+      s.num = s.den = s.Q = m.r1;
+      s.eprev = max(min(pd.my, pd.ny) - 1, 0);
+      s.sign = 0u;
+      s.degen = 0u;
+      prs_run<C>(A, B, s, m);
+      while (s.eprev > 0) {
+        s.den = mmul(s.den, s.Q, m);
+        --s.eprev;
+      }
+      const size_t idx = (size_t)pd.img_off + (size_t)tl.prime * pd.N + x;
+      a.num[idx] = s.sign ? mneg(s.num, m.p) : s.num;
+      a.den[idx] = s.den;
+      degen = s.degen;
+    }
+    const unsigned bu = __ballot_sync(0xffffffffu, unlucky);
+    const unsigned bd = __ballot_sync(0xffffffffu, degen);
+    if ((threadIdx.x & 31) == 0) {
+      if (bu) atomicAdd(a.stats + ST_UNLUCKY_POINTS, (unsigned long long)__popc(bu));
+      if (bd) atomicAdd(a.stats + ST_DEGENERATE, (unsigned long long)__popc(bd));
+    }
+    __syncthreads();  // the next tile restages shared memory
+  }
+}
+
+}  // namespace
+
+#ifndef RS_G1_CAP
+#error "compile this file once per register capacity with -DRS_G1_CAP=<8..72>"
+#endif
+#define RS_CAT2(a, b) a##b
+#define RS_CAT(a, b) RS_CAT2(a, b)
+
+cudaError_t RS_CAT(rs_g1_launch_, RS_G1_CAP)(int threads, int blocks, size_t smem, const G1Args &a,
+                                            cudaStream_t s) {
+  g1_kernel<RS_G1_CAP><<<blocks, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t RS_CAT(rs_g1_prepare_, RS_G1_CAP)(int threads, size_t smem, int *mb) {
+  cudaError_t e = cudaFuncSetAttribute(g1_kernel<RS_G1_CAP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(mb, g1_kernel<RS_G1_CAP>, threads, smem);
+}

@@ -1,0 +1,42 @@
+// Host-side planning of one resultant: trimmed degrees, the degree bound D,
+// the Hadamard bit bound, the prime count and the output limb count.
+#pragma once
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/rs.h"
+
+struct PolyInfo {
+  bool zero = true;
+  int my = -1;     // y-degree (largest j with f_j != 0)
+  int mx = -1;     // x-degree
+  int tdeg = -1;   // total degree
+  int L = 1;       // limbs per coefficient
+  int stride = 1;  // row stride of the input array (deg_y extent + 1)
+  int nc = 0;      // coefficients kept: sum_j (dx_j + 1)
+  std::vector<int> dx;  // x-degree of f_j, j = 0..my (-1 for f_j = 0)
+  double log2_rownorm2 = 0.0;  // log2 of sum_j ||f_j||_1^2 (rounded up)
+};
+
+struct PairPlan {
+  int status = RS_OK;
+  bool trivial_zero = false;  // f == 0 or g == 0: R = 0, no device work
+  PolyInfo f, g;
+  int D = 0;      // degree bound of R
+  int N = 0;      // points = D + 1
+  int bits = 0;   // |coef R| < 2^bits
+  int K = 0;      // primes
+  int Lout = 0;   // output limbs
+  int cap = 0;    // compiled register capacity class for G1
+  int staged = 0; // shared-memory words G1 stages per tile
+};
+
+// Analyse and plan; returns RS_OK or an error code (also stored in plan.status).
+// `log2p` lists log2 of the primes of the table in order (may be empty for
+// a bound-only query, in which case K is estimated from 31-bit primes).
+int rs_plan_pair(const rs_bipoly *f, const rs_bipoly *g, const std::vector<double> &log2p,
+                 PairPlan &plan, const char **why);
+
+// Primes in (2^31 - 2^20, 2^31), descending, by a sieve of Eratosthenes.
+std::vector<uint32_t> rs_prime_table(int count);

@@ -1,0 +1,81 @@
+// Internal layout shared by the host engine and the kernels of librs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "modarith.cuh"
+
+#define RS_VT_STRIDE 65  // V[k][l] = 2^(32 l) R^2 mod p_k, l = 0..RS_MAX_LIMBS
+
+// Stage counters written by the kernels (detection of unlucky / degenerate cases).
+enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT = 4 };
+
+// One resultant of a batch, as the kernels see it.  Degrees are trimmed.
+struct PairDesc {
+  int32_t my, ny;      // actual y-degrees of f and g
+  int32_t N;           // evaluation points = degree bound D + 1
+  int32_t K;           // primes
+  int32_t Lf, Lg;      // input limbs per coefficient
+  int32_t fstride, gstride;  // input row stride in coefficients (= array deg_y + 1)
+  int32_t fnc, gnc;    // coefficients kept (sum over j of deg_x f_j + 1)
+  int32_t Lout;        // output limbs per coefficient
+  int32_t pad;
+  int64_t f_off, g_off;  // word offsets of the input limb arrays
+  int64_t meta_off;      // int2 offset: (my+1) entries for f then (ny+1) for g
+  int64_t img_off;       // offset of the K*N image block (prime-major)
+  int64_t out_off;       // offset of the N*Lout output block (coefficient-major)
+};
+
+// G1 work item: points [x0, x0 + n) of one (pair, prime).
+struct Tile {
+  int32_t pair;
+  int32_t prime;
+  int32_t x0;
+  int32_t n;
+};
+
+struct G1Args {
+  const PairDesc *pairs;
+  const Tile *tiles;
+  int32_t ntiles;
+  int32_t persistent;
+  int32_t *counter;        // persistent tile counter (zeroed before launch)
+  const uint32_t *limbs;   // batch input limbs
+  const int2 *meta;        // per-j (start in the staged residue array, x-degree or -1)
+  const ModP *mods;
+  const uint32_t *vtab;    // [prime][RS_VT_STRIDE]
+  uint32_t *num;           // numerators  (Montgomery form, sign applied)
+  uint32_t *den;           // denominators (Montgomery form, non-zero)
+  unsigned long long *stats;
+};
+
+struct G2Args {
+  const PairDesc *pairs;
+  const int2 *tasks;       // (pair, prime)
+  const ModP *mods;
+  const uint32_t *num;     // in: numerators
+  const uint32_t *den;     // in: denominators
+  uint32_t *coef;          // out: R mod p coefficients, plain form (may alias num)
+};
+
+struct G3Args {
+  const PairDesc *pairs;
+  const int2 *tasks;       // (pair, first coefficient) per block
+  const ModP *mods;
+  const uint32_t *crt;     // (p_0 ... p_{k-1})^{-1} mod p_k, Montgomery form
+  uint32_t *coef;          // in: R mod p_k (plain); overwritten by mixed-radix digits
+  uint32_t *xl;            // scratch, limb-major per pair: [l][N]
+  uint32_t *out;           // out: [coefficient][limb]
+};
+
+// Launchers (kernels_*.cu).  Each returns the cudaGetLastError() of its launch.
+cudaError_t launch_g1(int cap, int threads, int blocks, size_t smem, const G1Args &a, cudaStream_t s);
+int g1_supported_cap(int cap);           // smallest compiled register capacity >= cap, or 0
+cudaError_t g1_prepare(int cap, int threads, size_t smem, int *max_blocks_per_sm);
+cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cudaStream_t s);
+cudaError_t g2_prepare(size_t smem);
+cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s);
+cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
+                               uint32_t *crt, cudaStream_t s);
+cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *num, const uint32_t *den,
+                                   uint32_t *z, int K, int N, cudaStream_t s);

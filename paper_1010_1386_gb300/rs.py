@@ -1,0 +1,267 @@
+"""ctypes binding of librs (include/rs.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts
+Python polynomials to the C structs and results back.  There is no fallback:
+if ``librs.so`` is missing or cannot be loaded, ``load()`` raises.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_uint32, c_void_p
+
+import numpy as np
+
+from .inputs import BiPoly
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librs.so")
+
+RS_OK, RS_PENDING = 0, 1
+ERRORS = {-1: "RS_ERR_ARG", -2: "RS_ERR_CAPACITY", -3: "RS_ERR_NOMEM", -4: "RS_ERR_CUDA",
+          -5: "RS_ERR_TIMEOUT", -6: "RS_ERR_LIMIT", -7: "RS_ERR_STATE"}
+RS_MAX_LIMBS, RS_MAX_DEG_Y, RS_MAX_POINTS, RS_MAX_PRIMES = 64, 71, 16384, 16384
+
+# Every function that include/rs.h declares, with its ctypes signature.
+EXPORTS = {}
+
+
+class rs_bipoly(ctypes.Structure):
+    _fields_ = [("deg_x", c_int32), ("deg_y", c_int32), ("limbs", c_int32),
+                ("coeffs", POINTER(c_uint32))]
+
+
+class rs_upoly(ctypes.Structure):
+    _fields_ = [("deg", c_int32), ("limbs", c_int32), ("capacity_words", c_int64),
+                ("coeffs", POINTER(c_uint32))]
+
+
+class rs_config(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("tile_points", c_int32), ("use_graphs", c_int32),
+                ("persistent", c_int32), ("timing", c_int32), ("reserved", c_int32),
+                ("mem_limit_bytes", c_int64)]
+
+
+class rs_batch_info(ctypes.Structure):
+    _fields_ = [("pairs", c_int64), ("images", c_int64), ("primes_total", c_int64),
+                ("coeffs_total", c_int64), ("modmul_eval", c_double), ("modmul_prs", c_double),
+                ("modmul_interp", c_double), ("modmul_crt", c_double), ("input_bytes", c_int64),
+                ("output_bytes", c_int64), ("ms_images", c_float), ("ms_interp", c_float),
+                ("ms_crt", c_float), ("ms_total", c_float), ("unlucky_points", c_int64),
+                ("degenerate_images", c_int64), ("unlucky_primes", c_int64)]
+
+
+_P = POINTER
+_SIGS = {
+    "rs_config_default": (c_int32, [_P(rs_config)]),
+    "rs_create": (c_int32, [_P(c_void_p), _P(rs_config)]),
+    "rs_destroy": (c_int32, [c_void_p]),
+    "rs_stream": (c_int32, [c_void_p, _P(c_void_p)]),
+    "rs_error_string": (c_char_p, [c_int32]),
+    "rs_last_error": (c_char_p, [c_void_p]),
+    "rs_result_bound": (c_int32, [_P(rs_bipoly), _P(rs_bipoly), _P(c_int32), _P(c_int32),
+                                  _P(c_int32), _P(c_int32)]),
+    "rs_resultant_y": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly)]),
+    "rs_resultant_batch": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly),
+                                     _P(rs_upoly), _P(c_int32)]),
+    "rs_batch_create": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), _P(c_void_p)]),
+    "rs_batch_upload": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
+    "rs_batch_run": (c_int32, [c_void_p]),
+    "rs_batch_sync": (c_int32, [c_void_p]),
+    "rs_batch_results": (c_int32, [c_void_p, _P(rs_upoly), _P(c_int32)]),
+    "rs_batch_destroy": (c_int32, [c_void_p]),
+    "rs_batch_info_get": (c_int32, [c_void_p, _P(rs_batch_info)]),
+    "rs_images": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, c_int32,
+                            _P(c_uint32), _P(c_uint32)]),
+}
+
+_lib = None
+
+
+def load(path=None):
+    """Load librs.so (raises OSError if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"librs.so not built at {p}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+        EXPORTS[name] = fn
+    if path is None:
+        _lib = lib
+    return lib
+
+
+class RsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(rc, ctx=None):
+    if rc < 0:
+        lib = load()
+        raise RsError(rc, (lib.rs_last_error(ctx) or b"").decode())
+    return rc
+
+
+def as_bipoly(f):
+    return f if isinstance(f, BiPoly) else BiPoly.from_ints(f)
+
+
+class _Polys:
+    """Keeps the limb arrays alive while C structs point at them."""
+
+    def __init__(self, polys):
+        self.arrays = [np.ascontiguousarray(as_bipoly(p).coeffs, dtype=np.uint32) for p in polys]
+        self.structs = (rs_bipoly * max(len(polys), 1))()
+        for s, a in zip(self.structs, self.arrays):
+            s.deg_x, s.deg_y, s.limbs = a.shape[0] - 1, a.shape[1] - 1, a.shape[2]
+            s.coeffs = a.ctypes.data_as(POINTER(c_uint32))
+
+
+def result_bound(f, g):
+    """Host-only planning: degree bound, output limbs, primes, bits."""
+    lib = load()
+    P = _Polys([f, g])
+    d, l, k, b = c_int32(), c_int32(), c_int32(), c_int32()
+    _check(lib.rs_result_bound(ctypes.byref(P.structs[0]), ctypes.byref(P.structs[1]),
+                               ctypes.byref(d), ctypes.byref(l), ctypes.byref(k), ctypes.byref(b)))
+    return {"deg": d.value, "limbs": l.value, "primes": k.value, "bits": b.value}
+
+
+def limbs_to_ints(words, deg, limbs):
+    if deg < 0:
+        return []
+    w = np.ascontiguousarray(words[: (deg + 1) * limbs]).astype("<u4").reshape(deg + 1, limbs)
+    return [int.from_bytes(r.tobytes(), "little", signed=True) for r in w]
+
+
+class _Outputs:
+    def __init__(self, pairs):
+        self.bufs = []
+        self.structs = (rs_upoly * max(len(pairs), 1))()
+        for s, (f, g) in zip(self.structs, pairs):
+            b = result_bound(f, g)
+            words = max(1, (b["deg"] + 1) * b["limbs"])
+            buf = np.zeros(words, dtype=np.uint32)
+            self.bufs.append(buf)
+            s.capacity_words = words
+            s.coeffs = buf.ctypes.data_as(POINTER(c_uint32))
+
+    def ints(self):
+        return [limbs_to_ints(b, s.deg, s.limbs) for s, b in zip(self.structs, self.bufs)]
+
+    def raw(self):
+        return [(s.deg, s.limbs, b) for s, b in zip(self.structs, self.bufs)]
+
+
+class Context:
+    """One librs context (device memory, stream, prime tables) on one GPU."""
+
+    def __init__(self, device=-1, tile_points=0, use_graphs=True, persistent=True, timing=False,
+                 mem_limit_bytes=0):
+        lib = load()
+        cfg = rs_config()
+        _check(lib.rs_config_default(ctypes.byref(cfg)))
+        cfg.device, cfg.tile_points = device, tile_points
+        cfg.use_graphs, cfg.persistent, cfg.timing = int(use_graphs), int(persistent), int(timing)
+        cfg.mem_limit_bytes = mem_limit_bytes
+        h = c_void_p()
+        _check(lib.rs_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self.lib, self.h = lib, h
+
+    def close(self):
+        if self.h:
+            self.lib.rs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self):
+        s = c_void_p()
+        _check(self.lib.rs_stream(self.h, ctypes.byref(s)), self.h)
+        return s.value or 0
+
+    def resultant_y(self, f, g):
+        """Res_y(f, g) as a list of Python ints (coefficient of x^i at i)."""
+        P = _Polys([f, g])
+        out = _Outputs([(f, g)])
+        _check(self.lib.rs_resultant_y(self.h, ctypes.byref(P.structs[0]),
+                                       ctypes.byref(P.structs[1]), out.structs), self.h)
+        return out.ints()[0]
+
+    def resultant_batch(self, pairs, raw=False):
+        F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        out = _Outputs(pairs)
+        status = (c_int32 * max(len(pairs), 1))()
+        _check(self.lib.rs_resultant_batch(self.h, len(pairs), F.structs, G.structs, out.structs,
+                                           status), self.h)
+        return out.raw() if raw else out.ints()
+
+    def images(self, f, g, nprimes, npoints):
+        """(primes[nprimes], images[nprimes, npoints]) with images[k, i] =
+        res(f(i, y), g(i, y), y) mod primes[k]."""
+        P = _Polys([f, g])
+        primes = np.zeros(nprimes, dtype=np.uint32)
+        imgs = np.zeros((nprimes, npoints), dtype=np.uint32)
+        _check(self.lib.rs_images(self.h, ctypes.byref(P.structs[0]), ctypes.byref(P.structs[1]),
+                                  nprimes, npoints, primes.ctypes.data_as(POINTER(c_uint32)),
+                                  imgs.ctypes.data_as(POINTER(c_uint32))), self.h)
+        return primes, imgs
+
+    def batch(self, pairs):
+        return Batch(self, pairs)
+
+
+class Batch:
+    """A prepared batch: inputs resident on the device, runs replayed."""
+
+    def __init__(self, ctx, pairs):
+        self.ctx, self.lib, self.n = ctx, ctx.lib, len(pairs)
+        self.F, self.G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        self.out = _Outputs(pairs)
+        self.status = (c_int32 * max(self.n, 1))()
+        h = c_void_p()
+        _check(self.lib.rs_batch_create(ctx.h, self.n, self.F.structs, self.G.structs,
+                                        ctypes.byref(h)), ctx.h)
+        self.h = h
+
+    def upload(self, pairs=None):
+        if pairs is not None:
+            self.F, self.G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        _check(self.lib.rs_batch_upload(self.h, self.n, self.F.structs, self.G.structs), self.ctx.h)
+
+    def run(self):
+        _check(self.lib.rs_batch_run(self.h), self.ctx.h)
+
+    def sync(self):
+        _check(self.lib.rs_batch_sync(self.h), self.ctx.h)
+
+    def results(self, raw=False):
+        _check(self.lib.rs_batch_results(self.h, self.out.structs, self.status), self.ctx.h)
+        return self.out.raw() if raw else self.out.ints()
+
+    def info(self):
+        i = rs_batch_info()
+        _check(self.lib.rs_batch_info_get(self.h, ctypes.byref(i)), self.ctx.h)
+        return {k: getattr(i, k) for k, _ in rs_batch_info._fields_}
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.lib.rs_batch_destroy(self.h)
+        self.h = None

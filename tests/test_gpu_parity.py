@@ -1,0 +1,219 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small inputs are compared coefficient by coefficient with the exact oracle;
+full-size workloads are checked on sampled values the oracle computes one by
+one: R(0), R(1), R(-1) exactly (determinants of integer Sylvester matrices),
+R(x0) mod q for random x0 and primes q outside the library's table, every
+sampled modular image z_i^{(p)} against det S(x_i) mod p, the degree bound
+and the coefficient bound.  Expected values never come from the GPU.
+"""
+import random
+
+import numpy as np
+import pytest
+
+from oracle import exact, modp
+from paper_1010_1386_gb300 import inputs, rs
+from tests.helpers import check_sampled_31, eval_mod, exact_points, rand_bipoly
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rs.Context(device=0, timing=True)
+    yield c
+    c.close()
+
+
+def oracle(f, g):
+    return exact.resultant_y(f, g)
+
+
+# ----------------------------------------------------------- exact, small
+
+def test_small_config_exact(ctx):
+    [(f, g)] = inputs.workload_small(0)
+    F, G = f.to_ints(), g.to_ints()
+    assert ctx.resultant_y(f, g) == oracle(F, G)
+
+
+def test_random_small_pairs_exact(ctx):
+    rng = random.Random(1)
+    pairs = []
+    for _ in range(60):
+        f = rand_bipoly(rng, rng.randint(0, 5), rng.randint(0, 6), bits=rng.choice([4, 20, 40, 90]))
+        g = rand_bipoly(rng, rng.randint(0, 5), rng.randint(0, 6), bits=rng.choice([4, 20, 40, 90]))
+        pairs.append((f, g))
+    got = ctx.resultant_batch(pairs)
+    for (f, g), r in zip(pairs, got):
+        assert r == oracle(f, g)
+    for f, g in pairs[:8]:
+        assert ctx.resultant_y(f, g) == oracle(f, g)
+
+
+def test_golden_examples(ctx):
+    from tests.test_oracle_pins import GOLDEN, load_golden
+    for path in GOLDEN:
+        f, g, R = load_golden(path)
+        assert ctx.resultant_y(f, g) == R
+
+
+def test_conventions_and_degenerate_inputs(ctx):
+    zero = [[0, 0], [0, 0]]
+    g = [[1, 2], [3, 4]]
+    assert ctx.resultant_y(zero, g) == []
+    assert ctx.resultant_y(g, zero) == []
+    assert ctx.resultant_y([[5]], [[7], [1]]) == [1]
+    f0 = [[2], [3]]  # m_y = 0: R = f^{n_y}
+    h = rand_bipoly(random.Random(2), 2, 3)
+    assert ctx.resultant_y(f0, h) == oracle(f0, h)
+    assert ctx.resultant_y(h, f0) == oracle(h, f0)
+    # common factor (y - x): R = 0, every image meets a zero pivot
+    rng = random.Random(3)
+    a, b = rand_bipoly(rng, 2, 2), rand_bipoly(rng, 1, 3)
+
+    def times_y_minus_x(p):
+        out = [[0] * (len(p[0]) + 1) for _ in range(len(p) + 1)]
+        for i, row in enumerate(p):
+            for j, c in enumerate(row):
+                out[i][j + 1] += c
+                out[i + 1][j] -= c
+        return out
+    assert ctx.resultant_y(times_y_minus_x(a), times_y_minus_x(b)) == []
+    # zero rows / columns are trimmed
+    padded = [row + [0, 0] for row in h] + [[0] * (len(h[0]) + 2)]
+    assert ctx.resultant_y(padded, f0) == oracle(h, f0)
+
+
+def test_unlucky_points_and_primes(ctx):
+    """lc_y f vanishing at x = 3 and 7 (every prime), and a leading
+    coefficient divisible by the first table prime 2^31 - 1."""
+    rng = random.Random(4)
+    g = rand_bipoly(rng, 3, 4, bits=30)
+    # lc_y f = (x - 3)(x - 7) = x^2 - 10 x + 21
+    f = rand_bipoly(rng, 2, 3, bits=30)
+    f[0][3], f[1][3], f[2][3] = 21, -10, 1
+    assert ctx.resultant_y(f, g) == oracle(f, g)
+    b = ctx.batch([(f, g)])
+    b.run()
+    info = b.info()
+    assert info["unlucky_points"] >= 2 * 1  # x = 3 and 7 for every prime
+    b.close()
+    f2 = rand_bipoly(rng, 2, 3, bits=30)
+    f2[0][3], f2[1][3], f2[2][3] = 2147483647, 0, 0
+    g2 = rand_bipoly(rng, 2, 3, bits=30)
+    g2[0][3], g2[1][3], g2[2][3] = 3 * 2147483647, 0, 0
+    assert ctx.resultant_y(f2, g2) == oracle(f2, g2)
+    b = ctx.batch([(f2, g2)])
+    b.run()
+    assert b.info()["unlucky_primes"] >= 1
+    b.close()
+
+
+def test_abnormal_remainder_sequences(ctx):
+    """Specialised pairs whose remainder sequences skip degrees (zero pivots)."""
+    rng = random.Random(5)
+    for _ in range(10):
+        # f = y^4 + c(x): g's odd terms vanish -> sparse sequences
+        f = [[0] * 5 for _ in range(3)]
+        f[0][4] = 1
+        f[0][0], f[1][0], f[2][0] = rng.randint(-9, 9), rng.randint(-9, 9), 1
+        g = [[0] * 3 for _ in range(2)]
+        g[0][2], g[1][0], g[0][0] = 1, rng.randint(-9, 9), rng.randint(-9, 9)
+        assert ctx.resultant_y(f, g) == oracle(f, g)
+        assert ctx.resultant_y(g, f) == oracle(g, f)
+
+
+# ------------------------------------------------------------ modular images
+
+def test_images_against_oracle(ctx):
+    rng = random.Random(6)
+    for dx, dy, bits in [(6, 6, 11), (3, 9, 64), (9, 2, 200)]:
+        f = rand_bipoly(rng, dx, dy, bits=bits)
+        g = rand_bipoly(rng, dx + 1, dy - 1 if dy > 1 else dy, bits=bits)
+        primes, imgs = ctx.images(f, g, 5, 70)
+        assert primes[0] == 2147483647 and all(primes[i] > primes[i + 1] for i in range(4))
+        for k in range(5):
+            for x in list(range(8)) + [rng.randrange(70) for _ in range(6)]:
+                assert int(imgs[k, x]) == modp.resultant_image(f, g, int(primes[k]), x)
+
+
+# ---------------------------------------------------------- full-size configs
+
+def test_single_dense30_full_size(ctx):
+    [(f, g)] = inputs.workload_single(1)
+    F, G = f.to_ints(), g.to_ints()
+    R = ctx.resultant_y(f, g)
+    bound = rs.result_bound(f, g)
+    assert len(R) - 1 <= bound["deg"] == 900
+    assert max(abs(c) for c in R).bit_length() < bound["bits"]
+    exact_points(F, G, R, points=(0, 1, -1, 2))
+    check_sampled_31(F, G, R, random.Random(7), samples=3)
+    primes, imgs = ctx.images(f, g, 3, 901)
+    for k in range(3):
+        for x in (0, 1, 450, 900):
+            assert int(imgs[k, x]) == eval_mod(R, x, int(primes[k]))
+
+
+def test_batch_full_size_sampled(ctx):
+    pairs = inputs.workload_batch(2, n=512)
+    got = ctx.resultant_batch(pairs)
+    rng = random.Random(8)
+    small = sorted(range(512), key=lambda i: pairs[i][0].deg_x * pairs[i][0].deg_y)[:2]
+    for i, ((f, g), R) in enumerate(zip(pairs, got)):
+        b = rs.result_bound(f, g)
+        assert len(R) - 1 <= b["deg"]
+        F, G = f.to_ints(), g.to_ints()
+        check_sampled_31(F, G, R, rng, samples=1)
+        if i in small or i < 2:
+            exact_points(F, G, R, points=(0,))
+
+
+def test_nongeneric_literal_is_zero(ctx):
+    pairs = inputs.workload_nongeneric(3, n=4)
+    for R in ctx.resultant_batch(pairs):
+        assert R == []
+
+
+def test_nongeneric_coprime_multiplicative(ctx):
+    """f = p q^2, g = d(pq)/dy: Res_y(f, g) = Res_y(p, g) Res_y(q, g)^2,
+    checked exactly with three independent GPU resultants, plus sampled
+    values against the oracle."""
+    rng = np.random.Generator(np.random.PCG64(3))
+    p = inputs.dense_total_degree(rng, 8, 64).to_ints()
+    q = inputs.dense_total_degree(rng, 4, 64).to_ints()
+    from paper_1010_1386_gb300.inputs import _dy, _from_dict, _mul_dict, _to_dict
+    P, Q = _to_dict(p), _to_dict(q)
+    PQ = _mul_dict(P, Q)
+    f = _from_dict(_mul_dict(PQ, Q))
+    g = _from_dict(_dy(PQ))
+    Rf, Rp, Rq = ctx.resultant_batch([(f, g), (p, g), (q, g)])
+    assert Rf == exact.zx_mul(Rp, exact.zx_mul(Rq, Rq))
+    check_sampled_31(f, g, Rf, random.Random(9), samples=2)
+
+
+def test_maximum_capacity_and_limbs(ctx):
+    rng = random.Random(10)
+    f = rand_bipoly(rng, 2, 71, bits=40)
+    g = rand_bipoly(rng, 1, 70, bits=40)
+    R = ctx.resultant_y(f, g)
+    check_sampled_31(f, g, R, rng, samples=2)
+    wide_f = rand_bipoly(rng, 2, 3, bits=2040)
+    wide_g = rand_bipoly(rng, 3, 2, bits=2040)
+    assert inputs.BiPoly.from_ints(wide_f).limbs == 64
+    assert ctx.resultant_y(wide_f, wide_g) == oracle(wide_f, wide_g)
+
+
+def test_errors(ctx):
+    rng = random.Random(11)
+    with pytest.raises(rs.RsError) as e:
+        ctx.resultant_y(rand_bipoly(rng, 1, 72), rand_bipoly(rng, 1, 2))
+    assert e.value.code == -6
+    lib = rs.load()
+    P = rs._Polys([[[1, 2], [3, 4]], [[5, 1]]])
+    out = (rs.rs_upoly * 1)()
+    out[0].capacity_words = 0
+    rc = lib.rs_resultant_y(ctx.h, P.structs, rs.ctypes.byref(P.structs[1]), out)
+    assert rc == -2 and out[0].deg >= 0
+    assert lib.rs_resultant_y(ctx.h, None, None, out) == -1
