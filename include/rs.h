@@ -167,6 +167,7 @@ typedef struct {
   int64_t unlucky_points;     /* images with lc_y f(x_i) lc_y g(x_i) = 0 mod p */
   int64_t degenerate_images;  /* images whose remainder sequence hit a zero pivot */
   int64_t unlucky_primes;     /* (pair, prime) with lc_y f or lc_y g = 0 mod p */
+  int64_t kernel_launches;    /* kernels of the library launched per run */
 } rs_batch_info;
 
 int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);

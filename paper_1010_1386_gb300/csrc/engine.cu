@@ -269,6 +269,7 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   b->ng2 = (int)g2.size();
   b->ng3 = (int)g3.size();
   b->g2smem = (size_t)3 * maxN * 4;
+  b->info.kernel_launches = (int64_t)b->classes.size() + (images_only ? 0 : (b->ng2 > 0) + (b->ng3 > 0));
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
 

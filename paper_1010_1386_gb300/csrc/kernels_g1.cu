@@ -246,8 +246,14 @@ cudaError_t RS_CAT(rs_g1_launch_, RS_G1_CAP)(int threads, int blocks, size_t sme
 }
 
 cudaError_t RS_CAT(rs_g1_prepare_, RS_G1_CAP)(int threads, size_t smem, int *mb) {
+  const size_t smem_used = smem;
+  // The attribute is per kernel, not per launch: always allow the largest
+  // staging any plan may request so that batches prepared earlier with more
+  // shared memory keep working.
+  (void)smem;
   cudaError_t e = cudaFuncSetAttribute(g1_kernel<RS_G1_CAP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       RS_G1_MAX_SMEM_BYTES);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(mb, g1_kernel<RS_G1_CAP>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(mb, g1_kernel<RS_G1_CAP>, threads, smem_used);
 }

@@ -219,7 +219,9 @@ __global__ void finalize_images_kernel(const ModP *mods, const uint32_t *num, co
 }  // namespace
 
 cudaError_t g2_prepare(size_t smem) {
-  return cudaFuncSetAttribute(g2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  (void)smem;  // per-kernel attribute: allow the largest any plan may need
+  return cudaFuncSetAttribute(g2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              RS_G2_MAX_SMEM_BYTES);
 }
 
 cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cudaStream_t s) {

@@ -6,6 +6,9 @@
 #include "modarith.cuh"
 
 #define RS_VT_STRIDE 65  // V[k][l] = 2^(32 l) R^2 mod p_k, l = 0..RS_MAX_LIMBS
+#define RS_G1_MAX_STAGED_WORDS (48 * 1024)  // staged residues + meta per G1 tile
+#define RS_G1_MAX_SMEM_BYTES (RS_G1_MAX_STAGED_WORDS * 4)
+#define RS_G2_MAX_SMEM_BYTES (3 * 16384 * 4)
 
 // Stage counters written by the kernels (detection of unlucky / degenerate cases).
 enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT = 4 };

@@ -46,7 +46,8 @@ class rs_batch_info(ctypes.Structure):
                 ("modmul_interp", c_double), ("modmul_crt", c_double), ("input_bytes", c_int64),
                 ("output_bytes", c_int64), ("ms_images", c_float), ("ms_interp", c_float),
                 ("ms_crt", c_float), ("ms_total", c_float), ("unlucky_points", c_int64),
-                ("degenerate_images", c_int64), ("unlucky_primes", c_int64)]
+                ("degenerate_images", c_int64), ("unlucky_primes", c_int64),
+                ("kernel_launches", c_int64)]
 
 
 _P = POINTER
