@@ -179,6 +179,36 @@ int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes,
               int32_t npoints, uint32_t *primes_out, uint32_t *images_out);
 
+/* Chinese remaindering that allocates nothing, for callers that may not
+ * allocate device memory (a plugin handed fixed buffers by its host
+ * application, code that must not call cudaMalloc/cudaFree because they can
+ * synchronise the device or fail under memory pressure, loops that forbid
+ * allocation).  The paper has no counterpart: this is a library facility.
+ *
+ * residues: DEVICE pointer, residues[k * ncoeffs + j] = R_j mod p_k (each
+ *   < p_k), p_k the k-th prime of the library's table (primes in
+ *   (2^31 - 2^20, 2^31), descending; rs_images reports them).
+ * out: DEVICE pointer, ncoeffs * limbs words; coefficient j is written as
+ *   two's-complement limbs out[j * limbs + l], the representative of R_j in
+ *   (-P/2, P/2), P = p_0 ... p_{nprimes-1}, truncated to `limbs` limbs.
+ * stream: a cudaStream_t (NULL = the legacy default stream); the call only
+ *   enqueues and returns, except on the first call on a device (below).
+ * Working memory is a fixed file-scope device array of 2^21 words (8 MiB)
+ * that every GPU which loads the library keeps until the process exits;
+ * calls need nprimes * ncoeffs + ncoeffs * limbs <= 2^21 and
+ * nprimes <= 2048, else RS_ERR_LIMIT without any device work.  Every word of
+ * that array is written before it is read, so no clearing is needed.
+ * The first call on each device (with that device current) sets up the
+ * device's constant tables and looks up the array's device address; it
+ * blocks until that is done, so make it before any stream capture.  All
+ * calls on a device share the one array: calls whose kernels overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or other allocating routine is called.
+ * Returns RS_OK, RS_ERR_ARG, RS_ERR_LIMIT or RS_ERR_CUDA (rs_last_error is
+ * not updated by this call). */
+int rs_crt_noalloc(const uint32_t *residues, int32_t nprimes, int32_t ncoeffs, int32_t limbs,
+                   uint32_t *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

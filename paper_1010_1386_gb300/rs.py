@@ -72,6 +72,7 @@ _SIGS = {
     "rs_batch_info_get": (c_int32, [c_void_p, _P(rs_batch_info)]),
     "rs_images": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, c_int32,
                             _P(c_uint32), _P(c_uint32)]),
+    "rs_crt_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
 }
 
 _lib = None

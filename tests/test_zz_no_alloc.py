@@ -1,0 +1,64 @@
+"""rs_crt_noalloc: the CRT entry point that allocates nothing, for callers
+that may not allocate device memory themselves or through the library (a
+plugin handed fixed buffers, code where cudaMalloc/cudaFree could
+synchronise the device or fail).  Its output must equal the regular
+resultant path's, bit for bit, on two calls in a row that share its fixed
+scratch array.  The test itself allocates the input and output buffers with
+torch, as such a caller's host application would."""
+import ctypes
+import random
+
+import numpy as np
+import pytest
+
+from paper_1010_1386_gb300 import rs
+from tests.helpers import rand_bipoly
+
+pytestmark = pytest.mark.gpu
+
+
+def _residues(R, primes, N):
+    res = np.zeros((len(primes), N), dtype=np.uint32)
+    for k, p in enumerate(primes):
+        for j, c in enumerate(R):
+            res[k, j] = c % p
+    return res
+
+
+def _run_noalloc(lib, torch, res, L):
+    K, N = res.shape
+    d_res = torch.from_numpy(res.view(np.int32).copy()).cuda()
+    d_out = torch.zeros(N * L, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.rs_crt_noalloc(ctypes.c_void_p(d_res.data_ptr()), K, N, L,
+                            ctypes.c_void_p(d_out.data_ptr()), ctypes.c_void_p(stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    out = d_out.cpu().numpy().view(np.uint32).reshape(N, L)
+    return [int.from_bytes(row.astype("<u4").tobytes(), "little", signed=True) for row in out]
+
+
+def test_noalloc_crt_matches_resultant_path():
+    torch = pytest.importorskip("torch")
+    lib = rs.load()
+    ctx = rs.Context(device=0)
+    rng = random.Random(31)
+    cases = [(rand_bipoly(rng, 4, 5, bits=40), rand_bipoly(rng, 3, 6, bits=40)),
+             (rand_bipoly(rng, 6, 3, bits=100), rand_bipoly(rng, 5, 4, bits=100))]
+    for f, g in cases:  # two calls in a row, different sizes, one shared scratch array
+        R = ctx.resultant_y(f, g)
+        b = rs.result_bound(f, g)
+        K, N, L = b["primes"], b["deg"] + 1, b["limbs"]
+        primes, _ = ctx.images(f, g, K, 1)
+        got = _run_noalloc(lib, torch, _residues(R, [int(p) for p in primes], N), L)
+        assert got == list(R) + [0] * (N - len(R))
+    ctx.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    lib = rs.load()
+    # both are refused on the host before any device work
+    assert lib.rs_crt_noalloc(ctypes.c_void_p(256), 4096, 10, 1, ctypes.c_void_p(256), None) == -6
+    assert lib.rs_crt_noalloc(ctypes.c_void_p(256), 100, 30000, 100, ctypes.c_void_p(256), None) == -6
+    assert lib.rs_crt_noalloc(None, 1, 1, 1, None, None) == -1
