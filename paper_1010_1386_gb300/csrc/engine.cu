@@ -54,6 +54,7 @@ struct rs_ctx {
   ModP *d_mods = nullptr;
   uint32_t *d_vtab = nullptr;
   uint32_t *d_crt = nullptr;
+  uint32_t *d_qbase = nullptr;
   std::string err;
   std::vector<rs_batch *> batches;
   rs_batch *cache = nullptr;
@@ -79,6 +80,9 @@ struct rs_batch {
   uint32_t *d_num = nullptr, *d_den = nullptr, *d_xl = nullptr, *d_out = nullptr;
   int2 *d_g2 = nullptr, *d_g3 = nullptr;
   unsigned long long *d_stats = nullptr;
+  uint32_t *d_finv = nullptr, *d_gtab = nullptr;  // interpolation tables [K][tab_stride]
+  int32_t *d_btab = nullptr;
+  int tab_k = 0, tab_stride = 0;
   uint32_t *h_in = nullptr, *h_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -137,8 +141,9 @@ static void free_batch(rs_batch *b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (auto &e : b->ev)
     if (e) cudaEventDestroy(e);
-  void *dev[] = {b->d_in, b->d_meta, b->d_pairs, b->d_tiles, b->d_counters, b->d_num, b->d_den,
-                 b->d_xl, b->d_out, b->d_g2, b->d_g3, b->d_stats};
+  void *dev[] = {b->d_in,  b->d_meta, b->d_pairs, b->d_tiles, b->d_counters, b->d_num,
+                 b->d_den, b->d_xl,   b->d_out,   b->d_g2,    b->d_g3,       b->d_stats,
+                 b->d_finv, b->d_gtab, b->d_btab};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_in) cudaFreeHost(b->h_in);
@@ -222,7 +227,7 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     const double imgs = (double)p.K * p.N;
     b->info.modmul_eval += imgs * (p.f.nc + p.g.nc);
     b->info.modmul_prs += imgs * 2.0 * prs_updates(p.f.my, p.g.my);
-    b->info.modmul_interp += (double)p.K * (1.5 * (double)p.D * (p.D + 1) + 6.0 * p.N);
+    b->info.modmul_interp += (double)p.K * ((double)p.N * p.N + 8.0 * p.N);
     b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
   }
 
@@ -256,10 +261,11 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
-  int maxN = 1;
+  int maxN = 1, maxK = 0;
   for (int i : byN) {
     const PairPlan &p = b->plans[i];
     maxN = std::max(maxN, p.N);
+    maxK = std::max(maxK, p.K);
     for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
   }
   for (int i : order) {
@@ -268,7 +274,9 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   }
   b->ng2 = (int)g2.size();
   b->ng3 = (int)g3.size();
-  b->g2smem = (size_t)3 * maxN * 4;
+  b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
+  b->tab_k = images_only ? 0 : maxK;
+  b->tab_stride = maxN;
   b->info.kernel_launches = (int64_t)b->classes.size() + (images_only ? 0 : (b->ng2 > 0) + (b->ng3 > 0));
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
@@ -292,6 +300,9 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   alloc((void **)&b->d_g2, g2.size() * sizeof(int2));
   alloc((void **)&b->d_g3, g3.size() * sizeof(int2));
   alloc((void **)&b->d_stats, ST_COUNT * sizeof(unsigned long long));
+  alloc((void **)&b->d_finv, (size_t)b->tab_k * b->tab_stride * 4);
+  alloc((void **)&b->d_gtab, (size_t)b->tab_k * b->tab_stride * 4);
+  alloc((void **)&b->d_btab, (size_t)b->tab_k * b->tab_stride * 4);
   if (rc == RS_OK && b->in_words) {
     cudaError_t e = cudaMallocHost((void **)&b->h_in, b->in_words * 4);
     if (e != cudaSuccess) rc = fail(ctx, RS_ERR_NOMEM, "cudaMallocHost (inputs)");
@@ -320,6 +331,12 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     }
     if (mb < 1) mb = 1;
     cl.blocks = ctx->cfg.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
+  }
+  if (rc == RS_OK && b->tab_k > 0) {
+    cudaError_t e = launch_interp_tables(ctx->d_mods, ctx->d_qbase, b->tab_k, b->tab_stride, b->d_finv,
+                                         b->d_gtab, b->d_btab, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("interpolation tables: ") + cudaGetErrorString(e));
   }
   if (rc == RS_OK && b->ng2) {
     cudaError_t e = g2_prepare(b->g2smem);
@@ -368,6 +385,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.limbs = b->d_in;
     a.meta = b->d_meta;
     a.mods = ctx->d_mods;
+    a.qbase = b->images_only ? nullptr : ctx->d_qbase;
     a.vtab = ctx->d_vtab;
     a.num = b->d_num;
     a.den = b->d_den;
@@ -384,6 +402,10 @@ static int enqueue(rs_batch *b, bool capturing) {
     a2.num = b->d_num;
     a2.den = b->d_den;
     a2.coef = b->d_num;
+    a2.finv = b->d_finv;
+    a2.gtab = b->d_gtab;
+    a2.btab = b->d_btab;
+    a2.tab_stride = b->tab_stride;
     RS_CUDA(ctx, launch_g2(256, b->ng2, b->g2smem, a2, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[2], s, capturing));
@@ -546,8 +568,9 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   chk(cudaMalloc(&ctx->d_mods, np * sizeof(ModP)), "cudaMalloc");
   chk(cudaMalloc(&ctx->d_vtab, (size_t)np * RS_VT_STRIDE * 4), "cudaMalloc");
   chk(cudaMalloc(&ctx->d_crt, np * 4), "cudaMalloc");
+  chk(cudaMalloc(&ctx->d_qbase, np * 4), "cudaMalloc");
   if (rc == RS_OK) chk(cudaMemcpy(ctx->d_primes, ctx->primes.data(), np * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-  if (rc == RS_OK) chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->stream), "prime tables");
+  if (rc == RS_OK) chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->stream), "prime tables");
   if (rc == RS_OK) chk(cudaStreamSynchronize(ctx->stream), "prime tables");
   if (rc != RS_OK) {
     rs_destroy(ctx);
@@ -564,7 +587,7 @@ int rs_destroy(rs_ctx *ctx) {
     for (rs_batch *b : ctx->batches) free_batch(b);
     if (ctx->cache) free_batch(ctx->cache);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt};
+    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase};
     for (void *p : dev)
       if (p) cudaFree(p);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -2,6 +2,9 @@
 // thread per modular image (pair, prime p, point x_i).  Paper, Section 4.1:
 // Collins' algorithm maps f, g to Z_p and evaluates them at points x_i
 // (steps 1-2), then takes z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p.
+// The points are the geometric progression x_i = q^i (q of multiplicative
+// order above the largest point count, chosen per prime), which G2 turns
+// back into coefficients with two convolutions.
 //
 // The univariate resultant keeps the formal degrees (a, b) = (m_y, n_y) of
 // the Sylvester matrix of Section 3.1, so z_i^{(p)} = R^{(y)}(x_i) mod p for
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(128) g1_kernel(G1Args a) {
     uint32_t unlucky = 0u, degen = 0u;
     if ((int)threadIdx.x < tl.n) {
       const int x = tl.x0 + (int)threadIdx.x;
-      const uint32_t xm = to_mont((uint32_t)x, m);
+      const uint32_t xm = a.qbase ? mpow(a.qbase[tl.prime], (uint32_t)x, m) : to_mont((uint32_t)x, m);
       uint32_t A[C], B[C];
       eval_poly<C>(A, sres, smeta, pd.my, xm, m);
       eval_poly<C>(B, sres, smeta + pd.my + 1, pd.ny, xm, m);

@@ -1,8 +1,8 @@
 // G2 (interpolation mod p), G3 (Garner CRT) and the per-prime constant
-// tables.  Paper, Section 4.1: "the resultant polynomial R^{(y)}(x) is
-// interpolated over the prime field Z_p and eventually lifted to an integer
-// solution via Chinese remaindering"; interpolation is the Vandermonde solve
-// on the points x_i, here the points 0, 1, ..., D, in Newton form.
+// tables.  Paper, Section 4.1: R^{(y)} is interpolated over Z_p from the
+// images z_i^{(p)} (a Vandermonde solve) and lifted to Z by Chinese
+// remaindering.
+#include "../../include/rs.h"
 #include "rs_internal.cuh"
 
 namespace {
@@ -75,9 +75,71 @@ __device__ void batch_invert(const uint32_t *d, uint32_t *out, int n, const ModP
   }
 }
 
-// One block per (pair, prime): images z_i = num_i / den_i at x_i = i, then
-// Newton divided differences c_k (x_i - x_{i-k} = k), then the Newton form
-// c_0 + x (c_1 + (x - 1) (c_2 + ...)) expanded to monomials.
+// Interpolation at the geometric points x_i = q^i, i = 0..D (Section 4.1
+// asks for the Vandermonde solve; on a geometric progression it factors into
+// two convolutions).  With F_t = prod_{s=1}^t (q^s - 1) and
+// b_t = (-1)^t q^{C(t,2)} / F_t:
+//   Newton coefficients  c_k = q^{-C(k,2)} sum_{j<=k} (z_j / F_j) b_{k-j}
+//   (the divided differences on a geometric progression, since
+//   prod_{l<=k, l!=j} (q^j - q^l) = q^{C(k,2)} (-1)^{k-j} F_j F_{k-j} / q^{C(k-j,2)}),
+//   monomial coefficients R_m = (1 / F_m) sum_{t<=D-m} (c_{m+t} F_{m+t}) b_t
+//   (q-binomial expansion of prod_{j<k} (x - q^j)).
+// Both sums are the convolution conv(x, b)_k = sum_{j<=k} x_j b_{k-j}, the
+// second one on the reversed sequence.  Residues enter it as signed
+// representatives |v| < 2^30, so 7 products accumulate exactly in an int64
+// and one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53
+// (every table prime exceeds 2^31 - 2^20, so 2^32 mod p <= 2^21).
+
+#define RS_CONV_R 7  // outputs per register block; odd, so lanes hit distinct banks
+
+__device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
+  return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
+}
+
+__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) {
+  return (s >> 32) * (int64_t)c32 + (int64_t)(uint32_t)s;
+}
+
+// Reduce a folded accumulator (|s| < 2^53) to [0, p) in Montgomery form.
+__device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
+  const uint64_t t = (uint64_t)(s + ((int64_t)m.p << 22));  // 0 <= t < 2^54 < p 2^32
+  return redc(t, m.p, m.pinv);
+}
+
+// y[k] = sum_{j<=k} x[j] b[k-j] for k < n (Montgomery form, reduced).  x and b
+// hold signed representatives and are zero for indices in [-RS_G2_PAD, 0)
+// and [n, n + RS_G2_PAD).
+__device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n, const ModP &m) {
+  constexpr int R = RS_CONV_R;
+  const uint32_t c32 = m.r1;  // 2^32 mod p
+  const int nblk = (n + R - 1) / R;
+  for (int bi = threadIdx.x; bi < nblk; bi += blockDim.x) {
+    const int k0 = bi * R;
+    int64_t acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
+    for (int j0 = 0; j0 <= k0; j0 += R) {
+      int32_t bw[2 * R - 1], av[R];
+      const int base = k0 - j0 - (R - 1);
+#pragma unroll
+      for (int i = 0; i < 2 * R - 1; ++i) bw[i] = b[base + i];
+#pragma unroll
+      for (int i = 0; i < R; ++i) av[i] = x[j0 + i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) acc[r] += (int64_t)av[jj] * bw[(R - 1) + r - jj];
+        acc[r] = fold64(acc[r], c32);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (k0 + r < n) y[k0 + r] = finish64(acc[r], m);
+  }
+}
+
+// One block per (pair, prime).  Shared memory: three regions of N words,
+// each with RS_G2_PAD zero words on both sides.
 __global__ void g2_kernel(G2Args a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t scratch[128];
@@ -85,53 +147,80 @@ __global__ void g2_kernel(G2Args a) {
   const PairDesc pd = a.pairs[task.x];
   const ModP m = a.mods[task.y];
   const int N = pd.N, D = N - 1, T = blockDim.x, tid = threadIdx.x;
-  uint32_t *B0 = sm, *B1 = sm + N, *B2 = sm + 2 * N;
+  const int W = N + 2 * RS_G2_PAD;
+  int32_t *X = reinterpret_cast<int32_t *>(sm) + RS_G2_PAD;
+  int32_t *Bs = X + W;
+  uint32_t *Y = reinterpret_cast<uint32_t *>(Bs + W);
   const size_t base = (size_t)pd.img_off + (size_t)task.y * N;
+  const size_t tb = (size_t)task.y * a.tab_stride;
+  const uint32_t *finv = a.finv + tb, *gt = a.gtab + tb;
+  const int32_t *bt = a.btab + tb;
 
-  for (int i = tid; i < N; i += T) {
-    B0[i] = a.num[base + i];
-    B1[i] = a.den[base + i];
+  // z_j = num_j / den_j (simultaneous inversion), then x_j = z_j / F_j
+  uint32_t *dens = reinterpret_cast<uint32_t *>(Bs);
+  for (int i = tid; i < N; i += T) dens[i] = a.den[base + i];
+  __syncthreads();
+  batch_invert(dens, Y, N, m, scratch);
+  __syncthreads();
+  for (int i = tid; i < N; i += T)
+    X[i] = signed_rep(mmul(mmul(a.num[base + i], Y[i], m), finv[i], m), m.p);
+  for (int i = tid; i < N; i += T) Bs[i] = bt[i];
+  for (int i = tid; i < RS_G2_PAD; i += T) {
+    X[-1 - i] = 0;
+    X[N + i] = 0;
+    Bs[-1 - i] = 0;
+    Bs[N + i] = 0;
   }
   __syncthreads();
-  batch_invert(B1, B2, N, m, scratch);
+  conv_lazy(X, Bs, Y, N, m);  // Y[k] = q^{C(k,2)} c_k
   __syncthreads();
-  for (int i = tid; i < N; i += T) {
-    B0[i] = mmul(B0[i], B2[i], m);  // z_i
-    B1[i] = i ? to_mont((uint32_t)i, m) : m.r1;
-  }
+  for (int k = tid; k < N; k += T) X[D - k] = signed_rep(mmul(Y[k], gt[k], m), m.p);  // c_k F_k reversed
   __syncthreads();
-  batch_invert(B1, B2, N, m, scratch);  // B2[k] = 1/k
+  conv_lazy(X, Bs, Y, N, m);  // Y[D - m] = sum_t c_{m+t} F_{m+t} b_t
   __syncthreads();
+  for (int i = tid; i < N; i += T) a.coef[base + i] = from_mont(mmul(Y[D - i], finv[i], m), m);
+}
 
-  for (int lev = 1; lev <= D; ++lev) {
-    const uint32_t *src = (lev & 1) ? B0 : B1;
-    uint32_t *dst = (lev & 1) ? B1 : B0;
-    const uint32_t ik = B2[lev];
-    for (int i = lev + tid; i <= D; i += T) dst[i] = mmul(msub(src[i], src[i - 1], m.p), ik, m);
-    __syncthreads();
-  }
-  for (int i = tid; i < N; i += T) B2[i] = (i & 1) ? B1[i] : B0[i];  // c_i
-  __syncthreads();
-
-  uint32_t *cur = B0, *nxt = B1;
-  if (tid == 0) cur[0] = B2[D];
-  __syncthreads();
-  for (int k = D - 1; k >= 0; --k) {
-    const uint32_t nk = mneg(to_mont((uint32_t)k, m), m.p);
-    const int len = D - k + 1;  // coefficients of the new polynomial
-    for (int j = tid; j < len; j += T) {
-      const uint32_t lo = j > 0 ? cur[j - 1] : 0u;
-      const uint32_t hi = j < len - 1 ? cur[j] : 0u;
-      uint32_t v = mmul2(lo, m.r1, hi, nk, m);  // lo - k hi
-      if (j == 0) v = madd(v, B2[k], m.p);
-      nxt[j] = v;
+// Per prime k < K, t < N: 1 / F_t, q^{-C(t,2)} F_t and the signed
+// (-1)^t q^{C(t,2)} / F_t, F_t = prod_{s=1}^t (q^s - 1).  One thread per prime.
+__global__ void interp_tables_kernel(const ModP *mods, const uint32_t *qbase, int K, int N,
+                                     uint32_t *finv, uint32_t *gtab, int32_t *btab) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const ModP m = mods[k];
+  const uint32_t q = qbase[k], qi = minv(q, m);
+  uint32_t *fi = finv + (size_t)k * N, *gt = gtab + (size_t)k * N;
+  int32_t *bt = btab + (size_t)k * N;
+  // forward: F_t (kept in fi for now) and q^{-C(t,2)} (kept in gt)
+  uint32_t F = m.r1, qt = m.r1, qneg = m.r1, qinvt = m.r1;  // q^t, q^{-C(t,2)}, q^{-(t-1)}
+  for (int t = 0; t < N; ++t) {
+    if (t > 0) {
+      qt = mmul(qt, q, m);
+      F = mmul(F, msub(qt, m.r1, m.p), m);
+      if (t > 1) qinvt = mmul(qinvt, qi, m);
+      qneg = mmul(qneg, qinvt, m);
     }
-    __syncthreads();
-    uint32_t *t = cur;
-    cur = nxt;
-    nxt = t;
+    fi[t] = F;
+    gt[t] = qneg;
   }
-  for (int j = tid; j < N; j += T) a.coef[base + j] = from_mont(cur[j], m);
+  // backward: 1 / F_t from 1 / F_{N-1}; q^{C(t,2)} from q^{C(N-1,2)}
+  uint32_t inv = minv(F, m);
+  uint32_t qc = minv(qneg, m);  // q^{C(N-1,2)}
+  uint32_t qm1 = qinvt;         // q^{-(t-1)} at t = N-1
+  for (int t = N - 1; t >= 0; --t) {
+    const uint32_t Ft = fi[t];
+    fi[t] = inv;
+    uint32_t bv = mmul(qc, inv, m);
+    if (t & 1) bv = mneg(bv, m.p);
+    bt[t] = signed_rep(bv, m.p);
+    gt[t] = mmul(gt[t], Ft, m);
+    if (t > 0) {
+      inv = mmul(inv, msub(qt, m.r1, m.p), m);  // 1/F_{t-1} = (q^t - 1) / F_t
+      qt = mmul(qt, qi, m);
+      qc = mmul(qc, qm1, m);                    // q^{C(t-1,2)} = q^{C(t,2)} q^{-(t-1)}
+      qm1 = mmul(qm1, q, m);
+    }
+  }
 }
 
 // One thread per output coefficient: Garner's mixed-radix digits in the
@@ -193,7 +282,7 @@ __global__ void g3_kernel(G3Args a) {
 // for the modular reduction of input coefficients) and the Garner constant
 // (p_0 ... p_{k-1})^{-1} mod p_k.
 __global__ void init_primes_kernel(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
-                                   uint32_t *crt) {
+                                   uint32_t *crt, uint32_t *qbase) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const ModP m = make_modp(primes[k]);
@@ -206,6 +295,22 @@ __global__ void init_primes_kernel(const uint32_t *primes, int n, ModP *mods, ui
   uint32_t acc = m.r1;
   for (int l = 0; l < k; ++l) acc = mmul(acc, to_mont(primes[l] - m.p, m), m);
   crt[k] = minv(acc, m);
+  // base of the geometric evaluation points: the smallest q >= 2 whose
+  // powers q^1 .. q^RS_MAX_POINTS all differ from 1 (so q^0 .. q^(N-1) are
+  // distinct and every q^t - 1 is invertible for t <= N - 1)
+  for (uint32_t c = 2;; ++c) {
+    const uint32_t qm = to_mont(c, m);
+    uint32_t x = qm;
+    int t = 1;
+    while (t <= RS_MAX_POINTS && x != m.r1) {
+      x = mmul(x, qm, m);
+      ++t;
+    }
+    if (t > RS_MAX_POINTS) {
+      qbase[k] = qm;
+      break;
+    }
+  }
 }
 
 __global__ void finalize_images_kernel(const ModP *mods, const uint32_t *num, const uint32_t *den,
@@ -217,6 +322,12 @@ __global__ void finalize_images_kernel(const ModP *mods, const uint32_t *num, co
 }
 
 }  // namespace
+
+cudaError_t launch_interp_tables(const ModP *mods, const uint32_t *qbase, int K, int N,
+                                 uint32_t *finv, uint32_t *gtab, int32_t *btab, cudaStream_t s) {
+  interp_tables_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, qbase, K, N, finv, gtab, btab);
+  return cudaGetLastError();
+}
 
 cudaError_t g2_prepare(size_t smem) {
   (void)smem;  // per-kernel attribute: allow the largest any plan may need
@@ -235,8 +346,8 @@ cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s) 
 }
 
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
-                               uint32_t *crt, cudaStream_t s) {
-  init_primes_kernel<<<(n + 127) / 128, 128, 0, s>>>(primes, n, mods, vtab, crt);
+                               uint32_t *crt, uint32_t *qbase, cudaStream_t s) {
+  init_primes_kernel<<<(n + 127) / 128, 128, 0, s>>>(primes, n, mods, vtab, crt, qbase);
   return cudaGetLastError();
 }
 

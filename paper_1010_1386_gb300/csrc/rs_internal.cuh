@@ -8,7 +8,8 @@
 #define RS_VT_STRIDE 65  // V[k][l] = 2^(32 l) R^2 mod p_k, l = 0..RS_MAX_LIMBS
 #define RS_G1_MAX_STAGED_WORDS (48 * 1024)  // staged residues + meta per G1 tile
 #define RS_G1_MAX_SMEM_BYTES (RS_G1_MAX_STAGED_WORDS * 4)
-#define RS_G2_MAX_SMEM_BYTES (3 * 16384 * 4)
+#define RS_G2_PAD 8          // zero words around each G2 shared-memory region
+#define RS_G2_MAX_SMEM_BYTES (3 * (16384 + 2 * RS_G2_PAD) * 4)
 
 // Stage counters written by the kernels (detection of unlucky / degenerate cases).
 enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT = 4 };
@@ -46,6 +47,7 @@ struct G1Args {
   const uint32_t *limbs;   // batch input limbs
   const int2 *meta;        // per-j (start in the staged residue array, x-degree or -1)
   const ModP *mods;
+  const uint32_t *qbase;   // q per prime (Montgomery): points x_i = q^i; NULL: x_i = i
   const uint32_t *vtab;    // [prime][RS_VT_STRIDE]
   uint32_t *num;           // numerators  (Montgomery form, sign applied)
   uint32_t *den;           // denominators (Montgomery form, non-zero)
@@ -59,6 +61,10 @@ struct G2Args {
   const uint32_t *num;     // in: numerators
   const uint32_t *den;     // in: denominators
   uint32_t *coef;          // out: R mod p coefficients, plain form (may alias num)
+  const uint32_t *finv;    // [prime][tab_stride] 1 / F_t           (Montgomery)
+  const uint32_t *gtab;    // [prime][tab_stride] q^{-C(t,2)} F_t   (Montgomery)
+  const int32_t *btab;     // [prime][tab_stride] (-1)^t q^{C(t,2)} / F_t, signed representative
+  int32_t tab_stride;
 };
 
 struct G3Args {
@@ -79,6 +85,8 @@ cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cud
 cudaError_t g2_prepare(size_t smem);
 cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
-                               uint32_t *crt, cudaStream_t s);
+                               uint32_t *crt, uint32_t *qbase, cudaStream_t s);
+cudaError_t launch_interp_tables(const ModP *mods, const uint32_t *qbase, int K, int N,
+                                 uint32_t *finv, uint32_t *gtab, int32_t *btab, cudaStream_t s);
 cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *num, const uint32_t *den,
                                    uint32_t *z, int K, int N, cudaStream_t s);

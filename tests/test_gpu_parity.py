@@ -87,18 +87,23 @@ def test_conventions_and_degenerate_inputs(ctx):
 
 
 def test_unlucky_points_and_primes(ctx):
-    """lc_y f vanishing at x = 3 and 7 (every prime), and a leading
-    coefficient divisible by the first table prime 2^31 - 1."""
+    """lc_y f vanishing at x = 1 (the first evaluation point q^0 for every
+    prime) and at x = 3, and a leading coefficient divisible by the first
+    table prime 2^31 - 1."""
     rng = random.Random(4)
     g = rand_bipoly(rng, 3, 4, bits=30)
-    # lc_y f = (x - 3)(x - 7) = x^2 - 10 x + 21
+    # lc_y f = (x - 1)(x - 3) = x^2 - 4 x + 3
     f = rand_bipoly(rng, 2, 3, bits=30)
-    f[0][3], f[1][3], f[2][3] = 21, -10, 1
+    f[0][3], f[1][3], f[2][3] = 3, -4, 1
     assert ctx.resultant_y(f, g) == oracle(f, g)
+    primes, imgs = ctx.images(f, g, 3, 8)  # integer points: x = 1 and 3 are unlucky
+    for k in range(3):
+        for x in (1, 3):
+            assert int(imgs[k, x]) == modp.resultant_image(f, g, int(primes[k]), x)
     b = ctx.batch([(f, g)])
     b.run()
     info = b.info()
-    assert info["unlucky_points"] >= 2 * 1  # x = 3 and 7 for every prime
+    assert info["unlucky_points"] >= rs.result_bound(f, g)["primes"]  # x = q^0 = 1, every prime
     b.close()
     f2 = rand_bipoly(rng, 2, 3, bits=30)
     f2[0][3], f2[1][3], f2[2][3] = 2147483647, 0, 0
