@@ -173,11 +173,15 @@ typedef struct {
 int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
 
 /* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
- * (Section 4.1) for the first nprimes primes of the library's table and the
- * points x_i = 0..npoints-1.  primes_out[nprimes] receives the primes,
- * images_out[k * npoints + i] the image for prime k at x_i (0 <= z < p). */
+ * (Section 4.1) that the resultant path computes, for the first nprimes
+ * primes of the library's table and its first npoints evaluation points,
+ * x_{k,i} = q_k^i mod p_k (a geometric progression per prime).
+ * primes_out[nprimes] receives the primes, points_out[k * npoints + i] the
+ * points (may be NULL) and images_out[k * npoints + i] the image for prime k
+ * at x_{k,i} (0 <= z < p_k). */
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes,
-              int32_t npoints, uint32_t *primes_out, uint32_t *images_out);
+              int32_t npoints, uint32_t *primes_out, uint32_t *points_out,
+              uint32_t *images_out);
 
 /* Chinese remaindering that allocates nothing, for callers that may not
  * allocate device memory (a plugin handed fixed buffers by its host

@@ -15,6 +15,7 @@ LIB = os.path.join(PKG, "librs.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+EXTRA = os.environ.get("RS_NVCC_EXTRA", "").split()  # experiments only
 G1_CAPS = (8, 16, 24, 32, 40, 48, 56, 64, 72)
 
 
@@ -49,7 +50,7 @@ def build(force=False, verbose=False, jobs=None):
         out = os.path.join(BUILD, obj)
         objs.append(out)
         if force or _stale(out, deps):
-            cmds.append([NVCC] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", out])
+            cmds.append([NVCC] + ARCH + FLAGS + EXTRA + extra + ["-c", os.path.join(CSRC, src), "-o", out])
 
     def run(cmd):
         if verbose:

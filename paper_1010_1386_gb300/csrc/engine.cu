@@ -82,7 +82,9 @@ struct rs_batch {
   unsigned long long *d_stats = nullptr;
   uint32_t *d_finv = nullptr, *d_gtab = nullptr;  // interpolation tables [K][tab_stride]
   int32_t *d_btab = nullptr;
-  int tab_k = 0, tab_stride = 0;
+  int32_t *d_qc = nullptr;   // chirp tables [K][chirp_stride]
+  uint32_t *d_qn = nullptr;
+  int tab_k = 0, tab_stride = 0, chirp_stride = 0;
   uint32_t *h_in = nullptr, *h_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -143,7 +145,7 @@ static void free_batch(rs_batch *b) {
     if (e) cudaEventDestroy(e);
   void *dev[] = {b->d_in,  b->d_meta, b->d_pairs, b->d_tiles, b->d_counters, b->d_num,
                  b->d_den, b->d_xl,   b->d_out,   b->d_g2,    b->d_g3,       b->d_stats,
-                 b->d_finv, b->d_gtab, b->d_btab};
+                 b->d_finv, b->d_gtab, b->d_btab, b->d_qc,  b->d_qn};
   for (void *p : dev)
     if (p) cudaFree(p);
   if (b->h_in) cudaFreeHost(b->h_in);
@@ -202,6 +204,8 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     d.fnc = p.f.nc;
     d.gnc = p.g.nc;
     d.Lout = p.Lout;
+    d.mxf = p.f.mx;
+    d.mxg = p.g.mx;
     d.f_off = b->in_f[i];
     d.g_off = b->in_g[i];
     d.meta_off = (int64_t)meta.size();
@@ -248,7 +252,7 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     for (int i : order) {
       const PairPlan &p = b->plans[i];
       if (g1_supported_cap(p.cap) != cap) continue;
-      cl.smem = std::max(cl.smem, (size_t)p.staged * 4);
+      cl.smem = std::max(cl.smem, (size_t)rs_g1_staged_words(p, cap, T) * 4);
       for (int k = 0; k < p.K; ++k)
         for (int x0 = 0; x0 < p.N; x0 += T) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T, p.N - x0)});
     }
@@ -261,11 +265,12 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
-  int maxN = 1, maxK = 0;
+  int maxN = 1, maxK = 0, maxDx = 0;
   for (int i : byN) {
     const PairPlan &p = b->plans[i];
     maxN = std::max(maxN, p.N);
     maxK = std::max(maxK, p.K);
+    maxDx = std::max(maxDx, std::max(p.f.mx, p.g.mx));
     for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
   }
   for (int i : order) {
@@ -275,8 +280,9 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   b->ng2 = (int)g2.size();
   b->ng3 = (int)g3.size();
   b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
-  b->tab_k = images_only ? 0 : maxK;
+  b->tab_k = maxK;
   b->tab_stride = maxN;
+  b->chirp_stride = maxN + T + maxDx + 1;
   b->info.kernel_launches = (int64_t)b->classes.size() + (images_only ? 0 : (b->ng2 > 0) + (b->ng3 > 0));
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
@@ -296,13 +302,17 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
   alloc((void **)&b->d_num, b->img_words * 4);
   alloc((void **)&b->d_den, b->img_words * 4);
   alloc((void **)&b->d_xl, std::max<int64_t>(b->out_words, images_only ? b->img_words : 0) * 4);
-  alloc((void **)&b->d_out, b->out_words * 4);
+  alloc((void **)&b->d_out, std::max<int64_t>(b->out_words, images_only ? b->img_words : 0) * 4);
   alloc((void **)&b->d_g2, g2.size() * sizeof(int2));
   alloc((void **)&b->d_g3, g3.size() * sizeof(int2));
   alloc((void **)&b->d_stats, ST_COUNT * sizeof(unsigned long long));
-  alloc((void **)&b->d_finv, (size_t)b->tab_k * b->tab_stride * 4);
-  alloc((void **)&b->d_gtab, (size_t)b->tab_k * b->tab_stride * 4);
-  alloc((void **)&b->d_btab, (size_t)b->tab_k * b->tab_stride * 4);
+  if (!images_only) {
+    alloc((void **)&b->d_finv, (size_t)b->tab_k * b->tab_stride * 4);
+    alloc((void **)&b->d_gtab, (size_t)b->tab_k * b->tab_stride * 4);
+    alloc((void **)&b->d_btab, (size_t)b->tab_k * b->tab_stride * 4);
+  }
+  alloc((void **)&b->d_qc, (size_t)b->tab_k * b->chirp_stride * 4);
+  alloc((void **)&b->d_qn, (size_t)b->tab_k * b->chirp_stride * 4);
   if (rc == RS_OK && b->in_words) {
     cudaError_t e = cudaMallocHost((void **)&b->h_in, b->in_words * 4);
     if (e != cudaSuccess) rc = fail(ctx, RS_ERR_NOMEM, "cudaMallocHost (inputs)");
@@ -333,10 +343,10 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     cl.blocks = ctx->cfg.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
   }
   if (rc == RS_OK && b->tab_k > 0) {
-    cudaError_t e = launch_interp_tables(ctx->d_mods, ctx->d_qbase, b->tab_k, b->tab_stride, b->d_finv,
-                                         b->d_gtab, b->d_btab, ctx->stream);
+    cudaError_t e = launch_tables(ctx->d_mods, ctx->d_qbase, b->tab_k, b->tab_stride, b->chirp_stride,
+                                  b->d_finv, b->d_gtab, b->d_btab, b->d_qc, b->d_qn, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("interpolation tables: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("point tables: ") + cudaGetErrorString(e));
   }
   if (rc == RS_OK && b->ng2) {
     cudaError_t e = g2_prepare(b->g2smem);
@@ -385,7 +395,9 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.limbs = b->d_in;
     a.meta = b->d_meta;
     a.mods = ctx->d_mods;
-    a.qbase = b->images_only ? nullptr : ctx->d_qbase;
+    a.qc = b->d_qc;
+    a.qn = b->d_qn;
+    a.tstride = b->chirp_stride;
     a.vtab = ctx->d_vtab;
     a.num = b->d_num;
     a.den = b->d_den;
@@ -731,7 +743,7 @@ int rs_resultant_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly
 }
 
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes, int32_t npoints,
-              uint32_t *primes_out, uint32_t *images_out) {
+              uint32_t *primes_out, uint32_t *points_out, uint32_t *images_out) {
   if (!ctx || !f || !g || !images_out || nprimes < 1 || npoints < 1)
     return fail(ctx, RS_ERR_ARG, "bad arguments");
   if (nprimes > (int)ctx->primes.size() || npoints > RS_MAX_POINTS)
@@ -742,11 +754,21 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
   if (first != RS_OK) return first;
   if (plans[0].trivial_zero) {
     memset(images_out, 0, (size_t)nprimes * npoints * 4);
+    if (points_out) {  // the points are not needed; report them from a host-side run of the table
+      std::vector<uint32_t> qb(nprimes);
+      DevGuard dg(ctx->device);
+      RS_CUDA(ctx, cudaMemcpy(qb.data(), ctx->d_qbase, (size_t)nprimes * 4, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < nprimes; ++k) {
+        const ModP m = make_modp(ctx->primes[k]);
+        for (int i = 0; i < npoints; ++i) points_out[(size_t)k * npoints + i] = from_mont(mpow(qb[k], i, m), m);
+      }
+    }
   } else {
     plans[0].K = nprimes;
     plans[0].N = npoints;
     plans[0].D = npoints - 1;
     plans[0].Lout = 1;
+    plans[0].cap = std::max(plans[0].f.my, plans[0].g.my) + 1;
     rs_batch *b = nullptr;
     int rc = build_batch(ctx, 1, f, g, std::move(plans), true, &b);
     if (rc != RS_OK) return rc;
@@ -754,9 +776,13 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
     rc = upload(b, f, g);
     if (rc == RS_OK) rc = run(b);
     if (rc == RS_OK) {
-      cudaError_t e = launch_finalize_images(ctx->d_mods, b->d_num, b->d_den, b->d_xl, nprimes, npoints, ctx->stream);
+      uint32_t *d_pts = points_out ? b->d_out : nullptr;  // images-only batches size d_out to K * N
+      cudaError_t e = launch_finalize_images(ctx->d_mods, ctx->d_qbase, b->d_num, b->d_den, b->d_xl, d_pts,
+                                             nprimes, npoints, ctx->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(images_out, b->d_xl, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, ctx->stream);
+      if (e == cudaSuccess && points_out)
+        e = cudaMemcpyAsync(points_out, d_pts, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, ctx->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("images: ") + cudaGetErrorString(e));
     }

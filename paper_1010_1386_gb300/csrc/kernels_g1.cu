@@ -3,8 +3,10 @@
 // Collins' algorithm maps f, g to Z_p and evaluates them at points x_i
 // (steps 1-2), then takes z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p.
 // The points are the geometric progression x_i = q^i (q of multiplicative
-// order above the largest point count, chosen per prime), which G2 turns
-// back into coefficients with two convolutions.
+// order above the largest point count, chosen per prime): f_j(q^i) is then a
+// correlation of chirp-scaled coefficients with the sequence q^{C(t,2)}
+// (accumulated without per-term reduction), and G2 turns the images back into
+// coefficients with two convolutions.
 //
 // The univariate resultant keeps the formal degrees (a, b) = (m_y, n_y) of
 // the Sylvester matrix of Section 3.1, so z_i^{(p)} = R^{(y)}(x_i) mod p for
@@ -30,6 +32,18 @@
 // C - 8 entries the state moves to arrays of C - 8 (registers are renamed,
 // nothing is copied), so the unrolled update loops shrink with the degrees.
 #include "rs_internal.cuh"
+
+#ifndef RS_G1_PSTEP
+#define RS_G1_PSTEP 8  // register capacity dropped per phase
+#endif
+// Minimum resident 128-thread blocks per SM requested from ptxas per register
+// capacity (caps registers at 65536 / (128 * MINB) per thread).
+#if defined(RS_G1_MINB_AT) && defined(RS_G1_MINB_SET) && RS_G1_MINB_AT == RS_G1_CAP
+#define RS_G1_MINB RS_G1_MINB_SET  // tuning override for one capacity
+#endif
+#ifndef RS_G1_MINB
+#define RS_G1_MINB (RS_G1_CAP <= 16 ? 6 : RS_G1_CAP <= 24 ? 5 : RS_G1_CAP <= 32 ? 4 : 3)
+#endif
 
 namespace {
 
@@ -71,7 +85,8 @@ __device__ __forceinline__ void drop_top(uint32_t (&P)[C]) {
 template <int C>
 __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs &s, const ModP &m) {
   // invariant: a, b <= C - 1
-  while (s.a > 0 && s.b > 0 && (C <= 8 || s.a > C - 9 || s.b > C - 9)) {
+  constexpr int S = RS_G1_PSTEP;
+  while (s.a > 0 && s.b > 0 && (C <= S || s.a > C - S - 1 || s.b > C - S - 1)) {
     if (s.a >= s.b) {
       const uint32_t lb = B[0];
       if (lb != 0u) {
@@ -102,15 +117,15 @@ __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs 
       }
     }
   }
-  if constexpr (C > 8) {
+  if constexpr (C > S) {
     if (s.a > 0 && s.b > 0) {
-      uint32_t A2[C - 8], B2[C - 8];
+      uint32_t A2[C - S], B2[C - S];
 #pragma unroll
-      for (int i = 0; i < C - 8; ++i) {
+      for (int i = 0; i < C - S; ++i) {
         A2[i] = A[i];
         B2[i] = B[i];
       }
-      prs_run<C - 8>(A2, B2, s, m);
+      prs_run<C - S>(A2, B2, s, m);
       return;
     }
   }
@@ -118,26 +133,6 @@ __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs 
     s.num = mmul(s.num, mpow(A[0], (uint32_t)s.b, m), m);
   else
     s.num = mmul(s.num, mpow(B[0], (uint32_t)s.a, m), m);
-}
-
-// P[r] = f_{deg - r}(x) (top-aligned), Horner over the staged residues.
-template <int C>
-__device__ __forceinline__ void eval_poly(uint32_t (&P)[C], const uint32_t *res, const int2 *meta,
-                                          int deg, uint32_t xm, const ModP &m) {
-#pragma unroll
-  for (int r = 0; r < C; ++r) {
-    uint32_t v = 0u;
-    const int j = deg - r;
-    if (j >= 0) {
-      const int2 mt = meta[j];
-      if (mt.y >= 0) {
-        const uint32_t *c = res + mt.x;
-        v = c[mt.y];
-        for (int i = mt.y - 1; i >= 0; --i) v = madd(mmul(v, xm, m), c[i], m.p);
-      }
-    }
-    P[r] = v;
-  }
 }
 
 // Montgomery form of a two's-complement limb integer:
@@ -150,18 +145,80 @@ __device__ __forceinline__ uint32_t reduce_coef(const uint32_t *src, int L, cons
   return acc;
 }
 
-__device__ __forceinline__ void stage_poly(uint32_t *sres, const int2 *smeta, int deg,
-                                           const uint32_t *limbs, int stride, int L,
-                                           const uint32_t *V, const ModP &m) {
-  for (int j = 0; j <= deg; ++j) {
-    const int2 mt = smeta[j];
-    for (int i = threadIdx.x; i <= mt.y; i += blockDim.x)
-      sres[mt.x + i] = reduce_coef(limbs + ((size_t)i * stride + j) * L, L, V, m);
+__device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
+  return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
+}
+
+// Evaluation at x_i = q^i by the chirp identity i k = C(i+k,2) - C(i,2) - C(k,2):
+//   f_j(q^i) = q^{-C(i,2)} sum_k (f_jk q^{-C(k,2)}) q^{C(i+k,2)}.
+// The staged coefficients a[k][r] = f_{deg-r,k} q^{-C(k,2)} (top-aligned in
+// r, zero past the degree) and the window w[t] = q^{C(x0+t,2)} are signed
+// representatives (|v| < 2^30): 7 products accumulate exactly in an int64,
+// then one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53.
+__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) {
+  return (s >> 32) * (int64_t)c32 + (int64_t)(uint32_t)s;
+}
+
+__device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
+  return redc((uint64_t)(s + ((int64_t)m.p << 22)), m.p, m.pinv);  // 0 <= . < 2^54 < p 2^32
+}
+
+template <int C>
+__device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, const int2 *meta,
+                                           int deg, const int32_t *win, uint32_t wi,
+                                           const ModP &m) {
+  const uint32_t c32 = m.r1;  // 2^32 mod p (<= 2^21 for every table prime)
+#pragma unroll
+  for (int r0 = 0; r0 < C; r0 += 8) {
+    int64_t acc[8];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = 0;
+    int kmax = -1;
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr)
+      if (deg - (r0 + rr) >= 0) kmax = max(kmax, meta[deg - (r0 + rr)].y);
+    int k = 0;
+    while (k <= kmax) {
+      const int kend = min(k + 7, kmax + 1);
+#pragma unroll 1
+      for (; k < kend; ++k) {
+        const int32_t c = win[k];
+        const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
+        const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
+        acc[0] += (int64_t)lo.x * c;
+        acc[1] += (int64_t)lo.y * c;
+        acc[2] += (int64_t)lo.z * c;
+        acc[3] += (int64_t)lo.w * c;
+        acc[4] += (int64_t)hi.x * c;
+        acc[5] += (int64_t)hi.y * c;
+        acc[6] += (int64_t)hi.z * c;
+        acc[7] += (int64_t)hi.w * c;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) acc[rr] = fold64(acc[rr], c32);
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) P[r0 + rr] = kmax >= 0 ? mmul(finish64(acc[rr], m), wi, m) : 0u;
+  }
+}
+
+// a[k][r] for k <= dx (the largest x-degree), r < C.
+template <int C>
+__device__ __forceinline__ void stage_chirp(int32_t *sa, const int2 *smeta, int deg, int dx,
+                                            const uint32_t *limbs, int stride, int L,
+                                            const uint32_t *V, const uint32_t *qn, const ModP &m) {
+  const int n = (dx + 1) * C;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int k = idx / C, r = idx - k * C, j = deg - r;
+    int32_t v = 0;
+    if (j >= 0 && k <= smeta[j].y)
+      v = signed_rep(mmul(reduce_coef(limbs + ((size_t)k * stride + j) * L, L, V, m), qn[k], m), m.p);
+    sa[idx] = v;
   }
 }
 
 template <int C>
-__global__ void __launch_bounds__(128) g1_kernel(G1Args a) {
+__global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ int s_tile;
   bool first = true;
@@ -182,30 +239,36 @@ __global__ void __launch_bounds__(128) g1_kernel(G1Args a) {
     const ModP m = a.mods[tl.prime];
     const uint32_t *V = a.vtab + (size_t)tl.prime * RS_VT_STRIDE;
     const int nmeta = pd.my + pd.ny + 2;
+    const int dxm = max(pd.mxf, pd.mxg);
     int2 *smeta = reinterpret_cast<int2 *>(sm);
-    uint32_t *sres = sm + 2 * nmeta;
+    int32_t *saf = reinterpret_cast<int32_t *>(sm) + ((2 * nmeta + 7) & ~7);  // 32-byte aligned
+    int32_t *sag = saf + (pd.mxf + 1) * C;
+    int32_t *swin = sag + (pd.mxg + 1) * C;
+    const size_t tb = (size_t)tl.prime * a.tstride;
 
     for (int i = threadIdx.x; i < nmeta; i += blockDim.x) smeta[i] = a.meta[pd.meta_off + i];
+    for (int t = threadIdx.x; t < (int)blockDim.x + dxm; t += blockDim.x)
+      swin[t] = a.qc[tb + tl.x0 + t];
     __syncthreads();
-    stage_poly(sres, smeta, pd.my, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, m);
-    stage_poly(sres, smeta + pd.my + 1, pd.ny, a.limbs + pd.g_off, pd.gstride, pd.Lg, V, m);
+    stage_chirp<C>(saf, smeta, pd.my, pd.mxf, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, a.qn + tb, m);
+    stage_chirp<C>(sag, smeta + pd.my + 1, pd.ny, pd.mxg, a.limbs + pd.g_off, pd.gstride, pd.Lg, V,
+                   a.qn + tb, m);
     __syncthreads();
 
     if (tl.x0 == 0 && threadIdx.x == 0) {  // unlucky prime: a leading coefficient vanishes mod p
       bool zf = true, zg = true;
-      const int2 mf = smeta[pd.my], mg = smeta[pd.my + 1 + pd.ny];
-      for (int i = 0; i <= mf.y; ++i) zf = zf && sres[mf.x + i] == 0u;
-      for (int i = 0; i <= mg.y; ++i) zg = zg && sres[mg.x + i] == 0u;
+      for (int k = 0; k <= pd.mxf; ++k) zf = zf && saf[k * C] == 0;
+      for (int k = 0; k <= pd.mxg; ++k) zg = zg && sag[k * C] == 0;
       if (zf || zg) atomicAdd(a.stats + ST_UNLUCKY_PRIMES, 1ull);
     }
 
     uint32_t unlucky = 0u, degen = 0u;
     if ((int)threadIdx.x < tl.n) {
       const int x = tl.x0 + (int)threadIdx.x;
-      const uint32_t xm = a.qbase ? mpow(a.qbase[tl.prime], (uint32_t)x, m) : to_mont((uint32_t)x, m);
+      const uint32_t wi = a.qn[tb + x];  // q^{-C(x,2)}
       uint32_t A[C], B[C];
-      eval_poly<C>(A, sres, smeta, pd.my, xm, m);
-      eval_poly<C>(B, sres, smeta + pd.my + 1, pd.ny, xm, m);
+      eval_chirp<C>(A, saf, smeta, pd.my, swin + threadIdx.x, wi, m);
+      eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + threadIdx.x, wi, m);
       unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
       Prs s;
       s.a = pd.my;

@@ -181,14 +181,32 @@ __global__ void g2_kernel(G2Args a) {
   for (int i = tid; i < N; i += T) a.coef[base + i] = from_mont(mmul(Y[D - i], finv[i], m), m);
 }
 
-// Per prime k < K, t < N: 1 / F_t, q^{-C(t,2)} F_t and the signed
-// (-1)^t q^{C(t,2)} / F_t, F_t = prod_{s=1}^t (q^s - 1).  One thread per prime.
-__global__ void interp_tables_kernel(const ModP *mods, const uint32_t *qbase, int K, int N,
-                                     uint32_t *finv, uint32_t *gtab, int32_t *btab) {
+// Per prime k < K: the chirp tables q^{C(t,2)} (signed representative) and
+// q^{-C(t,2)} for t < stride (evaluation in G1), and for t < N the
+// interpolation tables 1 / F_t, q^{-C(t,2)} F_t and the signed
+// (-1)^t q^{C(t,2)} / F_t, F_t = prod_{s=1}^t (q^s - 1) (G2; finv may be NULL
+// when only the chirp tables are wanted).  One thread per prime.
+__global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
+                              uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qct,
+                              uint32_t *qnt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   const ModP m = mods[k];
   const uint32_t q = qbase[k], qi = minv(q, m);
+  {
+    uint32_t up = m.r1, dn = m.r1, qt = m.r1, qit = m.r1;  // q^{C(t,2)}, q^{-C(t,2)}, q^t, q^{-t}
+    int32_t *qc = qct + (size_t)k * stride;
+    uint32_t *qn = qnt + (size_t)k * stride;
+    for (int t = 0; t < stride; ++t) {
+      qc[t] = signed_rep(up, m.p);
+      qn[t] = dn;
+      up = mmul(up, qt, m);  // C(t+1,2) = C(t,2) + t
+      dn = mmul(dn, qit, m);
+      qt = mmul(qt, q, m);
+      qit = mmul(qit, qi, m);
+    }
+  }
+  if (!finv) return;
   uint32_t *fi = finv + (size_t)k * N, *gt = gtab + (size_t)k * N;
   int32_t *bt = btab + (size_t)k * N;
   // forward: F_t (kept in fi for now) and q^{-C(t,2)} (kept in gt)
@@ -313,19 +331,23 @@ __global__ void init_primes_kernel(const uint32_t *primes, int n, ModP *mods, ui
   }
 }
 
-__global__ void finalize_images_kernel(const ModP *mods, const uint32_t *num, const uint32_t *den,
-                                       uint32_t *z, int K, int N) {
+__global__ void finalize_images_kernel(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
+                                       const uint32_t *den, uint32_t *z, uint32_t *points, int K,
+                                       int N) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)K * N) return;
-  const ModP m = mods[i / N];
+  const int k = (int)(i / N), x = (int)(i % N);
+  const ModP m = mods[k];
   z[i] = from_mont(mmul(num[i], minv(den[i], m), m), m);
+  if (points) points[i] = from_mont(mpow(qbase[k], (uint32_t)x, m), m);
 }
 
 }  // namespace
 
-cudaError_t launch_interp_tables(const ModP *mods, const uint32_t *qbase, int K, int N,
-                                 uint32_t *finv, uint32_t *gtab, int32_t *btab, cudaStream_t s) {
-  interp_tables_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, qbase, K, N, finv, gtab, btab);
+cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
+                          uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qc,
+                          uint32_t *qn, cudaStream_t s) {
+  tables_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, qbase, K, N, stride, finv, gtab, btab, qc, qn);
   return cudaGetLastError();
 }
 
@@ -351,9 +373,11 @@ cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *num, const uint32_t *den,
-                                   uint32_t *z, int K, int N, cudaStream_t s) {
+cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
+                                   const uint32_t *den, uint32_t *z, uint32_t *points, int K, int N,
+                                   cudaStream_t s) {
   const size_t n = (size_t)K * N;
-  finalize_images_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mods, num, den, z, K, N);
+  finalize_images_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mods, qbase, num, den, z, points,
+                                                                      K, N);
   return cudaGetLastError();
 }

@@ -152,7 +152,7 @@ int rs_plan_pair(const rs_bipoly *f, const rs_bipoly *g, const std::vector<doubl
   }
   plan.Lout = (plan.bits + 31) / 32;
   plan.cap = std::max(my, ny) + 1;
-  plan.staged = 2 * (my + ny + 2) + plan.f.nc + plan.g.nc;
+  plan.staged = rs_g1_staged_words(plan, ((plan.cap + 7) / 8) * 8, 128);
   if (plan.staged > 48 * 1024) {  // RS_G1_MAX_STAGED_WORDS
     *why = "too many coefficients to stage in shared memory";
     return plan.status = RS_ERR_LIMIT;

@@ -38,5 +38,14 @@ struct PairPlan {
 int rs_plan_pair(const rs_bipoly *f, const rs_bipoly *g, const std::vector<double> &log2p,
                  PairPlan &plan, const char **why);
 
+// Shared-memory words one G1 tile of `threads` points stages for plan p in
+// register-capacity class C: per-j x-degrees, chirp-scaled coefficients of
+// f and g ([x-degree + 1][C] each) and the window of q^{C(t,2)}.
+inline int rs_g1_staged_words(const PairPlan &p, int C, int threads) {
+  const int meta = (2 * (p.f.my + p.g.my + 2) + 7) & ~7;
+  const int dx = p.f.mx > p.g.mx ? p.f.mx : p.g.mx;
+  return meta + (p.f.mx + 1) * C + (p.g.mx + 1) * C + threads + dx;
+}
+
 // Primes in (2^31 - 2^20, 2^31), descending, by a sieve of Eratosthenes.
 std::vector<uint32_t> rs_prime_table(int count);

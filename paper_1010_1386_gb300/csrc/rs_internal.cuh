@@ -23,6 +23,7 @@ struct PairDesc {
   int32_t fstride, gstride;  // input row stride in coefficients (= array deg_y + 1)
   int32_t fnc, gnc;    // coefficients kept (sum over j of deg_x f_j + 1)
   int32_t Lout;        // output limbs per coefficient
+  int32_t mxf, mxg;    // x-degrees of f and g
   int32_t pad;
   int64_t f_off, g_off;  // word offsets of the input limb arrays
   int64_t meta_off;      // int2 offset: (my+1) entries for f then (ny+1) for g
@@ -47,7 +48,9 @@ struct G1Args {
   const uint32_t *limbs;   // batch input limbs
   const int2 *meta;        // per-j (start in the staged residue array, x-degree or -1)
   const ModP *mods;
-  const uint32_t *qbase;   // q per prime (Montgomery): points x_i = q^i; NULL: x_i = i
+  const int32_t *qc;       // [prime][tstride] q^{C(t,2)}, signed representative (Montgomery)
+  const uint32_t *qn;      // [prime][tstride] q^{-C(t,2)} (Montgomery)
+  int32_t tstride;
   const uint32_t *vtab;    // [prime][RS_VT_STRIDE]
   uint32_t *num;           // numerators  (Montgomery form, sign applied)
   uint32_t *den;           // denominators (Montgomery form, non-zero)
@@ -86,7 +89,9 @@ cudaError_t g2_prepare(size_t smem);
 cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s);
-cudaError_t launch_interp_tables(const ModP *mods, const uint32_t *qbase, int K, int N,
-                                 uint32_t *finv, uint32_t *gtab, int32_t *btab, cudaStream_t s);
-cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *num, const uint32_t *den,
-                                   uint32_t *z, int K, int N, cudaStream_t s);
+cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
+                          uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qc,
+                          uint32_t *qn, cudaStream_t s);
+cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
+                                   const uint32_t *den, uint32_t *z, uint32_t *points, int K, int N,
+                                   cudaStream_t s);

@@ -71,7 +71,7 @@ _SIGS = {
     "rs_batch_destroy": (c_int32, [c_void_p]),
     "rs_batch_info_get": (c_int32, [c_void_p, _P(rs_batch_info)]),
     "rs_images": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, c_int32,
-                            _P(c_uint32), _P(c_uint32)]),
+                            _P(c_uint32), _P(c_uint32), _P(c_uint32)]),
     "rs_crt_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
 }
 
@@ -216,15 +216,17 @@ class Context:
         return out.raw() if raw else out.ints()
 
     def images(self, f, g, nprimes, npoints):
-        """(primes[nprimes], images[nprimes, npoints]) with images[k, i] =
-        res(f(i, y), g(i, y), y) mod primes[k]."""
+        """(primes[K], points[K, N], images[K, N]): images[k, i] =
+        res(f(x, y), g(x, y), y) mod primes[k] at x = points[k, i]."""
         P = _Polys([f, g])
         primes = np.zeros(nprimes, dtype=np.uint32)
+        pts = np.zeros((nprimes, npoints), dtype=np.uint32)
         imgs = np.zeros((nprimes, npoints), dtype=np.uint32)
         _check(self.lib.rs_images(self.h, ctypes.byref(P.structs[0]), ctypes.byref(P.structs[1]),
                                   nprimes, npoints, primes.ctypes.data_as(POINTER(c_uint32)),
+                                  pts.ctypes.data_as(POINTER(c_uint32)),
                                   imgs.ctypes.data_as(POINTER(c_uint32))), self.h)
-        return primes, imgs
+        return primes, pts, imgs
 
     def batch(self, pairs):
         return Batch(self, pairs)

@@ -96,10 +96,11 @@ def test_unlucky_points_and_primes(ctx):
     f = rand_bipoly(rng, 2, 3, bits=30)
     f[0][3], f[1][3], f[2][3] = 3, -4, 1
     assert ctx.resultant_y(f, g) == oracle(f, g)
-    primes, imgs = ctx.images(f, g, 3, 8)  # integer points: x = 1 and 3 are unlucky
+    primes, pts, imgs = ctx.images(f, g, 3, 8)
     for k in range(3):
-        for x in (1, 3):
-            assert int(imgs[k, x]) == modp.resultant_image(f, g, int(primes[k]), x)
+        assert int(pts[k, 0]) == 1  # x = q^0 = 1: lc_y f vanishes there
+        for i in range(8):
+            assert int(imgs[k, i]) == modp.resultant_image(f, g, int(primes[k]), int(pts[k, i]))
     b = ctx.batch([(f, g)])
     b.run()
     info = b.info()
@@ -137,11 +138,14 @@ def test_images_against_oracle(ctx):
     for dx, dy, bits in [(6, 6, 11), (3, 9, 64), (9, 2, 200)]:
         f = rand_bipoly(rng, dx, dy, bits=bits)
         g = rand_bipoly(rng, dx + 1, dy - 1 if dy > 1 else dy, bits=bits)
-        primes, imgs = ctx.images(f, g, 5, 70)
+        primes, pts, imgs = ctx.images(f, g, 5, 70)
         assert primes[0] == 2147483647 and all(primes[i] > primes[i + 1] for i in range(4))
         for k in range(5):
-            for x in list(range(8)) + [rng.randrange(70) for _ in range(6)]:
-                assert int(imgs[k, x]) == modp.resultant_image(f, g, int(primes[k]), x)
+            p = int(primes[k])
+            assert len(set(int(v) for v in pts[k])) == 70  # distinct points
+            assert all(int(pts[k, i]) * int(pts[k, 1]) % p == int(pts[k, i + 1]) for i in range(69))
+            for i in list(range(8)) + [rng.randrange(70) for _ in range(6)]:
+                assert int(imgs[k, i]) == modp.resultant_image(f, g, p, int(pts[k, i]))
 
 
 # ---------------------------------------------------------- full-size configs
@@ -155,10 +159,10 @@ def test_single_dense30_full_size(ctx):
     assert max(abs(c) for c in R).bit_length() < bound["bits"]
     exact_points(F, G, R, points=(0, 1, -1, 2))
     check_sampled_31(F, G, R, random.Random(7), samples=3)
-    primes, imgs = ctx.images(f, g, 3, 901)
+    primes, pts, imgs = ctx.images(f, g, 3, 901)
     for k in range(3):
-        for x in (0, 1, 450, 900):
-            assert int(imgs[k, x]) == eval_mod(R, x, int(primes[k]))
+        for i in (0, 1, 450, 900):
+            assert int(imgs[k, i]) == eval_mod(R, int(pts[k, i]), int(primes[k]))
 
 
 def test_batch_full_size_sampled(ctx):

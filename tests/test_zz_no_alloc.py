@@ -50,7 +50,7 @@ def test_noalloc_crt_matches_resultant_path():
         R = ctx.resultant_y(f, g)
         b = rs.result_bound(f, g)
         K, N, L = b["primes"], b["deg"] + 1, b["limbs"]
-        primes, _ = ctx.images(f, g, K, 1)
+        primes, _, _ = ctx.images(f, g, K, 1)
         got = _run_noalloc(lib, torch, _residues(R, [int(p) for p in primes], N), L)
         assert got == list(R) + [0] * (N - len(R))
     ctx.close()
