@@ -183,6 +183,54 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
               int32_t npoints, uint32_t *primes_out, uint32_t *points_out,
               uint32_t *images_out);
 
+/* ---------------------------------------------------------------------
+ * Serving: a continuous-batching request server inside a context.
+ * Each request is one resultant Res_y(f, g).  Submission plans the request
+ * and copies its inputs (the caller may free them on return).  A scheduler
+ * thread admits pending requests in arrival order while their device
+ * footprint (the images K * (D+1) of numerators and denominators, the
+ * output limbs (D+1) * Lout and the inputs) fits the memory budget, groups
+ * them into a micro-batch and runs it on one of max_inflight CUDA streams;
+ * micro-batches on different streams overlap on the GPU, and requests that
+ * arrive while others run are admitted as soon as a stream and memory free
+ * up.  Residues stay on the device until their micro-batch completes.
+ * A request's result is the same whether it runs alone or in a mix.
+ * The server functions may be called from several host threads; other
+ * calls on the same context must not run concurrently with rs_server_stop.
+ * --------------------------------------------------------------------- */
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t pending;                 /* waiting for admission */
+  int64_t running;                 /* in micro-batches on the GPU now */
+  int64_t inflight_batches;        /* micro-batches on the GPU now */
+  int64_t batches;                 /* micro-batches launched so far */
+  int64_t peak_inflight_batches;   /* most micro-batches on the GPU at once */
+  int64_t peak_running;            /* most requests on the GPU at once */
+  int64_t mem_used, mem_limit;     /* admitted device bytes / budget */
+} rs_server_stats;
+
+/* Start the server (optional: the first submit starts it with defaults).
+ * max_inflight: concurrent micro-batches (streams), 0 = 4; max_batch:
+ * requests per micro-batch, 0 = 256; mem_limit_bytes: admission budget,
+ * 0 = rs_config.mem_limit_bytes or half of the free device memory. */
+int rs_server_start(rs_ctx *ctx, int32_t max_inflight, int32_t max_batch, int64_t mem_limit_bytes);
+/* Queue Res_y(f, g); *ticket identifies the request.  Planning errors
+ * (RS_ERR_ARG, RS_ERR_LIMIT) are returned here. */
+int rs_server_submit(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, uint64_t *ticket);
+/* RS_PENDING while the request runs; otherwise its status, with the result
+ * in *out on RS_OK (the ticket is then released; on RS_ERR_CAPACITY it is
+ * kept and out->deg / out->limbs give the size needed).  latency_ms (may be
+ * NULL) receives the time from submission to completion. */
+int rs_server_poll(rs_ctx *ctx, uint64_t ticket, rs_upoly *out, double *latency_ms);
+/* As rs_server_poll, but blocks up to timeout_us microseconds (< 0: no
+ * limit); RS_ERR_TIMEOUT when the request is still running. */
+int rs_server_wait(rs_ctx *ctx, uint64_t ticket, rs_upoly *out, double *latency_ms,
+                   int64_t timeout_us);
+int rs_server_stats_get(rs_ctx *ctx, rs_server_stats *stats);
+/* Finish every admitted and pending request, then stop the scheduler
+ * thread and release its streams (results not yet polled are dropped). */
+int rs_server_stop(rs_ctx *ctx);
+
 /* Chinese remaindering that allocates nothing, for callers that may not
  * allocate device memory (a plugin handed fixed buffers by its host
  * application, code that must not call cudaMalloc/cudaFree because they can

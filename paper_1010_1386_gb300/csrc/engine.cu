@@ -1,17 +1,14 @@
 // Host engine of librs: contexts, prepared batches, CUDA-graph replay and the
 // C ABI of include/rs.h.  The host plans (planner.cpp), packs inputs into one
 // pinned staging buffer, enqueues G1 (kernels_g1.cu), G2 and G3
-// (kernels_g23.cu) on the context's stream and unpacks the results.
-#include <cuda_runtime.h>
+// (kernels_g23.cu) on a stream and unpacks the results.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
-#include <string>
-#include <vector>
 
-#include "planner.h"
-#include "rs_internal.cuh"
+#include "engine.h"
 
 namespace {
 
@@ -28,133 +25,11 @@ struct DevGuard {
   }
 };
 
-struct ClassLaunch {
-  int cap = 0;
-  int threads = 128;
-  int blocks = 0;
-  int64_t tile_off = 0;
-  int ntiles = 0;
-  size_t smem = 0;
-};
-
-int cuda_code(cudaError_t e) {
-  return e == cudaErrorMemoryAllocation ? RS_ERR_NOMEM : RS_ERR_CUDA;
-}
-
-}  // namespace
-
-struct rs_ctx {
-  int device = 0;
-  rs_config cfg;
-  cudaStream_t stream = nullptr;
-  int sms = 0;
-  std::vector<uint32_t> primes;
-  std::vector<double> log2p;
-  uint32_t *d_primes = nullptr;
-  ModP *d_mods = nullptr;
-  uint32_t *d_vtab = nullptr;
-  uint32_t *d_crt = nullptr;
-  uint32_t *d_qbase = nullptr;
-  std::string err;
-  std::vector<rs_batch *> batches;
-  rs_batch *cache = nullptr;
-};
-
-struct rs_batch {
-  rs_ctx *ctx = nullptr;
-  int n = 0;
-  bool images_only = false;
-  std::vector<PairPlan> plans;
-  std::vector<int> dev_index;  // pair -> device pair index, -1 if none
-  std::vector<PairDesc> descs;
-  std::vector<int64_t> in_f, in_g;  // word offsets of each pair's inputs in the staging buffer
-  std::vector<ClassLaunch> classes;
-  int64_t in_words = 0, img_words = 0, out_words = 0;
-  int ng2 = 0, ng3 = 0;
-  size_t g2smem = 0;
-  uint32_t *d_in = nullptr;
-  int2 *d_meta = nullptr;
-  PairDesc *d_pairs = nullptr;
-  Tile *d_tiles = nullptr;
-  int32_t *d_counters = nullptr;
-  uint32_t *d_num = nullptr, *d_den = nullptr, *d_xl = nullptr, *d_out = nullptr;
-  int2 *d_g2 = nullptr, *d_g3 = nullptr;
-  unsigned long long *d_stats = nullptr;
-  uint32_t *d_finv = nullptr, *d_gtab = nullptr;  // interpolation tables [K][tab_stride]
-  int32_t *d_btab = nullptr;
-  int32_t *d_qc = nullptr;   // chirp tables [K][chirp_stride]
-  uint32_t *d_qn = nullptr;
-  int tab_k = 0, tab_stride = 0, chirp_stride = 0;
-  uint32_t *h_in = nullptr, *h_out = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  bool ran = false;
-  rs_batch_info info;
-};
-
-static int fail(rs_ctx *c, int code, const std::string &msg) {
-  if (c)
-    c->err = msg;
-  else
-    g_err = msg;
-  return code;
-}
-
-#define RS_CUDA(ctx, call)                                                                \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return fail((ctx), cuda_code(e_), std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
-
-// ------------------------------------------------------------------ helpers
-
-static int plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
-                    std::vector<PairPlan> &plans, int32_t *status, int *first_err) {
-  plans.assign(n, PairPlan());
-  *first_err = RS_OK;
-  for (int i = 0; i < n; ++i) {
-    const char *why = "";
-    int rc = rs_plan_pair(&f[i], &g[i], ctx->log2p, plans[i], &why);
-    plans[i].status = rc;
-    if (status) status[i] = rc;
-    if (rc != RS_OK && *first_err == RS_OK) {
-      *first_err = rc;
-      fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + why);
-    }
-  }
-  return *first_err;
-}
-
-static bool same_shape(const PairPlan &a, const PairPlan &b) {
-  return a.status == b.status && a.trivial_zero == b.trivial_zero && a.N == b.N && a.K == b.K &&
-         a.Lout == b.Lout && a.f.my == b.f.my && a.g.my == b.g.my && a.f.L == b.f.L &&
-         a.g.L == b.g.L && a.f.stride == b.f.stride && a.g.stride == b.g.stride &&
-         a.f.dx == b.f.dx && a.g.dx == b.g.dx;
-}
-
-static int64_t input_words(const rs_bipoly &p) {
-  return (int64_t)(p.deg_x + 1) * (p.deg_y + 1) * p.limbs;
-}
-
-static void free_batch(rs_batch *b) {
-  if (!b) return;
-  DevGuard dg(b->ctx->device);
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
-  for (auto &e : b->ev)
-    if (e) cudaEventDestroy(e);
-  void *dev[] = {b->d_in,  b->d_meta, b->d_pairs, b->d_tiles, b->d_counters, b->d_num,
-                 b->d_den, b->d_xl,   b->d_out,   b->d_g2,    b->d_g3,       b->d_stats,
-                 b->d_finv, b->d_gtab, b->d_btab, b->d_qc,  b->d_qn};
-  for (void *p : dev)
-    if (p) cudaFree(p);
-  if (b->h_in) cudaFreeHost(b->h_in);
-  if (b->h_out) cudaFreeHost(b->h_out);
-  delete b;
-}
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 // Normal-sequence coefficient updates of the remainder sequence (a4 count).
-static double prs_updates(int a, int b) {
+double prs_updates(int a, int b) {
   double u = 0;
   while (a > 0 && b > 0) {
     if (a >= b) {
@@ -168,27 +43,157 @@ static double prs_updates(int a, int b) {
   return u;
 }
 
-static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
-                       std::vector<PairPlan> &&plans, bool images_only, rs_batch **out) {
+}  // namespace
+
+int rs_cuda_code(cudaError_t e) { return e == cudaErrorMemoryAllocation ? RS_ERR_NOMEM : RS_ERR_CUDA; }
+
+int rs_fail(rs_ctx *c, int code, const std::string &msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_err = msg;
+  return code;
+}
+
+#define RS_CUDA(ctx, call)                                                                         \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return rs_fail((ctx), rs_cuda_code(e_), std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// ------------------------------------------------------------------ planning
+
+int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
+                std::vector<PairPlan> &plans, int32_t *status, int *first_err) {
+  plans.assign(n, PairPlan());
+  *first_err = RS_OK;
+  for (int i = 0; i < n; ++i) {
+    const char *why = "";
+    int rc = rs_plan_pair(&f[i], &g[i], ctx->log2p, plans[i], &why);
+    plans[i].status = rc;
+    if (status) status[i] = rc;
+    if (rc != RS_OK && *first_err == RS_OK) {
+      *first_err = rc;
+      rs_fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + why);
+    }
+  }
+  return *first_err;
+}
+
+bool rs_same_shape(const PairPlan &a, const PairPlan &b) {
+  return a.status == b.status && a.trivial_zero == b.trivial_zero && a.N == b.N && a.K == b.K &&
+         a.Lout == b.Lout && a.f.my == b.f.my && a.g.my == b.g.my && a.f.mx == b.f.mx &&
+         a.g.mx == b.g.mx && a.f.L == b.f.L && a.g.L == b.g.L && a.f.stride == b.f.stride &&
+         a.g.stride == b.g.stride && a.f.dx == b.f.dx && a.g.dx == b.g.dx;
+}
+
+int64_t rs_input_words(const rs_bipoly &p) { return (int64_t)(p.deg_x + 1) * (p.deg_y + 1) * p.limbs; }
+
+// ------------------------------------------------------------------ tables
+
+static void free_tables(RsTables &t) {
+  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc};
+  for (void *x : p)
+    if (x) cudaFree(x);
+  t = RsTables();
+}
+
+int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
+  std::lock_guard<std::mutex> lock(ctx->tab_mu);
+  const int need_c = N + 128 + dx + 1;
+  RsTables &t = ctx->tab;
+  if (K <= t.K && N <= t.N && need_c <= t.cstride) return RS_OK;
+  RsTables nt;
+  nt.K = std::min((int)ctx->primes.size(), ((std::max(K, t.K) + 63) / 64) * 64);
+  nt.N = ((std::max(N, t.N) + 255) / 256) * 256;
+  nt.cstride = ((std::max(need_c, t.cstride) + 255) / 256) * 256;
+  DevGuard dg(ctx->device);
+  const size_t ni = (size_t)nt.K * nt.N * 4, nc = (size_t)nt.K * nt.cstride * 4;
+  cudaError_t e = cudaMalloc(&nt.finv, ni);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.gtab, ni);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.btab, ni);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.qc, nc);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.qn, nc);
+  if (e == cudaSuccess)
+    e = launch_tables(ctx->d_mods, ctx->d_qbase, nt.K, nt.N, nt.cstride, nt.finv, nt.gtab, nt.btab,
+                      nt.qc, nt.qn, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    free_tables(nt);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("point tables: ") + cudaGetErrorString(e));
+  }
+  if (t.finv) ctx->retired.push_back(t);
+  t = nt;
+  return RS_OK;
+}
+
+// ------------------------------------------------------------------ batches
+
+void rs_free_batch(rs_batch *b) {
+  if (!b) return;
+  DevGuard dg(b->ctx->device);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (auto &e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->arena) {
+    if (b->opt.stream_ordered)
+      cudaFreeAsync(b->arena, b->stream);
+    else
+      cudaFree(b->arena);
+  }
+  if (b->own_host) {
+    if (b->h_in) cudaFreeHost(b->h_in);
+    if (b->h_out) cudaFreeHost(b->h_out);
+  }
+  delete b;
+}
+
+void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, const rs_bipoly *g,
+                    int64_t *in_words, int64_t *out_words, int64_t *device_bytes) {
+  int64_t in = 0, out = 0, img = 0, meta = 0, tiles = 0, g2 = 0, g3 = 0;
+  for (size_t i = 0; i < plans.size(); ++i) {
+    in += rs_input_words(f[i]) + rs_input_words(g[i]);
+    const PairPlan &p = plans[i];
+    if (p.status != RS_OK || p.trivial_zero) continue;
+    out += (int64_t)p.N * p.Lout;
+    img += (int64_t)p.K * p.N;
+    meta += p.f.my + p.g.my + 2;
+    tiles += (int64_t)p.K * ((p.N + 31) / 32);
+    g2 += p.K;
+    g3 += (p.N + 127) / 128;
+  }
+  *in_words = in;
+  *out_words = out;
+  *device_bytes = (int64_t)(align_up(in * 4) + align_up(meta * 8) + align_up(plans.size() * sizeof(PairDesc)) +
+                            align_up(tiles * sizeof(Tile)) + kAlign + 2 * align_up(img * 4) +
+                            2 * align_up(out * 4) + align_up(g2 * 8) + align_up(g3 * 8) + kAlign);
+}
+
+int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
+                   std::vector<PairPlan> &&plans, const RsBatchOpts &opt, rs_batch **out) {
   rs_batch *b = new rs_batch();
   b->ctx = ctx;
   b->n = n;
-  b->images_only = images_only;
+  b->opt = opt;
+  b->stream = opt.stream ? opt.stream : ctx->stream;
   b->plans = std::move(plans);
   b->dev_index.assign(n, -1);
   memset(&b->info, 0, sizeof(b->info));
   b->info.pairs = n;
+  const bool images_only = opt.images_only;
   const int T = ctx->cfg.tile_points > 0 ? ctx->cfg.tile_points : 128;
 
   std::vector<int2> meta;
   std::vector<int> order;
   b->in_f.assign(n, -1);
   b->in_g.assign(n, -1);
+  int maxN = 1, maxK = 0, maxDx = 0;
   for (int i = 0; i < n; ++i) {
     b->in_f[i] = b->in_words;
-    b->in_words += input_words(f[i]);
+    b->in_words += rs_input_words(f[i]);
     b->in_g[i] = b->in_words;
-    b->in_words += input_words(g[i]);
+    b->in_words += rs_input_words(g[i]);
     const PairPlan &p = b->plans[i];
     if (p.status != RS_OK || p.trivial_zero) continue;
     PairDesc d;
@@ -225,6 +230,9 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     b->dev_index[i] = (int)b->descs.size();
     b->descs.push_back(d);
     order.push_back(i);
+    maxN = std::max(maxN, p.N);
+    maxK = std::max(maxK, p.K);
+    maxDx = std::max(maxDx, std::max(p.f.mx, p.g.mx));
     b->info.images += (int64_t)p.K * p.N;
     b->info.primes_total += p.K;
     b->info.coeffs_total += p.N;
@@ -234,6 +242,7 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     b->info.modmul_interp += (double)p.K * ((double)p.N * p.N + 8.0 * p.N);
     b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
   }
+  if (images_only) b->out_words = std::max(b->out_words, b->img_words);
 
   // G1 tiles grouped by register-capacity class; costliest pairs first.
   std::sort(order.begin(), order.end(), [&](int x, int y) {
@@ -243,9 +252,8 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
     return ca > cc;
   });
   std::vector<Tile> tiles;
-  int ncap = 0;
   for (int cap = 8; cap <= 72; cap += 8) {
-    ClassLaunch cl;
+    RsClassLaunch cl;
     cl.cap = cap;
     cl.threads = T;
     cl.tile_off = (int64_t)tiles.size();
@@ -257,119 +265,125 @@ static int build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *
         for (int x0 = 0; x0 < p.N; x0 += T) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T, p.N - x0)});
     }
     cl.ntiles = (int)((int64_t)tiles.size() - cl.tile_off);
-    if (cl.ntiles > 0) {
-      b->classes.push_back(cl);
-      ++ncap;
-    }
+    if (cl.ntiles > 0) b->classes.push_back(cl);
   }
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
-  int maxN = 1, maxK = 0, maxDx = 0;
   for (int i : byN) {
     const PairPlan &p = b->plans[i];
-    maxN = std::max(maxN, p.N);
-    maxK = std::max(maxK, p.K);
-    maxDx = std::max(maxDx, std::max(p.f.mx, p.g.mx));
     for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
   }
   for (int i : order) {
     const PairPlan &p = b->plans[i];
     for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(b->dev_index[i], j));
   }
-  b->ng2 = (int)g2.size();
-  b->ng3 = (int)g3.size();
+  b->ng2 = images_only ? 0 : (int)g2.size();
+  b->ng3 = images_only ? 0 : (int)g3.size();
   b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
-  b->tab_k = maxK;
-  b->tab_stride = maxN;
-  b->chirp_stride = maxN + T + maxDx + 1;
-  b->info.kernel_launches = (int64_t)b->classes.size() + (images_only ? 0 : (b->ng2 > 0) + (b->ng3 > 0));
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
+  b->info.kernel_launches = (int64_t)b->classes.size() + (b->ng2 > 0) + (b->ng3 > 0);
 
-  DevGuard dg(ctx->device);
   int rc = RS_OK;
-  auto alloc = [&](void **p, size_t bytes) {
-    if (rc != RS_OK || bytes == 0) return;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) rc = fail(ctx, cuda_code(e), std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxN, maxDx);
+  if (rc != RS_OK) {
+    rs_free_batch(b);
+    return rc;
+  }
+  DevGuard dg(ctx->device);
+  size_t off = 0;  // one device arena carved into every buffer of the batch
+  auto carve = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
   };
-  alloc((void **)&b->d_in, b->in_words * 4);
-  alloc((void **)&b->d_meta, meta.size() * sizeof(int2));
-  alloc((void **)&b->d_pairs, b->descs.size() * sizeof(PairDesc));
-  alloc((void **)&b->d_tiles, tiles.size() * sizeof(Tile));
-  alloc((void **)&b->d_counters, 16 * sizeof(int32_t));
-  alloc((void **)&b->d_num, b->img_words * 4);
-  alloc((void **)&b->d_den, b->img_words * 4);
-  alloc((void **)&b->d_xl, std::max<int64_t>(b->out_words, images_only ? b->img_words : 0) * 4);
-  alloc((void **)&b->d_out, std::max<int64_t>(b->out_words, images_only ? b->img_words : 0) * 4);
-  alloc((void **)&b->d_g2, g2.size() * sizeof(int2));
-  alloc((void **)&b->d_g3, g3.size() * sizeof(int2));
-  alloc((void **)&b->d_stats, ST_COUNT * sizeof(unsigned long long));
-  if (!images_only) {
-    alloc((void **)&b->d_finv, (size_t)b->tab_k * b->tab_stride * 4);
-    alloc((void **)&b->d_gtab, (size_t)b->tab_k * b->tab_stride * 4);
-    alloc((void **)&b->d_btab, (size_t)b->tab_k * b->tab_stride * 4);
+  const size_t o_in = carve(b->in_words * 4), o_meta = carve(meta.size() * sizeof(int2)),
+               o_pairs = carve(b->descs.size() * sizeof(PairDesc)), o_tiles = carve(tiles.size() * sizeof(Tile)),
+               o_cnt = carve(16 * sizeof(int32_t)), o_num = carve(b->img_words * 4), o_den = carve(b->img_words * 4),
+               o_xl = carve(b->out_words * 4), o_out = carve(b->out_words * 4), o_g2 = carve(g2.size() * sizeof(int2)),
+               o_g3 = carve(g3.size() * sizeof(int2)), o_st = carve(ST_COUNT * sizeof(unsigned long long));
+  cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
+  if (e != cudaSuccess) {
+    b->arena = nullptr;
+    rs_free_batch(b);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("device arena: ") + cudaGetErrorString(e));
   }
-  alloc((void **)&b->d_qc, (size_t)b->tab_k * b->chirp_stride * 4);
-  alloc((void **)&b->d_qn, (size_t)b->tab_k * b->chirp_stride * 4);
-  if (rc == RS_OK && b->in_words) {
-    cudaError_t e = cudaMallocHost((void **)&b->h_in, b->in_words * 4);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_NOMEM, "cudaMallocHost (inputs)");
+  char *base = static_cast<char *>(b->arena);
+  b->d_in = (uint32_t *)(base + o_in);
+  b->d_meta = (int2 *)(base + o_meta);
+  b->d_pairs = (PairDesc *)(base + o_pairs);
+  b->d_tiles = (Tile *)(base + o_tiles);
+  b->d_counters = (int32_t *)(base + o_cnt);
+  b->d_num = (uint32_t *)(base + o_num);
+  b->d_den = (uint32_t *)(base + o_den);
+  b->d_xl = (uint32_t *)(base + o_xl);
+  b->d_out = (uint32_t *)(base + o_out);
+  b->d_g2 = (int2 *)(base + o_g2);
+  b->d_g3 = (int2 *)(base + o_g3);
+  b->d_stats = (unsigned long long *)(base + o_st);
+
+  if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
+    b->h_in = opt.h_in;
+    b->h_out = opt.h_out;
+  } else {
+    b->own_host = true;
+    if (b->in_words && cudaMallocHost((void **)&b->h_in, b->in_words * 4) != cudaSuccess) rc = RS_ERR_NOMEM;
+    if (rc == RS_OK && b->out_words && cudaMallocHost((void **)&b->h_out, b->out_words * 4) != cudaSuccess)
+      rc = RS_ERR_NOMEM;
+    if (rc != RS_OK) {
+      rs_free_batch(b);
+      return rs_fail(ctx, rc, "cudaMallocHost (staging)");
+    }
   }
-  if (rc == RS_OK && b->out_words) {
-    cudaError_t e = cudaMallocHost((void **)&b->h_out, b->out_words * 4);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_NOMEM, "cudaMallocHost (outputs)");
-  }
+  // Static per-batch tables, ordered on the batch stream.
   auto h2d = [&](void *dst, const void *src, size_t bytes) {
     if (rc != RS_OK || bytes == 0) return;
-    cudaError_t e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+    cudaError_t e2 = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e2));
   };
   h2d(b->d_meta, meta.data(), meta.size() * sizeof(int2));
   h2d(b->d_pairs, b->descs.data(), b->descs.size() * sizeof(PairDesc));
   h2d(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile));
   h2d(b->d_g2, g2.data(), g2.size() * sizeof(int2));
   h2d(b->d_g3, g3.data(), g3.size() * sizeof(int2));
+  if (rc == RS_OK) {  // the pageable sources above must outlive the copies
+    cudaError_t e2 = cudaStreamSynchronize(b->stream);
+    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e2));
+  }
   for (auto &cl : b->classes) {
     if (rc != RS_OK) break;
     int mb = 0;
-    cudaError_t e = g1_prepare(cl.cap, cl.threads, cl.smem, &mb);
-    if (e != cudaSuccess) {
-      rc = fail(ctx, RS_ERR_CUDA, std::string("G1 set-up: ") + cudaGetErrorString(e));
+    cudaError_t e2 = g1_prepare(cl.cap, cl.threads, cl.smem, &mb);
+    if (e2 != cudaSuccess) {
+      rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G1 set-up: ") + cudaGetErrorString(e2));
       break;
     }
     if (mb < 1) mb = 1;
-    cl.blocks = ctx->cfg.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
-  }
-  if (rc == RS_OK && b->tab_k > 0) {
-    cudaError_t e = launch_tables(ctx->d_mods, ctx->d_qbase, b->tab_k, b->tab_stride, b->chirp_stride,
-                                  b->d_finv, b->d_gtab, b->d_btab, b->d_qc, b->d_qn, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("point tables: ") + cudaGetErrorString(e));
+    cl.blocks = opt.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
   }
   if (rc == RS_OK && b->ng2) {
-    cudaError_t e = g2_prepare(b->g2smem);
-    if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e));
+    cudaError_t e2 = g2_prepare(b->g2smem);
+    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
   }
-  for (auto &e : b->ev)
-    if (rc == RS_OK && cudaEventCreate(&e) != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
+  for (auto &ev : b->ev)
+    if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
   if (rc != RS_OK) {
-    free_batch(b);
+    rs_free_batch(b);
     return rc;
   }
   *out = b;
   return RS_OK;
 }
 
-static int upload(rs_batch *b, const rs_bipoly *f, const rs_bipoly *g) {
+int rs_upload(rs_batch *b, const rs_bipoly *f, const rs_bipoly *g) {
   rs_ctx *ctx = b->ctx;
   for (int i = 0; i < b->n; ++i) {
-    memcpy(b->h_in + b->in_f[i], f[i].coeffs, input_words(f[i]) * 4);
-    memcpy(b->h_in + b->in_g[i], g[i].coeffs, input_words(g[i]) * 4);
+    memcpy(b->h_in + b->in_f[i], f[i].coeffs, rs_input_words(f[i]) * 4);
+    memcpy(b->h_in + b->in_g[i], g[i].coeffs, rs_input_words(g[i]) * 4);
   }
   if (b->in_words)
-    RS_CUDA(ctx, cudaMemcpyAsync(b->d_in, b->h_in, b->in_words * 4, cudaMemcpyHostToDevice, ctx->stream));
+    RS_CUDA(ctx, cudaMemcpyAsync(b->d_in, b->h_in, b->in_words * 4, cudaMemcpyHostToDevice, b->stream));
   return RS_OK;
 }
 
@@ -379,8 +393,13 @@ static cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
 
 static int enqueue(rs_batch *b, bool capturing) {
   rs_ctx *ctx = b->ctx;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = b->stream;
   const bool timing = ctx->cfg.timing != 0;
+  RsTables tab;
+  {
+    std::lock_guard<std::mutex> lock(ctx->tab_mu);
+    tab = ctx->tab;
+  }
   RS_CUDA(ctx, cudaMemsetAsync(b->d_counters, 0, 16 * sizeof(int32_t), s));
   RS_CUDA(ctx, cudaMemsetAsync(b->d_stats, 0, ST_COUNT * sizeof(unsigned long long), s));
   if (timing) RS_CUDA(ctx, record(b->ev[0], s, capturing));
@@ -390,14 +409,14 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.pairs = b->d_pairs;
     a.tiles = b->d_tiles + cl.tile_off;
     a.ntiles = cl.ntiles;
-    a.persistent = ctx->cfg.persistent ? 1 : 0;
+    a.persistent = b->opt.persistent ? 1 : 0;
     a.counter = b->d_counters + (ci++);
     a.limbs = b->d_in;
     a.meta = b->d_meta;
     a.mods = ctx->d_mods;
-    a.qc = b->d_qc;
-    a.qn = b->d_qn;
-    a.tstride = b->chirp_stride;
+    a.qc = tab.qc;
+    a.qn = tab.qn;
+    a.tstride = tab.cstride;
     a.vtab = ctx->d_vtab;
     a.num = b->d_num;
     a.den = b->d_den;
@@ -405,7 +424,6 @@ static int enqueue(rs_batch *b, bool capturing) {
     RS_CUDA(ctx, launch_g1(cl.cap, cl.threads, cl.blocks, cl.smem, a, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[1], s, capturing));
-  if (b->images_only) return RS_OK;
   if (b->ng2) {
     G2Args a2;
     a2.pairs = b->d_pairs;
@@ -414,11 +432,11 @@ static int enqueue(rs_batch *b, bool capturing) {
     a2.num = b->d_num;
     a2.den = b->d_den;
     a2.coef = b->d_num;
-    a2.finv = b->d_finv;
-    a2.gtab = b->d_gtab;
-    a2.btab = b->d_btab;
-    a2.tab_stride = b->tab_stride;
-    RS_CUDA(ctx, launch_g2(256, b->ng2, b->g2smem, a2, s));
+    a2.finv = tab.finv;
+    a2.gtab = tab.gtab;
+    a2.btab = tab.btab;
+    a2.tab_stride = tab.N;
+    RS_CUDA(ctx, launch_g2(b->g2_threads, b->ng2, b->g2smem, a2, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[2], s, capturing));
   if (b->ng3) {
@@ -436,30 +454,38 @@ static int enqueue(rs_batch *b, bool capturing) {
   return RS_OK;
 }
 
-static int run(rs_batch *b) {
+int rs_run(rs_batch *b) {
   rs_ctx *ctx = b->ctx;
   DevGuard dg(ctx->device);
-  if (ctx->cfg.use_graphs && !b->images_only) {
+  if (b->opt.use_graph && !b->opt.images_only) {
     if (!b->gexec) {
-      RS_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      RS_CUDA(ctx, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
       int rc = enqueue(b, true);
       cudaGraph_t graph = nullptr;
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+      cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
       if (rc != RS_OK) {
         if (graph) cudaGraphDestroy(graph);
         return rc;
       }
-      if (e != cudaSuccess) return fail(ctx, RS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      if (e != cudaSuccess) return rs_fail(ctx, RS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
       e = cudaGraphInstantiate(&b->gexec, graph, 0);
       cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return fail(ctx, RS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      if (e != cudaSuccess) return rs_fail(ctx, RS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
-    RS_CUDA(ctx, cudaGraphLaunch(b->gexec, ctx->stream));
+    RS_CUDA(ctx, cudaGraphLaunch(b->gexec, b->stream));
   } else {
     int rc = enqueue(b, false);
     if (rc != RS_OK) return rc;
   }
   b->ran = true;
+  return RS_OK;
+}
+
+int rs_fetch_async(rs_batch *b) {
+  rs_ctx *ctx = b->ctx;
+  if (!b->ran) return rs_fail(ctx, RS_ERR_STATE, "batch has not been run");
+  if (b->out_words)
+    RS_CUDA(ctx, cudaMemcpyAsync(b->h_out, b->d_out, b->out_words * 4, cudaMemcpyDeviceToHost, b->stream));
   return RS_OK;
 }
 
@@ -470,34 +496,45 @@ static int coef_limbs_needed(const uint32_t *c, int L) {
   return l;
 }
 
-static int fetch(rs_batch *b, rs_upoly *out, int32_t *status) {
+// Trimmed degree and limb count of pair i's result in the host staging buffer.
+static const uint32_t *result_shape(rs_batch *b, int i, int *deg, int *limbs) {
+  const PairPlan &p = b->plans[i];
+  *deg = -1;
+  *limbs = 1;
+  if (p.trivial_zero) return nullptr;
+  const uint32_t *w = b->h_out + b->descs[b->dev_index[i]].out_off;
+  for (int j = 0; j < p.N; ++j) {
+    const uint32_t *c = w + (size_t)j * p.Lout;
+    bool nz = false;
+    for (int l = 0; l < p.Lout; ++l) nz = nz || c[l];
+    if (nz) {
+      *deg = j;
+      *limbs = std::max(*limbs, coef_limbs_needed(c, p.Lout));
+    }
+  }
+  return w;
+}
+
+int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, int *limbs) {
+  const PairPlan &p = b->plans[i];
+  if (p.status != RS_OK) return p.status;
+  const uint32_t *w = result_shape(b, i, deg, limbs);
+  words.assign((size_t)(*deg + 1) * *limbs, 0u);
+  for (int j = 0; j <= *deg; ++j)
+    for (int l = 0; l < *limbs; ++l) words[(size_t)j * *limbs + l] = w[(size_t)j * p.Lout + l];
+  return RS_OK;
+}
+
+int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status) {
   rs_ctx *ctx = b->ctx;
-  DevGuard dg(ctx->device);
-  if (!b->ran) return fail(ctx, RS_ERR_STATE, "batch has not been run");
-  if (b->out_words)
-    RS_CUDA(ctx, cudaMemcpyAsync(b->h_out, b->d_out, b->out_words * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  RS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   int first = RS_OK;
   for (int i = 0; i < b->n; ++i) {
     const PairPlan &p = b->plans[i];
     int rc = p.status;
     if (rc == RS_OK && !out[i].coeffs && out[i].capacity_words > 0) rc = RS_ERR_ARG;
     if (rc == RS_OK) {
-      int deg = -1, L = 1;
-      const uint32_t *w = nullptr;
-      if (!p.trivial_zero) {
-        const PairDesc &d = b->descs[b->dev_index[i]];
-        w = b->h_out + d.out_off;
-        for (int j = 0; j < p.N; ++j) {
-          const uint32_t *c = w + (size_t)j * p.Lout;
-          bool nz = false;
-          for (int l = 0; l < p.Lout; ++l) nz = nz || c[l];
-          if (nz) {
-            deg = j;
-            L = std::max(L, coef_limbs_needed(c, p.Lout));
-          }
-        }
-      }
+      int deg, L;
+      const uint32_t *w = result_shape(b, i, &deg, &L);
       out[i].deg = deg;
       out[i].limbs = L;
       if ((int64_t)(deg + 1) * L > out[i].capacity_words) {
@@ -510,10 +547,26 @@ static int fetch(rs_batch *b, rs_upoly *out, int32_t *status) {
     if (status) status[i] = rc;
     if (rc != RS_OK && first == RS_OK) {
       first = rc;
-      fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + rs_error_string(rc));
+      rs_fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + rs_error_string(rc));
     }
   }
   return first;
+}
+
+static int fetch(rs_batch *b, rs_upoly *out, int32_t *status) {
+  rs_ctx *ctx = b->ctx;
+  DevGuard dg(ctx->device);
+  int rc = rs_fetch_async(b);
+  if (rc != RS_OK) return rc;
+  RS_CUDA(ctx, cudaStreamSynchronize(b->stream));
+  return rs_unpack(b, out, status);
+}
+
+static RsBatchOpts default_opts(rs_ctx *ctx) {
+  RsBatchOpts o;
+  o.use_graph = ctx->cfg.use_graphs != 0;
+  o.persistent = ctx->cfg.persistent != 0;
+  return o;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -528,7 +581,7 @@ const char *rs_error_string(int code) {
     case RS_ERR_CAPACITY: return "output capacity too small";
     case RS_ERR_NOMEM: return "out of memory";
     case RS_ERR_CUDA: return "CUDA error";
-    case RS_ERR_TIMEOUT: return "device wait timed out";
+    case RS_ERR_TIMEOUT: return "wait timed out";
     case RS_ERR_LIMIT: return "input exceeds a library limit";
     case RS_ERR_STATE: return "invalid state";
     default: return "unknown error";
@@ -538,7 +591,7 @@ const char *rs_error_string(int code) {
 const char *rs_last_error(const rs_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
 int rs_config_default(rs_config *cfg) {
-  if (!cfg) return fail(nullptr, RS_ERR_ARG, "cfg is NULL");
+  if (!cfg) return rs_fail(nullptr, RS_ERR_ARG, "cfg is NULL");
   memset(cfg, 0, sizeof(*cfg));
   cfg->device = -1;
   cfg->use_graphs = 1;
@@ -547,7 +600,7 @@ int rs_config_default(rs_config *cfg) {
 }
 
 int rs_create(rs_ctx **out, const rs_config *cfg) {
-  if (!out) return fail(nullptr, RS_ERR_ARG, "ctx is NULL");
+  if (!out) return rs_fail(nullptr, RS_ERR_ARG, "ctx is NULL");
   *out = nullptr;
   rs_config c;
   if (cfg)
@@ -555,21 +608,22 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   else
     rs_config_default(&c);
   if (c.tile_points != 0 && c.tile_points != 32 && c.tile_points != 64 && c.tile_points != 128)
-    return fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
+    return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
   int dev = c.device;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess || ndev == 0)
-    return fail(nullptr, RS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    return rs_fail(nullptr, RS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-  if (dev >= ndev) return fail(nullptr, RS_ERR_ARG, "device ordinal out of range");
+  if (dev >= ndev) return rs_fail(nullptr, RS_ERR_ARG, "device ordinal out of range");
   rs_ctx *ctx = new rs_ctx();
   ctx->device = dev;
   ctx->cfg = c;
   DevGuard dg(dev);
   int rc = RS_OK;
   auto chk = [&](cudaError_t e2, const char *what) {
-    if (rc == RS_OK && e2 != cudaSuccess) rc = fail(nullptr, cuda_code(e2), std::string(what) + ": " + cudaGetErrorString(e2));
+    if (rc == RS_OK && e2 != cudaSuccess)
+      rc = rs_fail(nullptr, rs_cuda_code(e2), std::string(what) + ": " + cudaGetErrorString(e2));
   };
   chk(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev), "device query");
   chk(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -582,7 +636,9 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   chk(cudaMalloc(&ctx->d_crt, np * 4), "cudaMalloc");
   chk(cudaMalloc(&ctx->d_qbase, np * 4), "cudaMalloc");
   if (rc == RS_OK) chk(cudaMemcpy(ctx->d_primes, ctx->primes.data(), np * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-  if (rc == RS_OK) chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->stream), "prime tables");
+  if (rc == RS_OK)
+    chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->stream),
+        "prime tables");
   if (rc == RS_OK) chk(cudaStreamSynchronize(ctx->stream), "prime tables");
   if (rc != RS_OK) {
     rs_destroy(ctx);
@@ -594,11 +650,14 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
 
 int rs_destroy(rs_ctx *ctx) {
   if (!ctx) return RS_OK;
+  rs_server_shutdown(ctx);
   {
     DevGuard dg(ctx->device);
-    for (rs_batch *b : ctx->batches) free_batch(b);
-    if (ctx->cache) free_batch(ctx->cache);
+    for (rs_batch *b : ctx->batches) rs_free_batch(b);
+    if (ctx->cache) rs_free_batch(ctx->cache);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    free_tables(ctx->tab);
+    for (auto &t : ctx->retired) free_tables(t);
     void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase};
     for (void *p : dev)
       if (p) cudaFree(p);
@@ -609,23 +668,22 @@ int rs_destroy(rs_ctx *ctx) {
 }
 
 int rs_stream(rs_ctx *ctx, void **stream) {
-  if (!ctx || !stream) return fail(ctx, RS_ERR_ARG, "NULL argument");
+  if (!ctx || !stream) return rs_fail(ctx, RS_ERR_ARG, "NULL argument");
   *stream = (void *)ctx->stream;
   return RS_OK;
 }
 
 int rs_result_bound(const rs_bipoly *f, const rs_bipoly *g, int32_t *deg_bound, int32_t *limbs_bound,
                     int32_t *primes, int32_t *bits) {
-  static std::vector<double> log2p;
-  static bool init = false;
-  if (!init) {
-    for (uint32_t p : rs_prime_table(RS_MAX_PRIMES)) log2p.push_back(log2((double)p) - 1e-12);
-    init = true;
-  }
+  static const std::vector<double> log2p = [] {
+    std::vector<double> v;
+    for (uint32_t p : rs_prime_table(RS_MAX_PRIMES)) v.push_back(log2((double)p) - 1e-12);
+    return v;
+  }();
   PairPlan p;
   const char *why = "";
   int rc = rs_plan_pair(f, g, log2p, p, &why);
-  if (rc != RS_OK) return fail(nullptr, rc, why);
+  if (rc != RS_OK) return rs_fail(nullptr, rc, why);
   if (deg_bound) *deg_bound = p.trivial_zero ? -1 : p.D;
   if (limbs_bound) *limbs_bound = p.Lout;
   if (primes) *primes = p.K;
@@ -634,17 +692,18 @@ int rs_result_bound(const rs_bipoly *f, const rs_bipoly *g, int32_t *deg_bound, 
 }
 
 int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_batch **batch) {
-  if (!ctx || !batch || n < 0 || (n > 0 && (!f || !g))) return fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
+  if (!ctx || !batch || n < 0 || (n > 0 && (!f || !g))) return rs_fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
   *batch = nullptr;
   std::vector<PairPlan> plans;
   int first = RS_OK;
-  plan_all(ctx, n, f, g, plans, nullptr, &first);
+  rs_plan_all(ctx, n, f, g, plans, nullptr, &first);
   rs_batch *b = nullptr;
-  int rc = build_batch(ctx, n, f, g, std::move(plans), false, &b);
+  int rc = rs_build_batch(ctx, n, f, g, std::move(plans), default_opts(ctx), &b);
   if (rc != RS_OK) return rc;
-  rc = upload(b, f, g);
+  DevGuard dg(ctx->device);
+  rc = rs_upload(b, f, g);
   if (rc != RS_OK) {
-    free_batch(b);
+    rs_free_batch(b);
     return rc;
   }
   ctx->batches.push_back(b);
@@ -653,31 +712,31 @@ int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly 
 }
 
 int rs_batch_upload(rs_batch *b, int32_t n, const rs_bipoly *f, const rs_bipoly *g) {
-  if (!b || n != b->n || (n > 0 && (!f || !g))) return fail(b ? b->ctx : nullptr, RS_ERR_ARG, "bad arguments");
+  if (!b || n != b->n || (n > 0 && (!f || !g))) return rs_fail(b ? b->ctx : nullptr, RS_ERR_ARG, "bad arguments");
   std::vector<PairPlan> plans;
   int first = RS_OK;
-  plan_all(b->ctx, n, f, g, plans, nullptr, &first);
+  rs_plan_all(b->ctx, n, f, g, plans, nullptr, &first);
   for (int i = 0; i < n; ++i)
-    if (!same_shape(plans[i], b->plans[i]))
-      return fail(b->ctx, RS_ERR_STATE, "inputs do not match the batch's plan (pair " + std::to_string(i) + ")");
+    if (!rs_same_shape(plans[i], b->plans[i]))
+      return rs_fail(b->ctx, RS_ERR_STATE, "inputs do not match the batch's plan (pair " + std::to_string(i) + ")");
   DevGuard dg(b->ctx->device);
-  return upload(b, f, g);
+  return rs_upload(b, f, g);
 }
 
 int rs_batch_run(rs_batch *b) {
-  if (!b) return fail(nullptr, RS_ERR_ARG, "batch is NULL");
-  return run(b);
+  if (!b) return rs_fail(nullptr, RS_ERR_ARG, "batch is NULL");
+  return rs_run(b);
 }
 
 int rs_batch_sync(rs_batch *b) {
-  if (!b) return fail(nullptr, RS_ERR_ARG, "batch is NULL");
+  if (!b) return rs_fail(nullptr, RS_ERR_ARG, "batch is NULL");
   DevGuard dg(b->ctx->device);
-  RS_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+  RS_CUDA(b->ctx, cudaStreamSynchronize(b->stream));
   return RS_OK;
 }
 
 int rs_batch_results(rs_batch *b, rs_upoly *out, int32_t *status) {
-  if (!b || (b->n > 0 && !out)) return fail(b ? b->ctx : nullptr, RS_ERR_ARG, "NULL argument");
+  if (!b || (b->n > 0 && !out)) return rs_fail(b ? b->ctx : nullptr, RS_ERR_ARG, "NULL argument");
   return fetch(b, out, status);
 }
 
@@ -685,18 +744,18 @@ int rs_batch_destroy(rs_batch *b) {
   if (!b) return RS_OK;
   auto &v = b->ctx->batches;
   v.erase(std::remove(v.begin(), v.end(), b), v.end());
-  free_batch(b);
+  rs_free_batch(b);
   return RS_OK;
 }
 
 int rs_batch_info_get(rs_batch *b, rs_batch_info *info) {
-  if (!b || !info) return fail(b ? b->ctx : nullptr, RS_ERR_ARG, "NULL argument");
+  if (!b || !info) return rs_fail(b ? b->ctx : nullptr, RS_ERR_ARG, "NULL argument");
   rs_ctx *ctx = b->ctx;
   DevGuard dg(ctx->device);
   *info = b->info;
   info->ms_images = info->ms_interp = info->ms_crt = info->ms_total = -1.0f;
   if (!b->ran) return RS_OK;
-  RS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  RS_CUDA(ctx, cudaStreamSynchronize(b->stream));
   unsigned long long st[ST_COUNT];
   RS_CUDA(ctx, cudaMemcpy(st, b->d_stats, sizeof(st), cudaMemcpyDeviceToHost));
   info->unlucky_points = (int64_t)st[ST_UNLUCKY_POINTS];
@@ -705,7 +764,7 @@ int rs_batch_info_get(rs_batch *b, rs_batch_info *info) {
   if (ctx->cfg.timing) {
     float t = 0;
     if (cudaEventElapsedTime(&t, b->ev[0], b->ev[1]) == cudaSuccess) info->ms_images = t;
-    if (!b->images_only) {
+    if (!b->opt.images_only) {
       if (cudaEventElapsedTime(&t, b->ev[1], b->ev[2]) == cudaSuccess) info->ms_interp = t;
       if (cudaEventElapsedTime(&t, b->ev[2], b->ev[3]) == cudaSuccess) info->ms_crt = t;
       if (cudaEventElapsedTime(&t, b->ev[0], b->ev[3]) == cudaSuccess) info->ms_total = t;
@@ -716,24 +775,24 @@ int rs_batch_info_get(rs_batch *b, rs_batch_info *info) {
 
 int rs_resultant_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out,
                        int32_t *status) {
-  if (!ctx || n < 0 || (n > 0 && (!f || !g || !out))) return fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
+  if (!ctx || n < 0 || (n > 0 && (!f || !g || !out))) return rs_fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
   if (n == 0) return RS_OK;
   std::vector<PairPlan> plans;
   int first = RS_OK;
-  plan_all(ctx, n, f, g, plans, status, &first);
+  rs_plan_all(ctx, n, f, g, plans, status, &first);
   rs_batch *b = ctx->cache;
   bool reuse = b && b->n == n;
-  for (int i = 0; reuse && i < n; ++i) reuse = same_shape(plans[i], b->plans[i]);
+  for (int i = 0; reuse && i < n; ++i) reuse = rs_same_shape(plans[i], b->plans[i]);
   if (!reuse) {
-    if (b) free_batch(b);
+    if (b) rs_free_batch(b);
     ctx->cache = nullptr;
-    int rc = build_batch(ctx, n, f, g, std::move(plans), false, &b);
+    int rc = rs_build_batch(ctx, n, f, g, std::move(plans), default_opts(ctx), &b);
     if (rc != RS_OK) return rc;
     ctx->cache = b;
   }
   DevGuard dg(ctx->device);
-  int rc = upload(b, f, g);
-  if (rc == RS_OK) rc = run(b);
+  int rc = rs_upload(b, f, g);
+  if (rc == RS_OK) rc = rs_run(b);
   if (rc == RS_OK) rc = fetch(b, out, status);
   return rc != RS_OK ? rc : first;
 }
@@ -745,18 +804,18 @@ int rs_resultant_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes, int32_t npoints,
               uint32_t *primes_out, uint32_t *points_out, uint32_t *images_out) {
   if (!ctx || !f || !g || !images_out || nprimes < 1 || npoints < 1)
-    return fail(ctx, RS_ERR_ARG, "bad arguments");
+    return rs_fail(ctx, RS_ERR_ARG, "bad arguments");
   if (nprimes > (int)ctx->primes.size() || npoints > RS_MAX_POINTS)
-    return fail(ctx, RS_ERR_LIMIT, "nprimes or npoints above the library limits");
+    return rs_fail(ctx, RS_ERR_LIMIT, "nprimes or npoints above the library limits");
   std::vector<PairPlan> plans;
   int first = RS_OK;
-  plan_all(ctx, 1, f, g, plans, nullptr, &first);
+  rs_plan_all(ctx, 1, f, g, plans, nullptr, &first);
   if (first != RS_OK) return first;
+  DevGuard dg(ctx->device);
   if (plans[0].trivial_zero) {
     memset(images_out, 0, (size_t)nprimes * npoints * 4);
-    if (points_out) {  // the points are not needed; report them from a host-side run of the table
+    if (points_out) {
       std::vector<uint32_t> qb(nprimes);
-      DevGuard dg(ctx->device);
       RS_CUDA(ctx, cudaMemcpy(qb.data(), ctx->d_qbase, (size_t)nprimes * 4, cudaMemcpyDeviceToHost));
       for (int k = 0; k < nprimes; ++k) {
         const ModP m = make_modp(ctx->primes[k]);
@@ -769,24 +828,26 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
     plans[0].D = npoints - 1;
     plans[0].Lout = 1;
     plans[0].cap = std::max(plans[0].f.my, plans[0].g.my) + 1;
+    RsBatchOpts o = default_opts(ctx);
+    o.images_only = true;
+    o.use_graph = false;
     rs_batch *b = nullptr;
-    int rc = build_batch(ctx, 1, f, g, std::move(plans), true, &b);
+    int rc = rs_build_batch(ctx, 1, f, g, std::move(plans), o, &b);
     if (rc != RS_OK) return rc;
-    DevGuard dg(ctx->device);
-    rc = upload(b, f, g);
-    if (rc == RS_OK) rc = run(b);
+    rc = rs_upload(b, f, g);
+    if (rc == RS_OK) rc = rs_run(b);
     if (rc == RS_OK) {
       uint32_t *d_pts = points_out ? b->d_out : nullptr;  // images-only batches size d_out to K * N
       cudaError_t e = launch_finalize_images(ctx->d_mods, ctx->d_qbase, b->d_num, b->d_den, b->d_xl, d_pts,
-                                             nprimes, npoints, ctx->stream);
+                                             nprimes, npoints, b->stream);
       if (e == cudaSuccess)
-        e = cudaMemcpyAsync(images_out, b->d_xl, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        e = cudaMemcpyAsync(images_out, b->d_xl, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, b->stream);
       if (e == cudaSuccess && points_out)
-        e = cudaMemcpyAsync(points_out, d_pts, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, ctx->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess) rc = fail(ctx, RS_ERR_CUDA, std::string("images: ") + cudaGetErrorString(e));
+        e = cudaMemcpyAsync(points_out, d_pts, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("images: ") + cudaGetErrorString(e));
     }
-    free_batch(b);
+    rs_free_batch(b);
     if (rc != RS_OK) return rc;
   }
   if (primes_out) memcpy(primes_out, ctx->primes.data(), (size_t)nprimes * 4);

@@ -1,0 +1,116 @@
+// Internal host-side structures of librs shared by engine.cu (contexts,
+// batches, C ABI) and server.cu (continuous-batching request server).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "rs_internal.cuh"
+
+struct RsServer;  // server.cu
+
+// Point and interpolation tables per prime, shared by every batch of a
+// context and grown on demand (old allocations are kept until the context is
+// destroyed, so captured graphs stay valid).
+struct RsTables {
+  int K = 0;        // primes covered
+  int N = 0;        // interpolation stride (points covered)
+  int cstride = 0;  // chirp stride (point + x-degree + tile window covered)
+  uint32_t *finv = nullptr, *gtab = nullptr, *qn = nullptr;
+  int32_t *btab = nullptr, *qc = nullptr;
+};
+
+struct rs_ctx {
+  int device = 0;
+  rs_config cfg;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  std::vector<uint32_t> primes;
+  std::vector<double> log2p;
+  uint32_t *d_primes = nullptr;
+  ModP *d_mods = nullptr;
+  uint32_t *d_vtab = nullptr;
+  uint32_t *d_crt = nullptr;
+  uint32_t *d_qbase = nullptr;
+  std::string err;
+  std::vector<rs_batch *> batches;
+  rs_batch *cache = nullptr;
+  std::mutex tab_mu;
+  RsTables tab;
+  std::vector<RsTables> retired;
+  RsServer *server = nullptr;
+};
+
+struct RsClassLaunch {
+  int cap = 0;
+  int threads = 128;
+  int blocks = 0;
+  int64_t tile_off = 0;
+  int ntiles = 0;
+  size_t smem = 0;
+};
+
+struct RsBatchOpts {
+  bool images_only = false;
+  cudaStream_t stream = nullptr;  // NULL: the context's stream
+  bool stream_ordered = false;    // allocate with cudaMallocAsync on `stream`
+  uint32_t *h_in = nullptr;       // borrowed pinned staging (NULL: allocate)
+  uint32_t *h_out = nullptr;
+  int64_t h_in_words = 0, h_out_words = 0;
+  bool use_graph = true;
+  bool persistent = true;
+};
+
+struct rs_batch {
+  rs_ctx *ctx = nullptr;
+  int n = 0;
+  RsBatchOpts opt;
+  cudaStream_t stream = nullptr;
+  std::vector<PairPlan> plans;
+  std::vector<int> dev_index;  // pair -> device pair index, -1 if none
+  std::vector<PairDesc> descs;
+  std::vector<int64_t> in_f, in_g;  // word offsets of each pair's inputs in the staging buffer
+  std::vector<RsClassLaunch> classes;
+  int64_t in_words = 0, img_words = 0, out_words = 0;
+  int ng2 = 0, ng3 = 0, g2_threads = 256;
+  size_t g2smem = 0;
+  void *arena = nullptr;  // one device allocation carved into the buffers below
+  uint32_t *d_in = nullptr;
+  int2 *d_meta = nullptr;
+  PairDesc *d_pairs = nullptr;
+  Tile *d_tiles = nullptr;
+  int32_t *d_counters = nullptr;
+  uint32_t *d_num = nullptr, *d_den = nullptr, *d_xl = nullptr, *d_out = nullptr;
+  int2 *d_g2 = nullptr, *d_g3 = nullptr;
+  unsigned long long *d_stats = nullptr;
+  uint32_t *h_in = nullptr, *h_out = nullptr;
+  bool own_host = false;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool ran = false;
+  rs_batch_info info;
+};
+
+int rs_fail(rs_ctx *c, int code, const std::string &msg);
+int rs_cuda_code(cudaError_t e);
+int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
+                std::vector<PairPlan> &plans, int32_t *status, int *first_err);
+bool rs_same_shape(const PairPlan &a, const PairPlan &b);
+int64_t rs_input_words(const rs_bipoly &p);
+int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx);
+int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
+                   std::vector<PairPlan> &&plans, const RsBatchOpts &opt, rs_batch **out);
+// Byte sizes a batch of these plans needs (device arena, host staging in/out).
+void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, const rs_bipoly *g,
+                    int64_t *in_words, int64_t *out_words, int64_t *device_bytes);
+int rs_upload(rs_batch *b, const rs_bipoly *f, const rs_bipoly *g);
+int rs_run(rs_batch *b);
+int rs_fetch_async(rs_batch *b);                                // enqueue the result copy
+int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status);     // after the copy completed
+// Unpack pair i into a freshly sized host vector (deg, limbs); returns status.
+int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, int *limbs);
+void rs_free_batch(rs_batch *b);
+void rs_server_shutdown(rs_ctx *ctx);  // server.cu

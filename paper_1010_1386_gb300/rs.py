@@ -50,6 +50,12 @@ class rs_batch_info(ctypes.Structure):
                 ("kernel_launches", c_int64)]
 
 
+class rs_server_stats(ctypes.Structure):
+    _fields_ = [(n, c_int64) for n in ("submitted", "completed", "failed", "pending", "running",
+                                        "inflight_batches", "batches", "peak_inflight_batches",
+                                        "peak_running", "mem_used", "mem_limit")]
+
+
 _P = POINTER
 _SIGS = {
     "rs_config_default": (c_int32, [_P(rs_config)]),
@@ -73,6 +79,12 @@ _SIGS = {
     "rs_images": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, c_int32,
                             _P(c_uint32), _P(c_uint32), _P(c_uint32)]),
     "rs_crt_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p]),
+    "rs_server_start": (c_int32, [c_void_p, c_int32, c_int32, c_int64]),
+    "rs_server_submit": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), _P(ctypes.c_uint64)]),
+    "rs_server_poll": (c_int32, [c_void_p, ctypes.c_uint64, _P(rs_upoly), _P(c_double)]),
+    "rs_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, _P(rs_upoly), _P(c_double), c_int64]),
+    "rs_server_stats_get": (c_int32, [c_void_p, _P(rs_server_stats)]),
+    "rs_server_stop": (c_int32, [c_void_p]),
 }
 
 _lib = None
@@ -269,3 +281,49 @@ class Batch:
         if self.h and self.ctx.h:
             self.lib.rs_batch_destroy(self.h)
         self.h = None
+
+
+class Server:
+    """Continuous-batching request server of a context (rs_server_*)."""
+
+    def __init__(self, ctx, max_inflight=0, max_batch=0, mem_limit_bytes=0):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.outs = {}
+        _check(self.lib.rs_server_start(ctx.h, max_inflight, max_batch, mem_limit_bytes), ctx.h)
+
+    def submit(self, f, g):
+        P = _Polys([f, g])
+        t = ctypes.c_uint64()
+        _check(self.lib.rs_server_submit(self.ctx.h, ctypes.byref(P.structs[0]),
+                                         ctypes.byref(P.structs[1]), ctypes.byref(t)), self.ctx.h)
+        self.outs[t.value] = _Outputs([(f, g)])
+        return t.value
+
+    def _finish(self, rc, ticket, lat):
+        if rc == RS_PENDING:
+            return None
+        out = self.outs.pop(ticket)
+        _check(rc, self.ctx.h)
+        return out.ints()[0], lat.value
+
+    def poll(self, ticket):
+        """None while running, else (coefficients, latency_ms)."""
+        lat = c_double()
+        rc = self.lib.rs_server_poll(self.ctx.h, ticket, self.outs[ticket].structs, ctypes.byref(lat))
+        return self._finish(rc, ticket, lat)
+
+    def wait(self, ticket, timeout_us=-1):
+        lat = c_double()
+        rc = self.lib.rs_server_wait(self.ctx.h, ticket, self.outs[ticket].structs, ctypes.byref(lat),
+                                     timeout_us)
+        if rc == -5:
+            return None
+        return self._finish(rc, ticket, lat)
+
+    def stats(self):
+        st = rs_server_stats()
+        _check(self.lib.rs_server_stats_get(self.ctx.h, ctypes.byref(st)), self.ctx.h)
+        return {k: getattr(st, k) for k, _ in rs_server_stats._fields_}
+
+    def stop(self):
+        _check(self.lib.rs_server_stop(self.ctx.h), self.ctx.h)
