@@ -1,17 +1,20 @@
 """Benchmark: exact bivariate resultants per second on one GB300 (or N, one
 process per GPU, independent batches: weak scaling).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batch|single]
-                    [--impl ours|reference] [--no-baseline]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch|small|single|nongeneric|nongeneric-coprime|serving]
+                    [--no-baseline] [--no-per-instance]
 
 Prints ONE JSON line.  A step is one pass of the whole path (G1 reduce +
 evaluate + univariate resultants, G2 interpolation, G3 CRT) over one batch of
-synthetic input (default: 512 pairs, per-pair deg_x, deg_y ~ U[8, 40],
-bidegree-dense, coefficient bits in {16, 32, 64}).  ``value`` is the batched
-throughput with inputs resident on the device; ``per_instance`` times the same
-kernels launched one pair at a time (no persistence, no graphs); ``e2e`` goes
-through the C ABI with host buffers (upload, run, result copy-back);
-``cpu_baseline`` times the CPU oracle on a bounded sample.
+synthetic input; the default workload is 512 pairs with per-pair deg_x,
+deg_y ~ U[8, 40], bidegree-dense, coefficient bits in {16, 32, 64}.
+``value`` is the batched throughput with inputs resident on the device;
+``per_instance`` times the same kernels launched one pair at a time (no
+persistence, no graphs); ``e2e`` goes through the C ABI with host buffers
+(upload, run, result copy-back); ``cpu_baseline`` times the CPU oracle on a
+bounded sample.  ``--workload serving`` runs a Poisson stream of 10,000
+requests through the continuous-batching server and reports p50/p99 latency.
 """
 import argparse
 import hashlib
@@ -34,15 +37,32 @@ IMAD_PER_SM_CLK = 64  # 32-bit integer multiply-add results per clock per SM
 WORKLOADS = {
     "batch": "batched: 512 pairs in one run, per-pair deg_x, deg_y ~ U[8,40] shared by f and g, "
              "bidegree-dense, coefficient bits per pair in {16,32,64}, seed 2",
+    "small": "single pair, dense total degree 6, coefficients uniform in [-2^10, 2^10], seed 0",
     "single": "single pair, dense total degree 30, signed 32-bit coefficients, seed 1",
+    "nongeneric": "batch of 32: f = p q^2 (p, q dense total degrees 24 and 12, 64-bit coefficients), "
+                  "g = df/dy (common factor q: Res_y = 0), seed 3",
+    "nongeneric-coprime": "batch of 32: f = p q^2 as above, g = d(pq)/dy (coprime, Res_y with repeated "
+                          "factors), seed 3",
+    "serving": "Poisson stream of 10,000 requests, total degrees of f and g ~ U[8,64], coefficient bits "
+               "~ U[16,128], total-degree-dense, seed 4",
 }
 
 
-def load_pairs(workload, npairs=512):
+def load_pairs(workload, npairs=None):
     from paper_1010_1386_gb300 import inputs
     if workload == "batch":
-        return inputs.workload_batch(2, n=512)[:npairs]
-    return inputs.workload_single(1)
+        pairs = inputs.workload_batch(2, n=512)
+    elif workload == "small":
+        pairs = inputs.workload_small(0)
+    elif workload == "single":
+        pairs = inputs.workload_single(1)
+    elif workload == "nongeneric":
+        pairs = inputs.workload_nongeneric(3, n=32)
+    elif workload == "nongeneric-coprime":
+        pairs = inputs.workload_nongeneric(3, n=32, coprime=True)
+    else:
+        pairs = inputs.workload_serving(4, n=10000)[0]
+    return pairs[:npairs] if npairs else pairs
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -62,8 +82,8 @@ def oracle_sample(workload, npairs, seed, cores):
     (interpolation not counted).  Returns (resultants/s over ``cores``
     processes, description)."""
     import random
-    from paper_1010_1386_gb300 import inputs, rs
-    pairs = load_pairs(workload)
+    from paper_1010_1386_gb300 import rs
+    pairs = load_pairs(workload, 512 if workload == "serving" else None)
     idx = random.Random(seed).sample(range(len(pairs)), min(npairs, len(pairs)))
     jobs, points = [], []
     for i in idx:
@@ -140,8 +160,8 @@ class ClockSampler:
 # -------------------------------------------------------------- profiles
 
 def g1_traffic():
-    """DRAM bytes per G1 stage from the committed ncu summary, if it was taken
-    on the current G1 source; else None."""
+    """DRAM bytes per G1 stage of the default workload from the committed ncu
+    summary, if it was taken on the current G1 source; else None."""
     path = os.path.join(ROOT, "profiles", "g1_images_batch512.md")
     src = os.path.join(ROOT, "paper_1010_1386_gb300", "csrc", "kernels_g1.cu")
     try:
@@ -156,7 +176,7 @@ def g1_traffic():
     return float(m_tr.group(1))
 
 
-# -------------------------------------------------------------- main legs
+# -------------------------------------------------------------- helpers
 
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -169,30 +189,76 @@ def dist_setup(args):
     return world, rank, local, dist
 
 
+def barrier(dist, local):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(local)
+
+
+def max_over_ranks(dist, local, value):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], device=f"cuda:{local}")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def roofline(info, g1_ms, clk):
+    sm_max = clk["sm_max_mhz"] or 2070.0
+    peak = SM_COUNT * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
+    achieved = 4.0 * (info["modmul_eval"] + info["modmul_prs"]) / (g1_ms * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "G1 (reduce + evaluate + univariate resultant)",
+            "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
+            "traffic": None,
+            "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
+                           "(no integer peak in MEASURED_PEAKS.json)"}
+
+
+def base_line(args, world, value, ms, workload_desc, extra_cfg):
+    return {"metric": METRIC, "value": value, "unit": "resultants/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": dict({"workload": workload_desc,
+                            "parallelism": f"independent batches, {world} GPU(s)"}, **extra_cfg)}
+
+
+def add_cpu_baseline(line, args, rank):
+    if rank != 0 or args.no_baseline:
+        return
+    cores = min(os.cpu_count() or 1, 8)
+    n = 8 if args.workload in ("batch", "serving", "nongeneric", "nongeneric-coprime") else 1
+    v, desc = oracle_sample(args.workload, n, 7, cores)
+    line["cpu_baseline"] = {"value": v, "unit": "resultants/s", "cores": cores, "kind": "oracle",
+                            "sample": desc}
+
+
+# ------------------------------------------------------------------ legs
+
 def reference_main(args, world, rank, dist):
     if rank != 0:
         return
-    cores = os.cpu_count() or 1
+    cores = min(os.cpu_count() or 1, 2)
     vals, t0 = [], time.perf_counter()
+    desc = ""
     for s in range(args.warmup + args.steps):
-        v, desc = oracle_sample(args.workload, 2, 1000 + s, min(cores, 2))
+        v, desc = oracle_sample(args.workload, 2, 1000 + s, cores)
         if s >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
     wall = time.perf_counter() - t0
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "resultants/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * wall / (args.steps + args.warmup),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (Python big integers)",
-            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload]},
-            "cpu_baseline": {"value": value, "unit": "resultants/s", "cores": min(cores, 2),
-                             "kind": "oracle", "sample": desc},
-            "e2e": {"value": value, "unit": "resultants/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+    line = base_line(args, 1, value, 1000.0 * wall / (args.steps + args.warmup),
+                     WORKLOADS[args.workload], {})
+    line.update({"impl": "reference", "dtype": "int (Python big integers)",
+                 "cpu_baseline": {"value": value, "unit": "resultants/s", "cores": cores,
+                                  "kind": "oracle", "sample": desc},
+                 "e2e": {"value": value, "unit": "resultants/s", "h2d_bytes_per_step": 0,
+                         "d2h_bytes_per_step": 0}})
     print(json.dumps(line), flush=True)
 
 
-def ours_main(args, world, rank, local, dist):
+def batch_main(args, world, rank, local, dist):
     import torch
     from paper_1010_1386_gb300 import rs
 
@@ -203,24 +269,17 @@ def ours_main(args, world, rank, local, dist):
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     batch = ctx.batch(pairs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(local)
-
     for _ in range(args.warmup):
         batch.run()
         batch.sync()
     info = batch.info()
 
-    # ---- timed region: batched, device-resident inputs
+    # timed region: device-resident inputs
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    g1_ms, stage = [], {"images": [], "interp": [], "crt": []}
-    barrier()
+    stage = {"images": [], "interp": [], "crt": []}
+    barrier(dist, local)
     with ClockSampler(local) as clocks:
-        t_wall = time.perf_counter()
         for s in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -233,19 +292,12 @@ def ours_main(args, world, rank, local, dist):
             stage["images"].append(i["ms_images"])
             stage["interp"].append(i["ms_interp"])
             stage["crt"].append(i["ms_crt"])
-        barrier()
-        t_wall = time.perf_counter() - t_wall
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        barrier(dist, local)
+    ms = max_over_ranks(dist, local, statistics.mean(a.elapsed_time(b) for a, b in ev))
     value = world * npairs / (ms * 1e-3)
 
-    # ---- per-instance form: same kernels, one pair per launch sequence
     per_inst = None
-    if args.workload == "batch" and not args.no_per_instance:
+    if npairs > 1 and not args.no_per_instance:
         ctx1 = rs.Context(device=local, use_graphs=False, persistent=False)
         singles = [ctx1.batch([p]) for p in pairs]
         for b in singles:
@@ -272,65 +324,121 @@ def ours_main(args, world, rank, local, dist):
             b.close()
         ctx1.close()
 
-    # ---- end to end through the C ABI with host buffers
     e2e_ms = []
-    for s in range(max(1, min(args.steps, 3))):
-        barrier()
+    for _ in range(max(1, min(args.steps, 3))):
+        barrier(dist, local)
         t = time.perf_counter()
         batch.upload(pairs)
         batch.run()
         batch.results(raw=True)
         e2e_ms.append(1e3 * (time.perf_counter() - t))
-    e2e_val = world * npairs / (statistics.mean(e2e_ms) * 1e-3)
+    e2e_val = world * npairs / (max_over_ranks(dist, local, statistics.mean(e2e_ms)) * 1e-3)
 
-    g1 = statistics.mean(stage["images"])
-    algo_imad = 4.0 * (info["modmul_eval"] + info["modmul_prs"])
     clk = clocks.summary()
-    sm_max = clk["sm_max_mhz"] or 2070.0
-    peak = SM_COUNT * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
-    achieved = algo_imad / (g1 * 1e-3) / 1e12
-    traffic = g1_traffic()
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "resultants/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload] + ("" if npairs == 512 or args.workload != "batch"
-                                                           else f" (first {npairs} pairs)"),
-                   "pairs_per_gpu": npairs,
-                   "images_per_step": info["images"],
-                   "l2": "256 MiB written before every timed step (outside its events); "
-                         "per-step working set (num/den images) %.0f MB" % (info["images"] * 8 / 1e6),
-                   "parallelism": f"independent batches, {world} GPU(s)"},
+    g1 = statistics.mean(stage["images"])
+    rf = roofline(info, g1, clk)
+    if args.workload == "batch" and npairs == 512:
+        rf["traffic"] = g1_traffic()
+    desc = WORKLOADS[args.workload] + ("" if args.pairs is None else f" (first {npairs} pairs)")
+    line = base_line(args, world, value, ms, desc,
+                     {"pairs_per_gpu": npairs, "images_per_step": info["images"],
+                      "l2": "256 MiB written before every timed step (outside its events); per-step "
+                            "working set (num/den images) %.0f MB" % (info["images"] * 8 / 1e6)})
+    line.update({
         "images_per_s": world * info["images"] / (ms * 1e-3),
         "stage_ms": {k: statistics.mean(v) for k, v in stage.items()},
         "per_instance": per_inst,
         "batched_over_per_instance": (value / world / per_inst["value"]) if per_inst else None,
-        "imad_frac_g1": achieved / peak,
-        "roofline": {"bound": "alu", "kernel": "G1 (reduce + evaluate + univariate resultant)",
-                     "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
-                     "traffic": traffic,
-                     "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x "
-                                    f"{sm_max:.0f} MHz (no integer peak in MEASURED_PEAKS.json)"},
+        "imad_frac_g1": rf["frac"],
+        "roofline": rf,
+        "gpu_launches": args.steps * info["kernel_launches"],
         "clocks": clk,
-        "e2e": {"value": e2e_val, "unit": "resultants/s",
-                "h2d_bytes_per_step": info["input_bytes"], "d2h_bytes_per_step": info["output_bytes"]},
+        "e2e": {"value": e2e_val, "unit": "resultants/s", "h2d_bytes_per_step": info["input_bytes"],
+                "d2h_bytes_per_step": info["output_bytes"]},
         "detections": {"unlucky_points": info["unlucky_points"],
                        "degenerate_images": info["degenerate_images"],
                        "unlucky_primes": info["unlucky_primes"]},
-    }
-    line["gpu_launches"] = args.steps * info["kernel_launches"]
-    if rank == 0 and not args.no_baseline:
-        cores = os.cpu_count() or 1
-        v, desc = oracle_sample(args.workload, 8 if args.workload == "batch" else 2, 7,
-                                min(cores, 8))
-        line["cpu_baseline"] = {"value": v, "unit": "resultants/s", "cores": min(cores, 8),
-                                "kind": "oracle", "sample": desc}
+    })
+    add_cpu_baseline(line, args, rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
     ctx.close()
+
+
+def serving_main(args, world, rank, local, dist):
+    """Closed-loop saturation pass, then a Poisson stream at --load x that
+    throughput through the continuous-batching server."""
+    import numpy as np
+    import torch
+    from paper_1010_1386_gb300 import inputs, rs
+
+    torch.cuda.set_device(local)
+    n = args.pairs or 10000
+    pairs, gaps = inputs.workload_serving(4, n=n)
+    ctx = rs.Context(device=local)
+    srv = rs.Server(ctx, max_inflight=args.inflight, max_batch=args.max_batch)
+    for f, g in pairs[: min(n, 256)]:  # warm-up: tables, streams, pinned staging
+        srv.wait(srv.submit(f, g))
+
+    def run_stream(times):
+        """Submit pair i at times[i] (seconds from start; None = at once)."""
+        tickets = [None] * n
+
+        def producer():
+            t0 = time.perf_counter()
+            for i, (f, g) in enumerate(pairs):
+                if times is not None:
+                    dt = times[i] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                tickets[i] = srv.submit(f, g)
+        t_start = time.perf_counter()
+        th = threading.Thread(target=producer)
+        th.start()
+        lat = []
+        for i in range(n):
+            while tickets[i] is None:
+                time.sleep(0.0001)
+            _, ms = srv.wait(tickets[i])
+            lat.append(ms)
+        th.join()
+        return time.perf_counter() - t_start, lat
+
+    barrier(dist, local)
+    with ClockSampler(local) as clocks:
+        sat_s, sat_lat = run_stream(None)
+        sat = n / sat_s
+        rate = args.load * sat
+        arrivals = np.cumsum(gaps) / rate
+        wall, lat = run_stream(arrivals)
+        barrier(dist, local)
+    st = srv.stats()
+    srv.stop()
+    ctx.close()
+    wall = max_over_ranks(dist, local, wall)
+    value = world * n / wall
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
+    line = base_line(args, world, value, 1e3 * wall, WORKLOADS["serving"],
+                     {"requests": n, "arrival_rate_per_s": rate, "load_vs_saturation": args.load,
+                      "max_inflight_batches": args.inflight, "max_batch": args.max_batch})
+    line.update({
+        "steps": 1,
+        "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat)},
+        "saturation": {"value": sat, "unit": "resultants/s", "p50_ms": sorted(sat_lat)[n // 2]},
+        "server": {k: st[k] for k in ("batches", "peak_inflight_batches", "peak_running", "failed")},
+        "gpu_launches": st["kernel_launches"],
+        "clocks": clocks.summary(),
+        "e2e": {"value": value, "unit": "resultants/s",
+                "h2d_bytes_per_step": int(sum(f.coeffs.nbytes + g.coeffs.nbytes for f, g in pairs)),
+                "d2h_bytes_per_step": None,
+                "note": "every request crosses the C ABI with host buffers; latency is submit to result"},
+    })
+    add_cpu_baseline(line, args, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():
@@ -342,14 +450,19 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
-    ap.add_argument("--pairs", type=int, default=512,
-                    help="profiling only: time the first PAIRS pairs of the batch")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="time only the first PAIRS pairs / requests (profiling)")
+    ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / saturation")
+    ap.add_argument("--inflight", type=int, default=4, help="serving: concurrent micro-batches")
+    ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per micro-batch")
     args = ap.parse_args()
     world, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
         reference_main(args, world, rank, dist)
+    elif args.workload == "serving":
+        serving_main(args, world, rank, local, dist)
     else:
-        ours_main(args, world, rank, local, dist)
+        batch_main(args, world, rank, local, dist)
     if dist is not None:
         dist.destroy_process_group()
 

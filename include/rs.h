@@ -207,6 +207,7 @@ typedef struct {
   int64_t peak_inflight_batches;   /* most micro-batches on the GPU at once */
   int64_t peak_running;            /* most requests on the GPU at once */
   int64_t mem_used, mem_limit;     /* admitted device bytes / budget */
+  int64_t kernel_launches;         /* kernels of the library launched so far */
 } rs_server_stats;
 
 /* Start the server (optional: the first submit starts it with defaults).

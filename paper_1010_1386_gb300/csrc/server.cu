@@ -197,6 +197,7 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
   fl.slot = slot;
   s->flights.push_back(fl);
   s->st.batches++;
+  s->st.kernel_launches += b->info.kernel_launches;
   s->st.running = 0;
   for (auto &f2 : s->flights) s->st.running += (int64_t)f2.reqs.size();
   if ((int64_t)s->flights.size() > s->st.peak_inflight_batches) s->st.peak_inflight_batches = (int64_t)s->flights.size();

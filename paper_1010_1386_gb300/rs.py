@@ -53,7 +53,8 @@ class rs_batch_info(ctypes.Structure):
 class rs_server_stats(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("submitted", "completed", "failed", "pending", "running",
                                         "inflight_batches", "batches", "peak_inflight_batches",
-                                        "peak_running", "mem_used", "mem_limit")]
+                                        "peak_running", "mem_used", "mem_limit",
+                                        "kernel_launches")]
 
 
 _P = POINTER
