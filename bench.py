@@ -48,18 +48,21 @@ WORKLOADS = {
 }
 
 
-def load_pairs(workload, npairs=None):
+def load_pairs(workload, npairs=None, rank=0):
+    """The workload's pairs; under weak scaling rank r > 0 draws its own
+    batch of the same distribution (seed + 1000 r)."""
     from paper_1010_1386_gb300 import inputs
+    from paper_1010_1386_gb300.sharding import rank_seed
     if workload == "batch":
-        pairs = inputs.workload_batch(2, n=512)
+        pairs = inputs.workload_batch(rank_seed(2, rank), n=512)
     elif workload == "small":
         pairs = inputs.workload_small(0)
     elif workload == "single":
         pairs = inputs.workload_single(1)
     elif workload == "nongeneric":
-        pairs = inputs.workload_nongeneric(3, n=32)
+        pairs = inputs.workload_nongeneric(rank_seed(3, rank), n=32)
     elif workload == "nongeneric-coprime":
-        pairs = inputs.workload_nongeneric(3, n=32, coprime=True)
+        pairs = inputs.workload_nongeneric(rank_seed(3, rank), n=32, coprime=True)
     else:
         pairs = inputs.workload_serving(4, n=10000)[0]
     return pairs[:npairs] if npairs else pairs
@@ -197,12 +200,8 @@ def barrier(dist, local):
 
 
 def max_over_ranks(dist, local, value):
-    if dist is None:
-        return value
-    import torch
-    t = torch.tensor([value], device=f"cuda:{local}")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1010_1386_gb300.sharding import max_over_ranks as mor
+    return mor(value, dist, device=f"cuda:{local}")
 
 
 def roofline(info, g1_ms, clk):
@@ -221,7 +220,8 @@ def base_line(args, world, value, ms, workload_desc, extra_cfg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": dict({"workload": workload_desc,
-                            "parallelism": f"independent batches, {world} GPU(s)"}, **extra_cfg)}
+                            "parallelism": f"independent batches, {world} GPU(s); rank r > 0 "
+                                           "draws its own batch (seed + 1000 r)"}, **extra_cfg)}
 
 
 def add_cpu_baseline(line, args, rank):
@@ -263,7 +263,7 @@ def batch_main(args, world, rank, local, dist):
     from paper_1010_1386_gb300 import rs
 
     torch.cuda.set_device(local)
-    pairs = load_pairs(args.workload, args.pairs)
+    pairs = load_pairs(args.workload, args.pairs, rank)
     npairs = len(pairs)
     ctx = rs.Context(device=local, timing=True)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
