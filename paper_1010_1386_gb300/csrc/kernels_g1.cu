@@ -42,7 +42,7 @@
 #define RS_G1_MINB RS_G1_MINB_SET  // tuning override for one capacity
 #endif
 #ifndef RS_G1_MINB
-#define RS_G1_MINB (RS_G1_CAP <= 16 ? 6 : RS_G1_CAP <= 24 ? 5 : RS_G1_CAP <= 32 ? 4 : 3)
+#define RS_G1_MINB (RS_G1_CAP <= 16 ? 6 : RS_G1_CAP <= 24 ? 5 : RS_G1_CAP <= 40 ? 4 : 3)
 #endif
 
 namespace {
@@ -82,10 +82,39 @@ __device__ __forceinline__ void drop_top(uint32_t (&P)[C]) {
   P[C - 1] = 0u;
 }
 
+// One normal step on A (a >= b, l_B != 0) or on B (a < b, l_A != 0).
+template <int C>
+__device__ __forceinline__ void step_a(uint32_t (&A)[C], const uint32_t (&B)[C], Prs &s, const ModP &m) {
+  const uint32_t lb = B[0], la = A[0];
+  settle(s, s.b - 1, lb, m);
+  reduce_into<C>(A, B, lb, mneg(la, m.p), m);
+  s.sign ^= (uint32_t)(s.b & 1);
+  --s.a;
+}
+
+template <int C>
+__device__ __forceinline__ void step_b(const uint32_t (&A)[C], uint32_t (&B)[C], Prs &s, const ModP &m) {
+  const uint32_t la = A[0], lb = B[0];
+  settle(s, s.a - 1, la, m);
+  reduce_into<C>(B, A, la, mneg(lb, m.p), m);
+  --s.b;
+}
+
 template <int C>
 __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs &s, const ModP &m) {
   // invariant: a, b <= C - 1
   constexpr int S = RS_G1_PSTEP;
+  // Fast path for the normal sequence, with a fixed role for each array in
+  // every loop (no data-dependent choice of which array to update): first
+  // reduce the larger degree down to the smaller, then alternate A, B.
+  while (s.a > s.b && s.b > 0 && B[0] != 0u && (C <= S || s.a > C - S - 1)) step_a<C>(A, B, s, m);
+  while (s.b > s.a && s.a > 0 && A[0] != 0u && (C <= S || s.b > C - S - 1)) step_b<C>(A, B, s, m);
+  while (s.a == s.b && s.a > 1 && B[0] != 0u && (C <= S || s.a > C - S - 1)) {
+    step_a<C>(A, B, s, m);  // (a, a) -> (a - 1, a)
+    if (A[0] == 0u) break;
+    step_b<C>(A, B, s, m);  // (a - 1, a) -> (a - 1, a - 1)
+  }
+  // General steps: zero pivots, the last steps, and the phase boundary.
   while (s.a > 0 && s.b > 0 && (C <= S || s.a > C - S - 1 || s.b > C - S - 1)) {
     if (s.a >= s.b) {
       const uint32_t lb = B[0];
@@ -155,9 +184,7 @@ __device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
 // r, zero past the degree) and the window w[t] = q^{C(x0+t,2)} are signed
 // representatives (|v| < 2^30): 7 products accumulate exactly in an int64,
 // then one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53.
-__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) {
-  return (s >> 32) * (int64_t)c32 + (int64_t)(uint32_t)s;
-}
+__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) { return rs_fold64(s, c32); }
 
 __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
   return redc((uint64_t)(s + ((int64_t)m.p << 22)), m.p, m.pinv);  // 0 <= . < 2^54 < p 2^32
@@ -185,14 +212,14 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
         const int32_t c = win[k];
         const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
         const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
-        acc[0] += (int64_t)lo.x * c;
-        acc[1] += (int64_t)lo.y * c;
-        acc[2] += (int64_t)lo.z * c;
-        acc[3] += (int64_t)lo.w * c;
-        acc[4] += (int64_t)hi.x * c;
-        acc[5] += (int64_t)hi.y * c;
-        acc[6] += (int64_t)hi.z * c;
-        acc[7] += (int64_t)hi.w * c;
+        acc[0] = rs_mac_s32(acc[0], lo.x, c);
+        acc[1] = rs_mac_s32(acc[1], lo.y, c);
+        acc[2] = rs_mac_s32(acc[2], lo.z, c);
+        acc[3] = rs_mac_s32(acc[3], lo.w, c);
+        acc[4] = rs_mac_s32(acc[4], hi.x, c);
+        acc[5] = rs_mac_s32(acc[5], hi.y, c);
+        acc[6] = rs_mac_s32(acc[6], hi.z, c);
+        acc[7] = rs_mac_s32(acc[7], hi.w, c);
       }
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) acc[rr] = fold64(acc[rr], c32);

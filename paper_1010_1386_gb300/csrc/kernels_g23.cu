@@ -96,9 +96,7 @@ __device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
 }
 
-__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) {
-  return (s >> 32) * (int64_t)c32 + (int64_t)(uint32_t)s;
-}
+__device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) { return rs_fold64(s, c32); }
 
 // Reduce a folded accumulator (|s| < 2^53) to [0, p) in Montgomery form.
 __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
@@ -128,7 +126,7 @@ __device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n
 #pragma unroll
       for (int r = 0; r < R; ++r) {
 #pragma unroll
-        for (int jj = 0; jj < R; ++jj) acc[r] += (int64_t)av[jj] * bw[(R - 1) + r - jj];
+        for (int jj = 0; jj < R; ++jj) acc[r] = rs_mac_s32(acc[r], av[jj], bw[(R - 1) + r - jj]);
         acc[r] = fold64(acc[r], c32);
       }
     }

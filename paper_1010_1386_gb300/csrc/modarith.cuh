@@ -91,3 +91,24 @@ RS_HD ModP make_modp(uint32_t p) {
   m.r2 = (uint32_t)((r1 * r1) % p);
   return m;
 }
+
+#if defined(__CUDACC__)
+// acc + a b for signed 32-bit a, b: one wide multiply-add.
+__device__ __forceinline__ int64_t rs_mac_s32(int64_t acc, int32_t a, int32_t b) {
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+  return acc;
+}
+
+// hi 2^32 + lo -> hi c + lo for s = hi 2^32 + lo (c = 2^32 mod p, |c| < 2^31):
+// congruent mod p, and |result| < 2^31 |c| + 2^32.
+__device__ __forceinline__ int64_t rs_fold64(int64_t s, uint32_t c) {
+  int64_t r;
+  asm("{\n\t.reg .b32 lo, hi;\n\t.reg .s64 l64;\n\t"
+      "mov.b64 {lo, hi}, %1;\n\t"
+      "cvt.u64.u32 l64, lo;\n\t"
+      "mad.wide.s32 %0, hi, %2, l64;\n\t}"
+      : "=l"(r)
+      : "l"(s), "r"(c));
+  return r;
+}
+#endif
