@@ -93,11 +93,15 @@ int64_t rs_input_words(const rs_bipoly &p) { return (int64_t)(p.deg_x + 1) * (p.
 // ------------------------------------------------------------------ tables
 
 static void free_tables(RsTables &t) {
-  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc};
+  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc, t.wtab, t.p16, t.poff, t.nh, t.plimbs};
   for (void *x : p)
     if (x) cudaFree(x);
   t = RsTables();
 }
+
+// Reserved 16-bit digits of row k of the prefix-product table: p_0 ... p_{k-1}
+// < 2^(31 k), rounded up to a multiple of 32.
+static int p16_row(int k) { return ((31 * k) / 16 + 2 + 31) / 32 * 32; }
 
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   std::lock_guard<std::mutex> lock(ctx->tab_mu);
@@ -118,6 +122,18 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   if (e == cudaSuccess)
     e = launch_tables(ctx->d_mods, ctx->d_qbase, nt.K, nt.N, nt.cstride, nt.finv, nt.gtab, nt.btab,
                       nt.qc, nt.qn, ctx->stream);
+  // Chinese-remaindering tables for the same primes.
+  std::vector<int32_t> poff(nt.K + 1, 0);
+  for (int k = 0; k < nt.K; ++k) poff[k + 1] = poff[k] + p16_row(k);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.wtab, std::max<size_t>(1, (size_t)nt.K * (nt.K - 1) / 2) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.p16, (size_t)poff[nt.K] * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.poff, (size_t)(nt.K + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.nh, (size_t)nt.K * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.plimbs, (size_t)(nt.K + 4) * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(nt.poff, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_crt_tables(ctx->d_mods, nt.K, nt.poff, nt.wtab, nt.p16, nt.nh, nt.plimbs, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     free_tables(nt);
@@ -151,23 +167,29 @@ void rs_free_batch(rs_batch *b) {
 
 void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, const rs_bipoly *g,
                     int64_t *in_words, int64_t *out_words, int64_t *device_bytes) {
-  int64_t in = 0, out = 0, img = 0, meta = 0, tiles = 0, g2 = 0, g3 = 0;
+  int64_t in = 0, out = 0, img = 0, meta = 0, tiles = 0, g2 = 0, g3 = 0, xl = 0, cy = 0, g3d = 0, g3b = 0;
   for (size_t i = 0; i < plans.size(); ++i) {
     in += rs_input_words(f[i]) + rs_input_words(g[i]);
     const PairPlan &p = plans[i];
     if (p.status != RS_OK || p.trivial_zero) continue;
+    const int64_t chunks = (p.Lout + 15) / 16;
     out += (int64_t)p.N * p.Lout;
+    xl += (int64_t)p.N * 16 * chunks;
+    cy += (int64_t)p.N * chunks;
     img += (int64_t)p.K * p.N;
     meta += p.f.my + p.g.my + 2;
     tiles += (int64_t)p.K * ((p.N + 31) / 32);
     g2 += p.K;
     g3 += (p.N + 127) / 128;
+    g3d += 2 * ((p.N + 1) / 2);  // bound for either digit mapping
+    g3b += (p.N + 127) / 128 * chunks;
   }
   *in_words = in;
   *out_words = out;
   *device_bytes = (int64_t)(align_up(in * 4) + align_up(meta * 8) + align_up(plans.size() * sizeof(PairDesc)) +
                             align_up(tiles * sizeof(Tile)) + kAlign + 2 * align_up(img * 4) +
-                            2 * align_up(out * 4) + align_up(g2 * 8) + align_up(g3 * 8) + kAlign);
+                            align_up(xl * 4) + align_up(out * 4) + align_up(cy * 8) + align_up(g2 * 8) +
+                            align_up(g3 * 8) + align_up(g3d * 8) + align_up(g3b * 16) + kAlign);
 }
 
 int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
@@ -227,6 +249,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     b->img_words += (int64_t)p.K * p.N;
     d.out_off = b->out_words;
     b->out_words += (int64_t)p.N * p.Lout;
+    const int64_t chunks = (p.Lout + 15) / 16;
+    d.xl_off = b->xl_words;
+    b->xl_words += (int64_t)p.N * 16 * chunks;
+    d.cy_off = b->cy_words;
+    b->cy_words += (int64_t)p.N * chunks;
     b->dev_index[i] = (int)b->descs.size();
     b->descs.push_back(d);
     order.push_back(i);
@@ -274,16 +301,36 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     const PairPlan &p = b->plans[i];
     for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
   }
+  const int dthreads = g3_digit_threads(std::max(maxK, 1));
+  int64_t ncoef = 0;
+  for (int i : order) ncoef += b->plans[i].N;
+  // CRT digits: one thread per coefficient when the batch has enough
+  // coefficients to fill the GPU and the pair few primes; one warp per
+  // coefficient otherwise (long dot products, or too few coefficients).
+  std::vector<int2> g3d, g3w;
+  std::vector<int4> g3b;  // CRT limb chunks: 128 coefficients x one chunk per block
   for (int i : order) {
     const PairPlan &p = b->plans[i];
-    for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(b->dev_index[i], j));
+    const int di = b->dev_index[i], chunks = (p.Lout + 15) / 16;
+    for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(di, j));
+    if (ncoef >= 65536 && p.K < 128)
+      for (int j = 0; j < p.N; j += dthreads) g3d.push_back(make_int2(di, j));
+    else
+      for (int j = 0; j < p.N; j += 2) g3w.push_back(make_int2(di, j));
+    for (int c = 0; c < chunks; ++c)
+      for (int j = 0; j < p.N; j += 128) g3b.push_back(make_int4(di, j, c, 0));
   }
   b->ng2 = images_only ? 0 : (int)g2.size();
   b->ng3 = images_only ? 0 : (int)g3.size();
+  b->ng3d = images_only ? 0 : (int)g3d.size();
+  b->ng3w = images_only ? 0 : (int)g3w.size();
+  b->ng3b = images_only ? 0 : (int)g3b.size();
+  b->kmax = maxK;
   b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
-  b->info.kernel_launches = (int64_t)b->classes.size() + (b->ng2 > 0) + (b->ng3 > 0);
+  b->info.kernel_launches = (int64_t)b->classes.size() + (b->ng2 > 0) + (b->ng3d > 0) + (b->ng3w > 0) + (b->ng3b > 0) +
+                            (b->ng3 > 0);
 
   int rc = RS_OK;
   if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxN, maxDx);
@@ -301,8 +348,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   const size_t o_in = carve(b->in_words * 4), o_meta = carve(meta.size() * sizeof(int2)),
                o_pairs = carve(b->descs.size() * sizeof(PairDesc)), o_tiles = carve(tiles.size() * sizeof(Tile)),
                o_cnt = carve(16 * sizeof(int32_t)), o_num = carve(b->img_words * 4), o_den = carve(b->img_words * 4),
-               o_xl = carve(b->out_words * 4), o_out = carve(b->out_words * 4), o_g2 = carve(g2.size() * sizeof(int2)),
-               o_g3 = carve(g3.size() * sizeof(int2)), o_st = carve(ST_COUNT * sizeof(unsigned long long));
+               o_xl = carve(std::max(b->xl_words, b->out_words) * 4), o_out = carve(b->out_words * 4),
+               o_g2 = carve(g2.size() * sizeof(int2)), o_g3 = carve(g3.size() * sizeof(int2)),
+               o_st = carve(ST_COUNT * sizeof(unsigned long long)), o_cy = carve(b->cy_words * 8),
+               o_g3d = carve(g3d.size() * sizeof(int2)), o_g3w = carve(g3w.size() * sizeof(int2)),
+               o_g3b = carve(g3b.size() * sizeof(int4));
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
     b->arena = nullptr;
@@ -322,6 +372,10 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_g2 = (int2 *)(base + o_g2);
   b->d_g3 = (int2 *)(base + o_g3);
   b->d_stats = (unsigned long long *)(base + o_st);
+  b->d_cy = (int64_t *)(base + o_cy);
+  b->d_g3d = (int2 *)(base + o_g3d);
+  b->d_g3w = (int2 *)(base + o_g3w);
+  b->d_g3b = (int4 *)(base + o_g3b);
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
     b->h_in = opt.h_in;
@@ -347,6 +401,13 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   h2d(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile));
   h2d(b->d_g2, g2.data(), g2.size() * sizeof(int2));
   h2d(b->d_g3, g3.data(), g3.size() * sizeof(int2));
+  h2d(b->d_g3d, g3d.data(), g3d.size() * sizeof(int2));
+  h2d(b->d_g3w, g3w.data(), g3w.size() * sizeof(int2));
+  h2d(b->d_g3b, g3b.data(), g3b.size() * sizeof(int4));
+  if (rc == RS_OK && (b->ng3d || b->ng3w)) {
+    cudaError_t e2 = g3_prepare(b->kmax);
+    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
+  }
   if (rc == RS_OK) {  // the pageable sources above must outlive the copies
     cudaError_t e2 = cudaStreamSynchronize(b->stream);
     if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e2));
@@ -443,12 +504,20 @@ static int enqueue(rs_batch *b, bool capturing) {
     G3Args a3;
     a3.pairs = b->d_pairs;
     a3.tasks = b->d_g3;
+    a3.ctasks = b->d_g3b;
     a3.mods = ctx->d_mods;
     a3.crt = ctx->d_crt;
+    a3.wtab = tab.wtab;
+    a3.p16 = tab.p16;
+    a3.poff = tab.poff;
+    a3.nh = tab.nh;
     a3.coef = b->d_num;
     a3.xl = b->d_xl;
+    a3.carry = b->d_cy;
     a3.out = b->d_out;
-    RS_CUDA(ctx, launch_g3(128, b->ng3, a3, s));
+    a3.kmax = b->kmax;
+    RS_CUDA(ctx, launch_g3(b->ng3d, g3_digit_threads(std::max(b->kmax, 1)), b->ng3w, b->ng3b, b->ng3, a3,
+                           b->d_g3d, b->d_g3w, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));
   return RS_OK;

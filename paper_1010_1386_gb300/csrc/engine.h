@@ -21,6 +21,12 @@ struct RsTables {
   int cstride = 0;  // chirp stride (point + x-degree + tile window covered)
   uint32_t *finv = nullptr, *gtab = nullptr, *qn = nullptr;
   int32_t *btab = nullptr, *qc = nullptr;
+  // Chinese-remaindering tables for the first K primes.
+  int32_t *wtab = nullptr;   // triangular p_0 ... p_{l-1} mod p_k
+  uint16_t *p16 = nullptr;   // prefix products in 16-bit digits
+  int32_t *poff = nullptr;   // K + 1 row offsets into p16
+  int32_t *nh = nullptr;     // digits per prefix product
+  uint32_t *plimbs = nullptr;  // scratch of the table kernel
 };
 
 struct rs_ctx {
@@ -76,6 +82,11 @@ struct rs_batch {
   std::vector<RsClassLaunch> classes;
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int ng2 = 0, ng3 = 0, g2_threads = 256;
+  int ng3d = 0, ng3w = 0, ng3b = 0, kmax = 0;  // CRT digit blocks (per thread / per warp), chunks, largest K
+  int64_t xl_words = 0, cy_words = 0;
+  int2 *d_g3d = nullptr, *d_g3w = nullptr;
+  int4 *d_g3b = nullptr;
+  int64_t *d_cy = nullptr;
   size_t g2smem = 0;
   void *arena = nullptr;  // one device allocation carved into the buffers below
   uint32_t *d_in = nullptr;

@@ -1,7 +1,6 @@
-// G2 (interpolation mod p), G3 (Garner CRT) and the per-prime constant
-// tables.  Paper, Section 4.1: R^{(y)} is interpolated over Z_p from the
-// images z_i^{(p)} (a Vandermonde solve) and lifted to Z by Chinese
-// remaindering.
+// G2 (interpolation mod p) and the per-prime constant tables.  Paper,
+// Section 4.1: R^{(y)} is interpolated over Z_p from the images z_i^{(p)}
+// (a Vandermonde solve); the Chinese remaindering is in kernels_g3.cu.
 #include "../../include/rs.h"
 #include "rs_internal.cuh"
 
@@ -239,61 +238,6 @@ __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, in
   }
 }
 
-// One thread per output coefficient: Garner's mixed-radix digits in the
-// symmetric range, R_j = v_0 + p_0 (v_1 + p_1 (v_2 + ...)), then the limbs.
-__global__ void g3_kernel(G3Args a) {
-  const int2 task = a.tasks[blockIdx.x];
-  const PairDesc pd = a.pairs[task.x];
-  const int j = task.y + (int)threadIdx.x;
-  if (j >= pd.N) return;
-  const int K = pd.K, N = pd.N, L = pd.Lout;
-  uint32_t *col = a.coef + pd.img_off + j;  // residue / digit k at col[k N]
-
-  for (int k = 0; k < K; ++k) {
-    const ModP mk = a.mods[k];
-    uint32_t t = 0u;
-    if (k > 0) {
-      const int32_t vp = (int32_t)col[(size_t)(k - 1) * N];
-      t = vp < 0 ? (uint32_t)(vp + (int32_t)mk.p) : (uint32_t)vp;
-      for (int l = k - 2; l >= 0; --l) {
-        const uint32_t ym = to_mont(a.mods[l].p - mk.p, mk);  // p_l mod p_k (table is descending)
-        const int32_t vl = (int32_t)col[(size_t)l * N];
-        const uint32_t vr = vl < 0 ? (uint32_t)(vl + (int32_t)mk.p) : (uint32_t)vl;
-        t = madd(mmul(t, ym, mk), vr, mk.p);  // plain t times Montgomery y -> plain
-      }
-    }
-    const uint32_t rk = col[(size_t)k * N];
-    const uint32_t v = mmul(msub(rk, t, mk.p), a.crt[k], mk);  // plain digit in [0, p_k)
-    const int32_t vs = v > (mk.p - 1u) / 2u ? (int32_t)v - (int32_t)mk.p : (int32_t)v;
-    col[(size_t)k * N] = (uint32_t)vs;
-  }
-
-  uint32_t *xl = a.xl + pd.out_off + j;  // limb l at xl[l N]
-  int act = 1;
-  xl[0] = col[(size_t)(K - 1) * N];
-  for (int k = K - 2; k >= 0; --k) {
-    int need = (31 * (K - k) + 1 + 31) / 32 + 1;
-    if (need > L) need = L;
-    if (need > act) {
-      const uint32_t ext = (xl[(size_t)(act - 1) * N] >> 31) ? 0xffffffffu : 0u;
-      for (int l = act; l < need; ++l) xl[(size_t)l * N] = ext;
-      act = need;
-    }
-    const uint64_t p = a.mods[k].p;
-    const int32_t vk = (int32_t)col[(size_t)k * N];
-    const uint64_t ext = vk < 0 ? 0xffffffffull : 0ull;
-    uint64_t c = (uint32_t)vk;
-    for (int l = 0; l < act; ++l) {
-      const uint64_t t = (uint64_t)xl[(size_t)l * N] * p + c + (l ? ext : 0ull);
-      xl[(size_t)l * N] = (uint32_t)t;
-      c = t >> 32;
-    }
-  }
-  const uint32_t ext = (xl[(size_t)(act - 1) * N] >> 31) ? 0xffffffffu : 0u;
-  uint32_t *o = a.out + pd.out_off + (size_t)j * L;
-  for (int l = 0; l < L; ++l) o[l] = l < act ? xl[(size_t)l * N] : ext;
-}
-
 // Per prime: Montgomery constants, V[l] = 2^(32 l) R^2 mod p (limb weights
 // for the modular reduction of input coefficients) and the Garner constant
 // (p_0 ... p_{k-1})^{-1} mod p_k.
@@ -360,10 +304,6 @@ cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s) {
-  g3_kernel<<<blocks, threads, 0, s>>>(a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s) {

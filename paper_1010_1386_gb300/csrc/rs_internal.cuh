@@ -29,6 +29,8 @@ struct PairDesc {
   int64_t meta_off;      // int2 offset: (my+1) entries for f then (ny+1) for g
   int64_t img_off;       // offset of the K*N image block (prime-major)
   int64_t out_off;       // offset of the N*Lout output block (coefficient-major)
+  int64_t xl_off;        // offset of the CRT digit scratch: N * 16 * ceil(Lout/16) words
+  int64_t cy_off;        // offset of the CRT chunk carries: N * ceil(Lout/16) int64
 };
 
 // G1 work item: points [x0, x0 + n) of one (pair, prime).
@@ -73,11 +75,19 @@ struct G2Args {
 struct G3Args {
   const PairDesc *pairs;
   const int2 *tasks;       // (pair, first coefficient) per block
+  const int4 *ctasks;      // (pair, first coefficient, chunk, -) per limb-chunk block
   const ModP *mods;
   const uint32_t *crt;     // (p_0 ... p_{k-1})^{-1} mod p_k, Montgomery form
+  const int32_t *wtab;     // triangular: W[k][l] = p_0 ... p_{l-1} mod p_k (Montgomery, signed)
+  const uint16_t *p16;     // prefix products p_0 ... p_{k-1} in 16-bit digits
+  const int32_t *poff;     // row offsets into p16 (u16 units, multiples of 32)
+  const int32_t *nh;       // digits of each prefix product
   uint32_t *coef;          // in: R mod p_k (plain); overwritten by mixed-radix digits
-  uint32_t *xl;            // scratch, limb-major per pair: [l][N]
+  uint32_t *xl;            // 16-bit digit pairs of R_j, [16 chunk + w][N] per pair
+  int64_t *carry;          // chunk carries [chunk][N] per pair
   uint32_t *out;           // out: [coefficient][limb]
+  int32_t kmax;            // largest K of the batch (digit kernel shared memory)
+  int32_t digits_in_smem;  // set by launch_g3: digit kernel keeps digits in shared memory
 };
 
 // Launchers (kernels_*.cu).  Each returns the cudaGetLastError() of its launch.
@@ -86,7 +96,12 @@ int g1_supported_cap(int cap);           // smallest compiled register capacity 
 cudaError_t g1_prepare(int cap, int threads, size_t smem, int *max_blocks_per_sm);
 cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cudaStream_t s);
 cudaError_t g2_prepare(size_t smem);
-cudaError_t launch_g3(int threads, int blocks, const G3Args &a, cudaStream_t s);
+cudaError_t launch_g3(int nd, int dthreads, int nw, int nb, int nc, const G3Args &a, const int2 *dtasks,
+                      const int2 *wtasks, const int2 *otasks, cudaStream_t s);
+int g3_digit_threads(int kmax);  // coefficients per digit block (shared memory: threads * kmax words)
+cudaError_t g3_prepare(int kmax);
+cudaError_t launch_crt_tables(const ModP *mods, int K, const int32_t *poff, int32_t *wtab, uint16_t *p16,
+                              int32_t *nh, uint32_t *limbs, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s);
 cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
