@@ -297,9 +297,25 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
-  for (int i : byN) {
-    const PairPlan &p = b->plans[i];
-    for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
+  // G2 launches by point count: blocks of 64, 128 or 256 threads so that each
+  // thread has about two output blocks of the convolutions.
+  const int g2cls_threads[3] = {64, 128, 256};
+  for (int c = 0; c < 3; ++c) {
+    RsG2Class gc;
+    gc.threads = g2cls_threads[c];
+    gc.off = (int64_t)g2.size();
+    int cmaxN = 0;
+    for (int i : byN) {
+      const PairPlan &p = b->plans[i];
+      const int npair = ((p.N + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;
+      const int cls = npair <= 64 ? 0 : npair <= 128 ? 1 : 2;
+      if (cls != c) continue;
+      cmaxN = std::max(cmaxN, p.N);
+      for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
+    }
+    gc.count = (int)((int64_t)g2.size() - gc.off);
+    gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
+    if (gc.count > 0 && !images_only) b->g2cls.push_back(gc);
   }
   const int dthreads = g3_digit_threads(std::max(maxK, 1));
   int64_t ncoef = 0;
@@ -329,7 +345,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
-  b->info.kernel_launches = (int64_t)b->classes.size() + (b->ng2 > 0) + (b->ng3d > 0) + (b->ng3w > 0) + (b->ng3b > 0) +
+  b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) +
+                            (b->ng3w > 0) + (b->ng3b > 0) +
                             (b->ng3 > 0);
 
   int rc = RS_OK;
@@ -485,10 +502,10 @@ static int enqueue(rs_batch *b, bool capturing) {
     RS_CUDA(ctx, launch_g1(cl.cap, cl.threads, cl.blocks, cl.smem, a, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[1], s, capturing));
-  if (b->ng2) {
+  for (const auto &gc : b->g2cls) {
     G2Args a2;
     a2.pairs = b->d_pairs;
-    a2.tasks = b->d_g2;
+    a2.tasks = b->d_g2 + gc.off;
     a2.mods = ctx->d_mods;
     a2.num = b->d_num;
     a2.den = b->d_den;
@@ -497,7 +514,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a2.gtab = tab.gtab;
     a2.btab = tab.btab;
     a2.tab_stride = tab.N;
-    RS_CUDA(ctx, launch_g2(b->g2_threads, b->ng2, b->g2smem, a2, s));
+    RS_CUDA(ctx, launch_g2(gc.threads, gc.count, gc.smem, a2, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[2], s, capturing));
   if (b->ng3) {

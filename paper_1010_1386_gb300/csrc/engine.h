@@ -59,6 +59,13 @@ struct RsClassLaunch {
   size_t smem = 0;
 };
 
+struct RsG2Class {
+  int threads = 256;
+  int64_t off = 0;  // first task of the class in the G2 task list
+  int count = 0;
+  size_t smem = 0;
+};
+
 struct RsBatchOpts {
   bool images_only = false;
   cudaStream_t stream = nullptr;  // NULL: the context's stream
@@ -80,6 +87,7 @@ struct rs_batch {
   std::vector<PairDesc> descs;
   std::vector<int64_t> in_f, in_g;  // word offsets of each pair's inputs in the staging buffer
   std::vector<RsClassLaunch> classes;
+  std::vector<RsG2Class> g2cls;
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int ng2 = 0, ng3 = 0, g2_threads = 256;
   int ng3d = 0, ng3w = 0, ng3b = 0, kmax = 0;  // CRT digit blocks (per thread / per warp), chunks, largest K

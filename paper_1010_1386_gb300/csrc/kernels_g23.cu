@@ -89,7 +89,6 @@ __device__ void batch_invert(const uint32_t *d, uint32_t *out, int n, const ModP
 // and one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53
 // (every table prime exceeds 2^31 - 2^20, so 2^32 mod p <= 2^21).
 
-#define RS_CONV_R 7  // outputs per register block; odd, so lanes hit distinct banks
 
 __device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
@@ -110,7 +109,14 @@ __device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n
   constexpr int R = RS_CONV_R;
   const uint32_t c32 = m.r1;  // 2^32 mod p
   const int nblk = (n + R - 1) / R;
-  for (int bi = threadIdx.x; bi < nblk; bi += blockDim.x) {
+  // Output block bi costs about bi chunks: thread t takes the blocks pi and
+  // nblk - 1 - pi for pi = t, t + T, ..., so every thread gets the same work.
+  const int npair = (nblk + 1) / 2;
+  for (int it = 0; it < 2 * ((npair + blockDim.x - 1) / blockDim.x); ++it) {
+    const int pi = threadIdx.x + (int)blockDim.x * (it >> 1);
+    if (pi >= npair) break;
+    const int bi = (it & 1) ? nblk - 1 - pi : pi;
+    if ((it & 1) && bi == pi) continue;  // odd count: the middle block once
     const int k0 = bi * R;
     int64_t acc[R];
 #pragma unroll

@@ -9,6 +9,7 @@
 #define RS_G1_MAX_STAGED_WORDS (48 * 1024)  // staged residues + meta per G1 tile
 #define RS_G1_MAX_SMEM_BYTES (RS_G1_MAX_STAGED_WORDS * 4)
 #define RS_G2_PAD 8          // zero words around each G2 shared-memory region
+#define RS_CONV_R 7          // G2 outputs per register block; odd, so lanes hit distinct banks
 #define RS_G2_MAX_SMEM_BYTES (3 * (16384 + 2 * RS_G2_PAD) * 4)
 
 // Stage counters written by the kernels (detection of unlucky / degenerate cases).
