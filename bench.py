@@ -400,7 +400,7 @@ def serving_main(args, world, rank, local, dist):
         for i in range(n):
             while tickets[i] is None:
                 time.sleep(0.0001)
-            _, ms = srv.wait(tickets[i])
+            _, ms = srv.wait(tickets[i], raw=True)  # limbs into a host buffer, no Python ints
             lat.append(ms)
         th.join()
         return time.perf_counter() - t_start, lat

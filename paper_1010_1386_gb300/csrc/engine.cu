@@ -184,7 +184,11 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     g3d += 2 * ((p.N + 1) / 2);  // bound for either digit mapping
     g3b += (p.N + 127) / 128 * chunks;
   }
-  *in_words = in;
+  // inputs plus room for the static tables (descriptors, tiles, task lists)
+  // that rs_build_batch packs behind them in borrowed pinned staging
+  const int64_t stat = meta * 2 + (int64_t)plans.size() * (int64_t)(sizeof(PairDesc) / 4) + tiles * 4 +
+                       g2 * 2 + g3 * 2 + g3d * 4 + g3b * 4 + 8 * 4;
+  *in_words = in + stat;
   *out_words = out;
   *device_bytes = (int64_t)(align_up(in * 4) + align_up(meta * 8) + align_up(plans.size() * sizeof(PairDesc)) +
                             align_up(tiles * sizeof(Tile)) + kAlign + 2 * align_up(img * 4) +
@@ -407,45 +411,77 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       return rs_fail(ctx, rc, "cudaMallocHost (staging)");
     }
   }
-  // Static per-batch tables, ordered on the batch stream.
-  auto h2d = [&](void *dst, const void *src, size_t bytes) {
-    if (rc != RS_OK || bytes == 0) return;
-    cudaError_t e2 = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, b->stream);
-    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e2));
+  // Static per-batch tables, ordered on the batch stream.  With borrowed
+  // pinned staging large enough they are packed behind the inputs and copied
+  // without waiting; otherwise they are copied from pageable memory and the
+  // stream is synchronised before the host vectors go away.
+  struct Piece {
+    void *dst;
+    const void *src;
+    size_t bytes;
   };
-  h2d(b->d_meta, meta.data(), meta.size() * sizeof(int2));
-  h2d(b->d_pairs, b->descs.data(), b->descs.size() * sizeof(PairDesc));
-  h2d(b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile));
-  h2d(b->d_g2, g2.data(), g2.size() * sizeof(int2));
-  h2d(b->d_g3, g3.data(), g3.size() * sizeof(int2));
-  h2d(b->d_g3d, g3d.data(), g3d.size() * sizeof(int2));
-  h2d(b->d_g3w, g3w.data(), g3w.size() * sizeof(int2));
-  h2d(b->d_g3b, g3b.data(), g3b.size() * sizeof(int4));
-  if (rc == RS_OK && (b->ng3d || b->ng3w)) {
-    cudaError_t e2 = g3_prepare(b->kmax);
-    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
+  const Piece pieces[] = {{b->d_meta, meta.data(), meta.size() * sizeof(int2)},
+                          {b->d_pairs, b->descs.data(), b->descs.size() * sizeof(PairDesc)},
+                          {b->d_tiles, tiles.data(), tiles.size() * sizeof(Tile)},
+                          {b->d_g2, g2.data(), g2.size() * sizeof(int2)},
+                          {b->d_g3, g3.data(), g3.size() * sizeof(int2)},
+                          {b->d_g3d, g3d.data(), g3d.size() * sizeof(int2)},
+                          {b->d_g3w, g3w.data(), g3w.size() * sizeof(int2)},
+                          {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)}};
+  size_t static_bytes = 0;
+  for (const Piece &pc : pieces) static_bytes += (pc.bytes + 15) & ~(size_t)15;
+  const bool pinned_static = !b->own_host && (size_t)opt.h_in_words * 4 >= (size_t)b->in_words * 4 + static_bytes;
+  char *stage = pinned_static ? reinterpret_cast<char *>(b->h_in + b->in_words) : nullptr;
+  for (const Piece &pc : pieces) {
+    if (rc != RS_OK || pc.bytes == 0) continue;
+    const void *src = pc.src;
+    if (stage) {
+      memcpy(stage, pc.src, pc.bytes);
+      src = stage;
+      stage += (pc.bytes + 15) & ~(size_t)15;
+    }
+    cudaError_t e2 = cudaMemcpyAsync(pc.dst, src, pc.bytes, cudaMemcpyHostToDevice, b->stream);
+    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e2));
   }
-  if (rc == RS_OK) {  // the pageable sources above must outlive the copies
+  if (rc == RS_OK && !pinned_static) {
     cudaError_t e2 = cudaStreamSynchronize(b->stream);
     if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("sync: ") + cudaGetErrorString(e2));
   }
-  for (auto &cl : b->classes) {
-    if (rc != RS_OK) break;
-    int mb = 0;
-    cudaError_t e2 = g1_prepare(cl.cap, cl.threads, cl.smem, &mb);
-    if (e2 != cudaSuccess) {
-      rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G1 set-up: ") + cudaGetErrorString(e2));
-      break;
+  {
+    // Kernel attributes and occupancies, once per context.
+    std::lock_guard<std::mutex> lock(ctx->prep_mu);
+    if (rc == RS_OK && (b->ng3d || b->ng3w) && !ctx->g3_ready) {
+      cudaError_t e2 = g3_prepare(b->kmax);
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
+      ctx->g3_ready = e2 == cudaSuccess;
     }
-    if (mb < 1) mb = 1;
-    cl.blocks = opt.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
+    if (rc == RS_OK && !b->g2cls.empty() && !ctx->g2_ready) {
+      cudaError_t e2 = g2_prepare(b->g2smem);
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
+      ctx->g2_ready = e2 == cudaSuccess;
+    }
+    for (auto &cl : b->classes) {
+      if (rc != RS_OK) break;
+      const int64_t key = ((int64_t)cl.cap << 40) | ((int64_t)cl.threads << 24) | (int64_t)((cl.smem + 1023) / 1024);
+      auto it = ctx->g1_occupancy.find(key);
+      int mb = 0;
+      if (it != ctx->g1_occupancy.end()) {
+        mb = it->second;
+      } else {
+        cudaError_t e2 = g1_prepare(cl.cap, cl.threads, ((cl.smem + 1023) / 1024) * 1024, &mb);
+        if (e2 != cudaSuccess) {
+          rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G1 set-up: ") + cudaGetErrorString(e2));
+          break;
+        }
+        ctx->g1_occupancy[key] = mb;
+      }
+      if (mb < 1) mb = 1;
+      cl.blocks = opt.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
+    }
   }
-  if (rc == RS_OK && b->ng2) {
-    cudaError_t e2 = g2_prepare(b->g2smem);
-    if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
-  }
-  for (auto &ev : b->ev)
-    if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
+  if (ctx->cfg.timing)
+    for (auto &ev : b->ev)
+      if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;

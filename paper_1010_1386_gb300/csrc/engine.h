@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -48,6 +49,9 @@ struct rs_ctx {
   RsTables tab;
   std::vector<RsTables> retired;
   RsServer *server = nullptr;
+  std::mutex prep_mu;  // kernel attributes and the occupancy cache below
+  bool g2_ready = false, g3_ready = false;
+  std::map<int64_t, int> g1_occupancy;  // (capacity, threads, staged KiB) -> blocks per SM
 };
 
 struct RsClassLaunch {

@@ -9,6 +9,7 @@
 // others run is admitted as soon as a stream slot and memory are free, so the
 // device never waits for a whole "epoch" to drain.  Results stay on the
 // device until their micro-batch finishes, then are copied back once.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -57,6 +58,8 @@ struct RsServer {
   uint64_t next_ticket = 1;
   int64_t mem_limit = 0, mem_used = 0;
   int max_inflight = 4, max_batch = 256;
+  int min_batch = 32;                                  // launch early once this many wait
+  std::chrono::microseconds max_wait{1000};            // or once the oldest waited this long
   std::vector<cudaStream_t> streams;
   std::vector<uint32_t *> h_in, h_out;
   std::vector<int64_t> h_in_words, h_out_words;
@@ -209,7 +212,15 @@ void loop(RsServer *s) {
   std::unique_lock<std::mutex> lk(s->mu);
   for (;;) {
     reap(s);
-    const bool can_launch = !s->pending.empty() && (int)s->flights.size() < s->max_inflight;
+    // Launch when a stream is free and either the GPU is idle, enough
+    // requests have accumulated for a full micro-batch share, or the oldest
+    // pending request has waited max_wait: larger micro-batches while the
+    // GPU is busy, no waiting when it is idle.
+    bool can_launch = !s->pending.empty() && (int)s->flights.size() < s->max_inflight;
+    if (can_launch && !s->flights.empty()) {
+      const auto age = Clock::now() - s->pending.front()->t_submit;
+      can_launch = (int)s->pending.size() >= s->min_batch || age >= s->max_wait;
+    }
     if (can_launch) {
       const size_t before = s->pending.size();
       launch(s, lk);
@@ -230,6 +241,7 @@ int start(rs_ctx *ctx, int32_t max_inflight, int32_t max_batch, int64_t mem_limi
   memset(&s->st, 0, sizeof(s->st));
   s->max_inflight = max_inflight > 0 ? max_inflight : 4;
   s->max_batch = max_batch > 0 ? max_batch : 256;
+  s->min_batch = std::max(1, std::min(32, s->max_batch / 4));
   if (mem_limit <= 0) mem_limit = ctx->cfg.mem_limit_bytes;
   if (mem_limit <= 0) {
     size_t fr = 0, tot = 0;

@@ -289,7 +289,6 @@ class Server:
 
     def __init__(self, ctx, max_inflight=0, max_batch=0, mem_limit_bytes=0):
         self.ctx, self.lib = ctx, ctx.lib
-        self.outs = {}
         _check(self.lib.rs_server_start(ctx.h, max_inflight, max_batch, mem_limit_bytes), ctx.h)
 
     def submit(self, f, g):
@@ -297,29 +296,40 @@ class Server:
         t = ctypes.c_uint64()
         _check(self.lib.rs_server_submit(self.ctx.h, ctypes.byref(P.structs[0]),
                                          ctypes.byref(P.structs[1]), ctypes.byref(t)), self.ctx.h)
-        self.outs[t.value] = _Outputs([(f, g)])
         return t.value
 
-    def _finish(self, rc, ticket, lat):
-        if rc == RS_PENDING:
+    def _take(self, call, ticket, raw=False):
+        """Run a poll/wait call with an empty buffer first; on RS_ERR_CAPACITY
+        (ticket kept, size reported) allocate exactly and call again."""
+        lat = c_double()
+        out = rs_upoly()
+        out.capacity_words = 0
+        rc = call(out, lat)
+        if rc == -2:
+            words = max(1, (out.deg + 1) * out.limbs)
+            buf = np.zeros(words, dtype=np.uint32)
+            out.capacity_words = words
+            out.coeffs = buf.ctypes.data_as(POINTER(c_uint32))
+            rc = call(out, lat)
+        else:
+            buf = np.zeros(1, dtype=np.uint32)
+        if rc in (RS_PENDING, -5):
             return None
-        out = self.outs.pop(ticket)
         _check(rc, self.ctx.h)
-        return out.ints()[0], lat.value
+        if raw:
+            return (out.deg, out.limbs, buf), lat.value
+        return limbs_to_ints(buf, out.deg, out.limbs), lat.value
 
-    def poll(self, ticket):
+    def poll(self, ticket, raw=False):
         """None while running, else (coefficients, latency_ms)."""
-        lat = c_double()
-        rc = self.lib.rs_server_poll(self.ctx.h, ticket, self.outs[ticket].structs, ctypes.byref(lat))
-        return self._finish(rc, ticket, lat)
+        return self._take(lambda o, l: self.lib.rs_server_poll(self.ctx.h, ticket, ctypes.byref(o),
+                                                               ctypes.byref(l)), ticket, raw)
 
-    def wait(self, ticket, timeout_us=-1):
-        lat = c_double()
-        rc = self.lib.rs_server_wait(self.ctx.h, ticket, self.outs[ticket].structs, ctypes.byref(lat),
-                                     timeout_us)
-        if rc == -5:
-            return None
-        return self._finish(rc, ticket, lat)
+    def wait(self, ticket, timeout_us=-1, raw=False):
+        """Block until done (or timeout: None); (coefficients, latency_ms)."""
+        return self._take(lambda o, l: self.lib.rs_server_wait(self.ctx.h, ticket, ctypes.byref(o),
+                                                               ctypes.byref(l), timeout_us),
+                          ticket, raw)
 
     def stats(self):
         st = rs_server_stats()
