@@ -84,19 +84,27 @@ typedef struct {
 
 typedef struct {
   int32_t device;            /* CUDA device ordinal, -1 = the current device */
-  int32_t tile_points;       /* G1 points per block: 32, 64 or 128; 0 = autotuned/default */
+  int32_t tile_points;       /* G1 points per block: 32, 64 or 128 forces that width for every
+                                class; 0 = per class from the tuner (see rs_autotune) */
   int32_t use_graphs;        /* 1 = replay batch runs as CUDA graphs */
-  int32_t persistent;        /* 1 = persistent G1 over a cost-sorted tile list */
+  int32_t persistent;        /* 1 = the tuner may pick persistent G1 launches over a cost-sorted
+                                tile list; 0 = one block per tile always */
   int32_t timing;            /* 1 = record per-stage CUDA events on each run */
-  int32_t reserved;
+  int32_t autotune;          /* 1 = a batch whose workload class is not in the tuner cache times
+                                the G1 candidates first; 0 = cached choices or the built-in
+                                default (128 points, persistent) */
   int64_t mem_limit_bytes;   /* serving: device bytes admitted requests may hold; 0 = auto */
+  const char *autotune_cache;  /* tuner cache file merged at rs_create (a missing file is not an
+                                  error) and rewritten at rs_destroy; NULL = none.  The string
+                                  is copied. */
 } rs_config;
 
 typedef struct rs_ctx rs_ctx;
 typedef struct rs_batch rs_batch;
 
 /* Fill *cfg with the defaults (device -1, tiles autotuned, graphs and
- * persistent kernels on, timing off, memory limit auto). */
+ * persistent kernels on, timing off, autotuning on without a cache file,
+ * memory limit auto). */
 int rs_config_default(rs_config *cfg);
 
 /* Create a context on the configured device: allocates the prime table and
@@ -182,6 +190,47 @@ int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes,
               int32_t npoints, uint32_t *primes_out, uint32_t *points_out,
               uint32_t *images_out);
+
+/* ---------------------------------------------------------------------
+ * Tuner of the image stage (G1: evaluation and univariate resultants,
+ * Section 4.1).  Its launch has two free choices that change no result: the
+ * points per block (the tile width: 32, 64 or 128) and the schedule (a
+ * persistent grid that draws tiles from a cost-sorted list, or one block per
+ * tile).  The best pair depends on the workload class: the register
+ * capacity of the remainder sequence (the larger y-degree, rounded up to a
+ * multiple of 8), floor(log2) of the class's largest point count D + 1 and
+ * floor(log2) of its modular images K (D + 1), plus the GPU's SM count.
+ * When a batch meets a class that the process-wide cache lacks (and
+ * rs_config.autotune is 1), it first builds image-only batches of the
+ * class's pairs (a stride sample of at most 2^22 images) for each of the six
+ * candidates, times their G1 launches with CUDA events (median of three
+ * after one warm-up) and caches the fastest; the built-in default is kept
+ * unless another candidate is more than 2% faster.  The server never tunes;
+ * it uses cached choices, so warm the cache with rs_autotune first.
+ * --------------------------------------------------------------------- */
+typedef struct {
+  int32_t sms, cap, lg_points, lg_images;  /* the class */
+  int32_t tile_points, persistent;         /* the choice */
+  float ms_best, ms_default;               /* G1 time of the choice and of the default on the
+                                              tuning sample (0 when loaded without timings) */
+} rs_tune_entry;
+
+/* Tune every class that these pairs form (as rs_batch_create would group
+ * them) and is not cached yet; no result is computed. */
+int rs_autotune(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g);
+/* Copy up to cap_entries cached choices into out (may be NULL when
+ * cap_entries is 0); *count receives the number cached.  Host only. */
+int rs_autotune_entries(rs_tune_entry *out, int32_t cap_entries, int32_t *count);
+/* Write the cache as text, one class per line:
+ *   sms cap lg_points lg_images tile_points persistent ms_best ms_default
+ * after a '#' header line.  Host only. */
+int rs_autotune_save(const char *path);
+/* Merge a file written by rs_autotune_save into the cache (its entries win).
+ * A malformed line rejects the whole file with RS_ERR_ARG and merges
+ * nothing.  Host only. */
+int rs_autotune_load(const char *path);
+/* Empty the cache.  Host only. */
+int rs_autotune_clear(void);
 
 /* ---------------------------------------------------------------------
  * Serving: a continuous-batching request server inside a context.

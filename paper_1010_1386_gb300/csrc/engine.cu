@@ -208,7 +208,6 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   memset(&b->info, 0, sizeof(b->info));
   b->info.pairs = n;
   const bool images_only = opt.images_only;
-  const int T = ctx->cfg.tile_points > 0 ? ctx->cfg.tile_points : 128;
 
   std::vector<int2> meta;
   std::vector<int> order;
@@ -282,15 +281,46 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     double cc = (double)c.K * c.N * (c.f.nc + c.g.nc + 2.0 * c.f.my * c.g.my);
     return ca > cc;
   });
+  // Tile width and schedule per class: forced by the options or the context,
+  // else the tuner's cached choice (timed now when missing and allowed), else
+  // 128 points on a persistent grid.
   std::vector<Tile> tiles;
   for (int cap = 8; cap <= 72; cap += 8) {
+    std::vector<int> members;
+    int cmaxN = 0;
+    int64_t cimages = 0;
+    for (int i : order)
+      if (g1_supported_cap(b->plans[i].cap) == cap) {
+        members.push_back(i);
+        cmaxN = std::max(cmaxN, b->plans[i].N);
+        cimages += (int64_t)b->plans[i].K * b->plans[i].N;
+      }
+    if (members.empty()) continue;
+    RsG1Choice ch;
+    if (opt.g1_threads > 0) {
+      ch.threads = opt.g1_threads;
+    } else if (ctx->cfg.tile_points > 0) {
+      ch.threads = ctx->cfg.tile_points;
+    } else {
+      const int64_t key = rs_tune_key(ctx->sms, cap, cmaxN, cimages);
+      if (!rs_tune_find(key, &ch) && opt.tune && ctx->cfg.autotune) {
+        const int rc = rs_tune_g1(ctx, f, g, b->plans, members, key, &ch);
+        if (rc != RS_OK) {
+          rs_free_batch(b);
+          return rc;
+        }
+      }
+    }
+    ch.persistent = (ch.persistent && opt.persistent) ? 1 : 0;
+    if (opt.g1_threads > 0 || ctx->cfg.tile_points > 0) ch.persistent = opt.persistent ? 1 : 0;
+    const int T = ch.threads;
     RsClassLaunch cl;
     cl.cap = cap;
     cl.threads = T;
+    cl.persistent = ch.persistent;
     cl.tile_off = (int64_t)tiles.size();
-    for (int i : order) {
+    for (int i : members) {
       const PairPlan &p = b->plans[i];
-      if (g1_supported_cap(p.cap) != cap) continue;
       cl.smem = std::max(cl.smem, (size_t)rs_g1_staged_words(p, cap, T) * 4);
       for (int k = 0; k < p.K; ++k)
         for (int x0 = 0; x0 < p.N; x0 += T) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T, p.N - x0)});
@@ -476,10 +506,10 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
         ctx->g1_occupancy[key] = mb;
       }
       if (mb < 1) mb = 1;
-      cl.blocks = opt.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
+      cl.blocks = cl.persistent ? std::min(cl.ntiles, mb * ctx->sms) : cl.ntiles;
     }
   }
-  if (ctx->cfg.timing)
+  if (ctx->cfg.timing || opt.timing)
     for (auto &ev : b->ev)
       if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
   if (rc != RS_OK) {
@@ -508,7 +538,7 @@ static cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
 static int enqueue(rs_batch *b, bool capturing) {
   rs_ctx *ctx = b->ctx;
   cudaStream_t s = b->stream;
-  const bool timing = ctx->cfg.timing != 0;
+  const bool timing = ctx->cfg.timing != 0 || b->opt.timing;
   RsTables tab;
   {
     std::lock_guard<std::mutex> lock(ctx->tab_mu);
@@ -523,7 +553,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.pairs = b->d_pairs;
     a.tiles = b->d_tiles + cl.tile_off;
     a.ntiles = cl.ntiles;
-    a.persistent = b->opt.persistent ? 1 : 0;
+    a.persistent = cl.persistent;
     a.counter = b->d_counters + (ci++);
     a.limbs = b->d_in;
     a.meta = b->d_meta;
@@ -718,6 +748,7 @@ int rs_config_default(rs_config *cfg) {
   cfg->device = -1;
   cfg->use_graphs = 1;
   cfg->persistent = 1;
+  cfg->autotune = 1;
   return RS_OK;
 }
 
@@ -738,9 +769,19 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
     return rs_fail(nullptr, RS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) dev = 0;
   if (dev >= ndev) return rs_fail(nullptr, RS_ERR_ARG, "device ordinal out of range");
+  if (c.autotune_cache && c.autotune_cache[0]) {
+    FILE *probe = fopen(c.autotune_cache, "r");
+    if (probe) {
+      fclose(probe);
+      int rc0 = rs_autotune_load(c.autotune_cache);
+      if (rc0 != RS_OK) return rc0;
+    }
+  }
   rs_ctx *ctx = new rs_ctx();
   ctx->device = dev;
   ctx->cfg = c;
+  if (c.autotune_cache) ctx->tune_path = c.autotune_cache;
+  ctx->cfg.autotune_cache = nullptr;  // the copy in tune_path is the one kept
   DevGuard dg(dev);
   int rc = RS_OK;
   auto chk = [&](cudaError_t e2, const char *what) {
@@ -773,6 +814,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
 int rs_destroy(rs_ctx *ctx) {
   if (!ctx) return RS_OK;
   rs_server_shutdown(ctx);
+  if (!ctx->tune_path.empty()) rs_autotune_save(ctx->tune_path.c_str());
   {
     DevGuard dg(ctx->device);
     for (rs_batch *b : ctx->batches) rs_free_batch(b);
@@ -953,6 +995,7 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
     RsBatchOpts o = default_opts(ctx);
     o.images_only = true;
     o.use_graph = false;
+    o.tune = false;
     rs_batch *b = nullptr;
     int rc = rs_build_batch(ctx, 1, f, g, std::move(plans), o, &b);
     if (rc != RS_OK) return rc;

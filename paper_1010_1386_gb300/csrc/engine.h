@@ -52,11 +52,13 @@ struct rs_ctx {
   std::mutex prep_mu;  // kernel attributes and the occupancy cache below
   bool g2_ready = false, g3_ready = false;
   std::map<int64_t, int> g1_occupancy;  // (capacity, threads, staged KiB) -> blocks per SM
+  std::string tune_path;                 // autotune cache file written at rs_destroy ("" = none)
 };
 
 struct RsClassLaunch {
   int cap = 0;
   int threads = 128;
+  int persistent = 1;
   int blocks = 0;
   int64_t tile_off = 0;
   int ntiles = 0;
@@ -79,6 +81,9 @@ struct RsBatchOpts {
   int64_t h_in_words = 0, h_out_words = 0;
   bool use_graph = true;
   bool persistent = true;
+  bool tune = true;     // time G1 choices for classes missing from the tuner cache
+  bool timing = false;  // record stage events even when the context does not time
+  int g1_threads = 0;   // > 0: force this tile width (and opt.persistent) for every class
 };
 
 struct rs_batch {
@@ -137,3 +142,17 @@ int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status);     // after the cop
 int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, int *limbs);
 void rs_free_batch(rs_batch *b);
 void rs_server_shutdown(rs_ctx *ctx);  // server.cu
+
+// G1 launch tuner (autotune.cu).  A workload class is (SM count, register
+// capacity, floor(log2 of its largest point count), floor(log2 of its images));
+// the process-wide cache maps it to a tile width and a schedule.
+struct RsG1Choice {
+  int threads = 128;
+  int persistent = 1;
+  float ms_best = 0.f, ms_default = 0.f;
+};
+int64_t rs_tune_key(int sms, int cap, int max_points, int64_t images);
+bool rs_tune_find(int64_t key, RsG1Choice *out);
+// Time every candidate on (a sample of) the class's pairs and cache the fastest.
+int rs_tune_g1(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::vector<PairPlan> &plans,
+               const std::vector<int> &members, int64_t key, RsG1Choice *out);

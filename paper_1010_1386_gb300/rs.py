@@ -36,8 +36,14 @@ class rs_upoly(ctypes.Structure):
 
 class rs_config(ctypes.Structure):
     _fields_ = [("device", c_int32), ("tile_points", c_int32), ("use_graphs", c_int32),
-                ("persistent", c_int32), ("timing", c_int32), ("reserved", c_int32),
-                ("mem_limit_bytes", c_int64)]
+                ("persistent", c_int32), ("timing", c_int32), ("autotune", c_int32),
+                ("mem_limit_bytes", c_int64), ("autotune_cache", c_char_p)]
+
+
+class rs_tune_entry(ctypes.Structure):
+    _fields_ = [(k, c_int32) for k in ("sms", "cap", "lg_points", "lg_images", "tile_points",
+                                       "persistent")] + [("ms_best", ctypes.c_float),
+                                                         ("ms_default", ctypes.c_float)]
 
 
 class rs_batch_info(ctypes.Structure):
@@ -86,6 +92,11 @@ _SIGS = {
     "rs_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, _P(rs_upoly), _P(c_double), c_int64]),
     "rs_server_stats_get": (c_int32, [c_void_p, _P(rs_server_stats)]),
     "rs_server_stop": (c_int32, [c_void_p]),
+    "rs_autotune": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
+    "rs_autotune_entries": (c_int32, [_P(rs_tune_entry), c_int32, _P(c_int32)]),
+    "rs_autotune_save": (c_int32, [c_char_p]),
+    "rs_autotune_load": (c_int32, [c_char_p]),
+    "rs_autotune_clear": (c_int32, []),
 }
 
 _lib = None
@@ -178,13 +189,15 @@ class Context:
     """One librs context (device memory, stream, prime tables) on one GPU."""
 
     def __init__(self, device=-1, tile_points=0, use_graphs=True, persistent=True, timing=False,
-                 mem_limit_bytes=0):
+                 mem_limit_bytes=0, autotune=True, autotune_cache=None):
         lib = load()
         cfg = rs_config()
         _check(lib.rs_config_default(ctypes.byref(cfg)))
         cfg.device, cfg.tile_points = device, tile_points
         cfg.use_graphs, cfg.persistent, cfg.timing = int(use_graphs), int(persistent), int(timing)
         cfg.mem_limit_bytes = mem_limit_bytes
+        cfg.autotune = int(autotune)
+        cfg.autotune_cache = os.fsencode(autotune_cache) if autotune_cache else None
         h = c_void_p()
         _check(lib.rs_create(ctypes.byref(h), ctypes.byref(cfg)))
         self.lib, self.h = lib, h
@@ -243,6 +256,34 @@ class Context:
 
     def batch(self, pairs):
         return Batch(self, pairs)
+
+    def autotune(self, pairs):
+        """Tune the G1 launch for every workload class of these pairs that the
+        process-wide cache lacks (nothing is computed)."""
+        F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        _check(self.lib.rs_autotune(self.h, len(pairs), F.structs, G.structs), self.h)
+
+
+def autotune_entries():
+    """The tuner cache as a list of dicts (class, choice and timings)."""
+    lib = load()
+    n = c_int32()
+    _check(lib.rs_autotune_entries(None, 0, ctypes.byref(n)))
+    buf = (rs_tune_entry * max(n.value, 1))()
+    _check(lib.rs_autotune_entries(buf, n.value, ctypes.byref(n)))
+    return [{k: getattr(e, k) for k, _ in rs_tune_entry._fields_} for e in buf[: n.value]]
+
+
+def autotune_save(path):
+    _check(load().rs_autotune_save(os.fsencode(path)))
+
+
+def autotune_load(path):
+    _check(load().rs_autotune_load(os.fsencode(path)))
+
+
+def autotune_clear():
+    _check(load().rs_autotune_clear())
 
 
 class Batch:
