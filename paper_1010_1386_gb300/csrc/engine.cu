@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <thread>
 
 #include "engine.h"
 
@@ -68,14 +69,35 @@ int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                 std::vector<PairPlan> &plans, int32_t *status, int *first_err) {
   plans.assign(n, PairPlan());
   *first_err = RS_OK;
+  std::vector<const char *> why(n, "");
+  auto plan_range = [&](int lo, int hi) {
+    for (int i = lo; i < hi; ++i) plans[i].status = rs_plan_pair(&f[i], &g[i], ctx->log2p, plans[i], &why[i]);
+  };
+  // Planning reads every input coefficient once; large batches are split
+  // over host threads in contiguous ranges of pairs.
+  auto sane = [](const rs_bipoly &p) {
+    return p.coeffs && p.deg_x >= 0 && p.deg_y >= 0 && p.deg_x < (1 << 26) && p.deg_y < (1 << 26) &&
+           p.limbs >= 1 && p.limbs <= RS_MAX_LIMBS;
+  };
+  int64_t words = 0;  // only steers the thread count
+  for (int i = 0; i < n; ++i)
+    if (sane(f[i]) && sane(g[i])) words += rs_input_words(f[i]) + rs_input_words(g[i]);
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>({(int64_t)std::min(hw, 16), (int64_t)n, words / (int64_t(1) << 18) + 1});
+  if (nt <= 1) {
+    plan_range(0, n);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back(plan_range, (int)((int64_t)n * t / nt), (int)((int64_t)n * (t + 1) / nt));
+    for (auto &x : th) x.join();
+  }
   for (int i = 0; i < n; ++i) {
-    const char *why = "";
-    int rc = rs_plan_pair(&f[i], &g[i], ctx->log2p, plans[i], &why);
-    plans[i].status = rc;
+    const int rc = plans[i].status;
     if (status) status[i] = rc;
     if (rc != RS_OK && *first_err == RS_OK) {
       *first_err = rc;
-      rs_fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + why);
+      rs_fail(ctx, rc, std::string("pair ") + std::to_string(i) + ": " + why[i]);
     }
   }
   return *first_err;
@@ -677,25 +699,55 @@ int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, in
   return RS_OK;
 }
 
+static int unpack_pair(rs_batch *b, int i, rs_upoly &o) {
+  const PairPlan &p = b->plans[i];
+  int rc = p.status;
+  if (rc == RS_OK && !o.coeffs && o.capacity_words > 0) rc = RS_ERR_ARG;
+  if (rc != RS_OK) return rc;
+  int deg, L;
+  const uint32_t *w = result_shape(b, i, &deg, &L);
+  o.deg = deg;
+  o.limbs = L;
+  if ((int64_t)(deg + 1) * L > o.capacity_words) return RS_ERR_CAPACITY;
+  if (L == p.Lout) {
+    if (deg >= 0) memcpy(o.coeffs, w, (size_t)(deg + 1) * L * 4);
+  } else {
+    for (int j = 0; j <= deg; ++j) memcpy(o.coeffs + (size_t)j * L, w + (size_t)j * p.Lout, (size_t)L * 4);
+  }
+  return RS_OK;
+}
+
 int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status) {
   rs_ctx *ctx = b->ctx;
-  int first = RS_OK;
-  for (int i = 0; i < b->n; ++i) {
-    const PairPlan &p = b->plans[i];
-    int rc = p.status;
-    if (rc == RS_OK && !out[i].coeffs && out[i].capacity_words > 0) rc = RS_ERR_ARG;
-    if (rc == RS_OK) {
-      int deg, L;
-      const uint32_t *w = result_shape(b, i, &deg, &L);
-      out[i].deg = deg;
-      out[i].limbs = L;
-      if ((int64_t)(deg + 1) * L > out[i].capacity_words) {
-        rc = RS_ERR_CAPACITY;
-      } else {
-        for (int j = 0; j <= deg; ++j)
-          for (int l = 0; l < L; ++l) out[i].coeffs[(size_t)j * L + l] = w[(size_t)j * p.Lout + l];
-      }
+  const int n = b->n;
+  std::vector<int> rcs(n, RS_OK);
+  // Large outputs are trimmed and copied by several host threads, each
+  // taking a contiguous range of pairs of about equal size.
+  const int64_t kWordsPerThread = int64_t(1) << 20;
+  const int hw = std::max(1, (int)std::thread::hardware_concurrency());
+  const int nt = (int)std::min<int64_t>({(int64_t)std::min(hw, 16), (int64_t)n, b->out_words / kWordsPerThread + 1});
+  if (nt <= 1) {
+    for (int i = 0; i < n; ++i) rcs[i] = unpack_pair(b, i, out[i]);
+  } else {
+    std::vector<int> cut(1, 0);
+    int64_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      const PairPlan &p = b->plans[i];
+      if (p.status == RS_OK && !p.trivial_zero) acc += (int64_t)p.N * p.Lout;
+      if (acc * nt >= b->out_words * (int64_t)cut.size() && (int)cut.size() < nt) cut.push_back(i + 1);
     }
+    while ((int)cut.size() <= nt) cut.push_back(n);
+    cut.back() = n;
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&, t] {
+        for (int i = cut[t]; i < cut[t + 1]; ++i) rcs[i] = unpack_pair(b, i, out[i]);
+      });
+    for (auto &x : th) x.join();
+  }
+  int first = RS_OK;
+  for (int i = 0; i < n; ++i) {
+    const int rc = rcs[i];
     if (status) status[i] = rc;
     if (rc != RS_OK && first == RS_OK) {
       first = rc;

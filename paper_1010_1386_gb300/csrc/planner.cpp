@@ -20,26 +20,42 @@
 
 namespace {
 
-// Upper bound of log2|c| for a non-zero two's-complement limb integer;
-// returns -INFINITY for zero.
-double log2_abs_upper(const uint32_t *c, int L) {
-  uint32_t mag[RS_MAX_LIMBS];
-  if (c[L - 1] >> 31) {
-    uint64_t carry = 1;
-    for (int l = 0; l < L; ++l) {
-      uint64_t t = (uint64_t)(uint32_t)~c[l] + carry;
-      mag[l] = (uint32_t)t;
-      carry = t >> 32;
-    }
-  } else {
-    memcpy(mag, c, sizeof(uint32_t) * L);
-  }
+// Upper bound of |c| for a two's-complement limb integer: returns the top
+// limb position t of the magnitude (-1 for c = 0) and sets hi so that
+// |c| <= hi * 2^(32 max(t - 1, 0)): the top two limbs plus one unit for
+// everything below them (hi <= 2^64 up to the rounding of one double
+// addition).  For c < 0 the magnitude ~c + 1 is bounded from the top limbs
+// of ~c alone, so no carry chain is taken.
+int abs_upper(const uint32_t *c, int L, double *hi) {
+  const bool neg = (c[L - 1] >> 31) != 0;
+  const uint32_t x = neg ? 0xffffffffu : 0u;  // limbs of ~c are c ^ x
   int t = L - 1;
-  while (t >= 0 && mag[t] == 0) --t;
-  if (t < 0) return -INFINITY;
-  if (t == 0) return log2((double)mag[0]);
-  double hi = (double)mag[t] * 4294967296.0 + (double)mag[t - 1] + 1.0;
-  return log2(hi) + 32.0 * (t - 1);
+  while (t >= 0 && (c[t] ^ x) == 0) --t;
+  if (t < 0) {
+    if (!neg) return -1;  // c = 0
+    *hi = 1.0;            // c = -1
+    return 0;
+  }
+  const double top = (double)(c[t] ^ x);
+  if (t == 0) {
+    *hi = top + 1.0;
+    return 0;
+  }
+  *hi = top * 4294967296.0 + (double)(c[t - 1] ^ x) + 1.0;
+  return t;
+}
+
+// log2 of sum_t acc[t] 2^(32 max(t - 1, 0)), rounded up
+// by the relative error `rel` of the sums that built acc; -INFINITY if empty.
+double log2_scaled_sum(const double *acc, int tmax, double rel) {
+  double mx = -INFINITY;
+  for (int t = 0; t <= tmax; ++t)
+    if (acc[t] > 0.0) mx = std::max(mx, log2(acc[t]) + 32.0 * (t > 0 ? t - 1 : 0));
+  if (mx == -INFINITY) return -INFINITY;
+  double s = 0.0;
+  for (int t = 0; t <= tmax; ++t)
+    if (acc[t] > 0.0) s += exp2(log2(acc[t]) + 32.0 * (t > 0 ? t - 1 : 0) - mx);
+  return mx + log2(s) * (1.0 + 1e-12) + log2(1.0 + rel) + 1e-12;
 }
 
 // log2(sum 2^x_i), upper-rounded a little.
@@ -75,26 +91,33 @@ int analyze(const rs_bipoly *f, PolyInfo &pi, const char **why) {
   pi.L = L;
   pi.stride = ny;
   std::vector<int> dx(ny, -1);
-  std::vector<std::vector<double>> logs(ny);
+  // ||f_j||_1 per row j, kept as sums of hi by limb position (hi < 2^64 + 1,
+  // at most 2^26 terms: the sums stay far below the double range).
+  std::vector<double> acc((size_t)ny * (RS_MAX_LIMBS + 1), 0.0);
+  std::vector<int> tmax(ny, -1);
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < ny; ++j) {
       const uint32_t *c = f->coeffs + ((size_t)i * ny + j) * L;
-      bool nz = false;
-      for (int l = 0; l < L; ++l) nz = nz || c[l] != 0;
-      if (!nz) continue;
+      double hi;
+      const int t = abs_upper(c, L, &hi);
+      if (t < 0) continue;
       dx[j] = i;
       pi.mx = std::max(pi.mx, i);
       pi.tdeg = std::max(pi.tdeg, i + j);
       pi.my = std::max(pi.my, j);
-      logs[j].push_back(log2_abs_upper(c, L));
+      acc[(size_t)j * (RS_MAX_LIMBS + 1) + t] += hi;
+      tmax[j] = std::max(tmax[j], t);
     }
   pi.zero = pi.my < 0;
   if (pi.zero) return RS_OK;
   pi.dx.assign(dx.begin(), dx.begin() + pi.my + 1);
+  // Each double operation errs by at most 2^-53 relative; a row sum of n
+  // terms by at most n 2^-53 (plus the conversions), taken as (n + 4) 2^-52.
+  const double rel = ((double)nx + 4.0) * 0x1p-52;
   std::vector<double> rows;
   for (int j = 0; j <= pi.my; ++j) {
     pi.nc += pi.dx[j] + 1;
-    if (!logs[j].empty()) rows.push_back(2.0 * lse2(logs[j]));
+    if (tmax[j] >= 0) rows.push_back(2.0 * log2_scaled_sum(&acc[(size_t)j * (RS_MAX_LIMBS + 1)], tmax[j], rel));
   }
   pi.log2_rownorm2 = lse2(rows);
   return RS_OK;
