@@ -174,6 +174,10 @@ void rs_free_batch(rs_batch *b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   for (auto &e : b->ev)
     if (e) cudaEventDestroy(e);
+  for (auto &e : b->fev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : b->jev)
+    if (e) cudaEventDestroy(e);
   if (b->arena) {
     if (b->opt.stream_ordered)
       cudaFreeAsync(b->arena, b->stream);
@@ -343,6 +347,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     cl.tile_off = (int64_t)tiles.size();
     for (int i : members) {
       const PairPlan &p = b->plans[i];
+      cl.cost += (double)p.K * p.N * (p.f.nc + p.g.nc + 2.0 * p.f.my * p.g.my);
       cl.smem = std::max(cl.smem, (size_t)rs_g1_staged_words(p, cap, T) * 4);
       for (int k = 0; k < p.K; ++k)
         for (int x0 = 0; x0 < p.N; x0 += T) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T, p.N - x0)});
@@ -350,28 +355,32 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     cl.ntiles = (int)((int64_t)tiles.size() - cl.tile_off);
     if (cl.ntiles > 0) b->classes.push_back(cl);
   }
+  std::stable_sort(b->classes.begin(), b->classes.end(),
+                   [](const RsClassLaunch &x, const RsClassLaunch &y) { return x.cost > y.cost; });
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
-  // G2 launches by point count: blocks of 64, 128 or 256 threads so that each
-  // thread has about two output blocks of the convolutions.
-  const int g2cls_threads[3] = {64, 128, 256};
-  for (int c = 0; c < 3; ++c) {
+  // G2 launches by point count: each thread owns one pair of output blocks
+  // of the convolutions per round; a (pair, prime) gets the fewest rounds
+  // with at most 256 threads, and the fewest warps for them, so the threads
+  // of a block carry equal work (classes of 32, 64, ..., 256 threads).
+  for (int c = 0; c < 8; ++c) {
     RsG2Class gc;
-    gc.threads = g2cls_threads[c];
+    gc.threads = 32 * (c + 1);
     gc.off = (int64_t)g2.size();
     int cmaxN = 0;
     for (int i : byN) {
       const PairPlan &p = b->plans[i];
       const int npair = ((p.N + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;
-      const int cls = npair <= 64 ? 0 : npair <= 128 ? 1 : 2;
-      if (cls != c) continue;
+      const int rounds = (npair + 255) / 256;
+      const int warps = (npair + 32 * rounds - 1) / (32 * rounds);
+      if (warps - 1 != c) continue;
       cmaxN = std::max(cmaxN, p.N);
       for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
     }
     gc.count = (int)((int64_t)g2.size() - gc.off);
     gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
-    if (gc.count > 0 && !images_only) b->g2cls.push_back(gc);
+    if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin(), gc);  // largest point counts first
   }
   const int dthreads = g3_digit_threads(std::max(maxK, 1));
   int64_t ncoef = 0;
@@ -534,6 +543,15 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   if (ctx->cfg.timing || opt.timing)
     for (auto &ev : b->ev)
       if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
+  if (opt.fork && (b->classes.size() > 1 || b->g2cls.size() > 1)) {
+    b->jev.assign(b->classes.size() + b->g2cls.size(), nullptr);
+    for (auto &ev : b->fev)
+      if (rc == RS_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
+    for (auto &ev : b->jev)
+      if (rc == RS_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
+  }
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;
@@ -555,6 +573,29 @@ int rs_upload(rs_batch *b, const rs_bipoly *f, const rs_bipoly *g) {
 
 static cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
   return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+// The launches of one stage are independent (disjoint tiles or tasks): with
+// fork events they run as parallel branches on the context's side streams
+// (inside a captured graph: parallel graph nodes), so the tail of one launch
+// overlaps the next instead of idling SMs.  Branch i of the stage uses side
+// stream i mod 8 and join event j0 + i.
+static cudaStream_t branch_begin(rs_batch *b, int stage, int i, cudaStream_t s, cudaError_t *e) {
+  if (!b->fev[stage]) return s;
+  cudaStream_t si = b->ctx->side[i % 8];
+  if (*e == cudaSuccess && i == 0) *e = cudaEventRecord(b->fev[stage], s);
+  if (*e == cudaSuccess) *e = cudaStreamWaitEvent(si, b->fev[stage], 0);
+  return si;
+}
+
+static void branch_end(rs_batch *b, int stage, int j, cudaStream_t si, cudaError_t *e) {
+  if (!b->fev[stage]) return;
+  if (*e == cudaSuccess) *e = cudaEventRecord(b->jev[j], si);
+}
+
+static void join_all(rs_batch *b, int stage, int j0, int n, cudaStream_t s, cudaError_t *e) {
+  if (!b->fev[stage]) return;
+  for (int j = j0; j < j0 + n && *e == cudaSuccess; ++j) *e = cudaStreamWaitEvent(s, b->jev[j], 0);
 }
 
 static int enqueue(rs_batch *b, bool capturing) {
@@ -587,9 +628,20 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.num = b->d_num;
     a.den = b->d_den;
     a.stats = b->d_stats;
-    RS_CUDA(ctx, launch_g1(cl.cap, cl.threads, cl.blocks, cl.smem, a, s));
+    cudaError_t fe = cudaSuccess;
+    cudaStream_t si = branch_begin(b, 0, ci - 1, s, &fe);
+    RS_CUDA(ctx, fe);
+    RS_CUDA(ctx, launch_g1(cl.cap, cl.threads, cl.blocks, cl.smem, a, si));
+    branch_end(b, 0, ci - 1, si, &fe);
+    RS_CUDA(ctx, fe);
+  }
+  {
+    cudaError_t fe = cudaSuccess;
+    join_all(b, 0, 0, (int)b->classes.size(), s, &fe);
+    RS_CUDA(ctx, fe);
   }
   if (timing) RS_CUDA(ctx, record(b->ev[1], s, capturing));
+  int gi = 0;
   for (const auto &gc : b->g2cls) {
     G2Args a2;
     a2.pairs = b->d_pairs;
@@ -602,7 +654,19 @@ static int enqueue(rs_batch *b, bool capturing) {
     a2.gtab = tab.gtab;
     a2.btab = tab.btab;
     a2.tab_stride = tab.N;
-    RS_CUDA(ctx, launch_g2(gc.threads, gc.count, gc.smem, a2, s));
+    const int j = (int)b->classes.size() + gi;
+    cudaError_t fe = cudaSuccess;
+    cudaStream_t si = branch_begin(b, 1, gi, s, &fe);
+    RS_CUDA(ctx, fe);
+    RS_CUDA(ctx, launch_g2(gc.threads, gc.count, gc.smem, a2, si));
+    branch_end(b, 1, j, si, &fe);
+    RS_CUDA(ctx, fe);
+    ++gi;
+  }
+  {
+    cudaError_t fe = cudaSuccess;
+    join_all(b, 1, (int)b->classes.size(), (int)b->g2cls.size(), s, &fe);
+    RS_CUDA(ctx, fe);
   }
   if (timing) RS_CUDA(ctx, record(b->ev[2], s, capturing));
   if (b->ng3) {
@@ -842,6 +906,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   };
   chk(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, dev), "device query");
   chk(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+  for (auto &ss : ctx->side) chk(cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking), "cudaStreamCreate");
   ctx->primes = rs_prime_table(RS_MAX_PRIMES);
   for (uint32_t p : ctx->primes) ctx->log2p.push_back(log2((double)p) - 1e-12);
   const int np = (int)ctx->primes.size();
@@ -877,6 +942,11 @@ int rs_destroy(rs_ctx *ctx) {
     void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase};
     for (void *p : dev)
       if (p) cudaFree(p);
+    for (auto ss : ctx->side)
+      if (ss) {
+        cudaStreamSynchronize(ss);
+        cudaStreamDestroy(ss);
+      }
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
   }
   delete ctx;

@@ -53,12 +53,14 @@ struct rs_ctx {
   bool g2_ready = false, g3_ready = false;
   std::map<int64_t, int> g1_occupancy;  // (capacity, threads, staged KiB) -> blocks per SM
   std::string tune_path;                 // autotune cache file written at rs_destroy ("" = none)
+  cudaStream_t side[8] = {};             // branches of the fork-join stage launches
 };
 
 struct RsClassLaunch {
   int cap = 0;
   int threads = 128;
   int persistent = 1;
+  double cost = 0.0;  // modular products of the class (launch order: costliest first)
   int blocks = 0;
   int64_t tile_off = 0;
   int ntiles = 0;
@@ -81,6 +83,7 @@ struct RsBatchOpts {
   int64_t h_in_words = 0, h_out_words = 0;
   bool use_graph = true;
   bool persistent = true;
+  bool fork = true;     // run the launches of a stage (capacity / G2 classes) as parallel branches
   bool tune = true;     // time G1 choices for classes missing from the tuner cache
   bool timing = false;  // record stage events even when the context does not time
   int g1_threads = 0;   // > 0: force this tile width (and opt.persistent) for every class
@@ -118,6 +121,8 @@ struct rs_batch {
   bool own_host = false;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fev[2] = {nullptr, nullptr};  // fork points of the G1 and G2 stages
+  std::vector<cudaEvent_t> jev;             // joins of the branches (one per launch of a forked stage)
   bool ran = false;
   rs_batch_info info;
 };

@@ -105,23 +105,28 @@ __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
 // y[k] = sum_{j<=k} x[j] b[k-j] for k < n (Montgomery form, reduced).  x and b
 // hold signed representatives and are zero for indices in [-RS_G2_PAD, 0)
 // and [n, n + RS_G2_PAD).
+//
+// Outputs come in blocks of R; block bi needs bi + 1 chunks of R inputs.
+// Thread t owns the block pair (pi, nblk - 1 - pi), pi = t, t + T, ..., and
+// walks both in one loop of nblk + 1 chunks, so every lane of a warp runs
+// the same trip count (no divergence in the multiply-accumulate loop).  In
+// the loop's first part neighbouring lanes read b and x R words apart (R odd:
+// distinct banks); in its second part every lane reads the same b words (a
+// broadcast).
 __device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n, const ModP &m) {
   constexpr int R = RS_CONV_R;
   const uint32_t c32 = m.r1;  // 2^32 mod p
   const int nblk = (n + R - 1) / R;
-  // Output block bi costs about bi chunks: thread t takes the blocks pi and
-  // nblk - 1 - pi for pi = t, t + T, ..., so every thread gets the same work.
   const int npair = (nblk + 1) / 2;
-  for (int it = 0; it < 2 * ((npair + blockDim.x - 1) / blockDim.x); ++it) {
-    const int pi = threadIdx.x + (int)blockDim.x * (it >> 1);
-    if (pi >= npair) break;
-    const int bi = (it & 1) ? nblk - 1 - pi : pi;
-    if ((it & 1) && bi == pi) continue;  // odd count: the middle block once
-    const int k0 = bi * R;
+  for (int pi = threadIdx.x; pi < npair; pi += blockDim.x) {
+    const int hb = nblk - 1 - pi;
+    const int steps = hb == pi ? pi + 1 : nblk + 1;  // odd count: the middle block once
+    int k0 = pi * R, j0 = 0;
     int64_t acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0;
-    for (int j0 = 0; j0 <= k0; j0 += R) {
+#pragma unroll 1
+    for (int c = 0; c < steps; ++c) {
       int32_t bw[2 * R - 1], av[R];
       const int base = k0 - j0 - (R - 1);
 #pragma unroll
@@ -134,10 +139,17 @@ __device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n
         for (int jj = 0; jj < R; ++jj) acc[r] = rs_mac_s32(acc[r], av[jj], bw[(R - 1) + r - jj]);
         acc[r] = fold64(acc[r], c32);
       }
-    }
+      j0 += R;
+      if (j0 > k0) {  // block complete: write it and move to the mirror block
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (k0 + r < n) y[k0 + r] = finish64(acc[r], m);
+        for (int r = 0; r < R; ++r) {
+          if (k0 + r < n) y[k0 + r] = finish64(acc[r], m);
+          acc[r] = 0;
+        }
+        k0 = hb * R;
+        j0 = 0;
+      }
+    }
   }
 }
 

@@ -162,6 +162,7 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
   o.use_graph = false;
   o.persistent = s->ctx->cfg.persistent != 0;
   o.tune = false;  // cached tuner choices only: timing here would stall the scheduler
+  o.fork = false;  // micro-batches already overlap on the server's streams
   o.h_in = s->h_in[slot];
   o.h_out = s->h_out[slot];
   o.h_in_words = s->h_in_words[slot];
