@@ -93,6 +93,10 @@ typedef struct {
   int32_t autotune;          /* 1 = a batch whose workload class is not in the tuner cache times
                                 the G1 candidates first; 0 = cached choices or the built-in
                                 default (128 points, persistent) */
+  int32_t g2_form;           /* interpolation convolutions: 0 = per pair by a cost model, 1 = direct
+                                (lazily reduced dot products) only, 2 = number-theoretic transforms
+                                wherever D + 1 <= 4096 */
+  int32_t reserved;
   int64_t mem_limit_bytes;   /* serving: device bytes admitted requests may hold; 0 = auto */
   const char *autotune_cache;  /* tuner cache file merged at rs_create (a missing file is not an
                                   error) and rewritten at rs_destroy; NULL = none.  The string

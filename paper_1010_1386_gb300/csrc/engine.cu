@@ -125,6 +125,104 @@ static void free_tables(RsTables &t) {
 // < 2^(31 k), rounded up to a multiple of 32.
 static int p16_row(int k) { return ((31 * k) / 16 + 2 + 31) / 32 * 32; }
 
+// ------------------------------------------------------------ NTT tables
+
+// The three NTT primes c 2^k + 1 (k >= 25) of the transform-based G2, in
+// (2^30, 2^31) and ascending; their product exceeds 2^92.
+static const uint32_t kNttPrimes[3] = {1811939329u, 2013265921u, 2113929217u};
+
+static uint32_t powmod_u32(uint64_t a, uint64_t e, uint32_t P) {
+  uint64_t r = 1;
+  a %= P;
+  while (e) {
+    if (e & 1) r = r * a % P;
+    a = a * a % P;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+// Smallest generator of Z_P^* (P prime): g^((P-1)/r) != 1 for every prime r | P - 1.
+static uint32_t generator_of(uint32_t P) {
+  std::vector<uint32_t> fac;
+  uint32_t n = P - 1;
+  for (uint32_t r = 2; (uint64_t)r * r <= n; ++r)
+    if (n % r == 0) {
+      fac.push_back(r);
+      while (n % r == 0) n /= r;
+    }
+  if (n > 1) fac.push_back(n);
+  for (uint32_t g = 2;; ++g) {
+    bool ok = true;
+    for (uint32_t r : fac) ok = ok && powmod_u32(g, (P - 1) / r, P) != 1;
+    if (ok) return g;
+  }
+}
+
+// Constants and twiddles [q][forward, inverse][2^LGMAX] as (w, floor(w 2^32 / P)):
+// for each length 2^lg a row of w_L^j (forward) or w_L^-j (inverse), j < 2^(lg-1),
+// starting at 2^(lg-1) - 1.
+static void ntt_host_tables(NttConst &nc, std::vector<uint2> &tw) {
+  const int ROW = 1 << RS_NTT_LGMAX;
+  tw.assign((size_t)6 * ROW, make_uint2(0, 0));
+  for (int q = 0; q < 3; ++q) {
+    const uint32_t P = kNttPrimes[q];
+    nc.m[q] = make_modp(P);
+    const uint32_t wmax = powmod_u32(generator_of(P), (P - 1) >> RS_NTT_LGMAX, P);
+    for (int lg = 1; lg <= RS_NTT_LGMAX; ++lg) {
+      const uint32_t w = powmod_u32(wmax, (uint64_t)1 << (RS_NTT_LGMAX - lg), P);
+      const uint32_t wi = powmod_u32(w, P - 2, P);
+      const int n = 1 << (lg - 1);
+      uint64_t f = 1, b = 1;
+      for (int j = 0; j < n; ++j) {
+        tw[(size_t)(2 * q) * ROW + (n - 1) + j] = make_uint2((uint32_t)f, (uint32_t)((f << 32) / P));
+        tw[(size_t)(2 * q + 1) * ROW + (n - 1) + j] = make_uint2((uint32_t)b, (uint32_t)((b << 32) / P));
+        f = f * w % P;
+        b = b * wi % P;
+      }
+    }
+  }
+  const uint32_t P0 = kNttPrimes[0], P1 = kNttPrimes[1], P2 = kNttPrimes[2];
+  const uint64_t R1 = ((uint64_t)1 << 32) % P1, R2 = ((uint64_t)1 << 32) % P2;
+  nc.c01 = (uint32_t)((uint64_t)powmod_u32(P0, P1 - 2, P1) * R1 % P1);
+  nc.p0_m2 = (uint32_t)((uint64_t)P0 % P2 * R2 % P2);
+  const uint32_t p01 = (uint32_t)((uint64_t)P0 * P1 % P2);
+  nc.c012 = (uint32_t)((uint64_t)powmod_u32(p01, P2 - 2, P2) * R2 % P2);
+}
+
+int rs_g2_ntt_lg(int N) {
+  int lg = 1;
+  while ((1 << lg) < 2 * N - 1) ++lg;
+  if (lg > RS_NTT_LGMAX) return 0;
+  // Issued instructions, from counters: a direct multiply-accumulate costs
+  // about 3.8, a butterfly with its shared-memory traffic about 12, and each
+  // (pair, prime) takes 12 transforms of (L/2) lg butterflies.
+  const double direct = 3.8 * (double)N * N, ntt = 12.0 * 12.0 * (double)(1 << (lg - 1)) * lg + 60.0 * N;
+  return ntt < direct ? lg : 0;
+}
+
+int rs_ensure_bhat(rs_ctx *ctx, int lg, int K) {
+  const int L = 1 << lg;
+  int rc = rs_ensure_tables(ctx, K, L / 2, 0);  // b_t for every t < L/2
+  if (rc != RS_OK) return rc;
+  std::lock_guard<std::mutex> lock(ctx->tab_mu);
+  if (ctx->bhat_K[lg] >= K) return RS_OK;
+  const RsTables &t = ctx->tab;
+  DevGuard dg(ctx->device);
+  uint32_t *nb = nullptr;
+  cudaError_t e = cudaMalloc(&nb, (size_t)t.K * 3 * L * 4);
+  if (e == cudaSuccess) e = launch_bhat(t.btab, t.N, t.N, t.K, lg, ctx->d_ntt_tw, ctx->nttc, nb, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (nb) cudaFree(nb);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("transform tables: ") + cudaGetErrorString(e));
+  }
+  if (ctx->bhat[lg]) ctx->bhat_retired.push_back(ctx->bhat[lg]);
+  ctx->bhat[lg] = nb;
+  ctx->bhat_K[lg] = t.K;
+  return RS_OK;
+}
+
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   std::lock_guard<std::mutex> lock(ctx->tab_mu);
   const int need_c = N + 128 + dx + 1;
@@ -364,6 +462,40 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // of the convolutions per round; a (pair, prime) gets the fewest rounds
   // with at most 256 threads, and the fewest warps for them, so the threads
   // of a block carry equal work (classes of 32, 64, ..., 256 threads).
+  // Pairs whose transform-based G2 is cheaper go to one launch per transform
+  // length instead (256 threads, shared memory 3 N + 2^lg words).
+  std::vector<int> g2lg(n, 0);
+  int bhatK[RS_NTT_LGMAX + 1] = {};
+  if (!images_only)
+    for (int i : byN) {
+      const int N = b->plans[i].N;
+      if (ctx->cfg.g2_form == 1) {
+        g2lg[i] = 0;
+      } else if (ctx->cfg.g2_form == 2) {
+        int lg = 1;
+        while ((1 << lg) < 2 * N - 1) ++lg;
+        g2lg[i] = lg <= RS_NTT_LGMAX ? lg : 0;
+      } else {
+        g2lg[i] = rs_g2_ntt_lg(N);
+      }
+      bhatK[g2lg[i]] = std::max(bhatK[g2lg[i]], b->plans[i].K);
+    }
+  for (int lg = RS_NTT_LGMAX; lg > 0; --lg) {
+    if (!bhatK[lg]) continue;
+    RsG2Class gc;
+    gc.lg = lg;
+    gc.off = (int64_t)g2.size();
+    int cmaxN = 0;
+    for (int i : byN) {
+      if (g2lg[i] != lg) continue;
+      cmaxN = std::max(cmaxN, b->plans[i].N);
+      for (int k = 0; k < b->plans[i].K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
+    }
+    gc.count = (int)((int64_t)g2.size() - gc.off);
+    gc.smem = (size_t)(3 * ((cmaxN + 3) & ~3) + 2 * (1 << lg)) * 4;
+    b->g2cls.push_back(gc);
+  }
+  const int nlg = (int)b->g2cls.size();
   for (int c = 0; c < 8; ++c) {
     RsG2Class gc;
     gc.threads = 32 * (c + 1);
@@ -371,6 +503,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     int cmaxN = 0;
     for (int i : byN) {
       const PairPlan &p = b->plans[i];
+      if (g2lg[i]) continue;
       const int npair = ((p.N + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;
       const int rounds = (npair + 255) / 256;
       const int warps = (npair + 32 * rounds - 1) / (32 * rounds);
@@ -380,7 +513,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     }
     gc.count = (int)((int64_t)g2.size() - gc.off);
     gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
-    if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin(), gc);  // largest point counts first
+    if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin() + nlg, gc);  // largest point counts first
   }
   const int dthreads = g3_digit_threads(std::max(maxK, 1));
   int64_t ncoef = 0;
@@ -416,6 +549,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
 
   int rc = RS_OK;
   if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxN, maxDx);
+  for (int lg = 1; lg <= RS_NTT_LGMAX && rc == RS_OK; ++lg)
+    if (bhatK[lg]) rc = rs_ensure_bhat(ctx, lg, bhatK[lg]);
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;
@@ -515,6 +650,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       cudaError_t e2 = g3_prepare(b->kmax);
       if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
       ctx->g3_ready = e2 == cudaSuccess;
+    }
+    if (rc == RS_OK && nlg > 0 && !ctx->g2n_ready) {
+      cudaError_t e2 = g2n_prepare();
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
+      ctx->g2n_ready = e2 == cudaSuccess;
     }
     if (rc == RS_OK && !b->g2cls.empty() && !ctx->g2_ready) {
       cudaError_t e2 = g2_prepare(b->g2smem);
@@ -641,8 +781,38 @@ static int enqueue(rs_batch *b, bool capturing) {
     RS_CUDA(ctx, fe);
   }
   if (timing) RS_CUDA(ctx, record(b->ev[1], s, capturing));
+  uint32_t *bhat[RS_NTT_LGMAX + 1];
+  {
+    std::lock_guard<std::mutex> lock(ctx->tab_mu);
+    for (int l = 0; l <= RS_NTT_LGMAX; ++l) bhat[l] = ctx->bhat[l];
+  }
   int gi = 0;
   for (const auto &gc : b->g2cls) {
+    if (gc.lg > 0) {
+      G2nArgs an;
+      an.pairs = b->d_pairs;
+      an.tasks = b->d_g2 + gc.off;
+      an.mods = ctx->d_mods;
+      an.num = b->d_num;
+      an.den = b->d_den;
+      an.coef = b->d_num;
+      an.finv = tab.finv;
+      an.gtab = tab.gtab;
+      an.tab_stride = tab.N;
+      an.tw = ctx->d_ntt_tw;
+      an.bhat = bhat[gc.lg];
+      an.nc = ctx->nttc;
+      an.lg = gc.lg;
+      const int j = (int)b->classes.size() + gi;
+      cudaError_t fe = cudaSuccess;
+      cudaStream_t si = branch_begin(b, 1, gi, s, &fe);
+      RS_CUDA(ctx, fe);
+      RS_CUDA(ctx, launch_g2n(gc.count, gc.smem, an, si));
+      branch_end(b, 1, j, si, &fe);
+      RS_CUDA(ctx, fe);
+      ++gi;
+      continue;
+    }
     G2Args a2;
     a2.pairs = b->d_pairs;
     a2.tasks = b->d_g2 + gc.off;
@@ -878,6 +1048,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
     rs_config_default(&c);
   if (c.tile_points != 0 && c.tile_points != 32 && c.tile_points != 64 && c.tile_points != 128)
     return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
+  if (c.g2_form < 0 || c.g2_form > 2) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1 or 2");
   int dev = c.device;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -919,6 +1090,12 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   if (rc == RS_OK)
     chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->stream),
         "prime tables");
+  if (rc == RS_OK) {
+    std::vector<uint2> tw;
+    ntt_host_tables(ctx->nttc, tw);
+    chk(cudaMalloc(&ctx->d_ntt_tw, tw.size() * sizeof(uint2)), "cudaMalloc");
+    if (rc == RS_OK) chk(cudaMemcpy(ctx->d_ntt_tw, tw.data(), tw.size() * sizeof(uint2), cudaMemcpyHostToDevice), "cudaMemcpy");
+  }
   if (rc == RS_OK) chk(cudaStreamSynchronize(ctx->stream), "prime tables");
   if (rc != RS_OK) {
     rs_destroy(ctx);
@@ -939,7 +1116,10 @@ int rs_destroy(rs_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_tables(ctx->tab);
     for (auto &t : ctx->retired) free_tables(t);
-    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase};
+    for (uint32_t *bh : ctx->bhat)
+      if (bh) cudaFree(bh);
+    for (void *bh : ctx->bhat_retired) cudaFree(bh);
+    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw};
     for (void *p : dev)
       if (p) cudaFree(p);
     for (auto ss : ctx->side)

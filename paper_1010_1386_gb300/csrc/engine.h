@@ -54,6 +54,16 @@ struct rs_ctx {
   std::map<int64_t, int> g1_occupancy;  // (capacity, threads, staged KiB) -> blocks per SM
   std::string tune_path;                 // autotune cache file written at rs_destroy ("" = none)
   cudaStream_t side[8] = {};             // branches of the fork-join stage launches
+  // Transform-based G2: NTT primes and twiddles, and per transform length 2^lg
+  // the transformed interpolation kernels of the first bhat_K[lg] primes
+  // (guarded by tab_mu; grown tables keep their old allocation until the
+  // context is destroyed).
+  NttConst nttc;
+  uint2 *d_ntt_tw = nullptr;
+  uint32_t *bhat[RS_NTT_LGMAX + 1] = {};
+  int bhat_K[RS_NTT_LGMAX + 1] = {};
+  std::vector<void *> bhat_retired;
+  bool g2n_ready = false;
 };
 
 struct RsClassLaunch {
@@ -68,6 +78,7 @@ struct RsClassLaunch {
 };
 
 struct RsG2Class {
+  int lg = 0;  // > 0: transform-based G2 of length 2^lg (256 threads); 0: direct convolutions
   int threads = 256;
   int64_t off = 0;  // first task of the class in the G2 task list
   int count = 0;
@@ -134,6 +145,11 @@ int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
 bool rs_same_shape(const PairPlan &a, const PairPlan &b);
 int64_t rs_input_words(const rs_bipoly &p);
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx);
+// Transformed interpolation kernels of length 2^lg for at least K primes.
+int rs_ensure_bhat(rs_ctx *ctx, int lg, int K);
+// Transform length exponent for the G2 of a pair with N points when the
+// transform-based form is cheaper than direct convolutions, else 0.
+int rs_g2_ntt_lg(int N);
 int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                    std::vector<PairPlan> &&plans, const RsBatchOpts &opt, rs_batch **out);
 // Byte sizes a batch of these plans needs (device arena, host staging in/out).

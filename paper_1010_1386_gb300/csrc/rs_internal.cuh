@@ -11,6 +11,8 @@
 #define RS_G2_PAD 8          // zero words around each G2 shared-memory region
 #define RS_CONV_R 7          // G2 outputs per register block; odd, so lanes hit distinct banks
 #define RS_G2_MAX_SMEM_BYTES (3 * (16384 + 2 * RS_G2_PAD) * 4)
+#define RS_NTT_LGMAX 13      // G2 transforms up to 2^13 points (N <= 2^12)
+#define RS_G2N_MAX_SMEM_BYTES ((3 * 4096 + 2 * (1 << RS_NTT_LGMAX)) * 4)
 
 // Stage counters written by the kernels (detection of unlucky / degenerate cases).
 enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT = 4 };
@@ -73,6 +75,30 @@ struct G2Args {
   int32_t tab_stride;
 };
 
+// The three NTT primes P0 < P1 < P2 of the transform-based G2 (each
+// c 2^k + 1 with k >= 25, in (2^30, 2^31)) and their Garner constants.
+struct NttConst {
+  ModP m[3];
+  uint32_t c01;    // P0^-1 mod P1, Montgomery form
+  uint32_t p0_m2;  // P0 R mod P2 (mmul(v, p0_m2) = v P0 mod P2)
+  uint32_t c012;   // (P0 P1)^-1 mod P2, Montgomery form
+};
+
+struct G2nArgs {
+  const PairDesc *pairs;
+  const int2 *tasks;       // (pair, prime), all with transform length 2^lg
+  const ModP *mods;
+  const uint32_t *num, *den;
+  uint32_t *coef;          // out (may alias num)
+  const uint32_t *finv, *gtab;  // as in G2Args
+  int32_t tab_stride;
+  const uint2 *tw;         // [q][forward, inverse][2^RS_NTT_LGMAX]: rows of 2^(lg-1) twiddles
+                           // (w_L^j, Shoup quotient), L = 2^lg, starting at 2^(lg-1) - 1
+  const uint32_t *bhat;    // [prime][q][2^lg] transformed interpolation kernel / 2^lg (Montgomery mod P_q)
+  NttConst nc;
+  int32_t lg;
+};
+
 struct G3Args {
   const PairDesc *pairs;
   const int2 *tasks;       // (pair, first coefficient) per block
@@ -97,6 +123,10 @@ int g1_supported_cap(int cap);           // smallest compiled register capacity 
 cudaError_t g1_prepare(int cap, int threads, size_t smem, int *max_blocks_per_sm);
 cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cudaStream_t s);
 cudaError_t g2_prepare(size_t smem);
+cudaError_t g2n_prepare();
+cudaError_t launch_g2n(int blocks, size_t smem, const G2nArgs &a, cudaStream_t s);
+cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
+                        const NttConst &nc, uint32_t *bhat, cudaStream_t s);
 cudaError_t launch_g3(int nd, int dthreads, int nw, int nb, int nc, const G3Args &a, const int2 *dtasks,
                       const int2 *wtasks, const int2 *otasks, cudaStream_t s);
 int g3_digit_threads(int kmax);  // coefficients per digit block (shared memory: threads * kmax words)

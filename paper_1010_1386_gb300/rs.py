@@ -37,6 +37,7 @@ class rs_upoly(ctypes.Structure):
 class rs_config(ctypes.Structure):
     _fields_ = [("device", c_int32), ("tile_points", c_int32), ("use_graphs", c_int32),
                 ("persistent", c_int32), ("timing", c_int32), ("autotune", c_int32),
+                ("g2_form", c_int32), ("reserved", c_int32),
                 ("mem_limit_bytes", c_int64), ("autotune_cache", c_char_p)]
 
 
@@ -189,7 +190,7 @@ class Context:
     """One librs context (device memory, stream, prime tables) on one GPU."""
 
     def __init__(self, device=-1, tile_points=0, use_graphs=True, persistent=True, timing=False,
-                 mem_limit_bytes=0, autotune=True, autotune_cache=None):
+                 mem_limit_bytes=0, autotune=True, autotune_cache=None, g2_form=0):
         lib = load()
         cfg = rs_config()
         _check(lib.rs_config_default(ctypes.byref(cfg)))
@@ -197,6 +198,7 @@ class Context:
         cfg.use_graphs, cfg.persistent, cfg.timing = int(use_graphs), int(persistent), int(timing)
         cfg.mem_limit_bytes = mem_limit_bytes
         cfg.autotune = int(autotune)
+        cfg.g2_form = int(g2_form)
         cfg.autotune_cache = os.fsencode(autotune_cache) if autotune_cache else None
         h = c_void_p()
         _check(lib.rs_create(ctypes.byref(h), ctypes.byref(cfg)))

@@ -129,4 +129,5 @@ def test_config_layout(lib):
     assert (cfg.device, cfg.tile_points, cfg.use_graphs, cfg.persistent, cfg.timing, cfg.autotune) == \
         (-1, 0, 1, 1, 0, 1)
     assert cfg.mem_limit_bytes == 0 and cfg.autotune_cache is None
-    assert rs.rs_config.mem_limit_bytes.offset == 24 and rs.rs_config.autotune_cache.offset == 32
+    assert cfg.g2_form == 0
+    assert rs.rs_config.mem_limit_bytes.offset == 32 and rs.rs_config.autotune_cache.offset == 40

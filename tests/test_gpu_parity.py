@@ -180,9 +180,42 @@ def test_batch_full_size_sampled(ctx):
 
 
 def test_nongeneric_literal_is_zero(ctx):
-    pairs = inputs.workload_nongeneric(3, n=4)
-    for R in ctx.resultant_batch(pairs):
-        assert R == []
+    """All 32 pairs of the literal topology workload at full size: q divides
+    f and g, so every resultant is exactly zero (and every image degenerate)."""
+    pairs = inputs.workload_nongeneric(3, n=32)
+    with rs.Context(device=0, timing=True) as c:
+        b = c.batch(pairs)
+        b.run()
+        got = b.results()
+        info = b.info()
+        b.close()
+    assert all(R == [] for R in got)
+    assert info["degenerate_images"] == info["images"]
+
+
+def test_nongeneric_coprime_full_size(ctx):
+    """The coprime topology workload at full size (f = p q^2, g = d(pq)/dy,
+    total degrees 48 and 35, 64-bit coefficients): sampled values against
+    the oracle for every pair, and for the first pair the exact identity
+    Res_y(p q^2, g) = Res_y(p, g) Res_y(q, g)^2 from three GPU resultants."""
+    pairs = inputs.workload_nongeneric(3, n=32, coprime=True)
+    got = ctx.resultant_batch(pairs)
+    rng = random.Random(31)
+    for (f, g), R in zip(pairs, got):
+        b = rs.result_bound(f, g)
+        assert len(R) - 1 <= b["deg"]
+        assert R and max(abs(c) for c in R).bit_length() < b["bits"]
+        check_sampled_31(f.to_ints(), g.to_ints(), R, rng, samples=1)
+    # the generator's first draw, replayed: p and q of pair 0
+    from paper_1010_1386_gb300.inputs import _dy, _from_dict, _mul_dict, _to_dict
+    g0 = np.random.Generator(np.random.PCG64(3))
+    p = inputs.dense_total_degree(g0, 24, 64).to_ints()
+    q = inputs.dense_total_degree(g0, 12, 64).to_ints()
+    PQ = _mul_dict(_to_dict(p), _to_dict(q))
+    f0, gg = _from_dict(_mul_dict(PQ, _to_dict(q))), _from_dict(_dy(PQ))
+    assert f0 == pairs[0][0].to_ints() and gg == pairs[0][1].to_ints()
+    Rp, Rq = ctx.resultant_batch([(p, gg), (q, gg)])
+    assert got[0] == exact.zx_mul(Rp, exact.zx_mul(Rq, Rq))
 
 
 def test_nongeneric_coprime_multiplicative(ctx):
@@ -200,6 +233,31 @@ def test_nongeneric_coprime_multiplicative(ctx):
     Rf, Rp, Rq = ctx.resultant_batch([(f, g), (p, g), (q, g)])
     assert Rf == exact.zx_mul(Rp, exact.zx_mul(Rq, Rq))
     check_sampled_31(f, g, Rf, random.Random(9), samples=2)
+
+
+def test_g2_transform_and_direct_forms_agree():
+    """The interpolation stage by number-theoretic transforms (three NTT
+    primes, exact integer convolutions) and by direct lazily reduced dot
+    products give the same residues, so the same resultants bit for bit:
+    point counts at and around transform-length boundaries (N = 2^k + 1 needs
+    the next length), tiny degrees, and the batched workload's first pairs;
+    small pairs also against the oracle."""
+    rng = random.Random(17)
+    pairs = []
+    for dx, dy in [(0, 1), (1, 1), (1, 2), (2, 3), (8, 16), (16, 16), (16, 32), (1, 64), (24, 40), (40, 40)]:
+        bits = rng.choice([8, 31, 64])
+        pairs.append((rand_bipoly(rng, dx, dy, bits=bits), rand_bipoly(rng, dx, dy, bits=bits)))
+    pairs += [(f.to_ints(), g.to_ints()) for f, g in inputs.workload_batch(2, n=512)[:24]]
+    got = {}
+    for form in (1, 2, 0):
+        with rs.Context(device=0, g2_form=form) as c:
+            got[form] = c.resultant_batch(pairs)
+    assert got[1] == got[2] and got[0] == got[1]
+    for (f, g), R in list(zip(pairs, got[2]))[:4]:
+        assert R == oracle(f, g)
+    rng2 = random.Random(18)
+    for (f, g), R in list(zip(pairs, got[2]))[4:10]:
+        check_sampled_31(f, g, R, rng2, samples=1)
 
 
 def test_maximum_capacity_and_limbs(ctx):

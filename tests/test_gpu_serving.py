@@ -11,7 +11,7 @@ import pytest
 
 from oracle import exact
 from paper_1010_1386_gb300 import inputs, rs
-from tests.helpers import check_sampled_31
+from tests.helpers import check_sampled_31, exact_points
 
 pytestmark = pytest.mark.gpu
 
@@ -113,3 +113,31 @@ def test_errors_and_timeouts():
             r = srv.wait(t)
         assert r is not None
         srv.stop()
+
+
+def test_serving_workload_sample_through_the_server():
+    """The first 64 requests of the serving stream (total degrees 8..64,
+    16..128-bit coefficients) through the server: each equals the batched
+    result bit for bit, lies within the degree and coefficient bounds and
+    matches the oracle at a random point modulo a prime outside the
+    library's table; the two smallest are checked exactly at x = 0."""
+    pairs, _ = inputs.workload_serving(4, n=64)
+    with rs.Context(device=0) as ctx:
+        batched = ctx.resultant_batch(pairs)
+        srv = rs.Server(ctx, max_inflight=4, max_batch=16)
+        tickets = [srv.submit(f, g) for f, g in pairs]
+        got = [srv.wait(t, timeout_us=120_000_000)[0] for t in tickets]
+        st = srv.stats()
+        srv.stop()
+    assert st["failed"] == 0 and st["completed"] == 64
+    rng = random.Random(44)
+    small = sorted(range(64), key=lambda i: pairs[i][0].deg_x + pairs[i][1].deg_x)[:2]
+    for i, ((f, g), R) in enumerate(zip(pairs, got)):
+        assert R == batched[i], f"request {i}: server and batch differ"
+        b = rs.result_bound(f, g)
+        assert len(R) - 1 <= b["deg"]
+        assert not R or max(abs(c) for c in R).bit_length() < b["bits"]
+        F, G = f.to_ints(), g.to_ints()
+        check_sampled_31(F, G, R, rng, samples=1)
+        if i in small:
+            exact_points(F, G, R, points=(0,))
