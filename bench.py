@@ -359,10 +359,12 @@ def batch_main(args, world, rank, local, dist):
         "e2e": {"value": e2e_val, "unit": "resultants/s", "h2d_bytes_per_step": info["input_bytes"],
                 "d2h_bytes_per_step": info["output_bytes"]},
         "autotune": {"build_s": t_tune,
-                     "classes": [{"cap": e["cap"], "lg_points": e["lg_points"],
-                                  "lg_images": e["lg_images"], "tile_points": e["tile_points"],
+                     "classes": [{"stage": "G1" if e["kind"] == 0 else "G2", "cap": e["cap"],
+                                  "lg_points": e["lg_points"], "lg_images": e["lg_images"],
+                                  "choice": (e["choice"] if e["kind"] == 0 else
+                                             ("transforms" if e["choice"] else "direct")),
                                   "persistent": e["persistent"],
-                                  "g1_gain": (e["ms_default"] / e["ms_best"]) if e["ms_best"] else None}
+                                  "gain": (e["ms_default"] / e["ms_best"]) if e["ms_best"] else None}
                                  for e in tuned]},
         "detections": {"unlucky_points": info["unlucky_points"],
                        "degenerate_images": info["degenerate_images"],

@@ -209,13 +209,25 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
  * class's pairs (a stride sample of at most 2^22 images) for each of the six
  * candidates, times their G1 launches with CUDA events (median of three
  * after one warm-up) and caches the fastest; the built-in default is kept
- * unless another candidate is more than 2% faster.  The server never tunes;
- * it uses cached choices, so warm the cache with rs_autotune first.
+ * unless another candidate is more than 2% faster.  The interpolation stage
+ * (G2) has one more free choice per pair: direct convolutions or
+ * number-theoretic transforms (for D + 1 <= 4096).  Pairs are grouped by
+ * transform length 2^lg; for a group missing from the cache the tuner times
+ * the whole path on a sample with each form and keeps the faster G2 (the
+ * instruction-count model's choice unless the other is more than 2%
+ * faster).  The server never tunes; it uses cached choices, so warm the
+ * cache with rs_autotune first.
  * --------------------------------------------------------------------- */
+enum { RS_TUNE_G1 = 0, RS_TUNE_G2 = 1 };
+
 typedef struct {
-  int32_t sms, cap, lg_points, lg_images;  /* the class */
-  int32_t tile_points, persistent;         /* the choice */
-  float ms_best, ms_default;               /* G1 time of the choice and of the default on the
+  int32_t kind;                            /* RS_TUNE_G1: image-stage launch; RS_TUNE_G2:
+                                              interpolation form */
+  int32_t sms, cap, lg_points, lg_images;  /* the class; for RS_TUNE_G2 cap is 0 and lg_points
+                                              is log2 of the transform length */
+  int32_t choice, persistent;              /* RS_TUNE_G1: tile points and schedule;
+                                              RS_TUNE_G2: 1 = transforms, 0 = direct (persistent 0) */
+  float ms_best, ms_default;               /* stage time of the choice and of the default on the
                                               tuning sample (0 when loaded without timings) */
 } rs_tune_entry;
 
@@ -226,7 +238,7 @@ int rs_autotune(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g);
  * cap_entries is 0); *count receives the number cached.  Host only. */
 int rs_autotune_entries(rs_tune_entry *out, int32_t cap_entries, int32_t *count);
 /* Write the cache as text, one class per line:
- *   sms cap lg_points lg_images tile_points persistent ms_best ms_default
+ *   kind sms cap lg_points lg_images choice persistent ms_best ms_default
  * after a '#' header line.  Host only. */
 int rs_autotune_save(const char *path);
 /* Merge a file written by rs_autotune_save into the cache (its entries win).

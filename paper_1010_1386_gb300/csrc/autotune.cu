@@ -1,7 +1,9 @@
-// Tuner of the G1 launch (tile width and schedule) per workload class, with a
-// process-wide cache and its text file form.  The candidates change only how
-// the (pair, prime, point) work list is cut into blocks and handed to SMs;
-// every image, and so every result, is the same under each of them.
+// Tuner of the G1 launch (tile width and schedule) and of the G2 form
+// (direct convolutions or number-theoretic transforms) per workload class,
+// with a process-wide cache and its text file form.  The G1 candidates change
+// only how the (pair, prime, point) work list is cut into blocks and handed
+// to SMs, and both G2 forms compute the same residues, so every result is
+// the same under each choice.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -32,18 +34,38 @@ int ilog2(int64_t v) {
   return r;
 }
 
-void unpack_key(int64_t key, int *sms, int *cap, int *lgN, int *lgI) {
-  *sms = (int)(key >> 32);
-  *cap = (int)((key >> 16) & 0xffff);
-  *lgN = (int)((key >> 8) & 0xff);
-  *lgI = (int)(key & 0xff);
+int64_t make_key(int kind, int sms, int cap, int lgN, int lgI) {
+  return ((int64_t)kind << 48) | ((int64_t)sms << 32) | ((int64_t)cap << 16) | ((int64_t)lgN << 8) | (int64_t)lgI;
+}
+
+void unpack_key(int64_t key, rs_tune_entry &e) {
+  e.kind = (int)(key >> 48);
+  e.sms = (int)((key >> 32) & 0xffff);
+  e.cap = (int)((key >> 16) & 0xffff);
+  e.lg_points = (int)((key >> 8) & 0xff);
+  e.lg_images = (int)(key & 0xff);
 }
 
 bool valid_entry(const rs_tune_entry &e) {
-  return e.sms > 0 && e.sms < 65536 && e.cap >= 8 && e.cap <= 72 && e.cap % 8 == 0 && e.lg_points >= 0 &&
-         e.lg_points < 32 && e.lg_images >= 0 && e.lg_images < 64 &&
-         (e.tile_points == 32 || e.tile_points == 64 || e.tile_points == 128) &&
-         (e.persistent == 0 || e.persistent == 1) && e.ms_best >= 0.f && e.ms_default >= 0.f;
+  const bool common = e.sms > 0 && e.sms < 65536 && e.lg_points >= 0 && e.lg_points < 32 && e.lg_images >= 0 &&
+                      e.lg_images < 64 && e.ms_best >= 0.f && e.ms_default >= 0.f;
+  if (e.kind == RS_TUNE_G1)
+    return common && e.cap >= 8 && e.cap <= 72 && e.cap % 8 == 0 &&
+           (e.choice == 32 || e.choice == 64 || e.choice == 128) && (e.persistent == 0 || e.persistent == 1);
+  if (e.kind == RS_TUNE_G2)
+    return common && e.cap == 0 && e.lg_points >= 1 && e.lg_points <= RS_NTT_LGMAX && (e.choice == 0 || e.choice == 1) &&
+           e.persistent == 0;
+  return false;
+}
+
+rs_tune_entry to_entry(int64_t key, const RsG1Choice &c) {
+  rs_tune_entry e;
+  unpack_key(key, e);
+  e.choice = c.threads;
+  e.persistent = c.persistent;
+  e.ms_best = c.ms_best;
+  e.ms_default = c.ms_default;
+  return e;
 }
 
 // G1 time (ms, median of kRuns) of one candidate on the sample.
@@ -82,8 +104,11 @@ int time_candidate(rs_ctx *ctx, const std::vector<rs_bipoly> &F, const std::vect
 }  // namespace
 
 int64_t rs_tune_key(int sms, int cap, int max_points, int64_t images) {
-  return ((int64_t)sms << 32) | ((int64_t)cap << 16) | ((int64_t)ilog2(std::max(max_points, 1)) << 8) |
-         (int64_t)ilog2(std::max<int64_t>(images, 1));
+  return make_key(RS_TUNE_G1, sms, cap, ilog2(std::max(max_points, 1)), ilog2(std::max<int64_t>(images, 1)));
+}
+
+int64_t rs_tune_key_g2(int sms, int lg, int64_t images) {
+  return make_key(RS_TUNE_G2, sms, 0, lg, ilog2(std::max<int64_t>(images, 1)));
 }
 
 bool rs_tune_find(int64_t key, RsG1Choice *out) {
@@ -137,6 +162,69 @@ int rs_tune_g1(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::v
   return RS_OK;
 }
 
+// G2 time (ms, median of kRuns) of the whole path on the sample with one form.
+static int time_g2_form(rs_ctx *ctx, const std::vector<rs_bipoly> &F, const std::vector<rs_bipoly> &G,
+                        const std::vector<PairPlan> &P, int form, float *ms) {
+  RsBatchOpts o;
+  o.use_graph = false;
+  o.persistent = ctx->cfg.persistent != 0;
+  o.tune = false;
+  o.timing = true;
+  o.g2_force = form;
+  std::vector<PairPlan> plans(P);
+  rs_batch *b = nullptr;
+  int rc = rs_build_batch(ctx, (int)F.size(), F.data(), G.data(), std::move(plans), o, &b);
+  if (rc != RS_OK) return rc;
+  rc = rs_upload(b, F.data(), G.data());
+  std::vector<float> t;
+  for (int r = 0; rc == RS_OK && r <= kRuns; ++r) {
+    rc = rs_run(b);
+    if (rc != RS_OK) break;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    float v = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&v, b->ev[1], b->ev[2]);
+    if (e != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("tuner: ") + cudaGetErrorString(e));
+    if (r > 0) t.push_back(v);
+  }
+  rs_free_batch(b);
+  if (rc != RS_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return RS_OK;
+}
+
+int rs_tune_g2(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::vector<PairPlan> &plans,
+               const std::vector<int> &members, int64_t key, int model_form, int *form) {
+  int64_t total = 0;
+  for (int i : members) total += (int64_t)plans[i].K * plans[i].N;
+  const int64_t stride = std::max<int64_t>(1, (total + kSampleImages - 1) / kSampleImages);
+  std::vector<rs_bipoly> F, G;
+  std::vector<PairPlan> P;
+  for (size_t s = 0; s < members.size(); s += (size_t)stride) {
+    F.push_back(f[members[s]]);
+    G.push_back(g[members[s]]);
+    P.push_back(plans[members[s]]);
+  }
+  float ms[2] = {0.f, 0.f};
+  for (int fm = 0; fm < 2; ++fm) {
+    const int rc = time_g2_form(ctx, F, G, P, fm, &ms[fm]);
+    if (rc != RS_OK) return rc;
+  }
+  int best = model_form;
+  if (ms[1 - model_form] * kKeepDefault < ms[model_form]) best = 1 - model_form;
+  RsG1Choice c;
+  c.threads = best;
+  c.persistent = 0;
+  c.ms_best = ms[best];
+  c.ms_default = ms[model_form];
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_cache[key] = c;
+  }
+  *form = best;
+  return RS_OK;
+}
+
 extern "C" {
 
 int rs_autotune(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g) {
@@ -145,8 +233,7 @@ int rs_autotune(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g) 
   std::vector<PairPlan> plans;
   int first = RS_OK;
   rs_plan_all(ctx, n, f, g, plans, nullptr, &first);
-  RsBatchOpts o;
-  o.images_only = true;  // the tuning happens while the batch is built; nothing is run
+  RsBatchOpts o;  // the tuning happens while the batch is built; nothing is run
   o.use_graph = false;
   o.persistent = ctx->cfg.persistent != 0;
   o.tune = true;
@@ -162,14 +249,7 @@ int rs_autotune_entries(rs_tune_entry *out, int32_t cap_entries, int32_t *count)
   std::lock_guard<std::mutex> lock(g_mu);
   int i = 0;
   for (const auto &kv : g_cache) {
-    if (i < cap_entries) {
-      rs_tune_entry &e = out[i];
-      unpack_key(kv.first, &e.sms, &e.cap, &e.lg_points, &e.lg_images);
-      e.tile_points = kv.second.threads;
-      e.persistent = kv.second.persistent;
-      e.ms_best = kv.second.ms_best;
-      e.ms_default = kv.second.ms_default;
-    }
+    if (i < cap_entries) out[i] = to_entry(kv.first, kv.second);
     ++i;
   }
   *count = (int32_t)g_cache.size();
@@ -181,22 +261,14 @@ int rs_autotune_save(const char *path) {
   std::vector<rs_tune_entry> v;
   {
     std::lock_guard<std::mutex> lock(g_mu);
-    for (const auto &kv : g_cache) {
-      rs_tune_entry e;
-      unpack_key(kv.first, &e.sms, &e.cap, &e.lg_points, &e.lg_images);
-      e.tile_points = kv.second.threads;
-      e.persistent = kv.second.persistent;
-      e.ms_best = kv.second.ms_best;
-      e.ms_default = kv.second.ms_default;
-      v.push_back(e);
-    }
+    for (const auto &kv : g_cache) v.push_back(to_entry(kv.first, kv.second));
   }
   const std::string tmp = std::string(path) + ".tmp";
   FILE *fp = fopen(tmp.c_str(), "w");
   if (!fp) return rs_fail(nullptr, RS_ERR_ARG, std::string("cannot write ") + tmp);
-  fprintf(fp, "# librs G1 tuner cache: sms cap lg_points lg_images tile_points persistent ms_best ms_default\n");
+  fprintf(fp, "# librs tuner cache: kind sms cap lg_points lg_images choice persistent ms_best ms_default\n");
   for (const rs_tune_entry &e : v)
-    fprintf(fp, "%d %d %d %d %d %d %.6g %.6g\n", e.sms, e.cap, e.lg_points, e.lg_images, e.tile_points,
+    fprintf(fp, "%d %d %d %d %d %d %d %.6g %.6g\n", e.kind, e.sms, e.cap, e.lg_points, e.lg_images, e.choice,
             e.persistent, (double)e.ms_best, (double)e.ms_default);
   const bool ok = fclose(fp) == 0;
   if (!ok || rename(tmp.c_str(), path) != 0) return rs_fail(nullptr, RS_ERR_ARG, std::string("cannot write ") + path);
@@ -218,9 +290,9 @@ int rs_autotune_load(const char *path) {
     if (*s == '#' || *s == '\n' || *s == '\r' || *s == 0) continue;
     rs_tune_entry e;
     char rest[8];
-    const int got = sscanf(s, "%d %d %d %d %d %d %f %f %7s", &e.sms, &e.cap, &e.lg_points, &e.lg_images,
-                           &e.tile_points, &e.persistent, &e.ms_best, &e.ms_default, rest);
-    if (got != 8 || !valid_entry(e)) {
+    const int got = sscanf(s, "%d %d %d %d %d %d %d %f %f %7s", &e.kind, &e.sms, &e.cap, &e.lg_points,
+                           &e.lg_images, &e.choice, &e.persistent, &e.ms_best, &e.ms_default, rest);
+    if (got != 9 || !valid_entry(e)) {
       rc = rs_fail(nullptr, RS_ERR_ARG, std::string(path) + ":" + std::to_string(lineno) + ": malformed entry");
       break;
     }
@@ -231,13 +303,11 @@ int rs_autotune_load(const char *path) {
   std::lock_guard<std::mutex> lock(g_mu);
   for (const rs_tune_entry &e : v) {
     RsG1Choice c;
-    c.threads = e.tile_points;
+    c.threads = e.choice;
     c.persistent = e.persistent;
     c.ms_best = e.ms_best;
     c.ms_default = e.ms_default;
-    const int64_t key = ((int64_t)e.sms << 32) | ((int64_t)e.cap << 16) | ((int64_t)e.lg_points << 8) |
-                        (int64_t)e.lg_images;
-    g_cache[key] = c;
+    g_cache[make_key(e.kind, e.sms, e.cap, e.lg_points, e.lg_images)] = c;
   }
   return RS_OK;
 }

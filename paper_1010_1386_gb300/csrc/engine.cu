@@ -190,15 +190,21 @@ static void ntt_host_tables(NttConst &nc, std::vector<uint2> &tw) {
   nc.c012 = (uint32_t)((uint64_t)powmod_u32(p01, P2 - 2, P2) * R2 % P2);
 }
 
-int rs_g2_ntt_lg(int N) {
+int rs_g2_len(int N) {
   int lg = 1;
   while ((1 << lg) < 2 * N - 1) ++lg;
-  if (lg > RS_NTT_LGMAX) return 0;
-  // Issued instructions, from counters: a direct multiply-accumulate costs
-  // about 3.8, a butterfly with its shared-memory traffic about 12, and each
-  // (pair, prime) takes 12 transforms of (L/2) lg butterflies.
-  const double direct = 3.8 * (double)N * N, ntt = 12.0 * 12.0 * (double)(1 << (lg - 1)) * lg + 60.0 * N;
-  return ntt < direct ? lg : 0;
+  return lg <= RS_NTT_LGMAX ? lg : 0;
+}
+
+// Cost per (pair, prime) in direct multiply-accumulate-equivalents of issue
+// time: a direct multiply-accumulate issues about 3.8 instructions (two
+// convolutions of N^2 / 2 each); the transform form takes 12 transforms of
+// (L/2) lg radix-4 butterflies, which timed at about 6.5 such units each on
+// GB300 (lengths 2^9 and 2^10 ran 1.08x and 1.44x faster than direct).
+double rs_g2_cost(int N, int form) {
+  const int lg = rs_g2_len(N);
+  if (form == 0 || lg == 0) return 3.8 * (double)N * N;
+  return 12.0 * 6.5 * (double)(1 << (lg - 1)) * lg + 60.0 * N;
 }
 
 int rs_ensure_bhat(rs_ctx *ctx, int lg, int K) {
@@ -464,22 +470,53 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // of a block carry equal work (classes of 32, 64, ..., 256 threads).
   // Pairs whose transform-based G2 is cheaper go to one launch per transform
   // length instead (256 threads, shared memory 3 N + 2^lg words).
+  // The form is chosen per transform-length group: forced by the context or
+  // the options, else the tuner's cached choice (timed now when missing and
+  // allowed; groups with lg < 9 keep the model's choice), else the model.
   std::vector<int> g2lg(n, 0);
   int bhatK[RS_NTT_LGMAX + 1] = {};
-  if (!images_only)
+  if (!images_only) {
+    std::vector<std::vector<int>> bylg(RS_NTT_LGMAX + 1);
     for (int i : byN) {
-      const int N = b->plans[i].N;
-      if (ctx->cfg.g2_form == 1) {
-        g2lg[i] = 0;
-      } else if (ctx->cfg.g2_form == 2) {
-        int lg = 1;
-        while ((1 << lg) < 2 * N - 1) ++lg;
-        g2lg[i] = lg <= RS_NTT_LGMAX ? lg : 0;
-      } else {
-        g2lg[i] = rs_g2_ntt_lg(N);
-      }
-      bhatK[g2lg[i]] = std::max(bhatK[g2lg[i]], b->plans[i].K);
+      const int lg = rs_g2_len(b->plans[i].N);
+      if (lg) bylg[lg].push_back(i);
     }
+    for (int lg = 1; lg <= RS_NTT_LGMAX; ++lg) {
+      if (bylg[lg].empty()) continue;
+      double cd = 0.0, cn = 0.0;
+      int64_t images = 0;
+      for (int i : bylg[lg]) {
+        const PairPlan &p = b->plans[i];
+        cd += p.K * rs_g2_cost(p.N, 0);
+        cn += p.K * rs_g2_cost(p.N, 1);
+        images += (int64_t)p.K * p.N;
+      }
+      const int model = cn < cd ? 1 : 0;
+      int form = model;
+      if (ctx->cfg.g2_form == 1 || ctx->cfg.g2_form == 2) {
+        form = ctx->cfg.g2_form == 2 ? 1 : 0;
+      } else if (opt.g2_force >= 0) {
+        form = opt.g2_force;
+      } else if (lg >= 9) {
+        const int64_t key = rs_tune_key_g2(ctx->sms, lg, images);
+        RsG1Choice c;
+        if (rs_tune_find(key, &c)) {
+          form = c.threads;
+        } else if (opt.tune && ctx->cfg.autotune) {
+          const int rc = rs_tune_g2(ctx, f, g, b->plans, bylg[lg], key, model, &form);
+          if (rc != RS_OK) {
+            rs_free_batch(b);
+            return rc;
+          }
+        }
+      }
+      if (!form) continue;
+      for (int i : bylg[lg]) {
+        g2lg[i] = lg;
+        bhatK[lg] = std::max(bhatK[lg], b->plans[i].K);
+      }
+    }
+  }
   for (int lg = RS_NTT_LGMAX; lg > 0; --lg) {
     if (!bhatK[lg]) continue;
     RsG2Class gc;

@@ -98,6 +98,7 @@ struct RsBatchOpts {
   bool tune = true;     // time G1 choices for classes missing from the tuner cache
   bool timing = false;  // record stage events even when the context does not time
   int g1_threads = 0;   // > 0: force this tile width (and opt.persistent) for every class
+  int g2_force = -1;    // 0: direct G2 for every pair, 1: transforms wherever possible, -1: choose
 };
 
 struct rs_batch {
@@ -147,9 +148,10 @@ int64_t rs_input_words(const rs_bipoly &p);
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx);
 // Transformed interpolation kernels of length 2^lg for at least K primes.
 int rs_ensure_bhat(rs_ctx *ctx, int lg, int K);
-// Transform length exponent for the G2 of a pair with N points when the
-// transform-based form is cheaper than direct convolutions, else 0.
-int rs_g2_ntt_lg(int N);
+// log2 of the G2 transform length for N points (2^lg >= 2N - 1), 0 when
+// above the transform limit; model cost of a form (0 direct, 1 transforms).
+int rs_g2_len(int N);
+double rs_g2_cost(int N, int form);
 int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                    std::vector<PairPlan> &&plans, const RsBatchOpts &opt, rs_batch **out);
 // Byte sizes a batch of these plans needs (device arena, host staging in/out).
@@ -168,11 +170,16 @@ void rs_server_shutdown(rs_ctx *ctx);  // server.cu
 // capacity, floor(log2 of its largest point count), floor(log2 of its images));
 // the process-wide cache maps it to a tile width and a schedule.
 struct RsG1Choice {
-  int threads = 128;
+  int threads = 128;  // G2 entries: the form (1 = transforms, 0 = direct)
   int persistent = 1;
   float ms_best = 0.f, ms_default = 0.f;
 };
 int64_t rs_tune_key(int sms, int cap, int max_points, int64_t images);
+int64_t rs_tune_key_g2(int sms, int lg, int64_t images);
+// Time the whole path on (a sample of) a transform-length group with each G2
+// form and cache the faster (the model's form unless the other wins by 2%).
+int rs_tune_g2(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::vector<PairPlan> &plans,
+               const std::vector<int> &members, int64_t key, int model_form, int *form);
 bool rs_tune_find(int64_t key, RsG1Choice *out);
 // Time every candidate on (a sample of) the class's pairs and cache the fastest.
 int rs_tune_g1(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::vector<PairPlan> &plans,

@@ -42,7 +42,7 @@ class rs_config(ctypes.Structure):
 
 
 class rs_tune_entry(ctypes.Structure):
-    _fields_ = [(k, c_int32) for k in ("sms", "cap", "lg_points", "lg_images", "tile_points",
+    _fields_ = [(k, c_int32) for k in ("kind", "sms", "cap", "lg_points", "lg_images", "choice",
                                        "persistent")] + [("ms_best", ctypes.c_float),
                                                          ("ms_default", ctypes.c_float)]
 

@@ -89,35 +89,41 @@ def test_autotune_cache_file_roundtrip(lib, tmp_path):
     assert rs.autotune_entries() == []
     good = tmp_path / "tune.txt"
     good.write_text("# comment\n"
-                    "152 40 10 21 64 1 3.5 3.75\n"
-                    "152 8 5 9 32 0 0.125 0.25\n"
+                    "0 152 40 10 21 64 1 3.5 3.75\n"
+                    "0 152 8 5 9 32 0 0.125 0.25\n"
                     "\n"
-                    "148 72 13 24 128 1 0 0\n")
+                    "0 148 72 13 24 128 1 0 0\n"
+                    "1 152 0 12 22 1 0 2.5 3\n")
     rs.autotune_load(str(good))
-    got = {(e["sms"], e["cap"], e["lg_points"], e["lg_images"]): e for e in rs.autotune_entries()}
-    assert set(got) == {(152, 40, 10, 21), (152, 8, 5, 9), (148, 72, 13, 24)}
-    e = got[(152, 40, 10, 21)]
-    assert (e["tile_points"], e["persistent"], e["ms_best"], e["ms_default"]) == (64, 1, 3.5, 3.75)
-    assert (got[(152, 8, 5, 9)]["tile_points"], got[(152, 8, 5, 9)]["persistent"]) == (32, 0)
+    key = lambda e: (e["kind"], e["sms"], e["cap"], e["lg_points"], e["lg_images"])
+    got = {key(e): e for e in rs.autotune_entries()}
+    assert set(got) == {(0, 152, 40, 10, 21), (0, 152, 8, 5, 9), (0, 148, 72, 13, 24), (1, 152, 0, 12, 22)}
+    e = got[(0, 152, 40, 10, 21)]
+    assert (e["choice"], e["persistent"], e["ms_best"], e["ms_default"]) == (64, 1, 3.5, 3.75)
+    assert (got[(0, 152, 8, 5, 9)]["choice"], got[(0, 152, 8, 5, 9)]["persistent"]) == (32, 0)
+    assert got[(1, 152, 0, 12, 22)]["choice"] == 1
     out = tmp_path / "out.txt"
     rs.autotune_save(str(out))
     rs.autotune_clear()
     assert rs.autotune_entries() == []
     rs.autotune_load(str(out))
-    again = {(e["sms"], e["cap"], e["lg_points"], e["lg_images"]): e for e in rs.autotune_entries()}
+    again = {key(e): e for e in rs.autotune_entries()}
     assert again == got
-    bad_lines = ["152 40 10 21 48 1 1 1",      # tile width not 32/64/128
-                 "152 44 10 21 64 1 1 1",      # capacity not a multiple of 8
-                 "152 40 10 21 64 2 1 1",      # schedule not 0/1
-                 "152 40 10 21 64 1 1",        # a field missing
-                 "152 40 10 21 64 1 1 1 9"]    # a field extra
+    bad_lines = ["0 152 40 10 21 48 1 1 1",      # tile width not 32/64/128
+                 "0 152 44 10 21 64 1 1 1",      # capacity not a multiple of 8
+                 "0 152 40 10 21 64 2 1 1",      # schedule not 0/1
+                 "1 152 0 12 22 2 0 1 1",        # G2 form not 0/1
+                 "1 152 8 12 22 1 0 1 1",        # G2 entry with a capacity
+                 "2 152 40 10 21 64 1 1 1",      # unknown kind
+                 "0 152 40 10 21 64 1 1",        # a field missing
+                 "0 152 40 10 21 64 1 1 1 9"]    # a field extra
     for i, line in enumerate(bad_lines):
         bad = tmp_path / f"bad{i}.txt"
-        bad.write_text("152 16 6 10 128 1 1 1\n" + line + "\n")
+        bad.write_text("0 152 16 6 10 128 1 1 1\n" + line + "\n")
         with pytest.raises(rs.RsError) as ei:
             rs.autotune_load(str(bad))
         assert ei.value.code == -1 and ":2:" in str(ei.value)
-        assert len(rs.autotune_entries()) == 3, "a rejected file merges nothing"
+        assert len(rs.autotune_entries()) == 4, "a rejected file merges nothing"
     with pytest.raises(rs.RsError):
         rs.autotune_load(str(tmp_path / "missing.txt"))
     rs.autotune_clear()
