@@ -265,7 +265,7 @@ def batch_main(args, world, rank, local, dist):
     torch.cuda.set_device(local)
     pairs = load_pairs(args.workload, args.pairs, rank)
     npairs = len(pairs)
-    ctx = rs.Context(device=local, timing=True)
+    ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     t_tune = time.perf_counter()
     batch = ctx.batch(pairs)  # tunes the G1 launch of every class of the batch first
@@ -463,6 +463,8 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
+    ap.add_argument("--autotune-cache", default=None,
+                    help="tuner cache file read before and written after the run")
     ap.add_argument("--pairs", type=int, default=None,
                     help="time only the first PAIRS pairs / requests (profiling)")
     ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / saturation")

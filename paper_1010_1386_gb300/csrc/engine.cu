@@ -552,9 +552,17 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
     if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin() + nlg, gc);  // largest point counts first
   }
-  const int dthreads = g3_digit_threads(std::max(maxK, 1));
   int64_t ncoef = 0;
   for (int i : order) ncoef += b->plans[i].N;
+  auto thread_mode = [&](const PairPlan &p) { return ncoef >= 65536 && p.K < 128; };
+  for (int i : order) {
+    const PairPlan &p = b->plans[i];
+    if (thread_mode(p))
+      b->kd = std::max(b->kd, p.K);
+    else
+      b->kw = std::max(b->kw, p.K);
+  }
+  const int dthreads = b->dthreads = g3_digit_threads(std::max(b->kd, 1));
   // CRT digits: one thread per coefficient when the batch has enough
   // coefficients to fill the GPU and the pair few primes; one warp per
   // coefficient otherwise (long dot products, or too few coefficients).
@@ -564,7 +572,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     const PairPlan &p = b->plans[i];
     const int di = b->dev_index[i], chunks = (p.Lout + 15) / 16;
     for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(di, j));
-    if (ncoef >= 65536 && p.K < 128)
+    if (thread_mode(p))
       for (int j = 0; j < p.N; j += dthreads) g3d.push_back(make_int2(di, j));
     else
       for (int j = 0; j < p.N; j += 2) g3w.push_back(make_int2(di, j));
@@ -720,8 +728,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   if (ctx->cfg.timing || opt.timing)
     for (auto &ev : b->ev)
       if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
-  if (opt.fork && (b->classes.size() > 1 || b->g2cls.size() > 1)) {
-    b->jev.assign(b->classes.size() + b->g2cls.size(), nullptr);
+  if (opt.fork && (b->classes.size() > 1 || b->g2cls.size() > 1 || (b->ng3d && b->ng3w))) {
+    b->jev.assign(b->classes.size() + b->g2cls.size() + 2, nullptr);
     for (auto &ev : b->fev)
       if (rc == RS_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
         rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
@@ -892,8 +900,27 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.carry = b->d_cy;
     a3.out = b->d_out;
     a3.kmax = b->kmax;
-    RS_CUDA(ctx, launch_g3(b->ng3d, g3_digit_threads(std::max(b->kmax, 1)), b->ng3w, b->ng3b, b->ng3, a3,
-                           b->d_g3d, b->d_g3w, b->d_g3, s));
+    // the two digit launches cover disjoint pairs: parallel branches
+    const int j0 = (int)(b->classes.size() + b->g2cls.size());
+    cudaError_t fe = cudaSuccess;
+    int nbr = 0;
+    if (b->ng3d) {
+      cudaStream_t si = branch_begin(b, 2, nbr, s, &fe);
+      RS_CUDA(ctx, fe);
+      RS_CUDA(ctx, launch_g3a(b->ng3d, b->dthreads, b->kd, a3, b->d_g3d, si));
+      branch_end(b, 2, j0 + nbr++, si, &fe);
+      RS_CUDA(ctx, fe);
+    }
+    if (b->ng3w) {
+      cudaStream_t si = branch_begin(b, 2, nbr, s, &fe);
+      RS_CUDA(ctx, fe);
+      RS_CUDA(ctx, launch_g3w(b->ng3w, b->kw, a3, b->d_g3w, si));
+      branch_end(b, 2, j0 + nbr++, si, &fe);
+      RS_CUDA(ctx, fe);
+    }
+    join_all(b, 2, j0, nbr, s, &fe);
+    RS_CUDA(ctx, fe);
+    RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));
   return RS_OK;

@@ -115,6 +115,7 @@ struct rs_batch {
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int ng2 = 0, ng3 = 0, g2_threads = 256;
   int ng3d = 0, ng3w = 0, ng3b = 0, kmax = 0;  // CRT digit blocks (per thread / per warp), chunks, largest K
+  int kd = 0, kw = 0, dthreads = 128;            // largest K of the thread / warp digit pairs, digit block size
   int64_t xl_words = 0, cy_words = 0;
   int2 *d_g3d = nullptr, *d_g3w = nullptr;
   int4 *d_g3b = nullptr;
@@ -133,7 +134,7 @@ struct rs_batch {
   bool own_host = false;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fev[2] = {nullptr, nullptr};  // fork points of the G1 and G2 stages
+  cudaEvent_t fev[3] = {nullptr, nullptr, nullptr};  // fork points of the G1, G2 and G3-digit stages
   std::vector<cudaEvent_t> jev;             // joins of the branches (one per launch of a forked stage)
   bool ran = false;
   rs_batch_info info;

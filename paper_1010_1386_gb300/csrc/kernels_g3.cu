@@ -223,21 +223,26 @@ __global__ void crt_p16_kernel(const ModP *mods, int K, const int32_t *poff, uin
 
 }  // namespace
 
-cudaError_t launch_g3(int nd, int dthreads, int nw, int nb, int nc, const G3Args &a, const int2 *dtasks,
-                      const int2 *wtasks, const int2 *otasks, cudaStream_t s) {
+cudaError_t launch_g3a(int nd, int dthreads, int kd, const G3Args &a, const int2 *dtasks, cudaStream_t s) {
   G3Args ad = a;
   ad.tasks = dtasks;
-  ad.digits_in_smem = (size_t)dthreads * a.kmax * 4 <= 200 * 1024;
-  if (nd) g3a_kernel<<<nd, dthreads, ad.digits_in_smem ? (size_t)dthreads * a.kmax * 4 : 0, s>>>(ad);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  ad.kmax = kd;
+  ad.digits_in_smem = (size_t)dthreads * kd * 4 <= 200 * 1024;
+  if (nd) g3a_kernel<<<nd, dthreads, ad.digits_in_smem ? (size_t)dthreads * kd * 4 : 0, s>>>(ad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g3w(int nw, int kw, const G3Args &a, const int2 *wtasks, cudaStream_t s) {
   G3Args aw = a;
   aw.tasks = wtasks;
-  if (nw) g3w_kernel<<<nw, 64, (size_t)2 * a.kmax * 4, s>>>(aw);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  aw.kmax = kw;
+  if (nw) g3w_kernel<<<nw, 64, (size_t)2 * kw * 4, s>>>(aw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s) {
   if (nb) g3b_kernel<<<nb, 128, 0, s>>>(a);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   G3Args ao = a;
   ao.tasks = otasks;

@@ -127,8 +127,11 @@ cudaError_t g2n_prepare();
 cudaError_t launch_g2n(int blocks, size_t smem, const G2nArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
-cudaError_t launch_g3(int nd, int dthreads, int nw, int nb, int nc, const G3Args &a, const int2 *dtasks,
-                      const int2 *wtasks, const int2 *otasks, cudaStream_t s);
+// CRT digits (thread per coefficient: dthreads coefficients per block, kd the
+// largest K of those pairs; warp per coefficient: kw likewise), then limbs.
+cudaError_t launch_g3a(int nd, int dthreads, int kd, const G3Args &a, const int2 *dtasks, cudaStream_t s);
+cudaError_t launch_g3w(int nw, int kw, const G3Args &a, const int2 *wtasks, cudaStream_t s);
+cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
 int g3_digit_threads(int kmax);  // coefficients per digit block (shared memory: threads * kmax words)
 cudaError_t g3_prepare(int kmax);
 cudaError_t launch_crt_tables(const ModP *mods, int K, const int32_t *poff, int32_t *wtab, uint16_t *p16,
