@@ -45,14 +45,25 @@ WORKLOADS = {
                           "factors), seed 3",
     "serving": "Poisson stream of 10,000 requests, total degrees of f and g ~ U[8,64], coefficient bits "
                "~ U[16,128], total-degree-dense, seed 4",
+    "shift": "both projections Res_y and Res_x of all 10 pairs of five random curves (total degree "
+             "--shift-deg, dense or --shift-sparse, 16-bit coefficients) multiplied by 2^k "
+             "(--shift-k) with the constant term raised by one, seed 5: 20 resultants",
 }
 
 
-def load_pairs(workload, npairs=None, rank=0):
+SHIFT = (15, 512, False)  # shift workload (degree, k, sparse); main() sets it from the flags
+
+
+def load_pairs(workload, npairs=None, rank=0, args=None):
     """The workload's pairs; under weak scaling rank r > 0 draws its own
     batch of the same distribution (seed + 1000 r)."""
-    from paper_1010_1386_gb300 import inputs
+    from paper_1010_1386_gb300 import inputs, rs
     from paper_1010_1386_gb300.sharding import rank_seed
+    if workload == "shift":
+        deg, k, sparse = (args.shift_deg, args.shift_k, args.shift_sparse) if args else SHIFT
+        base = inputs.workload_shift(rank_seed(5, rank), deg, sparse, k)
+        pairs = base + [(rs.swap_xy(f), rs.swap_xy(g)) for f, g in base]  # R^{(y)}, then R^{(x)}
+        return pairs[:npairs] if npairs else pairs
     if workload == "batch":
         pairs = inputs.workload_batch(rank_seed(2, rank), n=512)
     elif workload == "small":
@@ -263,7 +274,7 @@ def batch_main(args, world, rank, local, dist):
     from paper_1010_1386_gb300 import rs
 
     torch.cuda.set_device(local)
-    pairs = load_pairs(args.workload, args.pairs, rank)
+    pairs = load_pairs(args.workload, args.pairs, rank, args)
     npairs = len(pairs)
     ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
@@ -466,6 +477,9 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
+    ap.add_argument("--shift-deg", type=int, default=15, help="shift workload: total degree (9 or 15)")
+    ap.add_argument("--shift-k", type=int, default=512, help="shift workload: coefficients times 2^k")
+    ap.add_argument("--shift-sparse", action="store_true", help="shift workload: sparse curves")
     ap.add_argument("--autotune-cache", default=None,
                     help="tuner cache file read before and written after the run")
     ap.add_argument("--pairs", type=int, default=None,
@@ -474,6 +488,8 @@ def main():
     ap.add_argument("--inflight", type=int, default=4, help="serving: concurrent micro-batches")
     ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per micro-batch")
     args = ap.parse_args()
+    global SHIFT
+    SHIFT = (args.shift_deg, args.shift_k, args.shift_sparse)
     world, rank, local, dist = dist_setup(args)
     if args.impl == "reference":
         reference_main(args, world, rank, dist)

@@ -54,7 +54,7 @@ enum {
 };
 
 /* Library limits. */
-#define RS_MAX_LIMBS 64        /* input coefficients up to 2048 bits */
+#define RS_MAX_LIMBS 128       /* input coefficients up to 4096 bits */
 #define RS_MAX_DEG_Y 71        /* y-degree of f and of g */
 #define RS_MAX_POINTS 16384    /* degree bound D + 1 of the resultant */
 #define RS_MAX_PRIMES 16384    /* 31-bit primes available for the CRT */
@@ -183,6 +183,21 @@ typedef struct {
 } rs_batch_info;
 
 int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
+
+/* R^{(x)} = res(f, g, x) in Z[y] (Section 3.1: defined like R^{(y)} with f
+ * and g read as polynomials in x over Z[y]).  The library exchanges the
+ * variables of copies of f and g on the host and runs the same path; out
+ * receives the coefficients of y^0 .. y^deg.  Errors as rs_resultant_y. */
+int rs_resultant_x(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out);
+
+/* Both projections of each pair (the PROJECT phase of the paper's solver
+ * computes R^{(y)} and R^{(x)}, Section 3.1 / Theorem 3.1): out_y[i] =
+ * res(f_i, g_i, y) in Z[x] and out_x[i] = res(f_i, g_i, x) in Z[y], all 2n
+ * resultants in one batch (one pass over the GPU).  status (may be NULL)
+ * receives 2n entries: the y-projections, then the x-projections.  Returns
+ * the first failure, as rs_resultant_batch. */
+int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
+                   rs_upoly *out_y, rs_upoly *out_x, int32_t *status);
 
 /* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
  * (Section 4.1) that the resultant path computes, for the first nprimes

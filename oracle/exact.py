@@ -265,6 +265,22 @@ def resultant_y(f, g):
     return zx_trim(out)
 
 
+def transpose(f):
+    """The same polynomial with the two variables exchanged: rows indexed by
+    the y-exponent, entries by the x-exponent."""
+    nx = len(f)
+    ny = max((len(r) for r in f), default=0)
+    return [[f[i][j] if j < len(f[i]) else 0 for i in range(nx)] for j in range(ny)]
+
+
+def resultant_x(f, g):
+    """R^{(x)} = res(f, g, x) in Z[y] (Section 3.1: defined like R^{(y)}, with
+    f and g read as polynomials in x whose coefficients lie in Z[y]).  After
+    exchanging the variables the Sylvester determinant is taken exactly as
+    for R^{(y)}; the result's coefficient k belongs to y^k."""
+    return resultant_y(transpose(f), transpose(g))
+
+
 def resultant_y_at(f, g, x0):
     """R^{(y)}(x0) = det S^{(y)}(f(x0, y), g(x0, y)) in Z (evaluation commutes
     with the determinant because the formal y-degrees are kept)."""

@@ -115,7 +115,7 @@ int64_t rs_input_words(const rs_bipoly &p) { return (int64_t)(p.deg_x + 1) * (p.
 // ------------------------------------------------------------------ tables
 
 static void free_tables(RsTables &t) {
-  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc, t.wtab, t.p16, t.poff, t.nh, t.plimbs};
+  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc, t.wtab, t.p16, t.poff, t.nh};
   for (void *x : p)
     if (x) cudaFree(x);
   t = RsTables();
@@ -255,11 +255,37 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   if (e == cudaSuccess) e = cudaMalloc(&nt.p16, (size_t)poff[nt.K] * 2);
   if (e == cudaSuccess) e = cudaMalloc(&nt.poff, (size_t)(nt.K + 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&nt.nh, (size_t)nt.K * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&nt.plimbs, (size_t)(nt.K + 4) * 4);
+  // Prefix products P_k = p_0 ... p_{k-1} as 16-bit digits (row k at poff[k],
+  // zero padded to its reserved length) and nh[k] = digits up to the top
+  // non-zero one, built on the host: P_{k+1} = P_k p_k on 32-bit limbs.
+  std::vector<uint16_t> p16((size_t)poff[nt.K], 0);
+  std::vector<int32_t> nh(nt.K, 0);
+  {
+    std::vector<uint32_t> limbs(1, 1u);
+    for (int k = 0; k < nt.K; ++k) {
+      uint16_t *row = p16.data() + poff[k];
+      const int reserved = poff[k + 1] - poff[k];
+      int top = 0;
+      for (int i = 0; i < reserved && (i >> 1) < (int)limbs.size(); ++i) {
+        const uint32_t d = (i & 1) ? (limbs[i >> 1] >> 16) : (limbs[i >> 1] & 0xffffu);
+        row[i] = (uint16_t)d;
+        if (d) top = i + 1;
+      }
+      nh[k] = top;
+      uint64_t carry = 0;
+      for (uint32_t &l : limbs) {
+        const uint64_t v = (uint64_t)l * ctx->primes[k] + carry;
+        l = (uint32_t)v;
+        carry = v >> 32;
+      }
+      if (carry) limbs.push_back((uint32_t)carry);
+    }
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(nt.poff, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess)
-    e = launch_crt_tables(ctx->d_mods, nt.K, nt.poff, nt.wtab, nt.p16, nt.nh, nt.plimbs, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nt.p16, p16.data(), p16.size() * 2, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nt.nh, nh.data(), nh.size() * 4, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_crt_tables(ctx->d_mods, nt.K, nt.wtab, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     free_tables(nt);
@@ -311,7 +337,7 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     tiles += (int64_t)p.K * ((p.N + 31) / 32);
     g2 += p.K;
     g3 += (p.N + 127) / 128;
-    g3d += 2 * ((p.N + 1) / 2);  // bound for either digit mapping
+    g3d += (p.N + 31) / 32;  // digit tiles
     g3b += (p.N + 127) / 128 * chunks;
   }
   // inputs plus room for the static tables (descriptors, tiles, task lists)
@@ -552,44 +578,28 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
     if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin() + nlg, gc);  // largest point counts first
   }
-  int64_t ncoef = 0;
-  for (int i : order) ncoef += b->plans[i].N;
-  auto thread_mode = [&](const PairPlan &p) { return ncoef >= 65536 && p.K < 128; };
-  for (int i : order) {
-    const PairPlan &p = b->plans[i];
-    if (thread_mode(p))
-      b->kd = std::max(b->kd, p.K);
-    else
-      b->kw = std::max(b->kw, p.K);
-  }
-  const int dthreads = b->dthreads = g3_digit_threads(std::max(b->kd, 1));
-  // CRT digits: one thread per coefficient when the batch has enough
-  // coefficients to fill the GPU and the pair few primes; one warp per
-  // coefficient otherwise (long dot products, or too few coefficients).
-  std::vector<int2> g3d, g3w;
+  // CRT digits in tiles of 32 coefficients; limbs in blocks of 128
+  // coefficients by chunks of 16 output limbs.
+  std::vector<int2> g3d;
   std::vector<int4> g3b;  // CRT limb chunks: 128 coefficients x one chunk per block
   for (int i : order) {
     const PairPlan &p = b->plans[i];
     const int di = b->dev_index[i], chunks = (p.Lout + 15) / 16;
     for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(di, j));
-    if (thread_mode(p))
-      for (int j = 0; j < p.N; j += dthreads) g3d.push_back(make_int2(di, j));
-    else
-      for (int j = 0; j < p.N; j += 2) g3w.push_back(make_int2(di, j));
+    for (int j = 0; j < p.N; j += 32) g3d.push_back(make_int2(di, j));  // digit tiles of 32 coefficients
     for (int c = 0; c < chunks; ++c)
       for (int j = 0; j < p.N; j += 128) g3b.push_back(make_int4(di, j, c, 0));
   }
   b->ng2 = images_only ? 0 : (int)g2.size();
   b->ng3 = images_only ? 0 : (int)g3.size();
   b->ng3d = images_only ? 0 : (int)g3d.size();
-  b->ng3w = images_only ? 0 : (int)g3w.size();
   b->ng3b = images_only ? 0 : (int)g3b.size();
   b->kmax = maxK;
   b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
   b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) +
-                            (b->ng3w > 0) + (b->ng3b > 0) +
+                            (b->ng3b > 0) +
                             (b->ng3 > 0);
 
   int rc = RS_OK;
@@ -613,7 +623,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                o_xl = carve(std::max(b->xl_words, b->out_words) * 4), o_out = carve(b->out_words * 4),
                o_g2 = carve(g2.size() * sizeof(int2)), o_g3 = carve(g3.size() * sizeof(int2)),
                o_st = carve(ST_COUNT * sizeof(unsigned long long)), o_cy = carve(b->cy_words * 8),
-               o_g3d = carve(g3d.size() * sizeof(int2)), o_g3w = carve(g3w.size() * sizeof(int2)),
+               o_g3d = carve(g3d.size() * sizeof(int2)),
                o_g3b = carve(g3b.size() * sizeof(int4));
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
@@ -636,7 +646,6 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_stats = (unsigned long long *)(base + o_st);
   b->d_cy = (int64_t *)(base + o_cy);
   b->d_g3d = (int2 *)(base + o_g3d);
-  b->d_g3w = (int2 *)(base + o_g3w);
   b->d_g3b = (int4 *)(base + o_g3b);
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
@@ -667,7 +676,6 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                           {b->d_g2, g2.data(), g2.size() * sizeof(int2)},
                           {b->d_g3, g3.data(), g3.size() * sizeof(int2)},
                           {b->d_g3d, g3d.data(), g3d.size() * sizeof(int2)},
-                          {b->d_g3w, g3w.data(), g3w.size() * sizeof(int2)},
                           {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)}};
   size_t static_bytes = 0;
   for (const Piece &pc : pieces) static_bytes += (pc.bytes + 15) & ~(size_t)15;
@@ -691,11 +699,6 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   {
     // Kernel attributes and occupancies, once per context.
     std::lock_guard<std::mutex> lock(ctx->prep_mu);
-    if (rc == RS_OK && (b->ng3d || b->ng3w) && !ctx->g3_ready) {
-      cudaError_t e2 = g3_prepare(b->kmax);
-      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
-      ctx->g3_ready = e2 == cudaSuccess;
-    }
     if (rc == RS_OK && nlg > 0 && !ctx->g2n_ready) {
       cudaError_t e2 = g2n_prepare();
       if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
@@ -728,8 +731,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   if (ctx->cfg.timing || opt.timing)
     for (auto &ev : b->ev)
       if (rc == RS_OK && cudaEventCreate(&ev) != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
-  if (opt.fork && (b->classes.size() > 1 || b->g2cls.size() > 1 || (b->ng3d && b->ng3w))) {
-    b->jev.assign(b->classes.size() + b->g2cls.size() + 2, nullptr);
+  if (opt.fork && (b->classes.size() > 1 || b->g2cls.size() > 1)) {
+    b->jev.assign(b->classes.size() + b->g2cls.size(), nullptr);
     for (auto &ev : b->fev)
       if (rc == RS_OK && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
         rc = rs_fail(ctx, RS_ERR_CUDA, "cudaEventCreate");
@@ -900,26 +903,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.carry = b->d_cy;
     a3.out = b->d_out;
     a3.kmax = b->kmax;
-    // the two digit launches cover disjoint pairs: parallel branches
-    const int j0 = (int)(b->classes.size() + b->g2cls.size());
-    cudaError_t fe = cudaSuccess;
-    int nbr = 0;
-    if (b->ng3d) {
-      cudaStream_t si = branch_begin(b, 2, nbr, s, &fe);
-      RS_CUDA(ctx, fe);
-      RS_CUDA(ctx, launch_g3a(b->ng3d, b->dthreads, b->kd, a3, b->d_g3d, si));
-      branch_end(b, 2, j0 + nbr++, si, &fe);
-      RS_CUDA(ctx, fe);
-    }
-    if (b->ng3w) {
-      cudaStream_t si = branch_begin(b, 2, nbr, s, &fe);
-      RS_CUDA(ctx, fe);
-      RS_CUDA(ctx, launch_g3w(b->ng3w, b->kw, a3, b->d_g3w, si));
-      branch_end(b, 2, j0 + nbr++, si, &fe);
-      RS_CUDA(ctx, fe);
-    }
-    join_all(b, 2, j0, nbr, s, &fe);
-    RS_CUDA(ctx, fe);
+    RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s));
     RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));
@@ -1329,6 +1313,58 @@ int rs_resultant_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipo
 
 int rs_resultant_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out) {
   return rs_resultant_batch(ctx, 1, f, g, out, nullptr);
+}
+
+// Copy of p with x and y exchanged (storage in `buf`); an input the planner
+// would reject is passed through unchanged so that it fails the same way.
+static rs_bipoly transposed(const rs_bipoly &p, std::vector<uint32_t> &buf) {
+  if (!p.coeffs || p.deg_x < 0 || p.deg_y < 0 || p.limbs < 1 || p.limbs > RS_MAX_LIMBS ||
+      (int64_t)(p.deg_x + 1) * (p.deg_y + 1) > ((int64_t)1 << 26))
+    return p;
+  const int nx = p.deg_x + 1, ny = p.deg_y + 1, L = p.limbs;
+  buf.resize((size_t)nx * ny * L);
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < ny; ++j)
+      memcpy(&buf[((size_t)j * nx + i) * L], p.coeffs + ((size_t)i * ny + j) * L, (size_t)L * 4);
+  rs_bipoly t;
+  t.deg_x = p.deg_y;
+  t.deg_y = p.deg_x;
+  t.limbs = L;
+  t.coeffs = buf.data();
+  return t;
+}
+
+int rs_resultant_x(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out) {
+  if (!ctx || !f || !g || !out) return rs_fail(ctx, RS_ERR_ARG, "NULL argument");
+  std::vector<uint32_t> bf, bg;
+  const rs_bipoly ft = transposed(*f, bf), gt = transposed(*g, bg);
+  return rs_resultant_batch(ctx, 1, &ft, &gt, out, nullptr);
+}
+
+int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out_y,
+                   rs_upoly *out_x, int32_t *status) {
+  if (!ctx || n < 0 || (n > 0 && (!f || !g || !out_y || !out_x)))
+    return rs_fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
+  if (n == 0) return RS_OK;
+  std::vector<std::vector<uint32_t>> bufs(2 * (size_t)n);
+  std::vector<rs_bipoly> F(2 * (size_t)n), G(2 * (size_t)n);
+  std::vector<rs_upoly> O(2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    F[i] = f[i];
+    G[i] = g[i];
+    F[n + i] = transposed(f[i], bufs[2 * (size_t)i]);
+    G[n + i] = transposed(g[i], bufs[2 * (size_t)i + 1]);
+    O[i] = out_y[i];
+    O[n + i] = out_x[i];
+  }
+  const int rc = rs_resultant_batch(ctx, 2 * n, F.data(), G.data(), O.data(), status);
+  for (int i = 0; i < n; ++i) {  // deg and limbs are written on success and on RS_ERR_CAPACITY
+    out_y[i].deg = O[i].deg;
+    out_y[i].limbs = O[i].limbs;
+    out_x[i].deg = O[n + i].deg;
+    out_x[i].limbs = O[n + i].limbs;
+  }
+  return rc;
 }
 
 int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprimes, int32_t npoints,

@@ -27,7 +27,6 @@ struct RsTables {
   uint16_t *p16 = nullptr;   // prefix products in 16-bit digits
   int32_t *poff = nullptr;   // K + 1 row offsets into p16
   int32_t *nh = nullptr;     // digits per prefix product
-  uint32_t *plimbs = nullptr;  // scratch of the table kernel
 };
 
 struct rs_ctx {
@@ -50,7 +49,7 @@ struct rs_ctx {
   std::vector<RsTables> retired;
   RsServer *server = nullptr;
   std::mutex prep_mu;  // kernel attributes and the occupancy cache below
-  bool g2_ready = false, g3_ready = false;
+  bool g2_ready = false;
   std::map<int64_t, int> g1_occupancy;  // (capacity, threads, staged KiB) -> blocks per SM
   std::string tune_path;                 // autotune cache file written at rs_destroy ("" = none)
   cudaStream_t side[8] = {};             // branches of the fork-join stage launches
@@ -114,10 +113,9 @@ struct rs_batch {
   std::vector<RsG2Class> g2cls;
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int ng2 = 0, ng3 = 0, g2_threads = 256;
-  int ng3d = 0, ng3w = 0, ng3b = 0, kmax = 0;  // CRT digit blocks (per thread / per warp), chunks, largest K
-  int kd = 0, kw = 0, dthreads = 128;            // largest K of the thread / warp digit pairs, digit block size
+  int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int64_t xl_words = 0, cy_words = 0;
-  int2 *d_g3d = nullptr, *d_g3w = nullptr;
+  int2 *d_g3d = nullptr;
   int4 *d_g3b = nullptr;
   int64_t *d_cy = nullptr;
   size_t g2smem = 0;
@@ -134,7 +132,7 @@ struct rs_batch {
   bool own_host = false;
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fev[3] = {nullptr, nullptr, nullptr};  // fork points of the G1, G2 and G3-digit stages
+  cudaEvent_t fev[2] = {nullptr, nullptr};  // fork points of the G1 and G2 stages
   std::vector<cudaEvent_t> jev;             // joins of the branches (one per launch of a forked stage)
   bool ran = false;
   rs_batch_info info;

@@ -8,14 +8,16 @@
 //   W[k][l] = p_0 ... p_{l-1} mod p_k,  c_k = (p_0 ... p_{k-1})^{-1} mod p_k,
 // and the integer is R_j = sum_k v_k P_k with P_k = p_0 ... p_{k-1}.
 //
-// G3a: the digits, each dot product over the previous digits lazily
-//      accumulated in int64: one thread per coefficient when a batch has many
-//      coefficients and few primes, one warp per coefficient otherwise.
+// G3t: the digits, in tiles of 32 coefficients by blocks of 64 digits (a
+//      rectangular update from the earlier digits, then a small triangular
+//      solve), every dot product lazily accumulated in int64.
 // G3b: one thread per (coefficient, chunk of 32 sixteen-bit digits of R_j)
 //      accumulates sum_k v_k P_k[h] exactly in int64 (|v_k P_k[h]| < 2^46)
 //      and normalises the chunk, keeping its carry.
 // G3c: one thread per coefficient ripples the chunk carries and writes the
 //      two's-complement 32-bit limbs.
+#include <algorithm>
+
 #include "../../include/rs.h"
 #include "rs_internal.cuh"
 
@@ -29,76 +31,124 @@ __device__ __forceinline__ uint32_t finish64_3(int64_t s, const ModP &m) {
   return redc((uint64_t)(s + ((int64_t)m.p << 22)), m.p, m.pinv);  // 0 <= . < 2^54 < p 2^32
 }
 
-// Digits: one thread per coefficient, blockDim = T consecutive coefficients
-// of one pair; each thread keeps its digits in shared memory (digit l of
-// thread t at sdig[l T + t], conflict-free) and reads W[k][l] as a broadcast.
-__global__ void g3a_kernel(G3Args a) {
-  extern __shared__ int32_t sdig[];
-  const int2 task = a.tasks[blockIdx.x];
-  const PairDesc pd = a.pairs[task.x];
-  const int T = blockDim.x, tid = threadIdx.x;
-  const int j = task.y + tid;
-  if (j >= pd.N) return;
-  const int K = pd.K, N = pd.N;
-  uint32_t *col = a.coef + pd.img_off + j;  // residue, then digit, k at col[k N]
-  for (int k = 0; k < K; ++k) {
-    const ModP mk = a.mods[k];
-    const int32_t *wk = a.wtab + (size_t)k * (k - 1) / 2;
-    int64_t acc = 0;
-    int l = 0;
-    while (l < k) {
-      const int lend = min(l + 7, k);
-      if (a.digits_in_smem)
-        for (; l < lend; ++l) acc = rs_mac_s32(acc, sdig[l * T + tid], __ldg(wk + l));
-      else
-        for (; l < lend; ++l) acc = rs_mac_s32(acc, (int32_t)col[(size_t)l * N], __ldg(wk + l));
-      acc = rs_fold64(acc, mk.r1);
-    }
-    const uint32_t t = finish64_3(acc, mk);  // sum_l v_l W[k][l] (plain: W is in Montgomery form)
-    const uint32_t v = mmul(msub(col[(size_t)k * N], t, mk.p), a.crt[k], mk);  // plain, [0, p_k)
-    const int32_t vs = signed_rep3(v, mk.p);
-    if (a.digits_in_smem) sdig[k * T + tid] = vs;
-    col[(size_t)k * N] = (uint32_t)vs;
-  }
-}
+#define G3T_JT 32  // coefficients per tile
+#define G3T_BK 64  // digits per digit block
+#define G3T_LC 32  // earlier digits per staged chunk
 
-// Digits, one warp per coefficient (for many primes or few coefficients):
-// blockDim = 64 (two coefficients), dynamic shared memory 2 * kmax words.
-// Each dot product is split over the 32 lanes, lazily accumulated, folded,
-// reduced and summed with shuffles.
-__global__ void g3w_kernel(G3Args a) {
-  extern __shared__ int32_t sdig_w[];
+// Digits by tiles: a block of 256 threads owns 32 consecutive coefficients
+// of one pair and produces their digits 64 at a time.  For the digit block
+// [k0, k0 + 64) the contribution of every earlier digit,
+//   A[k][j] = sum_{l < k0} W[k][l] v_l(j),
+// is the product of a 64 x k0 slice of W and a k0 x 32 slice of digits:
+// chunks of both are staged in shared memory and each thread accumulates a
+// 4 x 2 block lazily in int64 (a fold with its row's 2^32 mod p_k every 7
+// products).  The 64 digits of the block then follow one by one (one warp,
+// lane = coefficient) from the triangle of W inside the block, with the
+// residues, constants and that triangle prefetched into shared memory.
+// The work per coefficient is still K^2 / 2 products, but W and the digits
+// come from shared memory, each value reused 32 and 64 times.
+__global__ void __launch_bounds__(256) g3t_kernel(G3Args a) {
+  __shared__ int32_t Ws[G3T_LC][G3T_BK + 1];  // W[k0 + r][l0 + c] at Ws[c][r]
+  __shared__ int32_t Vs[G3T_LC][G3T_JT];      // digit l0 + c of coefficient j0 + jj
+  __shared__ int32_t Wt[G3T_BK][G3T_BK + 1];  // W[k0 + r][k0 + c], c < r
+  __shared__ uint32_t Ds[G3T_BK][G3T_JT];     // r_k(j) - A[k][j] mod p_k
+  __shared__ int32_t Vb[G3T_BK][G3T_JT];      // the block's digits
+  __shared__ ModP Ms[G3T_BK];
+  __shared__ uint32_t Cs[G3T_BK];
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = task.y + warp;
-  if (j >= pd.N) return;  // the whole warp leaves together
-  const int K = pd.K, N = pd.N;
-  int32_t *sd = sdig_w + warp * a.kmax;
-  uint32_t *col = a.coef + pd.img_off + j;
-  for (int k = 0; k < K; ++k) {
-    const ModP mk = a.mods[k];
-    const int32_t *wk = a.wtab + (size_t)k * (k - 1) / 2;
-    int64_t acc = 0;
+  const int K = pd.K, N = pd.N, j0 = task.y, tid = threadIdx.x;
+  const int rg = tid >> 4, cg = tid & 15;  // rows 4 rg .. 4 rg + 3, columns 2 cg, 2 cg + 1
+  uint32_t *col = a.coef + pd.img_off;     // residue, then digit, of (k, j) at col[k N + j]
+  for (int k0 = 0; k0 < K; k0 += G3T_BK) {
+    const int bk = min(G3T_BK, K - k0);
+    for (int r = tid; r < bk; r += blockDim.x) {
+      Ms[r] = a.mods[k0 + r];
+      Cs[r] = a.crt[k0 + r];
+    }
+    __syncthreads();
+    uint32_t c32[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c32[i] = 4 * rg + i < bk ? Ms[4 * rg + i].r1 : 0u;
+    int64_t acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0;
     int cnt = 0;
-    for (int l = lane; l < k; l += 32) {
-      acc = rs_mac_s32(acc, sd[l], __ldg(wk + l));
-      if (++cnt == 7) {
-        acc = rs_fold64(acc, mk.r1);
-        cnt = 0;
+    for (int l0 = 0; l0 < k0; l0 += G3T_LC) {  // k0 is a multiple of G3T_LC: full chunks
+      for (int e = tid; e < G3T_LC * G3T_BK; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31, k = k0 + r;
+        Ws[c][r] = r < bk ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + l0 + c) : 0;
+      }
+      for (int e = tid; e < G3T_LC * G3T_JT; e += blockDim.x) {
+        const int c = e >> 5, jj = e & 31, j = j0 + jj;
+        Vs[c][jj] = j < N ? (int32_t)col[(size_t)(l0 + c) * N + j] : 0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int c = 0; c < G3T_LC; ++c) {
+        int32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = Ws[c][4 * rg + i];
+        const int32_t v0 = Vs[c][2 * cg], v1 = Vs[c][2 * cg + 1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i][0] = rs_mac_s32(acc[i][0], w[i], v0);
+          acc[i][1] = rs_mac_s32(acc[i][1], w[i], v1);
+        }
+        if (++cnt == 7) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[i][0] = rs_fold64(acc[i][0], c32[i]);
+            acc[i][1] = rs_fold64(acc[i][1], c32[i]);
+          }
+          cnt = 0;
+        }
+      }
+      __syncthreads();
+    }
+    // D = r - A mod p_k (plain: W is in Montgomery form, the finish removes R)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = 4 * rg + i;
+      if (r >= bk) continue;
+      const ModP m = Ms[r];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int jj = 2 * cg + c, j = j0 + jj;
+        const uint32_t tA = finish64_3(rs_fold64(acc[i][c], m.r1), m);
+        const uint32_t res = j < N ? col[(size_t)(k0 + r) * N + j] : 0u;
+        Ds[r][jj] = msub(res, tA, m.p);
       }
     }
-    acc = rs_fold64(acc, mk.r1);
-    uint32_t t = finish64_3(acc, mk);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t = madd(t, __shfl_xor_sync(0xffffffffu, t, off), mk.p);
-    const uint32_t v = mmul(msub(col[(size_t)k * N], t, mk.p), a.crt[k], mk);
-    const int32_t vs = signed_rep3(v, mk.p);
-    if (lane == 0) {
-      sd[k] = vs;
-      col[(size_t)k * N] = (uint32_t)vs;
+    for (int e = tid; e < G3T_BK * G3T_BK; e += blockDim.x) {
+      const int r = e >> 6, c = e & 63, k = k0 + r;
+      Wt[r][c] = (c < r && r < bk) ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + k0 + c) : 0;
     }
-    __syncwarp();
+    __syncthreads();
+    if (tid < 32) {  // the block's digits in order, lane = coefficient
+      const int jj = tid, j = j0 + jj;
+      for (int r = 0; r < bk; ++r) {
+        const ModP m = Ms[r];
+        int64_t s0 = 0, s1 = 0;
+        int n = 0;
+        for (int c = 0; c + 1 < r; c += 2) {
+          s0 = rs_mac_s32(s0, Wt[r][c], Vb[c][jj]);
+          s1 = rs_mac_s32(s1, Wt[r][c + 1], Vb[c + 1][jj]);
+          if (++n == 7) {
+            s0 = rs_fold64(s0, m.r1);
+            s1 = rs_fold64(s1, m.r1);
+            n = 0;
+          }
+        }
+        if (r & 1) s0 = rs_mac_s32(s0, Wt[r][r - 1], Vb[r - 1][jj]);
+        const int64_t s = rs_fold64(rs_fold64(s0, m.r1) + rs_fold64(s1, m.r1), m.r1);
+        const uint32_t v = mmul(msub(Ds[r][jj], finish64_3(s, m), m.p), Cs[r], m);
+        const int32_t vs = signed_rep3(v, m.p);
+        Vb[r][jj] = vs;
+        if (j < N) col[(size_t)(k0 + r) * N + j] = (uint32_t)vs;
+      }
+    }
+    __syncthreads();  // this block's digits are read by the next digit blocks
   }
 }
 
@@ -191,52 +241,12 @@ __global__ void crt_w_kernel(const ModP *mods, int K, int32_t *wtab) {
   }
 }
 
-// Prefix products P_k = p_0 ... p_{k-1} as 16-bit digits, row k at poff[k]
-// (zero padded to its reserved length), nh[k] = digits up to the top
-// non-zero one.  A single thread: P_{k+1} = P_k p_k on 32-bit limbs.
-__global__ void crt_p16_kernel(const ModP *mods, int K, const int32_t *poff, uint16_t *p16, int32_t *nh,
-                               uint32_t *limbs) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  int n = 1;
-  limbs[0] = 1u;
-  for (int k = 0; k < K; ++k) {
-    uint16_t *row = p16 + poff[k];
-    const int reserved = poff[k + 1] - poff[k];
-    int top = 0;
-    for (int i = 0; i < reserved; ++i) {
-      const int li = i >> 1;
-      const uint32_t d = li < n ? ((i & 1) ? (limbs[li] >> 16) : (limbs[li] & 0xffffu)) : 0u;
-      row[i] = (uint16_t)d;
-      if (d) top = i + 1;
-    }
-    nh[k] = top;
-    const uint64_t p = mods[k].p;
-    uint64_t carry = 0;
-    for (int i = 0; i < n; ++i) {
-      const uint64_t t = (uint64_t)limbs[i] * p + carry;
-      limbs[i] = (uint32_t)t;
-      carry = t >> 32;
-    }
-    if (carry) limbs[n++] = (uint32_t)carry;
-  }
-}
-
 }  // namespace
 
-cudaError_t launch_g3a(int nd, int dthreads, int kd, const G3Args &a, const int2 *dtasks, cudaStream_t s) {
-  G3Args ad = a;
-  ad.tasks = dtasks;
-  ad.kmax = kd;
-  ad.digits_in_smem = (size_t)dthreads * kd * 4 <= 200 * 1024;
-  if (nd) g3a_kernel<<<nd, dthreads, ad.digits_in_smem ? (size_t)dthreads * kd * 4 : 0, s>>>(ad);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_g3w(int nw, int kw, const G3Args &a, const int2 *wtasks, cudaStream_t s) {
-  G3Args aw = a;
-  aw.tasks = wtasks;
-  aw.kmax = kw;
-  if (nw) g3w_kernel<<<nw, 64, (size_t)2 * kw * 4, s>>>(aw);
+cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s) {
+  G3Args at = a;
+  at.tasks = ttasks;
+  if (nt) g3t_kernel<<<nt, 256, 0, s>>>(at);
   return cudaGetLastError();
 }
 
@@ -250,24 +260,7 @@ cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cud
   return cudaGetLastError();
 }
 
-int g3_digit_threads(int kmax) {
-  int t = 128;
-  while (t > 32 && (size_t)t * kmax * 4 > 96 * 1024) t >>= 1;
-  return t;
-}
-
-cudaError_t g3_prepare(int kmax) {
-  (void)kmax;  // beyond 200 KB of digits per block the kernel reads them from global memory
-  cudaError_t e = cudaFuncSetAttribute(g3a_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(g3w_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
-cudaError_t launch_crt_tables(const ModP *mods, int K, const int32_t *poff, int32_t *wtab, uint16_t *p16,
-                              int32_t *nh, uint32_t *limbs, cudaStream_t s) {
+cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s) {
   crt_w_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, K, wtab);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  crt_p16_kernel<<<1, 1, 0, s>>>(mods, K, poff, p16, nh, limbs);
   return cudaGetLastError();
 }

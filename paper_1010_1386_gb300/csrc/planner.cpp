@@ -79,7 +79,7 @@ int analyze(const rs_bipoly *f, PolyInfo &pi, const char **why) {
     return RS_ERR_ARG;
   }
   if (f->limbs < 1 || f->limbs > RS_MAX_LIMBS) {
-    *why = "limbs must be in 1..64";
+    *why = "limbs must be in 1..RS_MAX_LIMBS (128)";
     return RS_ERR_ARG;
   }
   if ((int64_t)(f->deg_x + 1) * (f->deg_y + 1) > ((int64_t)1 << 26)) {

@@ -3,9 +3,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/rs.h"
 #include "modarith.cuh"
 
-#define RS_VT_STRIDE 65  // V[k][l] = 2^(32 l) R^2 mod p_k, l = 0..RS_MAX_LIMBS
+#define RS_VT_STRIDE (RS_MAX_LIMBS + 1)  // V[k][l] = 2^(32 l) R^2 mod p_k, l = 0..RS_MAX_LIMBS
 #define RS_G1_MAX_STAGED_WORDS (48 * 1024)  // staged residues + meta per G1 tile
 #define RS_G1_MAX_SMEM_BYTES (RS_G1_MAX_STAGED_WORDS * 4)
 #define RS_G2_PAD 8          // zero words around each G2 shared-memory region
@@ -101,7 +102,7 @@ struct G2nArgs {
 
 struct G3Args {
   const PairDesc *pairs;
-  const int2 *tasks;       // (pair, first coefficient) per block
+  const int2 *tasks;       // (pair, first coefficient) per block (digit tiles of 32 coefficients)
   const int4 *ctasks;      // (pair, first coefficient, chunk, -) per limb-chunk block
   const ModP *mods;
   const uint32_t *crt;     // (p_0 ... p_{k-1})^{-1} mod p_k, Montgomery form
@@ -113,8 +114,7 @@ struct G3Args {
   uint32_t *xl;            // 16-bit digit pairs of R_j, [16 chunk + w][N] per pair
   int64_t *carry;          // chunk carries [chunk][N] per pair
   uint32_t *out;           // out: [coefficient][limb]
-  int32_t kmax;            // largest K of the batch (digit kernel shared memory)
-  int32_t digits_in_smem;  // set by launch_g3: digit kernel keeps digits in shared memory
+  int32_t kmax;            // largest K of the batch
 };
 
 // Launchers (kernels_*.cu).  Each returns the cudaGetLastError() of its launch.
@@ -127,15 +127,10 @@ cudaError_t g2n_prepare();
 cudaError_t launch_g2n(int blocks, size_t smem, const G2nArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
-// CRT digits (thread per coefficient: dthreads coefficients per block, kd the
-// largest K of those pairs; warp per coefficient: kw likewise), then limbs.
-cudaError_t launch_g3a(int nd, int dthreads, int kd, const G3Args &a, const int2 *dtasks, cudaStream_t s);
-cudaError_t launch_g3w(int nw, int kw, const G3Args &a, const int2 *wtasks, cudaStream_t s);
+// CRT digits by tiles of 32 coefficients (tasks step by 32), any prime count.
+cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s);
 cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
-int g3_digit_threads(int kmax);  // coefficients per digit block (shared memory: threads * kmax words)
-cudaError_t g3_prepare(int kmax);
-cudaError_t launch_crt_tables(const ModP *mods, int K, const int32_t *poff, int32_t *wtab, uint16_t *p16,
-                              int32_t *nh, uint32_t *limbs, cudaStream_t s);
+cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s);
 cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,

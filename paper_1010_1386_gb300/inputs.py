@@ -211,3 +211,29 @@ def workload_serving(seed=4, n=10000, deg_lo=8, deg_hi=64, bits_lo=16, bits_hi=1
         pairs.append((dense_total_degree(rng, df, b, L), dense_total_degree(rng, dg, b, L)))
     gaps = rng.exponential(1.0, size=n)
     return pairs, gaps
+
+
+def workload_shift(seed=5, deg=9, sparse=False, k=128, curves=5):
+    """The random-curve experiment with shifted coefficients: ``curves``
+    random curves of total degree ``deg`` (dense: every monomial x^i y^j with
+    i + j <= deg; sparse: each kept with probability 1/4, the x^deg and y^deg
+    terms always), coefficients uniform signed 16-bit; each curve multiplied
+    by 2^k with its constant coefficient raised by one.  Returns all
+    curves * (curves - 1) / 2 pairs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    polys = []
+    for _ in range(curves):
+        v = rng.integers(-(1 << 15), 1 << 15, size=(deg + 1, deg + 1), dtype=np.int64)
+        i = np.arange(deg + 1)[:, None]
+        j = np.arange(deg + 1)[None, :]
+        v[(i + j) > deg] = 0
+        if sparse:
+            v[rng.random(size=v.shape) >= 0.25] = 0
+        for a, b in ((0, deg), (deg, 0)):
+            if v[a, b] == 0:
+                v[a, b] = 1
+        rows = [[int(c) << k for c in r] for r in v.tolist()]
+        rows[0][0] += 1
+        polys.append(BiPoly.from_ints(rows))
+    return [(polys[a], polys[b]) for a in range(curves) for b in range(a + 1, curves)]
+

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "librs.so")
 RS_OK, RS_PENDING = 0, 1
 ERRORS = {-1: "RS_ERR_ARG", -2: "RS_ERR_CAPACITY", -3: "RS_ERR_NOMEM", -4: "RS_ERR_CUDA",
           -5: "RS_ERR_TIMEOUT", -6: "RS_ERR_LIMIT", -7: "RS_ERR_STATE"}
-RS_MAX_LIMBS, RS_MAX_DEG_Y, RS_MAX_POINTS, RS_MAX_PRIMES = 64, 71, 16384, 16384
+RS_MAX_LIMBS, RS_MAX_DEG_Y, RS_MAX_POINTS, RS_MAX_PRIMES = 128, 71, 16384, 16384
 
 # Every function that include/rs.h declares, with its ctypes signature.
 EXPORTS = {}
@@ -93,6 +93,9 @@ _SIGS = {
     "rs_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, _P(rs_upoly), _P(c_double), c_int64]),
     "rs_server_stats_get": (c_int32, [c_void_p, _P(rs_server_stats)]),
     "rs_server_stop": (c_int32, [c_void_p]),
+    "rs_resultant_x": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly)]),
+    "rs_projections": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly),
+                                 _P(rs_upoly), _P(c_int32)]),
     "rs_autotune": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
     "rs_autotune_entries": (c_int32, [_P(rs_tune_entry), c_int32, _P(c_int32)]),
     "rs_autotune_save": (c_int32, [c_char_p]),
@@ -148,6 +151,13 @@ class _Polys:
         for s, a in zip(self.structs, self.arrays):
             s.deg_x, s.deg_y, s.limbs = a.shape[0] - 1, a.shape[1] - 1, a.shape[2]
             s.coeffs = a.ctypes.data_as(POINTER(c_uint32))
+
+
+def swap_xy(f):
+    """The same polynomial with x and y exchanged (only used here to size the
+    output buffers of Res_x; the library exchanges the variables itself)."""
+    b = as_bipoly(f)
+    return BiPoly(np.ascontiguousarray(b.coeffs.transpose(1, 0, 2)))
 
 
 def result_bound(f, g):
@@ -242,6 +252,26 @@ class Context:
         _check(self.lib.rs_resultant_batch(self.h, len(pairs), F.structs, G.structs, out.structs,
                                            status), self.h)
         return out.raw() if raw else out.ints()
+
+    def resultant_x(self, f, g):
+        """Res_x(f, g) in Z[y] as a list of Python ints (coefficient k of y^k)."""
+        P = _Polys([f, g])
+        out = _Outputs([(swap_xy(f), swap_xy(g))])
+        _check(self.lib.rs_resultant_x(self.h, ctypes.byref(P.structs[0]),
+                                       ctypes.byref(P.structs[1]), out.structs), self.h)
+        return out.ints()[0]
+
+    def projections(self, pairs, raw=False):
+        """(Res_y list, Res_x list) of every pair, computed in one batch."""
+        F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        oy = _Outputs(pairs)
+        ox = _Outputs([(swap_xy(f), swap_xy(g)) for f, g in pairs])
+        status = (c_int32 * max(2 * len(pairs), 1))()
+        _check(self.lib.rs_projections(self.h, len(pairs), F.structs, G.structs, oy.structs,
+                                       ox.structs, status), self.h)
+        if raw:
+            return oy.raw(), ox.raw()
+        return oy.ints(), ox.ints()
 
     def images(self, f, g, nprimes, npoints):
         """(primes[K], points[K, N], images[K, N]): images[k, i] =

@@ -266,9 +266,9 @@ def test_maximum_capacity_and_limbs(ctx):
     g = rand_bipoly(rng, 1, 70, bits=40)
     R = ctx.resultant_y(f, g)
     check_sampled_31(f, g, R, rng, samples=2)
-    wide_f = rand_bipoly(rng, 2, 3, bits=2040)
-    wide_g = rand_bipoly(rng, 3, 2, bits=2040)
-    assert inputs.BiPoly.from_ints(wide_f).limbs == 64
+    wide_f = rand_bipoly(rng, 2, 3, bits=4090)
+    wide_g = rand_bipoly(rng, 3, 2, bits=4090)
+    assert inputs.BiPoly.from_ints(wide_f).limbs == rs.RS_MAX_LIMBS
     assert ctx.resultant_y(wide_f, wide_g) == oracle(wide_f, wide_g)
 
 

@@ -25,11 +25,20 @@ def rand_bipoly(rng, dx, dy, bound=20, density=1.0):
     return f
 
 
+def golden_var(path):
+    """'y' for Res_y fixtures, 'x' for files with a `var: x` line."""
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line.startswith("var:"):
+            return line.split(":")[1].strip()
+    return "y"
+
+
 def load_golden(path):
     f, g, R = {}, {}, {}
     for line in open(path):
         line = line.split("#")[0].strip()
-        if not line:
+        if not line or line.startswith("var:"):
             continue
         tag, rest = line.split(":")
         nums = [int(t) for t in rest.split()]
@@ -50,7 +59,9 @@ def load_golden(path):
     return dense(f), dense(g), zx_trim([R.get(k, 0) for k in range(deg + 1)])
 
 
-GOLDEN = sorted(glob.glob(os.path.join(HERE, "golden", "*.txt")))
+ALL_GOLDEN = sorted(glob.glob(os.path.join(HERE, "golden", "*.txt")))
+GOLDEN = [p for p in ALL_GOLDEN if golden_var(p) == "y"]
+GOLDEN_X = [p for p in ALL_GOLDEN if golden_var(p) == "x"]
 
 
 @pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p) for p in GOLDEN])
@@ -60,6 +71,59 @@ def test_golden(path):
     assert exact.resultant_y_bareiss_zx(f, g) == R
     assert exact.resultant_y(f, g) == R
     assert exact.resultant_y_interp(f, g) == R
+
+
+@pytest.mark.parametrize("path", GOLDEN_X, ids=[os.path.basename(p) for p in GOLDEN_X])
+def test_golden_resultant_x(path):
+    f, g, R = load_golden(path)
+    assert exact.resultant_x(f, g) == R
+
+
+def test_resultant_x_product_formula_and_projections():
+    """Res_x(f, g) = lc_x(f)^{n_x} prod_i g(a_i(y), y) for f = c * prod_i (x - a_i(y))
+    with a_i in Z[y]; and both projections vanish at the coordinates of a
+    planted common root (Theorem 3.1)."""
+    rng = random.Random(41)
+    for trial in range(6):
+        c = rng.choice([1, -2, 3])
+        roots = [[rng.randint(-3, 3) for _ in range(rng.randint(1, 3))] for _ in range(rng.randint(1, 3))]
+        # f(x, y) = c * prod (x - a_i(y)) as rows f[i][j] (x^i y^j)
+        fx = [[c]]  # coefficients in x, each a Z[y] polynomial
+        for a in roots:
+            nxt = [[] for _ in range(len(fx) + 1)]
+            for i, ci in enumerate(fx):
+                nxt[i + 1] = zx_add(nxt[i + 1], ci)
+                nxt[i] = zx_add(nxt[i], zx_mul([-1], zx_mul(a, ci)))
+            fx = nxt
+        f = exact.transpose(exact.transpose([list(r) for r in fx]))  # rows by x-exponent
+        g = rand_bipoly(rng, rng.randint(1, 3), rng.randint(0, 3))
+        R = exact.resultant_x(f, g)
+        # prod_i g(a_i(y), y): evaluate g at x = a_i(y) in Z[y]
+        want = [c ** (len(g) - 1)] if len(g) > 1 else [1]
+        for a in roots:
+            val = []
+            for i, row in enumerate(g):
+                term = list(row)
+                for _ in range(i):
+                    term = zx_mul(term, a)
+                val = zx_add(val, term)
+            want = zx_mul(want, val)
+        assert R == zx_trim(want), trial
+    # planted common root (x0, y0) = (2, -1)
+    f = [[1, 0, 1], [0, 1, 0], [-1, 0, 0]]        # 1 + y^2 + x y - x^2 -> f(2,-1) = 1 + 1 - 2 - 4 != 0
+    f[0][0] -= (1 + 1 - 2 - 4)                    # shift so that f(2, -1) = 0
+    g = [[3, 1], [1, 0]]                          # 3 + y + x -> g(2, -1) = 4
+    g[0][0] -= 4
+    Ry, Rx = exact.resultant_y(f, g), exact.resultant_x(f, g)
+    assert exact.zx_eval(Ry, 2) == 0 and exact.zx_eval(Rx, -1) == 0
+    assert Ry and Rx
+
+
+def test_planted_transpose_mistake_is_caught():
+    """An x-projection that forgot to exchange the variables is caught by the
+    worked examples."""
+    wrong = [exact.resultant_y(*load_golden(p)[:2]) == load_golden(p)[2] for p in GOLDEN_X]
+    assert not all(wrong)
 
 
 def test_leibniz_bareiss_kronecker_interp_agree():
