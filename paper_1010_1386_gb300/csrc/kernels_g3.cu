@@ -47,7 +47,7 @@ __device__ __forceinline__ uint32_t finish64_3(int64_t s, const ModP &m) {
 // residues, constants and that triangle prefetched into shared memory.
 // The work per coefficient is still K^2 / 2 products, but W and the digits
 // come from shared memory, each value reused 32 and 64 times.
-__global__ void __launch_bounds__(256) g3t_kernel(G3Args a) {
+__global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
   __shared__ int32_t Ws[G3T_LC][G3T_BK + 1];  // W[k0 + r][l0 + c] at Ws[c][r]
   __shared__ int32_t Vs[G3T_LC][G3T_JT];      // digit l0 + c of coefficient j0 + jj
   __shared__ int32_t Wt[G3T_BK][G3T_BK + 1];  // W[k0 + r][k0 + c], c < r
@@ -74,16 +74,36 @@ __global__ void __launch_bounds__(256) g3t_kernel(G3Args a) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0;
     int cnt = 0;
-    for (int l0 = 0; l0 < k0; l0 += G3T_LC) {  // k0 is a multiple of G3T_LC: full chunks
-      for (int e = tid; e < G3T_LC * G3T_BK; e += blockDim.x) {
-        const int r = e >> 5, c = e & 31, k = k0 + r;
-        Ws[c][r] = r < bk ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + l0 + c) : 0;
+    // Chunks of W (8 values per thread) and digits (4 per thread) are loaded
+    // into registers one chunk ahead, so their latency overlaps the products.
+    constexpr int NW = G3T_LC * G3T_BK / 256, NV = G3T_LC * G3T_JT / 256;
+    int32_t wreg[NW], vreg[NV];
+    auto fetch = [&](int l0) {
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        const int e = tid + 256 * q, r = e >> 5, c = e & 31, k = k0 + r;
+        wreg[q] = r < bk ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + l0 + c) : 0;
       }
-      for (int e = tid; e < G3T_LC * G3T_JT; e += blockDim.x) {
-        const int c = e >> 5, jj = e & 31, j = j0 + jj;
-        Vs[c][jj] = j < N ? (int32_t)col[(size_t)(l0 + c) * N + j] : 0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int e = tid + 256 * q, c = e >> 5, jj = e & 31, j = j0 + jj;
+        vreg[q] = j < N ? (int32_t)col[(size_t)(l0 + c) * N + j] : 0;
+      }
+    };
+    if (k0 > 0) fetch(0);
+    for (int l0 = 0; l0 < k0; l0 += G3T_LC) {  // k0 is a multiple of G3T_LC: full chunks
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        const int e = tid + 256 * q;
+        Ws[e & 31][e >> 5] = wreg[q];
+      }
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int e = tid + 256 * q;
+        Vs[e >> 5][e & 31] = vreg[q];
       }
       __syncthreads();
+      if (l0 + G3T_LC < k0) fetch(l0 + G3T_LC);
 #pragma unroll 4
       for (int c = 0; c < G3T_LC; ++c) {
         int32_t w[4];
