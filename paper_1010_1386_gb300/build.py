@@ -66,7 +66,7 @@ def build(force=False, verbose=False, jobs=None):
         list(ex.map(run, cmds))
     if force or cmds or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs)
+        run([NVCC] + ARCH + ["-shared", "-Xlinker", "--no-undefined", "-o", tmp] + objs)
         os.replace(tmp, LIB)
     return LIB
 

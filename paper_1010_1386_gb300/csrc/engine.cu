@@ -329,7 +329,7 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     const PairPlan &p = plans[i];
     if (p.status != RS_OK || p.trivial_zero) continue;
     const int64_t chunks = (p.Lout + 15) / 16;
-    out += (int64_t)p.N * p.Lout;
+    out += (int64_t)p.N * p.Lout + 2;
     xl += (int64_t)p.N * 16 * chunks;
     cy += (int64_t)p.N * chunks;
     img += (int64_t)p.K * p.N;
@@ -428,6 +428,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     b->info.modmul_interp += (double)p.K * ((double)p.N * p.N + 8.0 * p.N);
     b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
   }
+  b->shape_off = b->out_words;  // per pair (1 + degree, limbs), written by the last CRT kernel
+  if (!images_only) b->out_words += 2 * (int64_t)b->descs.size();
   if (images_only) b->out_words = std::max(b->out_words, b->img_words);
 
   // G1 tiles grouped by register-capacity class; costliest pairs first.
@@ -902,6 +904,8 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.xl = b->d_xl;
     a3.carry = b->d_cy;
     a3.out = b->d_out;
+    a3.shape = reinterpret_cast<int32_t *>(b->d_out + b->shape_off);
+    RS_CUDA(ctx, cudaMemsetAsync(a3.shape, 0, b->descs.size() * 2 * sizeof(int32_t), s));
     a3.kmax = b->kmax;
     RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s));
     RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
@@ -945,30 +949,19 @@ int rs_fetch_async(rs_batch *b) {
   return RS_OK;
 }
 
-static int coef_limbs_needed(const uint32_t *c, int L) {
-  const uint32_t ext = (c[L - 1] >> 31) ? 0xffffffffu : 0u;
-  int l = L;
-  while (l > 1 && c[l - 1] == ext && ((c[l - 2] >> 31) ? 0xffffffffu : 0u) == ext) --l;
-  return l;
-}
-
-// Trimmed degree and limb count of pair i's result in the host staging buffer.
+// Degree and limb count of pair i's result (recorded on the device by the
+// last CRT kernel and copied back with the limbs), and its limbs in the host
+// staging buffer.
 static const uint32_t *result_shape(rs_batch *b, int i, int *deg, int *limbs) {
   const PairPlan &p = b->plans[i];
   *deg = -1;
   *limbs = 1;
   if (p.trivial_zero) return nullptr;
-  const uint32_t *w = b->h_out + b->descs[b->dev_index[i]].out_off;
-  for (int j = 0; j < p.N; ++j) {
-    const uint32_t *c = w + (size_t)j * p.Lout;
-    bool nz = false;
-    for (int l = 0; l < p.Lout; ++l) nz = nz || c[l];
-    if (nz) {
-      *deg = j;
-      *limbs = std::max(*limbs, coef_limbs_needed(c, p.Lout));
-    }
-  }
-  return w;
+  const int d = b->dev_index[i];
+  const int32_t *shape = reinterpret_cast<const int32_t *>(b->h_out + b->shape_off) + 2 * (size_t)d;
+  *deg = shape[0] - 1;
+  *limbs = std::max(1, (int)shape[1]);
+  return b->h_out + b->descs[d].out_off;
 }
 
 int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, int *limbs) {
@@ -977,7 +970,7 @@ int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, in
   const uint32_t *w = result_shape(b, i, deg, limbs);
   words.assign((size_t)(*deg + 1) * *limbs, 0u);
   for (int j = 0; j <= *deg; ++j)
-    for (int l = 0; l < *limbs; ++l) words[(size_t)j * *limbs + l] = w[(size_t)j * p.Lout + l];
+    memcpy(&words[(size_t)j * *limbs], w + (size_t)j * p.Lout, (size_t)*limbs * 4);
   return RS_OK;
 }
 

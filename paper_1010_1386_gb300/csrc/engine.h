@@ -112,6 +112,7 @@ struct rs_batch {
   std::vector<RsClassLaunch> classes;
   std::vector<RsG2Class> g2cls;
   int64_t in_words = 0, img_words = 0, out_words = 0;
+  int64_t shape_off = 0;  // word offset of the per-pair result shapes in the output buffer
   int ng2 = 0, ng3 = 0, g2_threads = 256;
   int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int64_t xl_words = 0, cy_words = 0;

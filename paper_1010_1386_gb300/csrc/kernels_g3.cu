@@ -222,7 +222,10 @@ __global__ void g3b_kernel(G3Args a) {
   a.carry[pd.cy_off + (size_t)c * N + j] = carry;
 }
 
-// Carries and output: one thread per coefficient.
+// Carries and output: one thread per coefficient.  Also records the shape of
+// each pair's result: shape[2 pair] = 1 + the largest index of a non-zero
+// coefficient (0 for R = 0) and shape[2 pair + 1] = the most two's-complement
+// limbs any coefficient needs (both by atomicMax on zeroed words).
 __global__ void g3c_kernel(G3Args a) {
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
@@ -232,6 +235,8 @@ __global__ void g3c_kernel(G3Args a) {
   const uint32_t *xl = a.xl + pd.xl_off + j;
   uint32_t *o = a.out + pd.out_off + (size_t)j * L;
   int64_t r = 0;
+  int last_nz = -1, last_nf = -1;  // last limb != 0, last limb != 0xffffffff
+  uint32_t top_nz = 0u, top_nf = 0u, top = 0u;
   for (int c = 0; c < C; ++c) {
     for (int w = 0; w < 16; ++w) {
       const uint32_t word = xl[(size_t)(16 * c + w) * N];
@@ -242,10 +247,29 @@ __global__ void g3c_kernel(G3Args a) {
       const uint32_t e1 = (uint32_t)t1 & 0xffffu;
       r = (t1 - (int64_t)e1) >> 16;
       const int l = 16 * c + w;
-      if (l < L) o[l] = e0 | (e1 << 16);
+      if (l < L) {
+        const uint32_t limb = e0 | (e1 << 16);
+        o[l] = limb;
+        if (limb != 0u) {
+          last_nz = l;
+          top_nz = limb;
+        }
+        if (limb != 0xffffffffu) {
+          last_nf = l;
+          top_nf = limb;
+        }
+        top = limb;
+      }
     }
     r += a.carry[pd.cy_off + (size_t)c * N + j];
   }
+  // fewest limbs whose two's-complement value is this coefficient
+  const bool neg = (top >> 31) != 0u;
+  if (!neg && last_nz < 0) return;  // a zero coefficient
+  int need = neg ? last_nf + 1 + ((top_nf >> 31) ? 0 : 1) : last_nz + 1 + ((top_nz >> 31) ? 1 : 0);
+  need = max(1, min(need, L));
+  atomicMax(a.shape + 2 * task.x, j + 1);
+  atomicMax(a.shape + 2 * task.x + 1, need);
 }
 
 // W[k][l] = p_0 ... p_{l-1} mod p_k (Montgomery form, signed), one thread per k.

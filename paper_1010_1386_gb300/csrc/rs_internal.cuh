@@ -114,6 +114,7 @@ struct G3Args {
   uint32_t *xl;            // 16-bit digit pairs of R_j, [16 chunk + w][N] per pair
   int64_t *carry;          // chunk carries [chunk][N] per pair
   uint32_t *out;           // out: [coefficient][limb]
+  int32_t *shape;          // out: per pair (1 + degree, limbs needed), zeroed before the launch
   int32_t kmax;            // largest K of the batch
 };
 

@@ -142,15 +142,26 @@ def as_bipoly(f):
     return f if isinstance(f, BiPoly) else BiPoly.from_ints(f)
 
 
+# Host image of rs_bipoly (three int32, padding, a pointer), filled with
+# vectorised numpy and viewed as the ctypes struct array.
+_BIPOLY_DT = np.dtype([("deg_x", "<i4"), ("deg_y", "<i4"), ("limbs", "<i4"), ("pad", "<i4"),
+                       ("coeffs", "<u8")])
+
+
 class _Polys:
     """Keeps the limb arrays alive while C structs point at them."""
 
     def __init__(self, polys):
         self.arrays = [np.ascontiguousarray(as_bipoly(p).coeffs, dtype=np.uint32) for p in polys]
-        self.structs = (rs_bipoly * max(len(polys), 1))()
-        for s, a in zip(self.structs, self.arrays):
-            s.deg_x, s.deg_y, s.limbs = a.shape[0] - 1, a.shape[1] - 1, a.shape[2]
-            s.coeffs = a.ctypes.data_as(POINTER(c_uint32))
+        n = len(self.arrays)
+        self.raw = np.zeros(max(n, 1), dtype=_BIPOLY_DT)
+        if n:
+            shp = np.array([a.shape for a in self.arrays], dtype=np.int32)
+            self.raw["deg_x"][:n] = shp[:, 0] - 1
+            self.raw["deg_y"][:n] = shp[:, 1] - 1
+            self.raw["limbs"][:n] = shp[:, 2]
+            self.raw["coeffs"][:n] = [a.__array_interface__["data"][0] for a in self.arrays]
+        self.structs = (rs_bipoly * max(n, 1)).from_buffer(self.raw)
 
 
 def swap_xy(f):
