@@ -166,7 +166,9 @@ typedef struct {
   int64_t images;             /* (pair, prime, point) univariate resultants */
   int64_t primes_total;       /* sum over pairs of the prime count K */
   int64_t coeffs_total;       /* sum over pairs of D + 1 */
-  double modmul_eval;         /* algorithmic modular products: evaluation (a3) */
+  double modmul_eval;         /* algorithmic modular products: evaluation (a3; the two images of
+                                  a point pair +-x share one evaluation of the even and odd
+                                  parts, plus one product per coefficient each) */
   double modmul_prs;          /* univariate resultants (a4) */
   double modmul_interp;       /* interpolation (a5) */
   double modmul_crt;          /* Garner CRT (a6) */
@@ -202,7 +204,7 @@ int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *
 /* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
  * (Section 4.1) that the resultant path computes, for the first nprimes
  * primes of the library's table and its first npoints evaluation points,
- * x_{k,i} = q_k^i mod p_k (a geometric progression per prime).
+ * which come in pairs: x_{k,2t} = q_k^t and x_{k,2t+1} = -q_k^t mod p_k.
  * primes_out[nprimes] receives the primes, points_out[k * npoints + i] the
  * points (may be NULL) and images_out[k * npoints + i] the image for prime k
  * at x_{k,i} (0 <= z < p_k). */

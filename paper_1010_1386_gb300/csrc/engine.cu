@@ -115,7 +115,7 @@ int64_t rs_input_words(const rs_bipoly &p) { return (int64_t)(p.deg_x + 1) * (p.
 // ------------------------------------------------------------------ tables
 
 static void free_tables(RsTables &t) {
-  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc, t.wtab, t.p16, t.poff, t.nh};
+  void *p[] = {t.finv, t.gtab, t.qn, t.btab, t.qc, t.qp, t.hq, t.wtab, t.p16, t.poff, t.nh};
   for (void *x : p)
     if (x) cudaFree(x);
   t = RsTables();
@@ -243,11 +243,13 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   cudaError_t e = cudaMalloc(&nt.finv, ni);
   if (e == cudaSuccess) e = cudaMalloc(&nt.gtab, ni);
   if (e == cudaSuccess) e = cudaMalloc(&nt.btab, ni);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.hq, ni);
   if (e == cudaSuccess) e = cudaMalloc(&nt.qc, nc);
   if (e == cudaSuccess) e = cudaMalloc(&nt.qn, nc);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.qp, nc);
   if (e == cudaSuccess)
     e = launch_tables(ctx->d_mods, ctx->d_qbase, nt.K, nt.N, nt.cstride, nt.finv, nt.gtab, nt.btab,
-                      nt.qc, nt.qn, ctx->stream);
+                      nt.hq, nt.qc, nt.qn, nt.qp, ctx->stream);
   // Chinese-remaindering tables for the same primes.
   std::vector<int32_t> poff(nt.K + 1, 0);
   for (int k = 0; k < nt.K; ++k) poff[k + 1] = poff[k] + p16_row(k);
@@ -332,9 +334,9 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     out += (int64_t)p.N * p.Lout + 2;
     xl += (int64_t)p.N * 16 * chunks;
     cy += (int64_t)p.N * chunks;
-    img += (int64_t)p.K * p.N;
+    img += (int64_t)p.K * 2 * ((p.N + 1) / 2);
     meta += p.f.my + p.g.my + 2;
-    tiles += (int64_t)p.K * ((p.N + 31) / 32);
+    tiles += (int64_t)p.K * (((p.N + 1) / 2 + 15) / 16);
     g2 += p.K;
     g3 += (p.N + 127) / 128;
     g3d += (p.N + 31) / 32;  // digit tiles
@@ -369,7 +371,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   std::vector<int> order;
   b->in_f.assign(n, -1);
   b->in_g.assign(n, -1);
-  int maxN = 1, maxK = 0, maxDx = 0;
+  int maxM = 1, maxK = 0, maxDx = 0;  // largest point-pair count, prime count, x-degree
   for (int i = 0; i < n; ++i) {
     b->in_f[i] = b->in_words;
     b->in_words += rs_input_words(f[i]);
@@ -382,6 +384,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     d.my = p.f.my;
     d.ny = p.g.my;
     d.N = p.N;
+    d.NI = 2 * ((p.N + 1) / 2);
     d.K = p.K;
     d.Lf = p.f.L;
     d.Lg = p.g.L;
@@ -405,7 +408,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       start += p.g.dx[j] + 1;
     }
     d.img_off = b->img_words;
-    b->img_words += (int64_t)p.K * p.N;
+    b->img_words += (int64_t)p.K * d.NI;
     d.out_off = b->out_words;
     b->out_words += (int64_t)p.N * p.Lout;
     const int64_t chunks = (p.Lout + 15) / 16;
@@ -416,16 +419,18 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     b->dev_index[i] = (int)b->descs.size();
     b->descs.push_back(d);
     order.push_back(i);
-    maxN = std::max(maxN, p.N);
+    maxM = std::max(maxM, d.NI / 2);
     maxK = std::max(maxK, p.K);
     maxDx = std::max(maxDx, std::max(p.f.mx, p.g.mx));
-    b->info.images += (int64_t)p.K * p.N;
+    b->info.images += (int64_t)p.K * d.NI;
     b->info.primes_total += p.K;
     b->info.coeffs_total += p.N;
-    const double imgs = (double)p.K * p.N;
-    b->info.modmul_eval += imgs * (p.f.nc + p.g.nc);
+    const double imgs = (double)p.K * d.NI;
+    // per image: half of the evaluation (the two images of a point pair share
+    // the even and odd parts) plus one product per coefficient to combine them
+    b->info.modmul_eval += imgs * (0.5 * (p.f.nc + p.g.nc) + (p.f.my + 1) + (p.g.my + 1));
     b->info.modmul_prs += imgs * 2.0 * prs_updates(p.f.my, p.g.my);
-    b->info.modmul_interp += (double)p.K * ((double)p.N * p.N + 8.0 * p.N);
+    b->info.modmul_interp += (double)p.K * ((double)d.NI * d.NI / 2 + 8.0 * d.NI);  // two interpolations of NI / 2
     b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
   }
   b->shape_off = b->out_words;  // per pair (1 + degree, limbs), written by the last CRT kernel
@@ -482,7 +487,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       cl.cost += (double)p.K * p.N * (p.f.nc + p.g.nc + 2.0 * p.f.my * p.g.my);
       cl.smem = std::max(cl.smem, (size_t)rs_g1_staged_words(p, cap, T) * 4);
       for (int k = 0; k < p.K; ++k)
-        for (int x0 = 0; x0 < p.N; x0 += T) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T, p.N - x0)});
+        for (int x0 = 0; x0 < (p.N + 1) / 2; x0 += T / 2)  // point pairs: two threads each
+          tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T / 2, (p.N + 1) / 2 - x0)});
     }
     cl.ntiles = (int)((int64_t)tiles.size() - cl.tile_off);
     if (cl.ntiles > 0) b->classes.push_back(cl);
@@ -506,7 +512,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   if (!images_only) {
     std::vector<std::vector<int>> bylg(RS_NTT_LGMAX + 1);
     for (int i : byN) {
-      const int lg = rs_g2_len(b->plans[i].N);
+      const int lg = rs_g2_len((b->plans[i].N + 1) / 2);
       if (lg) bylg[lg].push_back(i);
     }
     for (int lg = 1; lg <= RS_NTT_LGMAX; ++lg) {
@@ -515,8 +521,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       int64_t images = 0;
       for (int i : bylg[lg]) {
         const PairPlan &p = b->plans[i];
-        cd += p.K * rs_g2_cost(p.N, 0);
-        cn += p.K * rs_g2_cost(p.N, 1);
+        cd += p.K * rs_g2_cost((p.N + 1) / 2, 0);
+        cn += p.K * rs_g2_cost((p.N + 1) / 2, 1);
         images += (int64_t)p.K * p.N;
       }
       const int model = cn < cd ? 1 : 0;
@@ -553,11 +559,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     int cmaxN = 0;
     for (int i : byN) {
       if (g2lg[i] != lg) continue;
-      cmaxN = std::max(cmaxN, b->plans[i].N);
+      cmaxN = std::max(cmaxN, (b->plans[i].N + 1) / 2);  // point pairs
       for (int k = 0; k < b->plans[i].K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
     }
     gc.count = (int)((int64_t)g2.size() - gc.off);
-    gc.smem = (size_t)(3 * ((cmaxN + 3) & ~3) + 2 * (1 << lg)) * 4;
+    gc.smem = (size_t)(4 * ((cmaxN + 3) & ~3) + 2 * (1 << lg)) * 4;
     b->g2cls.push_back(gc);
   }
   const int nlg = (int)b->g2cls.size();
@@ -569,15 +575,15 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     for (int i : byN) {
       const PairPlan &p = b->plans[i];
       if (g2lg[i]) continue;
-      const int npair = ((p.N + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;
+      const int npair = (((p.N + 1) / 2 + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;  // output-block pairs
       const int rounds = (npair + 255) / 256;
       const int warps = (npair + 32 * rounds - 1) / (32 * rounds);
       if (warps - 1 != c) continue;
-      cmaxN = std::max(cmaxN, p.N);
+      cmaxN = std::max(cmaxN, (p.N + 1) / 2);
       for (int k = 0; k < p.K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
     }
     gc.count = (int)((int64_t)g2.size() - gc.off);
-    gc.smem = (size_t)3 * (cmaxN + 2 * RS_G2_PAD) * 4;
+    gc.smem = (size_t)4 * (cmaxN + 2 * RS_G2_PAD) * 4;
     if (gc.count > 0 && !images_only) b->g2cls.insert(b->g2cls.begin() + nlg, gc);  // largest point counts first
   }
   // CRT digits in tiles of 32 coefficients; limbs in blocks of 128
@@ -597,7 +603,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->ng3d = images_only ? 0 : (int)g3d.size();
   b->ng3b = images_only ? 0 : (int)g3b.size();
   b->kmax = maxK;
-  b->g2smem = (size_t)3 * (maxN + 2 * RS_G2_PAD) * 4;
+  b->g2smem = (size_t)4 * (maxM + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
   b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) +
@@ -605,7 +611,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                             (b->ng3 > 0);
 
   int rc = RS_OK;
-  if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxN, maxDx);
+  if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxM, maxDx);
   for (int lg = 1; lg <= RS_NTT_LGMAX && rc == RS_OK; ++lg)
     if (bhatK[lg]) rc = rs_ensure_bhat(ctx, lg, bhatK[lg]);
   if (rc != RS_OK) {
@@ -813,6 +819,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a.mods = ctx->d_mods;
     a.qc = tab.qc;
     a.qn = tab.qn;
+    a.qp = tab.qp;
     a.tstride = tab.cstride;
     a.vtab = ctx->d_vtab;
     a.num = b->d_num;
@@ -847,6 +854,7 @@ static int enqueue(rs_batch *b, bool capturing) {
       an.den = b->d_den;
       an.coef = b->d_num;
       an.finv = tab.finv;
+      an.hq = tab.hq;
       an.gtab = tab.gtab;
       an.tab_stride = tab.N;
       an.tw = ctx->d_ntt_tw;
@@ -871,6 +879,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a2.den = b->d_den;
     a2.coef = b->d_num;
     a2.finv = tab.finv;
+    a2.hq = tab.hq;
     a2.gtab = tab.gtab;
     a2.btab = tab.btab;
     a2.tab_stride = tab.N;
@@ -1378,7 +1387,10 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
       RS_CUDA(ctx, cudaMemcpy(qb.data(), ctx->d_qbase, (size_t)nprimes * 4, cudaMemcpyDeviceToHost));
       for (int k = 0; k < nprimes; ++k) {
         const ModP m = make_modp(ctx->primes[k]);
-        for (int i = 0; i < npoints; ++i) points_out[(size_t)k * npoints + i] = from_mont(mpow(qb[k], i, m), m);
+        for (int i = 0; i < npoints; ++i) {  // point 2 t + s is (-1)^s q^t
+          const uint32_t pw = from_mont(mpow(qb[k], (uint32_t)(i >> 1), m), m);
+          points_out[(size_t)k * npoints + i] = (i & 1) ? mneg(pw, m.p) : pw;
+        }
       }
     }
   } else {
@@ -1399,7 +1411,7 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
     if (rc == RS_OK) {
       uint32_t *d_pts = points_out ? b->d_out : nullptr;  // images-only batches size d_out to K * N
       cudaError_t e = launch_finalize_images(ctx->d_mods, ctx->d_qbase, b->d_num, b->d_den, b->d_xl, d_pts,
-                                             nprimes, npoints, b->stream);
+                                             nprimes, npoints, b->descs[0].NI, b->stream);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(images_out, b->d_xl, (size_t)nprimes * npoints * 4, cudaMemcpyDeviceToHost, b->stream);
       if (e == cudaSuccess && points_out)

@@ -18,9 +18,9 @@ struct RsServer;  // server.cu
 // destroyed, so captured graphs stay valid).
 struct RsTables {
   int K = 0;        // primes covered
-  int N = 0;        // interpolation stride (points covered)
-  int cstride = 0;  // chirp stride (point + x-degree + tile window covered)
-  uint32_t *finv = nullptr, *gtab = nullptr, *qn = nullptr;
+  int N = 0;        // interpolation stride (point pairs covered)
+  int cstride = 0;  // chirp stride (point pair + x-degree + tile window covered)
+  uint32_t *finv = nullptr, *gtab = nullptr, *hq = nullptr, *qn = nullptr, *qp = nullptr;
   int32_t *btab = nullptr, *qc = nullptr;
   // Chinese-remaindering tables for the first K primes.
   int32_t *wtab = nullptr;   // triangular p_0 ... p_{l-1} mod p_k

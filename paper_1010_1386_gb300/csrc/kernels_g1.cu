@@ -2,11 +2,14 @@
 // thread per modular image (pair, prime p, point x_i).  Paper, Section 4.1:
 // Collins' algorithm maps f, g to Z_p and evaluates them at points x_i
 // (steps 1-2), then takes z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p.
-// The points are the geometric progression x_i = q^i (q of multiplicative
-// order above the largest point count, chosen per prime): f_j(q^i) is then a
-// correlation of chirp-scaled coefficients with the sequence q^{C(t,2)}
-// (accumulated without per-term reduction), and G2 turns the images back into
-// coefficients with two convolutions.
+// The points come in pairs +-q^i (q of multiplicative order above the
+// largest point count, chosen per prime).  With f_j(x) = E_j(x^2) + x O_j(x^2)
+// (even and odd parts), both images of a pair need E_j and O_j at Q^i only,
+// Q = q^2: the two threads of a pair each evaluate one part, as a correlation
+// of chirp-scaled coefficients with the sequence Q^{C(t,2)} (accumulated
+// without per-term reduction), and exchange it with a shuffle:
+// f_j(+-q^i) = E_j(Q^i) +- q^i O_j(Q^i).  G2 splits the images back into
+// E and O and interpolates each with two convolutions.
 //
 // The univariate resultant keeps the formal degrees (a, b) = (m_y, n_y) of
 // the Sylvester matrix of Section 3.1, so z_i^{(p)} = R^{(y)}(x_i) mod p for
@@ -178,10 +181,11 @@ __device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
 }
 
-// Evaluation at x_i = q^i by the chirp identity i k = C(i+k,2) - C(i,2) - C(k,2):
-//   f_j(q^i) = q^{-C(i,2)} sum_k (f_jk q^{-C(k,2)}) q^{C(i+k,2)}.
-// The staged coefficients a[k][r] = f_{deg-r,k} q^{-C(k,2)} (top-aligned in
-// r, zero past the degree) and the window w[t] = q^{C(x0+t,2)} are signed
+// Evaluation of the even (par = 0) or odd (par = 1) part at Q^i by the chirp
+// identity i m = C(i+m,2) - C(i,2) - C(m,2):
+//   sum_m f_{j,2m+par} Q^{im} = Q^{-C(i,2)} sum_m (f_{j,2m+par} Q^{-C(m,2)}) Q^{C(i+m,2)}.
+// The staged coefficients a[k][r] = f_{deg-r,k} Q^{-C(k div 2,2)} (top-aligned
+// in r, zero past the degree) and the window w[t] = Q^{C(x0+t,2)} are signed
 // representatives (|v| < 2^30): 7 products accumulate exactly in an int64,
 // then one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53.
 __device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) { return rs_fold64(s, c32); }
@@ -192,7 +196,7 @@ __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
 
 template <int C>
 __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, const int2 *meta,
-                                           int deg, const int32_t *win, uint32_t wi,
+                                           int deg, const int32_t *win, uint32_t wi, int par,
                                            const ModP &m) {
   const uint32_t c32 = m.r1;  // 2^32 mod p (<= 2^21 for every table prime)
 #pragma unroll
@@ -204,12 +208,12 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr)
       if (deg - (r0 + rr) >= 0) kmax = max(kmax, meta[deg - (r0 + rr)].y);
-    int k = 0;
+    int k = par;  // rows par, par + 2, ...: window entry k / 2
     while (k <= kmax) {
-      const int kend = min(k + 7, kmax + 1);
+      const int kend = min(k + 14, kmax + 1);  // 7 products per fold
 #pragma unroll 1
-      for (; k < kend; ++k) {
-        const int32_t c = win[k];
+      for (; k < kend; k += 2) {
+        const int32_t c = win[k >> 1];
         const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
         const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
         acc[0] = rs_mac_s32(acc[0], lo.x, c);
@@ -229,7 +233,19 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
   }
 }
 
-// a[k][r] for k <= dx (the largest x-degree), r < C.
+// f_j(+-x) = E_j + (+-x) O_j from the partner lane's part: lane par = 0 holds
+// E_j and keeps +x, lane par = 1 holds O_j and takes -x (xs = +-x).
+template <int C>
+__device__ __forceinline__ void combine_pm(uint32_t (&P)[C], int par, uint32_t xs, const ModP &m) {
+#pragma unroll
+  for (int r = 0; r < C; ++r) {
+    const uint32_t other = __shfl_xor_sync(0xffffffffu, P[r], 1);
+    const uint32_t e = par ? other : P[r], o = par ? P[r] : other;
+    P[r] = madd(e, mmul(o, xs, m), m.p);
+  }
+}
+
+// a[k][r] for k <= dx (the largest x-degree), r < C; qn[t] = Q^{-C(t,2)}.
 template <int C>
 __device__ __forceinline__ void stage_chirp(int32_t *sa, const int2 *smeta, int deg, int dx,
                                             const uint32_t *limbs, int stride, int L,
@@ -239,7 +255,7 @@ __device__ __forceinline__ void stage_chirp(int32_t *sa, const int2 *smeta, int 
     const int k = idx / C, r = idx - k * C, j = deg - r;
     int32_t v = 0;
     if (j >= 0 && k <= smeta[j].y)
-      v = signed_rep(mmul(reduce_coef(limbs + ((size_t)k * stride + j) * L, L, V, m), qn[k], m), m.p);
+      v = signed_rep(mmul(reduce_coef(limbs + ((size_t)k * stride + j) * L, L, V, m), qn[k >> 1], m), m.p);
     sa[idx] = v;
   }
 }
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
     const size_t tb = (size_t)tl.prime * a.tstride;
 
     for (int i = threadIdx.x; i < nmeta; i += blockDim.x) smeta[i] = a.meta[pd.meta_off + i];
-    for (int t = threadIdx.x; t < (int)blockDim.x + dxm; t += blockDim.x)
+    for (int t = threadIdx.x; t < (int)(blockDim.x >> 1) + (dxm >> 1) + 1; t += blockDim.x)
       swin[t] = a.qc[tb + tl.x0 + t];
     __syncthreads();
     stage_chirp<C>(saf, smeta, pd.my, pd.mxf, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, a.qn + tb, m);
@@ -290,12 +306,18 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
     }
 
     uint32_t unlucky = 0u, degen = 0u;
-    if ((int)threadIdx.x < tl.n) {
-      const int x = tl.x0 + (int)threadIdx.x;
-      const uint32_t wi = a.qn[tb + x];  // q^{-C(x,2)}
-      uint32_t A[C], B[C];
-      eval_chirp<C>(A, saf, smeta, pd.my, swin + threadIdx.x, wi, m);
-      eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + threadIdx.x, wi, m);
+    const int ti = (int)threadIdx.x >> 1, par = (int)threadIdx.x & 1;
+    const int i = tl.x0 + ti;  // point pair: this thread's image is at (-1)^par q^i
+    // every thread evaluates (the shuffles need the whole warp); only the
+    // threads of the tile's pairs run the remainder sequence
+    const uint32_t wi = a.qn[tb + i], x = a.qp[tb + i];  // Q^{-C(i,2)}, q^i
+    const uint32_t xs = par ? mneg(x, m.p) : x;
+    uint32_t A[C], B[C];
+    eval_chirp<C>(A, saf, smeta, pd.my, swin + ti, wi, par, m);
+    eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + ti, wi, par, m);
+    combine_pm<C>(A, par, xs, m);
+    combine_pm<C>(B, par, xs, m);
+    if (ti < tl.n) {
       unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
       Prs s;
       s.a = pd.my;
@@ -309,7 +331,7 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
         s.den = mmul(s.den, s.Q, m);
         --s.eprev;
       }
-      const size_t idx = (size_t)pd.img_off + (size_t)tl.prime * pd.N + x;
+      const size_t idx = (size_t)pd.img_off + (size_t)tl.prime * pd.NI + 2 * i + par;
       a.num[idx] = s.sign ? mneg(s.num, m.p) : s.num;
       a.den[idx] = s.den;
       degen = s.degen;

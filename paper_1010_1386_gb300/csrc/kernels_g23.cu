@@ -86,79 +86,114 @@ __device__ void conv_lazy(const int32_t *x, const int32_t *b, uint32_t *y, int n
   }
 }
 
-// One block per (pair, prime).  Shared memory: three regions of N words,
-// each with RS_G2_PAD zero words on both sides.
+// One block per (pair, prime).  The images come in pairs z+-_i at +-q^i,
+// i < M = NI / 2, with R(x) = E(x^2) + x O(x^2):
+//   E(Q^i) = (z+_i + z-_i) / 2,  O(Q^i) = (z+_i - z-_i) / (2 q^i),  Q = q^2,
+// and with z = num / den both are fractions over D_i = den+ den-, inverted
+// together.  E and O (degrees < M) are then interpolated in turn on the
+// geometric points Q^i by the two convolutions above, giving the even and
+// the odd coefficients of R.  Shared memory: four regions of M words, each
+// with RS_G2_PAD zero words on both sides.
 __global__ void g2_kernel(G2Args a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t scratch[128];
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const ModP m = a.mods[task.y];
-  const int N = pd.N, D = N - 1, T = blockDim.x, tid = threadIdx.x;
-  const int W = N + 2 * RS_G2_PAD;
+  const int N = pd.N, NI = pd.NI, M = NI >> 1, D = M - 1, T = blockDim.x, tid = threadIdx.x;
+  const int W = M + 2 * RS_G2_PAD;
   int32_t *X = reinterpret_cast<int32_t *>(sm) + RS_G2_PAD;
   int32_t *Bs = X + W;
   uint32_t *Y = reinterpret_cast<uint32_t *>(Bs + W);
-  const size_t base = (size_t)pd.img_off + (size_t)task.y * N;
+  uint32_t *Oh = Y + W;  // O's interpolation input while E is interpolated
+  const size_t base = (size_t)pd.img_off + (size_t)task.y * NI;
   const size_t tb = (size_t)task.y * a.tab_stride;
-  const uint32_t *finv = a.finv + tb, *gt = a.gtab + tb;
+  const uint32_t *finv = a.finv + tb, *gt = a.gtab + tb, *hq = a.hq + tb;
   const int32_t *bt = a.btab + tb;
 
-  // z_j = num_j / den_j (simultaneous inversion), then x_j = z_j / F_j
   uint32_t *dens = reinterpret_cast<uint32_t *>(Bs);
-  for (int i = tid; i < N; i += T) dens[i] = a.den[base + i];
+  for (int i = tid; i < M; i += T) dens[i] = mmul(a.den[base + 2 * i], a.den[base + 2 * i + 1], m);
   __syncthreads();
-  batch_invert(dens, Y, N, m, scratch);
+  batch_invert(dens, Y, M, m, scratch);
   __syncthreads();
-  for (int i = tid; i < N; i += T)
-    X[i] = signed_rep(mmul(mmul(a.num[base + i], Y[i], m), finv[i], m), m.p);
-  for (int i = tid; i < N; i += T) Bs[i] = bt[i];
-  for (int i = tid; i < RS_G2_PAD; i += T) {
-    X[-1 - i] = 0;
-    X[N + i] = 0;
-    Bs[-1 - i] = 0;
-    Bs[N + i] = 0;
+  for (int i = tid; i < M; i += T) {
+    const uint32_t np = a.num[base + 2 * i], dp = a.den[base + 2 * i];
+    const uint32_t nm = a.num[base + 2 * i + 1], dm = a.den[base + 2 * i + 1];
+    const uint32_t e = mmul(mmul2(np, dm, nm, dp, m), Y[i], m);             // z+ + z-
+    const uint32_t o = mmul(mmul2(np, dm, mneg(nm, m.p), dp, m), Y[i], m);  // z+ - z-
+    X[i] = signed_rep(mmul(mmul(e, hq[0], m), finv[i], m), m.p);  // (E / F_i); hq[0] = 1/2
+    Oh[i] = mmul(mmul(o, hq[i], m), finv[i], m);                   // (O / F_i)
   }
   __syncthreads();
-  conv_lazy(X, Bs, Y, N, m);  // Y[k] = q^{C(k,2)} c_k
+  for (int i = tid; i < M; i += T) Bs[i] = bt[i];
+  for (int i = tid; i < RS_G2_PAD; i += T) {
+    X[-1 - i] = 0;
+    X[M + i] = 0;
+    Bs[-1 - i] = 0;
+    Bs[M + i] = 0;
+  }
   __syncthreads();
-  for (int k = tid; k < N; k += T) X[D - k] = signed_rep(mmul(Y[k], gt[k], m), m.p);  // c_k F_k reversed
-  __syncthreads();
-  conv_lazy(X, Bs, Y, N, m);  // Y[D - m] = sum_t c_{m+t} F_{m+t} b_t
-  __syncthreads();
-  for (int i = tid; i < N; i += T) a.coef[base + i] = from_mont(mmul(Y[D - i], finv[i], m), m);
+  for (int half = 0; half < 2; ++half) {  // E: even coefficients, then O: odd ones
+    conv_lazy(X, Bs, Y, M, m);  // Y[k] = Q^{C(k,2)} c_k
+    __syncthreads();
+    for (int k = tid; k < M; k += T) X[D - k] = signed_rep(mmul(Y[k], gt[k], m), m.p);  // c_k F_k reversed
+    __syncthreads();
+    conv_lazy(X, Bs, Y, M, m);  // Y[D - t] = sum_s c_{t+s} F_{t+s} b_s
+    __syncthreads();
+    for (int i = tid; i < M; i += T) {
+      const int c = 2 * i + half;
+      if (c < N) a.coef[base + c] = from_mont(mmul(Y[D - i], finv[i], m), m);
+    }
+    if (half == 0) {
+      for (int i = tid; i < M; i += T) X[i] = signed_rep(Oh[i], m.p);
+      __syncthreads();
+    }
+  }
 }
 
-// Per prime k < K: the chirp tables q^{C(t,2)} (signed representative) and
-// q^{-C(t,2)} for t < stride (evaluation in G1), and for t < N the
-// interpolation tables 1 / F_t, q^{-C(t,2)} F_t and the signed
-// (-1)^t q^{C(t,2)} / F_t, F_t = prod_{s=1}^t (q^s - 1) (G2; finv may be NULL
-// when only the chirp tables are wanted).  One thread per prime.
+// Per prime k < K, with q its point base and Q = q^2: for t < stride the
+// chirp tables Q^{C(t,2)} (signed representative) and Q^{-C(t,2)} and the
+// powers q^t (evaluation in G1), and for t < N the interpolation tables
+// 1 / F_t, Q^{-C(t,2)} F_t, the signed (-1)^t Q^{C(t,2)} / F_t,
+// F_t = prod_{s=1}^t (Q^s - 1), and 1 / (2 q^t) (G2; finv may be NULL when
+// only the chirp tables are wanted).  One thread per prime.
 __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
-                              uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qct,
-                              uint32_t *qnt) {
+                              uint32_t *finv, uint32_t *gtab, int32_t *btab, uint32_t *hqt, int32_t *qct,
+                              uint32_t *qnt, uint32_t *qpt) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   const ModP m = mods[k];
-  const uint32_t q = qbase[k], qi = minv(q, m);
+  const uint32_t qb = qbase[k], qbi = minv(qb, m);
+  const uint32_t q = mmul(qb, qb, m), qi = minv(q, m);  // Q and 1/Q
   {
-    uint32_t up = m.r1, dn = m.r1, qt = m.r1, qit = m.r1;  // q^{C(t,2)}, q^{-C(t,2)}, q^t, q^{-t}
+    uint32_t up = m.r1, dn = m.r1, qt = m.r1, qit = m.r1, pw = m.r1;  // Q^{C(t,2)}, Q^{-C(t,2)}, Q^t, Q^{-t}, q^t
     int32_t *qc = qct + (size_t)k * stride;
     uint32_t *qn = qnt + (size_t)k * stride;
+    uint32_t *qp = qpt + (size_t)k * stride;
     for (int t = 0; t < stride; ++t) {
       qc[t] = signed_rep(up, m.p);
       qn[t] = dn;
+      qp[t] = pw;
       up = mmul(up, qt, m);  // C(t+1,2) = C(t,2) + t
       dn = mmul(dn, qit, m);
       qt = mmul(qt, q, m);
       qit = mmul(qit, qi, m);
+      pw = mmul(pw, qb, m);
     }
   }
   if (!finv) return;
-  uint32_t *fi = finv + (size_t)k * N, *gt = gtab + (size_t)k * N;
+  uint32_t *fi = finv + (size_t)k * N, *gt = gtab + (size_t)k * N, *hq = hqt + (size_t)k * N;
   int32_t *bt = btab + (size_t)k * N;
-  // forward: F_t (kept in fi for now) and q^{-C(t,2)} (kept in gt)
-  uint32_t F = m.r1, qt = m.r1, qneg = m.r1, qinvt = m.r1;  // q^t, q^{-C(t,2)}, q^{-(t-1)}
+  {
+    const uint32_t inv2 = minv(madd(m.r1, m.r1, m.p), m);
+    uint32_t w = inv2;  // 1 / (2 q^t)
+    for (int t = 0; t < N; ++t) {
+      hq[t] = w;
+      w = mmul(w, qbi, m);
+    }
+  }
+  // forward: F_t (kept in fi for now) and Q^{-C(t,2)} (kept in gt)
+  uint32_t F = m.r1, qt = m.r1, qneg = m.r1, qinvt = m.r1;  // Q^t, Q^{-C(t,2)}, Q^{-(t-1)}
   for (int t = 0; t < N; ++t) {
     if (t > 0) {
       qt = mmul(qt, q, m);
@@ -169,10 +204,10 @@ __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, in
     fi[t] = F;
     gt[t] = qneg;
   }
-  // backward: 1 / F_t from 1 / F_{N-1}; q^{C(t,2)} from q^{C(N-1,2)}
+  // backward: 1 / F_t from 1 / F_{N-1}; Q^{C(t,2)} from Q^{C(N-1,2)}
   uint32_t inv = minv(F, m);
-  uint32_t qc = minv(qneg, m);  // q^{C(N-1,2)}
-  uint32_t qm1 = qinvt;         // q^{-(t-1)} at t = N-1
+  uint32_t qc = minv(qneg, m);  // Q^{C(N-1,2)}
+  uint32_t qm1 = qinvt;         // Q^{-(t-1)} at t = N-1
   for (int t = N - 1; t >= 0; --t) {
     const uint32_t Ft = fi[t];
     fi[t] = inv;
@@ -181,9 +216,9 @@ __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, in
     bt[t] = signed_rep(bv, m.p);
     gt[t] = mmul(gt[t], Ft, m);
     if (t > 0) {
-      inv = mmul(inv, msub(qt, m.r1, m.p), m);  // 1/F_{t-1} = (q^t - 1) / F_t
+      inv = mmul(inv, msub(qt, m.r1, m.p), m);  // 1/F_{t-1} = (Q^t - 1) / F_t
       qt = mmul(qt, qi, m);
-      qc = mmul(qc, qm1, m);                    // q^{C(t-1,2)} = q^{C(t,2)} q^{-(t-1)}
+      qc = mmul(qc, qm1, m);                    // Q^{C(t-1,2)} = Q^{C(t,2)} Q^{-(t-1)}
       qm1 = mmul(qm1, q, m);
     }
   }
@@ -206,9 +241,11 @@ __global__ void init_primes_kernel(const uint32_t *primes, int n, ModP *mods, ui
   uint32_t acc = m.r1;
   for (int l = 0; l < k; ++l) acc = mmul(acc, to_mont(primes[l] - m.p, m), m);
   crt[k] = minv(acc, m);
-  // base of the geometric evaluation points: the smallest q >= 2 whose
-  // powers q^1 .. q^RS_MAX_POINTS all differ from 1 (so q^0 .. q^(N-1) are
-  // distinct and every q^t - 1 is invertible for t <= N - 1)
+  // base of the evaluation points: the smallest q >= 2 whose powers
+  // q^1 .. q^RS_MAX_POINTS all differ from 1.  Then the points +-q^i,
+  // i < RS_MAX_POINTS / 2, are distinct (q^d = -1 would give q^(2d) = 1 with
+  // 2d <= RS_MAX_POINTS) and every Q^t - 1 = q^(2t) - 1, 0 < t <
+  // RS_MAX_POINTS / 2, is invertible.
   for (uint32_t c = 2;; ++c) {
     const uint32_t qm = to_mont(c, m);
     uint32_t x = qm;
@@ -226,21 +263,25 @@ __global__ void init_primes_kernel(const uint32_t *primes, int n, ModP *mods, ui
 
 __global__ void finalize_images_kernel(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
                                        const uint32_t *den, uint32_t *z, uint32_t *points, int K,
-                                       int N) {
+                                       int N, int NI) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (size_t)K * N) return;
   const int k = (int)(i / N), x = (int)(i % N);
   const ModP m = mods[k];
-  z[i] = from_mont(mmul(num[i], minv(den[i], m), m), m);
-  if (points) points[i] = from_mont(mpow(qbase[k], (uint32_t)x, m), m);
+  const size_t src = (size_t)k * NI + x;
+  z[i] = from_mont(mmul(num[src], minv(den[src], m), m), m);
+  if (points) {  // image 2 i + s is at (-1)^s q^i
+    const uint32_t pw = from_mont(mpow(qbase[k], (uint32_t)(x >> 1), m), m);
+    points[i] = (x & 1) ? mneg(pw, m.p) : pw;
+  }
 }
 
 }  // namespace
 
 cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
-                          uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qc,
-                          uint32_t *qn, cudaStream_t s) {
-  tables_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, qbase, K, N, stride, finv, gtab, btab, qc, qn);
+                          uint32_t *finv, uint32_t *gtab, int32_t *btab, uint32_t *hq, int32_t *qc,
+                          uint32_t *qn, uint32_t *qp, cudaStream_t s) {
+  tables_kernel<<<(K + 63) / 64, 64, 0, s>>>(mods, qbase, K, N, stride, finv, gtab, btab, hq, qc, qn, qp);
   return cudaGetLastError();
 }
 
@@ -264,9 +305,9 @@ cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32
 
 cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
                                    const uint32_t *den, uint32_t *z, uint32_t *points, int K, int N,
-                                   cudaStream_t s) {
+                                   int NI, cudaStream_t s) {
   const size_t n = (size_t)K * N;
   finalize_images_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(mods, qbase, num, den, z, points,
-                                                                      K, N);
+                                                                      K, N, NI);
   return cudaGetLastError();
 }

@@ -3,12 +3,12 @@
 // computed exactly over Z with three NTT primes and Chinese remaindering,
 // then reduced mod the resultant's prime p.
 //
-// The convolution S_k = sum_{j<=k} x_j b_{k-j}, k < N, of signed residues
-// |x_j|, |b_t| < 2^30 satisfies |S_k| < N 2^60 <= 2^72 (N <= 2^12), and the
+// The convolution S_k = sum_{j<=k} x_j b_{k-j}, k < n, of signed residues
+// |x_j|, |b_t| < 2^30 satisfies |S_k| < n 2^60 <= 2^72 (n <= 2^12), and the
 // three primes below multiply to more than 2^92, so S_k is recovered exactly
-// in the symmetric range.  A cyclic transform of length L >= 2N - 1 holds the
+// in the symmetric range.  A cyclic transform of length L >= 2n - 1 holds the
 // linear convolution without wrap-around when b is truncated to t < L/2
-// (terms with t >= N only reach outputs k >= N, which are discarded).
+// (terms with t >= n only reach outputs k >= n, which are discarded).
 //
 // Transforms: forward decimation in frequency (natural order in,
 // bit-reversed out), inverse decimation in time (bit-reversed in, natural
@@ -170,41 +170,61 @@ __device__ __forceinline__ int32_t srep(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
 }
 
-// One block per (pair, prime) whose transform length is 2^lg.  Shared
-// memory: X (N words), V0, V1 (N words each), W (2^lg words), twiddle rows
-// 1 .. lg-1 (2^(lg-1) - 1 pairs).
+// One block per (pair, prime) whose transform length is 2^lg (2^lg >= 2M - 1
+// for the M = NI / 2 point pairs).  As in the direct kernel, the paired
+// images give E(Q^i) and O(Q^i), interpolated in turn into the even and the
+// odd coefficients.  Shared memory: X, V0, V1, Oh (M words each), W (2^lg
+// words), twiddle rows 1 .. lg-1 (2^(lg-1) - 1 pairs).
 __global__ void __launch_bounds__(256) g2n_kernel(G2nArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t scratch[128];
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const ModP m = a.mods[task.y];
-  const int N = pd.N, D = N - 1, T = blockDim.x, tid = threadIdx.x;
+  const int N = pd.N, NI = pd.NI, M = NI >> 1, D = M - 1, T = blockDim.x, tid = threadIdx.x;
+  const int Mp = (M + 3) & ~3;
   int32_t *X = reinterpret_cast<int32_t *>(sm);
-  uint32_t *V0 = reinterpret_cast<uint32_t *>(X + ((N + 3) & ~3));
-  uint32_t *V1 = V0 + ((N + 3) & ~3);
-  uint32_t *W = V1 + ((N + 3) & ~3);
+  uint32_t *V0 = reinterpret_cast<uint32_t *>(X + Mp);
+  uint32_t *V1 = V0 + Mp;
+  uint32_t *Oh = V1 + Mp;
+  uint32_t *W = Oh + Mp;
   uint2 *TWS = reinterpret_cast<uint2 *>(W + (1 << a.lg));
-  const size_t base = (size_t)pd.img_off + (size_t)task.y * N;
+  const size_t base = (size_t)pd.img_off + (size_t)task.y * NI;
   const size_t tb = (size_t)task.y * a.tab_stride;
-  const uint32_t *finv = a.finv + tb, *gt = a.gtab + tb;
+  const uint32_t *finv = a.finv + tb, *gt = a.gtab + tb, *hq = a.hq + tb;
   const uint32_t *bhat = a.bhat + (size_t)task.y * 3 * ((size_t)1 << a.lg);
   // P0 < p, so P0 mod p = P0; P0 P1 mod p and P0 P1 P2 mod p once per block.
   const uint32_t cp0 = a.nc.m[0].p;
   const uint32_t cp01 = (uint32_t)(((uint64_t)a.nc.m[0].p * a.nc.m[1].p) % m.p);
   const uint32_t cneg = redc((uint64_t)(((uint64_t)cp01 * a.nc.m[2].p) % m.p), m.p, m.pinv);  // P R^-1 mod p
 
-  for (int i = tid; i < N; i += T) V0[i] = a.den[base + i];
+  for (int i = tid; i < M; i += T) V0[i] = mmul(a.den[base + 2 * i], a.den[base + 2 * i + 1], m);
   __syncthreads();
-  batch_invert(V0, V1, N, m, scratch);
+  batch_invert(V0, V1, M, m, scratch);
   __syncthreads();
-  for (int i = tid; i < N; i += T) X[i] = srep(mmul(mmul(a.num[base + i], V1[i], m), finv[i], m), m.p);
+  for (int i = tid; i < M; i += T) {
+    const uint32_t np = a.num[base + 2 * i], dp = a.den[base + 2 * i];
+    const uint32_t nm = a.num[base + 2 * i + 1], dm = a.den[base + 2 * i + 1];
+    const uint32_t e = mmul(mmul2(np, dm, nm, dp, m), V1[i], m);             // z+ + z-
+    const uint32_t o = mmul(mmul2(np, dm, mneg(nm, m.p), dp, m), V1[i], m);  // z+ - z-
+    X[i] = srep(mmul(mmul(e, hq[0], m), finv[i], m), m.p);  // (E / F_i); hq[0] = 1/2
+    Oh[i] = mmul(mmul(o, hq[i], m), finv[i], m);             // (O / F_i)
+  }
   __syncthreads();
-  conv_ntt(X, N, a.lg, bhat, a, W, TWS, V0, V1, V0, m, cp0, cp01, cneg);  // V0[k] = q^{C(k,2)} c_k
-  for (int k = tid; k < N; k += T) X[D - k] = srep(mmul(V0[k], gt[k], m), m.p);  // c_k F_k reversed
-  __syncthreads();
-  conv_ntt(X, N, a.lg, bhat, a, W, TWS, V0, V1, V0, m, cp0, cp01, cneg);
-  for (int i = tid; i < N; i += T) a.coef[base + i] = from_mont(mmul(V0[D - i], finv[i], m), m);
+  for (int half = 0; half < 2; ++half) {  // E: even coefficients, then O: odd ones
+    conv_ntt(X, M, a.lg, bhat, a, W, TWS, V0, V1, V0, m, cp0, cp01, cneg);  // V0[k] = Q^{C(k,2)} c_k
+    for (int k = tid; k < M; k += T) X[D - k] = srep(mmul(V0[k], gt[k], m), m.p);  // c_k F_k reversed
+    __syncthreads();
+    conv_ntt(X, M, a.lg, bhat, a, W, TWS, V0, V1, V0, m, cp0, cp01, cneg);
+    for (int i = tid; i < M; i += T) {
+      const int c = 2 * i + half;
+      if (c < N) a.coef[base + c] = from_mont(mmul(V0[D - i], finv[i], m), m);
+    }
+    if (half == 0) {
+      for (int i = tid; i < M; i += T) X[i] = srep(Oh[i], m.p);
+      __syncthreads();
+    }
+  }
 }
 
 // bhat[k][q][i] for prime k < K and NTT prime q: the forward transform of

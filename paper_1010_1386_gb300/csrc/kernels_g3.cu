@@ -57,9 +57,9 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
   __shared__ uint32_t Cs[G3T_BK];
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
-  const int K = pd.K, N = pd.N, j0 = task.y, tid = threadIdx.x;
+  const int K = pd.K, N = pd.N, S = pd.NI, j0 = task.y, tid = threadIdx.x;
   const int rg = tid >> 4, cg = tid & 15;  // rows 4 rg .. 4 rg + 3, columns 2 cg, 2 cg + 1
-  uint32_t *col = a.coef + pd.img_off;     // residue, then digit, of (k, j) at col[k N + j]
+  uint32_t *col = a.coef + pd.img_off;     // residue, then digit, of (k, j) at col[k S + j]
   for (int k0 = 0; k0 < K; k0 += G3T_BK) {
     const int bk = min(G3T_BK, K - k0);
     for (int r = tid; r < bk; r += blockDim.x) {
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const int e = tid + 256 * q, c = e >> 5, jj = e & 31, j = j0 + jj;
-        vreg[q] = j < N ? (int32_t)col[(size_t)(l0 + c) * N + j] : 0;
+        vreg[q] = j < N ? (int32_t)col[(size_t)(l0 + c) * S + j] : 0;
       }
     };
     if (k0 > 0) fetch(0);
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
       for (int c = 0; c < 2; ++c) {
         const int jj = 2 * cg + c, j = j0 + jj;
         const uint32_t tA = finish64_3(rs_fold64(acc[i][c], m.r1), m);
-        const uint32_t res = j < N ? col[(size_t)(k0 + r) * N + j] : 0u;
+        const uint32_t res = j < N ? col[(size_t)(k0 + r) * S + j] : 0u;
         Ds[r][jj] = msub(res, tA, m.p);
       }
     }
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
         const uint32_t v = mmul(msub(Ds[r][jj], finish64_3(s, m), m.p), Cs[r], m);
         const int32_t vs = signed_rep3(v, m.p);
         Vb[r][jj] = vs;
-        if (j < N) col[(size_t)(k0 + r) * N + j] = (uint32_t)vs;
+        if (j < N) col[(size_t)(k0 + r) * S + j] = (uint32_t)vs;
       }
     }
     __syncthreads();  // this block's digits are read by the next digit blocks
@@ -194,7 +194,7 @@ __global__ void g3b_kernel(G3Args a) {
   for (int h = 0; h < 32; ++h) acc[h] = 0;
   const uint32_t *col = a.coef + pd.img_off + j;
   for (int k = lo; k < K; ++k) {
-    const int32_t v = (int32_t)col[(size_t)k * N];
+    const int32_t v = (int32_t)col[(size_t)k * pd.NI];
     const uint4 *row = reinterpret_cast<const uint4 *>(a.p16 + a.poff[k] + 32 * c);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {

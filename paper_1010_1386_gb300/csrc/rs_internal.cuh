@@ -11,9 +11,9 @@
 #define RS_G1_MAX_SMEM_BYTES (RS_G1_MAX_STAGED_WORDS * 4)
 #define RS_G2_PAD 8          // zero words around each G2 shared-memory region
 #define RS_CONV_R 7          // G2 outputs per register block; odd, so lanes hit distinct banks
-#define RS_G2_MAX_SMEM_BYTES (3 * (16384 + 2 * RS_G2_PAD) * 4)
+#define RS_G2_MAX_SMEM_BYTES (4 * (8192 + 2 * RS_G2_PAD) * 4)  // four regions of M <= 8192 pairs
 #define RS_NTT_LGMAX 13      // G2 transforms up to 2^13 points (N <= 2^12)
-#define RS_G2N_MAX_SMEM_BYTES ((3 * 4096 + 2 * (1 << RS_NTT_LGMAX)) * 4)
+#define RS_G2N_MAX_SMEM_BYTES ((4 * 4096 + 2 * (1 << RS_NTT_LGMAX)) * 4)
 
 // Stage counters written by the kernels (detection of unlucky / degenerate cases).
 enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT = 4 };
@@ -21,23 +21,27 @@ enum { ST_UNLUCKY_POINTS = 0, ST_DEGENERATE = 1, ST_UNLUCKY_PRIMES = 2, ST_COUNT
 // One resultant of a batch, as the kernels see it.  Degrees are trimmed.
 struct PairDesc {
   int32_t my, ny;      // actual y-degrees of f and g
-  int32_t N;           // evaluation points = degree bound D + 1
+  int32_t N;           // coefficients = degree bound D + 1
+  // Points come in pairs +-q^i, i < M = ceil(N / 2); the images of prime k are
+  // [k NI, k NI + NI), NI = 2 M, image 2 i + s at x = (-1)^s q^i, and the
+  // interpolated residues (then the CRT digits) keep that stride.
   int32_t K;           // primes
   int32_t Lf, Lg;      // input limbs per coefficient
   int32_t fstride, gstride;  // input row stride in coefficients (= array deg_y + 1)
   int32_t fnc, gnc;    // coefficients kept (sum over j of deg_x f_j + 1)
   int32_t Lout;        // output limbs per coefficient
   int32_t mxf, mxg;    // x-degrees of f and g
-  int32_t pad;
+  int32_t NI;          // images per prime (2 M)
   int64_t f_off, g_off;  // word offsets of the input limb arrays
   int64_t meta_off;      // int2 offset: (my+1) entries for f then (ny+1) for g
-  int64_t img_off;       // offset of the K*N image block (prime-major)
+  int64_t img_off;       // offset of the K*NI image block (prime-major)
   int64_t out_off;       // offset of the N*Lout output block (coefficient-major)
   int64_t xl_off;        // offset of the CRT digit scratch: N * 16 * ceil(Lout/16) words
   int64_t cy_off;        // offset of the CRT chunk carries: N * ceil(Lout/16) int64
 };
 
-// G1 work item: points [x0, x0 + n) of one (pair, prime).
+// G1 work item: point pairs [x0, x0 + n) of one (pair, prime), two threads
+// (the images at +q^i and -q^i) per pair.
 struct Tile {
   int32_t pair;
   int32_t prime;
@@ -54,8 +58,9 @@ struct G1Args {
   const uint32_t *limbs;   // batch input limbs
   const int2 *meta;        // per-j (start in the staged residue array, x-degree or -1)
   const ModP *mods;
-  const int32_t *qc;       // [prime][tstride] q^{C(t,2)}, signed representative (Montgomery)
-  const uint32_t *qn;      // [prime][tstride] q^{-C(t,2)} (Montgomery)
+  const int32_t *qc;       // [prime][tstride] Q^{C(t,2)}, Q = q^2, signed representative (Montgomery)
+  const uint32_t *qn;      // [prime][tstride] Q^{-C(t,2)} (Montgomery)
+  const uint32_t *qp;      // [prime][tstride] q^t (Montgomery)
   int32_t tstride;
   const uint32_t *vtab;    // [prime][RS_VT_STRIDE]
   uint32_t *num;           // numerators  (Montgomery form, sign applied)
@@ -70,9 +75,10 @@ struct G2Args {
   const uint32_t *num;     // in: numerators
   const uint32_t *den;     // in: denominators
   uint32_t *coef;          // out: R mod p coefficients, plain form (may alias num)
-  const uint32_t *finv;    // [prime][tab_stride] 1 / F_t           (Montgomery)
-  const uint32_t *gtab;    // [prime][tab_stride] q^{-C(t,2)} F_t   (Montgomery)
-  const int32_t *btab;     // [prime][tab_stride] (-1)^t q^{C(t,2)} / F_t, signed representative
+  const uint32_t *finv;    // [prime][tab_stride] 1 / F_t, F_t = prod_{s<=t} (Q^s - 1)  (Montgomery)
+  const uint32_t *gtab;    // [prime][tab_stride] Q^{-C(t,2)} F_t   (Montgomery)
+  const int32_t *btab;     // [prime][tab_stride] (-1)^t Q^{C(t,2)} / F_t, signed representative
+  const uint32_t *hq;      // [prime][tab_stride] 1 / (2 q^t)  (Montgomery)
   int32_t tab_stride;
 };
 
@@ -91,7 +97,7 @@ struct G2nArgs {
   const ModP *mods;
   const uint32_t *num, *den;
   uint32_t *coef;          // out (may alias num)
-  const uint32_t *finv, *gtab;  // as in G2Args
+  const uint32_t *finv, *gtab, *hq;  // as in G2Args
   int32_t tab_stride;
   const uint2 *tw;         // [q][forward, inverse][2^RS_NTT_LGMAX]: rows of 2^(lg-1) twiddles
                            // (w_L^j, Shoup quotient), L = 2^lg, starting at 2^(lg-1) - 1
@@ -135,8 +141,9 @@ cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s);
 cudaError_t launch_tables(const ModP *mods, const uint32_t *qbase, int K, int N, int stride,
-                          uint32_t *finv, uint32_t *gtab, int32_t *btab, int32_t *qc,
-                          uint32_t *qn, cudaStream_t s);
+                          uint32_t *finv, uint32_t *gtab, int32_t *btab, uint32_t *hq, int32_t *qc,
+                          uint32_t *qn, uint32_t *qp, cudaStream_t s);
+// z[k N + x] and the point of image x for x < N, from images of stride NI.
 cudaError_t launch_finalize_images(const ModP *mods, const uint32_t *qbase, const uint32_t *num,
                                    const uint32_t *den, uint32_t *z, uint32_t *points, int K, int N,
-                                   cudaStream_t s);
+                                   int NI, cudaStream_t s);

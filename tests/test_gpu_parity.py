@@ -87,7 +87,7 @@ def test_conventions_and_degenerate_inputs(ctx):
 
 
 def test_unlucky_points_and_primes(ctx):
-    """lc_y f vanishing at x = 1 (the first evaluation point q^0 for every
+    """lc_y f vanishing at x = 1 (the first evaluation point +q^0 for every
     prime) and at x = 3, and a leading coefficient divisible by the first
     table prime 2^31 - 1."""
     rng = random.Random(4)
@@ -138,14 +138,19 @@ def test_images_against_oracle(ctx):
     for dx, dy, bits in [(6, 6, 11), (3, 9, 64), (9, 2, 200)]:
         f = rand_bipoly(rng, dx, dy, bits=bits)
         g = rand_bipoly(rng, dx + 1, dy - 1 if dy > 1 else dy, bits=bits)
-        primes, pts, imgs = ctx.images(f, g, 5, 70)
-        assert primes[0] == 2147483647 and all(primes[i] > primes[i + 1] for i in range(4))
-        for k in range(5):
-            p = int(primes[k])
-            assert len(set(int(v) for v in pts[k])) == 70  # distinct points
-            assert all(int(pts[k, i]) * int(pts[k, 1]) % p == int(pts[k, i + 1]) for i in range(69))
-            for i in list(range(8)) + [rng.randrange(70) for _ in range(6)]:
-                assert int(imgs[k, i]) == modp.resultant_image(f, g, p, int(pts[k, i]))
+        for npts in (70, 71):  # an even and an odd number of points
+            primes, pts, imgs = ctx.images(f, g, 5, npts)
+            assert primes[0] == 2147483647 and all(primes[i] > primes[i + 1] for i in range(4))
+            for k in range(5):
+                p = int(primes[k])
+                assert len(set(int(v) for v in pts[k])) == npts  # distinct points
+                # pairs +-q^t: x_{2t+1} = -x_{2t}, x_{2t+2} = x_{2t} x_2
+                assert int(pts[k, 0]) == 1
+                assert all((int(pts[k, 2 * t]) + int(pts[k, 2 * t + 1])) % p == 0 for t in range(npts // 2))
+                assert all(int(pts[k, 2 * t]) * int(pts[k, 2]) % p == int(pts[k, 2 * t + 2])
+                           for t in range((npts - 1) // 2))
+                for i in list(range(8)) + [npts - 1] + [rng.randrange(npts) for _ in range(6)]:
+                    assert int(imgs[k, i]) == modp.resultant_image(f, g, p, int(pts[k, i]))
 
 
 # ---------------------------------------------------------- full-size configs
