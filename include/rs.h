@@ -201,6 +201,24 @@ int rs_resultant_x(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly
 int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
                    rs_upoly *out_y, rs_upoly *out_x, int32_t *status);
 
+/* Square-free factorisation of R = R^{(y)} = res(f, g, y) (the paper's
+ * solver computes R^{(y)} "and a corresponding square-free factorization",
+ * Section 5, PROJECT): R = c * prod_{i >= 1} R_i^i with c an integer and
+ * every R_i in Z[x] primitive, square-free, pairwise coprime, with a
+ * positive leading coefficient.  One GPU pass computes R over enough primes
+ * for the factors' coefficient bound and Yun's algorithm mod every prime;
+ * the factors are lifted by the Chinese remaindering kernels and made
+ * primitive on the host.  content receives c (deg 0); factors[i - 1]
+ * receives R_i for i = 1..max_mult (the constant 1 when R has no factor of
+ * multiplicity i); *nmult the largest multiplicity present (0 when R is a
+ * constant).  Outputs are written on RS_OK; on RS_ERR_CAPACITY the deg and
+ * limbs of the outputs that did not fit give the room needed (a multiplicity
+ * above max_mult also returns RS_ERR_CAPACITY).  R = 0 gives RS_ERR_ARG.
+ * RS_ERR_LIMIT when one of the primes used divides a discriminant of R's
+ * factors (the result would need other primes; not met in practice). */
+int rs_squarefree_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
+                    rs_upoly *content, rs_upoly *factors, int32_t *nmult);
+
 /* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
  * (Section 4.1) that the resultant path computes, for the first nprimes
  * primes of the library's table and its first npoints evaluation points,

@@ -15,17 +15,6 @@ namespace {
 
 thread_local std::string g_err;
 
-struct DevGuard {
-  int prev = -1;
-  explicit DevGuard(int d) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (d >= 0 && prev != d) cudaSetDevice(d);
-  }
-  ~DevGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -598,6 +587,18 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     for (int c = 0; c < chunks; ++c)
       for (int j = 0; j < p.N; j += 128) g3b.push_back(make_int4(di, j, c, 0));
   }
+  std::vector<int2> yun;  // square-free factorisation tasks: every (pair, prime), pairs in order
+  if (opt.yun_maxm > 0 && !images_only) {
+    int maxNp = 1;
+    for (int i = 0; i < n; ++i) {
+      if (b->dev_index[i] < 0) continue;
+      maxNp = std::max(maxNp, b->plans[i].N);
+      for (int k = 0; k < b->plans[i].K; ++k) yun.push_back(make_int2(b->dev_index[i], k));
+    }
+    b->yun_wstride = ((int64_t)maxNp + 3) & ~(int64_t)3;
+    b->yun_ostride = ((int64_t)maxNp + 2 * opt.yun_maxm + 2 + 3) & ~(int64_t)3;
+  }
+  b->nyun = (int)yun.size();
   b->ng2 = images_only ? 0 : (int)g2.size();
   b->ng3 = images_only ? 0 : (int)g3.size();
   b->ng3d = images_only ? 0 : (int)g3d.size();
@@ -606,7 +607,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->g2smem = (size_t)4 * (maxM + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
-  b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) +
+  b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) + (b->nyun > 0) +
                             (b->ng3b > 0) +
                             (b->ng3 > 0);
 
@@ -631,7 +632,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                o_xl = carve(std::max(b->xl_words, b->out_words) * 4), o_out = carve(b->out_words * 4),
                o_g2 = carve(g2.size() * sizeof(int2)), o_g3 = carve(g3.size() * sizeof(int2)),
                o_st = carve(ST_COUNT * sizeof(unsigned long long)), o_cy = carve(b->cy_words * 8),
-               o_g3d = carve(g3d.size() * sizeof(int2)),
+               o_g3d = carve(g3d.size() * sizeof(int2)), o_yt = carve(yun.size() * sizeof(int2)),
+               o_yo = carve((size_t)b->nyun * b->yun_ostride * 4), o_yw = carve((size_t)b->nyun * 8 * b->yun_wstride * 4),
                o_g3b = carve(g3b.size() * sizeof(int4));
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
@@ -654,6 +656,9 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_stats = (unsigned long long *)(base + o_st);
   b->d_cy = (int64_t *)(base + o_cy);
   b->d_g3d = (int2 *)(base + o_g3d);
+  b->d_yun_tasks = (int2 *)(base + o_yt);
+  b->d_yun_out = (uint32_t *)(base + o_yo);
+  b->d_yun_work = (uint32_t *)(base + o_yw);
   b->d_g3b = (int4 *)(base + o_g3b);
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
@@ -684,6 +689,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                           {b->d_g2, g2.data(), g2.size() * sizeof(int2)},
                           {b->d_g3, g3.data(), g3.size() * sizeof(int2)},
                           {b->d_g3d, g3d.data(), g3d.size() * sizeof(int2)},
+                          {b->d_yun_tasks, yun.data(), yun.size() * sizeof(int2)},
                           {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)}};
   size_t static_bytes = 0;
   for (const Piece &pc : pieces) static_bytes += (pc.bytes + 15) & ~(size_t)15;
@@ -896,6 +902,19 @@ static int enqueue(rs_batch *b, bool capturing) {
     cudaError_t fe = cudaSuccess;
     join_all(b, 1, (int)b->classes.size(), (int)b->g2cls.size(), s, &fe);
     RS_CUDA(ctx, fe);
+  }
+  if (b->nyun) {  // square-free factorisation of R mod p, before G3 overwrites the residues
+    YunArgs ya;
+    ya.pairs = b->d_pairs;
+    ya.tasks = b->d_yun_tasks;
+    ya.mods = ctx->d_mods;
+    ya.coef = b->d_num;
+    ya.out = b->d_yun_out;
+    ya.work = b->d_yun_work;
+    ya.ostride = b->yun_ostride;
+    ya.wstride = b->yun_wstride;
+    ya.maxm = b->opt.yun_maxm;
+    RS_CUDA(ctx, launch_yun(b->nyun, ya, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[2], s, capturing));
   if (b->ng3) {

@@ -13,6 +13,18 @@
 
 struct RsServer;  // server.cu
 
+// Makes device d current for the scope and restores the previous device.
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (d >= 0 && prev != d) cudaSetDevice(d);
+  }
+  ~DevGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 // Point and interpolation tables per prime, shared by every batch of a
 // context and grown on demand (old allocations are kept until the context is
 // destroyed, so captured graphs stay valid).
@@ -98,6 +110,7 @@ struct RsBatchOpts {
   bool timing = false;  // record stage events even when the context does not time
   int g1_threads = 0;   // > 0: force this tile width (and opt.persistent) for every class
   int g2_force = -1;    // 0: direct G2 for every pair, 1: transforms wherever possible, -1: choose
+  int yun_maxm = 0;     // > 0: square-free factorisation of R mod every prime after G2 (up to this multiplicity)
 };
 
 struct rs_batch {
@@ -117,6 +130,10 @@ struct rs_batch {
   int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int64_t xl_words = 0, cy_words = 0;
   int2 *d_g3d = nullptr;
+  int nyun = 0;                         // square-free tasks (pair, prime)
+  int64_t yun_ostride = 0, yun_wstride = 0;
+  int2 *d_yun_tasks = nullptr;
+  uint32_t *d_yun_out = nullptr, *d_yun_work = nullptr;
   int4 *d_g3b = nullptr;
   int64_t *d_cy = nullptr;
   size_t g2smem = 0;

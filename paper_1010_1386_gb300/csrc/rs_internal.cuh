@@ -106,6 +106,19 @@ struct G2nArgs {
   int32_t lg;
 };
 
+// Square-free factorisation of R mod p (kernels_yun.cu), one task per
+// (pair, prime) after G2: output layout documented there.
+struct YunArgs {
+  const PairDesc *pairs;
+  const int2 *tasks;       // (pair, prime)
+  const ModP *mods;
+  const uint32_t *coef;    // G2's residues of R (plain), stride NI per prime
+  uint32_t *out;           // [task][ostride]
+  uint32_t *work;          // [task][8][wstride] scratch
+  int64_t ostride, wstride;
+  int32_t maxm;            // largest multiplicity reported
+};
+
 struct G3Args {
   const PairDesc *pairs;
   const int2 *tasks;       // (pair, first coefficient) per block (digit tiles of 32 coefficients)
@@ -136,6 +149,7 @@ cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int 
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
 // CRT digits by tiles of 32 coefficients (tasks step by 32), any prime count.
 cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s);
+cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s);
 cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
 cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,

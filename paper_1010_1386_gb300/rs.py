@@ -96,6 +96,8 @@ _SIGS = {
     "rs_resultant_x": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly)]),
     "rs_projections": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly),
                                  _P(rs_upoly), _P(c_int32)]),
+    "rs_squarefree_y": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, _P(rs_upoly),
+                                  _P(rs_upoly), _P(c_int32)]),
     "rs_autotune": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
     "rs_autotune_entries": (c_int32, [_P(rs_tune_entry), c_int32, _P(c_int32)]),
     "rs_autotune_save": (c_int32, [c_char_p]),
@@ -283,6 +285,38 @@ class Context:
         if raw:
             return oy.raw(), ox.raw()
         return oy.ints(), ox.ints()
+
+    def squarefree(self, f, g, max_mult=8):
+        """Square-free factorisation of Res_y(f, g): (c, [(i, R_i), ...]) with
+        Res_y = c * prod R_i^i (R_i as lists of Python ints, ascending; only
+        the non-constant factors, in increasing multiplicity)."""
+        P = _Polys([f, g])
+        b = result_bound(f, g)
+        words = [max(1, b["limbs"]), max(1, (b["deg"] + 1) * (2 * b["limbs"] + 2))]
+        for _ in range(2):  # the second call has the exact sizes the first reported
+            content = rs_upoly()
+            cbuf = np.zeros(words[0], dtype=np.uint32)
+            content.capacity_words, content.coeffs = words[0], cbuf.ctypes.data_as(POINTER(c_uint32))
+            facs = (rs_upoly * max_mult)()
+            fbufs = []
+            for fs in facs:
+                fb = np.zeros(words[1], dtype=np.uint32)
+                fbufs.append(fb)
+                fs.capacity_words, fs.coeffs = words[1], fb.ctypes.data_as(POINTER(c_uint32))
+            nm = c_int32()
+            rc = self.lib.rs_squarefree_y(self.h, ctypes.byref(P.structs[0]), ctypes.byref(P.structs[1]),
+                                          max_mult, ctypes.byref(content), facs, ctypes.byref(nm))
+            if rc != -2:
+                break
+            words = [max(1, (content.deg + 1) * content.limbs),
+                     max(max(1, (fs.deg + 1) * fs.limbs) for fs in facs)]
+        _check(rc, self.h)
+        c = limbs_to_ints(cbuf, content.deg, content.limbs)[0]
+        out = []
+        for i, (fs, fb) in enumerate(zip(facs, fbufs), start=1):
+            if fs.deg > 0:
+                out.append((i, limbs_to_ints(fb, fs.deg, fs.limbs)))
+        return c, out
 
     def images(self, f, g, nprimes, npoints):
         """(primes[K], points[K, N], images[K, N]): images[k, i] =

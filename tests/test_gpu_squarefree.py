@@ -1,0 +1,78 @@
+"""Square-free factorisation of Res_y(f, g) through rs_squarefree_y against
+the oracle (exact resultant, then Yun over Z): pairs whose resultant has
+planted repeated factors (f = p q^2 with g = d(pq)/dy gives Res_y(p, g)
+Res_y(q, g)^2), random pairs (square-free resultants), a degree-0 and a zero
+resultant, too small a max_mult; and the non-generic workload at full size
+checked by expanding the factors back to the GPU resultant."""
+import random
+
+import pytest
+
+from oracle import exact, squarefree as sq
+from paper_1010_1386_gb300 import inputs, rs
+from paper_1010_1386_gb300.inputs import _dy, _from_dict, _mul_dict, _to_dict
+from tests.helpers import rand_bipoly
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rs.Context(device=0)
+    yield c
+    c.close()
+
+
+def planted(rng, dp, dq, bits):
+    p = rand_bipoly(rng, dp, dp, bits=bits)
+    q = rand_bipoly(rng, dq, dq, bits=bits)
+    pq = _mul_dict(_to_dict(p), _to_dict(q))
+    f = _from_dict(_mul_dict(pq, _to_dict(q)))
+    g = _from_dict(_dy(pq))
+    return f, g
+
+
+def test_planted_repeated_factors_exact(ctx):
+    rng = random.Random(71)
+    for dp, dq, bits in [(1, 1, 4), (2, 1, 6), (2, 1, 20), (3, 1, 8), (2, 2, 5)]:
+        f, g = planted(rng, dp, dq, bits)
+        want = sq.squarefree(exact.resultant_y(f, g))
+        got = ctx.squarefree(f, g)
+        assert got == want, (dp, dq, bits)
+        assert any(m >= 2 for m, _ in got[1])
+
+
+def test_random_pairs_exact(ctx):
+    rng = random.Random(72)
+    for _ in range(12):
+        f = rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 4), bits=rng.choice([4, 30, 70]))
+        g = rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 4), bits=rng.choice([4, 30, 70]))
+        R = exact.resultant_y(f, g)
+        if not R:
+            continue
+        assert ctx.squarefree(f, g) == sq.squarefree(R)
+
+
+def test_constant_zero_and_multiplicity_limit(ctx):
+    assert ctx.squarefree([[3]], [[0, 1]]) == (3, [])          # Res_y(3, y) = 3
+    with pytest.raises(rs.RsError) as ei:
+        ctx.squarefree([[0, 1]], [[0, 2]])                     # Res_y(y, 2y) = 0
+    assert ei.value.code == -1
+    f = [[0, 1]]                                               # f = y
+    g = [[0, 0, 0, 1], [0], [0], [-1]]                         # g = y^3 - x^3: Res_y(y, g) = -x^3
+    assert ctx.squarefree(f, g) == (-1, [(3, [0, 1])])
+    with pytest.raises(rs.RsError) as ei:
+        ctx.squarefree(f, g, max_mult=2)
+    assert ei.value.code == -2
+
+
+def test_nongeneric_workload_full_size(ctx):
+    """The first pair of the coprime topology workload (f = p q^2, g =
+    d(pq)/dy, total degrees 48 and 35): the factors multiply back to the GPU
+    resultant, and a factor of multiplicity 2 carries Res_y(q, g)."""
+    (f, g), = inputs.workload_nongeneric(3, n=1, coprime=True)
+    R = ctx.resultant_y(f, g)
+    c, facs = ctx.squarefree(f, g)
+    assert sq.expand(c, facs) == R
+    assert all(P[-1] > 0 for _, P in facs) and [m for m, _ in facs] == sorted(m for m, _ in facs)
+    assert any(m >= 2 for m, _ in facs)
