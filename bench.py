@@ -2,7 +2,7 @@
 process per GPU, independent batches: weak scaling).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload batch|small|single|nongeneric|nongeneric-coprime|serving]
+                    [--workload batch|small|single|nongeneric|nongeneric-coprime|serving|shift|squarefree]
                     [--no-baseline] [--no-per-instance]
 
 Prints ONE JSON line.  A step is one pass of the whole path (G1 reduce +
@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "resultants/s batched vs per-instance launch, same GB300; % of INT32 IMAD peak"
+SQF_METRIC = "square-free factorisations of Res_y(f, g) per second (R = c prod R_i^i), one GB300"
 SM_COUNT = 152
 IMAD_PER_SM_CLK = 64  # 32-bit integer multiply-add results per clock per SM
 WORKLOADS = {
@@ -45,6 +46,10 @@ WORKLOADS = {
                           "factors), seed 3",
     "serving": "Poisson stream of 10,000 requests, total degrees of f and g ~ U[8,64], coefficient bits "
                "~ U[16,128], total-degree-dense, seed 4",
+    "squarefree": "square-free factorisation Res_y = c prod R_i^i of each pair of the non-generic "
+                  "coprime batch (32 pairs, f = p q^2, g = d(pq)/dy, p and q dense total degrees 24 and "
+                  "12, 64-bit coefficients, seed 3): one call through the C ABI per step, host buffers "
+                  "in and out",
     "shift": "both projections Res_y and Res_x of all 10 pairs of five random curves (total degree "
              "--shift-deg, dense or --shift-sparse, 16-bit coefficients) multiplied by 2^k "
              "(--shift-k) with the constant term raised by one, seed 5: 20 resultants",
@@ -113,6 +118,33 @@ def oracle_sample(workload, npairs, seed, cores):
     desc = (f"exact integer Sylvester determinant at x = D/2 for {len(jobs)} random pairs "
             f"(mean {statistics.mean(times):.2f} s each), scaled by D+1 points per pair, "
             f"interpolation not counted; {cores} processes")
+    return value, desc
+
+
+def _oracle_sqf(args):
+    f, g = args
+    from oracle import exact, squarefree
+    t = time.perf_counter()
+    squarefree.squarefree(exact.resultant_y(f, g))
+    return time.perf_counter() - t
+
+
+def oracle_sqf_sample(npairs, seed, cores):
+    """Time the oracle (exact resultant, then Yun over Z) on ``npairs`` pairs
+    of the non-generic coprime generator at reduced degrees (p, q of total
+    degrees 4 and 2; at 6 and 3 one pair already takes the oracle two
+    minutes, the full-size pairs far longer).  Returns
+    (factorisations/s over ``cores`` processes, description)."""
+    from paper_1010_1386_gb300 import inputs
+    pairs = inputs.workload_nongeneric(seed, n=npairs, deg_p=4, deg_q=2, bits=64, coprime=True)
+    jobs = [(f.to_ints(), g.to_ints()) for f, g in pairs]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(cores, len(jobs))) as pool:
+        times = pool.map(_oracle_sqf, jobs)
+    value = cores / statistics.mean(times)
+    desc = (f"oracle exact Res_y then Yun over Z for {len(jobs)} pairs of the same generator at "
+            f"reduced size (p, q total degrees 4 and 2; mean {statistics.mean(times):.2f} s each); "
+            f"{cores} processes")
     return value, desc
 
 
@@ -239,6 +271,11 @@ def add_cpu_baseline(line, args, rank):
     if rank != 0 or args.no_baseline:
         return
     cores = min(os.cpu_count() or 1, 8)
+    if args.workload == "squarefree":
+        v, desc = oracle_sqf_sample(8, 7, cores)
+        line["cpu_baseline"] = {"value": v, "unit": "factorisations/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+        return
     n = 8 if args.workload in ("batch", "serving", "nongeneric", "nongeneric-coprime") else 1
     v, desc = oracle_sample(args.workload, n, 7, cores)
     line["cpu_baseline"] = {"value": v, "unit": "resultants/s", "cores": cores, "kind": "oracle",
@@ -253,18 +290,25 @@ def reference_main(args, world, rank, dist):
     cores = min(os.cpu_count() or 1, 2)
     vals, t0 = [], time.perf_counter()
     desc = ""
+    sqf = args.workload == "squarefree"
+    unit = "factorisations/s" if sqf else "resultants/s"
     for s in range(args.warmup + args.steps):
-        v, desc = oracle_sample(args.workload, 2, 1000 + s, cores)
+        if sqf:
+            v, desc = oracle_sqf_sample(2, 1000 + s, cores)
+        else:
+            v, desc = oracle_sample(args.workload, 2, 1000 + s, cores)
         if s >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
     wall = time.perf_counter() - t0
     line = base_line(args, 1, value, 1000.0 * wall / (args.steps + args.warmup),
                      WORKLOADS[args.workload], {})
+    if sqf:
+        line.update({"metric": SQF_METRIC, "unit": unit})
     line.update({"impl": "reference", "dtype": "int (Python big integers)",
-                 "cpu_baseline": {"value": value, "unit": "resultants/s", "cores": cores,
+                 "cpu_baseline": {"value": value, "unit": unit, "cores": cores,
                                   "kind": "oracle", "sample": desc},
-                 "e2e": {"value": value, "unit": "resultants/s", "h2d_bytes_per_step": 0,
+                 "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0}})
     print(json.dumps(line), flush=True)
 
@@ -391,6 +435,78 @@ def batch_main(args, world, rank, local, dist):
     ctx.close()
 
 
+def squarefree_main(args, world, rank, local, dist):
+    """One rs_squarefree_batch call per step (GPU pass over the factors'
+    primes, Yun mod p, CRT of the factors, primitive parts on the host); the
+    resultant alone on the same pairs is timed beside it."""
+    import torch
+    from paper_1010_1386_gb300 import rs
+
+    torch.cuda.set_device(local)
+    pairs = load_pairs("nongeneric-coprime", args.pairs, rank, args)
+    npairs = len(pairs)
+    ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache)
+    batch = ctx.batch(pairs)
+    for _ in range(args.warmup):
+        batch.run()
+        batch.sync()
+    res_ms = []
+    for _ in range(max(3, min(args.steps, 5))):
+        batch.run()
+        batch.sync()
+        res_ms.append(batch.info()["ms_total"])
+    batch.close()
+    maxm = 4
+    for _ in range(args.warmup):
+        st = ctx.squarefree_batch(pairs, maxm, raw=True)
+        assert all(c == 0 for c in st), st
+    times, infos = [], []
+    barrier(dist, local)
+    with ClockSampler(local) as clocks:
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            st = ctx.squarefree_batch(pairs, maxm, raw=True)
+            times.append(1e3 * (time.perf_counter() - t))
+            infos.append(ctx.squarefree_info())
+        barrier(dist, local)
+    assert all(c == 0 for c in st), st
+    ms = max_over_ranks(dist, local, statistics.mean(times))
+    value = world * npairs / (ms * 1e-3)
+    last = infos[-1]
+    bi = last["batch"]
+    mean = lambda k: statistics.mean(i[k] for i in infos)
+    bmean = lambda k: statistics.mean(i["batch"][k] for i in infos)
+    clk = clocks.summary()
+    rf = roofline(bi, bmean("ms_images"), clk)
+    out = ctx.squarefree_batch(pairs[:1], maxm)[0]
+    line = base_line(args, world, value, ms, WORKLOADS["squarefree"],
+                     {"pairs_per_gpu": npairs, "max_mult": maxm, "images_per_step": bi["images"],
+                      "primes_per_pair": bi["primes_total"] / max(1, bi["pairs"]),
+                      "l2": "inputs and the per-step working set (%.0f MB of images) exceed L2"
+                            % (bi["images"] * 8 / 1e6)})
+    line.update({
+        "metric": SQF_METRIC, "unit": "factorisations/s",
+        "stage_ms": {"G1": bmean("ms_images"), "G2": bmean("ms_interp"), "yun": bmean("ms_yun"),
+                     "G3 (R)": bmean("ms_crt"), "lift (factor CRT)": mean("ms_lift"),
+                     "host (selection, contents, primitive parts)": mean("ms_host"),
+                     "call": mean("ms_total")},
+        "resultant_only": {"ms_per_step": statistics.mean(res_ms),
+                           "value": npairs / (statistics.mean(res_ms) * 1e-3), "unit": "resultants/s",
+                           "note": "same pairs, device-resident inputs, resultant primes only"},
+        "factor_degrees_pair0": [(m, len(r) - 1) for m, r in out[1]],
+        "roofline": rf,
+        "gpu_launches": args.steps * (bi["kernel_launches"] + 3),
+        "clocks": clk,
+        "e2e": {"value": value, "unit": "factorisations/s",
+                "h2d_bytes_per_step": bi["input_bytes"], "d2h_bytes_per_step": None,
+                "note": "the call is end to end (host inputs, host outputs); value is the same number"},
+    })
+    add_cpu_baseline(line, args, rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def serving_main(args, world, rank, local, dist):
     """Closed-loop saturation pass, then a Poisson stream at --load x that
     throughput through the continuous-batching server."""
@@ -495,6 +611,8 @@ def main():
         reference_main(args, world, rank, dist)
     elif args.workload == "serving":
         serving_main(args, world, rank, local, dist)
+    elif args.workload == "squarefree":
+        squarefree_main(args, world, rank, local, dist)
     else:
         batch_main(args, world, rank, local, dist)
     if dist is not None:

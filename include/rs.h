@@ -182,6 +182,9 @@ typedef struct {
   int64_t degenerate_images;  /* images whose remainder sequence hit a zero pivot */
   int64_t unlucky_primes;     /* (pair, prime) with lc_y f or lc_y g = 0 mod p */
   int64_t kernel_launches;    /* kernels of the library launched per run */
+  float ms_yun;               /* square-free factorisation mod p (rs_squarefree_batch only; inside
+                                 the span ms_interp measures otherwise) */
+  int32_t reserved;
 } rs_batch_info;
 
 int rs_batch_info_get(rs_batch *batch, rs_batch_info *info);
@@ -218,6 +221,29 @@ int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *
  * factors (the result would need other primes; not met in practice). */
 int rs_squarefree_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
                     rs_upoly *content, rs_upoly *factors, int32_t *nmult);
+
+/* rs_squarefree_y for n pairs in one GPU pass: content[i], factors[i *
+ * max_mult + m - 1] (m = 1..max_mult) and nmult[i] for pair i, as above.
+ * status (may be NULL) receives each pair's code; the return value is the
+ * first failure in pair order (its message in rs_last_error), RS_OK when
+ * every pair succeeded.  A pair's outputs are written when its status is
+ * RS_OK. */
+int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
+                        rs_upoly *content, rs_upoly *factors, int32_t *nmult, int32_t *status);
+
+/* Where the last rs_squarefree_y / rs_squarefree_batch call of this context
+ * spent its time. */
+typedef struct {
+  rs_batch_info batch;  /* the GPU pass over the factors' primes (stage times, ms_yun) */
+  int64_t yun_tasks;    /* (pair, prime) factorisations mod p */
+  int64_t factors;      /* non-constant factors lifted */
+  float ms_lift;        /* CRT of the factors on the device */
+  float ms_host;        /* host work after the GPU pass: prime selection, contents, primitive parts */
+  float ms_total;       /* wall time of the call */
+  int32_t reserved;
+} rs_sqf_info;
+
+int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info);
 
 /* Diagnostics: the modular images z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) mod p
  * (Section 4.1) that the resultant path computes, for the first nprimes

@@ -904,6 +904,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     RS_CUDA(ctx, fe);
   }
   if (b->nyun) {  // square-free factorisation of R mod p, before G3 overwrites the residues
+    if (timing) RS_CUDA(ctx, record(b->ev[4], s, capturing));
     YunArgs ya;
     ya.pairs = b->d_pairs;
     ya.tasks = b->d_yun_tasks;
@@ -1289,6 +1290,8 @@ int rs_batch_info_get(rs_batch *b, rs_batch_info *info) {
   DevGuard dg(ctx->device);
   *info = b->info;
   info->ms_images = info->ms_interp = info->ms_crt = info->ms_total = -1.0f;
+  info->ms_yun = 0.0f;
+  info->reserved = 0;
   if (!b->ran) return RS_OK;
   RS_CUDA(ctx, cudaStreamSynchronize(b->stream));
   unsigned long long st[ST_COUNT];
@@ -1300,7 +1303,8 @@ int rs_batch_info_get(rs_batch *b, rs_batch_info *info) {
     float t = 0;
     if (cudaEventElapsedTime(&t, b->ev[0], b->ev[1]) == cudaSuccess) info->ms_images = t;
     if (!b->opt.images_only) {
-      if (cudaEventElapsedTime(&t, b->ev[1], b->ev[2]) == cudaSuccess) info->ms_interp = t;
+      if (cudaEventElapsedTime(&t, b->ev[1], b->ev[b->nyun ? 4 : 2]) == cudaSuccess) info->ms_interp = t;
+      if (b->nyun && cudaEventElapsedTime(&t, b->ev[4], b->ev[2]) == cudaSuccess) info->ms_yun = t;
       if (cudaEventElapsedTime(&t, b->ev[2], b->ev[3]) == cudaSuccess) info->ms_crt = t;
       if (cudaEventElapsedTime(&t, b->ev[0], b->ev[3]) == cudaSuccess) info->ms_total = t;
     }

@@ -44,6 +44,7 @@ struct RsTables {
 struct rs_ctx {
   int device = 0;
   rs_config cfg;
+  rs_sqf_info sqf_info{};  // the last square-free call
   cudaStream_t stream = nullptr;
   int sms = 0;
   std::vector<uint32_t> primes;
@@ -149,7 +150,7 @@ struct rs_batch {
   uint32_t *h_in = nullptr, *h_out = nullptr;
   bool own_host = false;
   cudaGraphExec_t gexec = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage bounds; [4] before Yun
   cudaEvent_t fev[2] = {nullptr, nullptr};  // fork points of the G1 and G2 stages
   std::vector<cudaEvent_t> jev;             // joins of the branches (one per launch of a forked stage)
   bool ran = false;

@@ -9,7 +9,9 @@
 // lc(X) x^s Y, the degree drops by one per step; a gcd is only defined up to
 // a unit), exact divisions use one inverse of the divisor's leading
 // coefficient, and every step is spread over the block's threads with a
-// barrier.  Polynomials live in global scratch (L1/L2 resident per block).
+// barrier.  The polynomials live in global scratch, except the two that every
+// remainder and division step rewrites (the gcd operands and the division
+// remainder), which live in shared memory when they fit.
 //
 // Output per task (word offsets from out + task * ostride):
 //   [0]            degree of R mod p (-1 if R = 0 mod p)
@@ -150,8 +152,13 @@ __global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
   const int N = pd.N;
   uint32_t *o = a.out + (size_t)blockIdx.x * a.ostride;
   uint32_t *w = a.work + (size_t)blockIdx.x * 8 * (size_t)a.wstride;
+  extern __shared__ uint32_t ysm[];
   Poly P[8];
   for (int i = 0; i < 8; ++i) P[i] = Poly{w + (size_t)i * a.wstride, -1};
+  if (a.shared_scratch) {
+    P[6].c = ysm;
+    P[7].c = ysm + a.wstride;
+  }
   Poly &F = P[0], &Fd = P[1], &A = P[2], &B = P[3], &C = P[4], &D = P[5], &T1 = P[6], &T2 = P[7];
   const uint32_t *res = a.coef + pd.img_off + (size_t)task.y * pd.NI;
   for (int j = threadIdx.x; j < N; j += blockDim.x) F.c[j] = to_mont(res[j], m);
@@ -205,6 +212,17 @@ __global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
 }  // namespace
 
 cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s) {
-  if (ntasks) yun_kernel<<<ntasks, 256, 0, s>>>(a);
+  if (!ntasks) return cudaSuccess;
+  YunArgs b = a;
+  const size_t smem = 2 * (size_t)a.wstride * sizeof(uint32_t);
+  size_t dyn = 0;
+  b.shared_scratch = 0;
+  if (smem <= RS_YUN_MAX_SMEM_BYTES) {
+    const cudaError_t e = cudaFuncSetAttribute(yun_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dyn = smem;
+    b.shared_scratch = 1;
+  }
+  yun_kernel<<<ntasks, 256, dyn, s>>>(b);
   return cudaGetLastError();
 }

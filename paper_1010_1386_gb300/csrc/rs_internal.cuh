@@ -106,6 +106,10 @@ struct G2nArgs {
   int32_t lg;
 };
 
+// Square-free factorisation mod p keeps its two scratch polynomials in
+// shared memory up to this size (2 x the scratch stride in words).
+#define RS_YUN_MAX_SMEM_BYTES (96 * 1024)
+
 // Square-free factorisation of R mod p (kernels_yun.cu), one task per
 // (pair, prime) after G2: output layout documented there.
 struct YunArgs {
@@ -117,6 +121,7 @@ struct YunArgs {
   uint32_t *work;          // [task][8][wstride] scratch
   int64_t ostride, wstride;
   int32_t maxm;            // largest multiplicity reported
+  int32_t shared_scratch;  // set by launch_yun: the two scratch polynomials in shared memory
 };
 
 struct G3Args {

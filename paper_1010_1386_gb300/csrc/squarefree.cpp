@@ -19,9 +19,13 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <functional>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "engine.h"
@@ -202,247 +206,607 @@ Big big_divexact(Big a, Big b) {
   return q;
 }
 
+// Quotient and remainder of magnitudes, b non-zero (D. E. Knuth, The Art of
+// Computer Programming vol. 2, 4.3.1, Algorithm D), on 64-bit limbs with
+// 128-bit products: normalise b's top limb, estimate each quotient limb from
+// the top two limbs, multiply and subtract, add back when the estimate was one
+// too large.
+using u64 = uint64_t;
+using u128 = unsigned __int128;
+
+std::vector<u64> pack64(const Big &a, size_t extra = 0) {
+  std::vector<u64> r((a.size() + 1) / 2 + extra, 0u);
+  for (size_t i = 0; i < a.size(); ++i) r[i / 2] |= (u64)a[i] << (32 * (i & 1));
+  return r;
+}
+
+Big unpack32(const u64 *r, size_t n) {
+  Big a(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    a[2 * i] = (uint32_t)r[i];
+    a[2 * i + 1] = (uint32_t)(r[i] >> 32);
+  }
+  trim(a);
+  return a;
+}
+
+Big big_divmod(const Big &a, const Big &b, Big *rem) {
+  if (cmp(a, b) < 0) {
+    *rem = a;
+    return Big();
+  }
+  if (b.size() == 1) {
+    Big q(a.size());
+    uint64_t r = 0;
+    for (size_t i = a.size(); i-- > 0;) {
+      const uint64_t cur = (r << 32) | a[i];
+      q[i] = (uint32_t)(cur / b[0]);
+      r = cur % b[0];
+    }
+    trim(q);
+    *rem = r ? Big{(uint32_t)r} : Big();
+    return q;
+  }
+  std::vector<u64> v = pack64(b), u = pack64(a, 1);
+  while (!v.empty() && v.back() == 0u) v.pop_back();
+  const size_t n = v.size();
+  size_t ua = u.size() - 1;  // limbs of a
+  while (ua > 0 && u[ua - 1] == 0u) --ua;
+  u.resize(ua + 1);
+  u[ua] = 0u;
+  if (n == 1) {  // one 64-bit limb: schoolbook with 128-bit steps
+    std::vector<u64> q(ua, 0u);
+    u128 r = 0;
+    for (size_t i = ua; i-- > 0;) {
+      const u128 cur = (r << 64) | u[i];
+      q[i] = (u64)(cur / v[0]);
+      r = cur % v[0];
+    }
+    const u64 rr = (u64)r;
+    *rem = unpack32(&rr, 1);
+    return unpack32(q.data(), q.size());
+  }
+  const size_t m = ua - n;
+  const int s = __builtin_clzll(v.back());
+  if (s) {
+    for (size_t i = n; i-- > 1;) v[i] = (v[i] << s) | (v[i - 1] >> (64 - s));
+    v[0] <<= s;
+    u[ua] = u[ua - 1] >> (64 - s);
+    for (size_t i = ua; i-- > 1;) u[i] = (u[i] << s) | (u[i - 1] >> (64 - s));
+    u[0] <<= s;
+  }
+  std::vector<u64> q(m + 1, 0u);
+  const u64 vt = v[n - 1], vs = v[n - 2];
+  for (size_t j = m + 1; j-- > 0;) {
+    const u128 num = ((u128)u[j + n] << 64) | u[j + n - 1];
+    u128 qh = num / vt, rh = num % vt;
+    while ((qh >> 64) != 0 || qh * vs > ((rh << 64) | u[j + n - 2])) {
+      --qh;
+      rh += vt;
+      if ((rh >> 64) != 0) break;
+    }
+    const u64 q64 = (u64)qh;
+    u64 carry = 0, borrow = 0;
+    for (size_t i = 0; i < n; ++i) {
+      const u128 pr = (u128)q64 * v[i] + carry;
+      carry = (u64)(pr >> 64);
+      const u64 lo = (u64)pr, x = u[i + j];
+      const u64 t = x - lo;
+      const u64 b1 = x < lo;
+      u[i + j] = t - borrow;
+      borrow = b1 + (t < borrow);
+    }
+    const u128 top = (u128)carry + borrow;
+    const bool neg = (u128)u[j + n] < top;
+    u[j + n] = (u64)((u128)u[j + n] - top);
+    if (neg) {  // the estimate was one too large: add b back
+      q[j] = q64 - 1;
+      u64 c = 0;
+      for (size_t i = 0; i < n; ++i) {
+        const u128 sm = (u128)u[i + j] + v[i] + c;
+        u[i + j] = (u64)sm;
+        c = (u64)(sm >> 64);
+      }
+      u[j + n] += c;
+    } else {
+      q[j] = q64;
+    }
+  }
+  std::vector<u64> r(n);
+  for (size_t i = 0; i < n; ++i) r[i] = s ? (u[i] >> s) | (u[i + 1] << (64 - s)) : u[i];
+  *rem = unpack32(r.data(), n);
+  return unpack32(q.data(), q.size());
+}
+
+int bitlen(const Big &a) { return a.empty() ? 0 : 32 * ((int)a.size() - 1) + (32 - __builtin_clz(a.back())); }
+
+// Bits [sh, sh + 62) of a (a < 2^(sh + 62)).
+u64 top_bits(const Big &a, int sh) {
+  const int w = sh / 32, o = sh % 32;
+  u128 r = 0;
+  for (int k = 3; k >= 0; --k) {
+    const size_t i = (size_t)(w + k);
+    r = (r << 32) | (i < a.size() ? a[i] : 0u);
+  }
+  return (u64)(r >> o);
+}
+
+// X a + Y b for signed single-word cofactors with X a + Y b >= 0.
+Big lin_comb(const Big &a, __int128 X, const Big &b, __int128 Y) {
+  const size_t n = std::max(a.size(), b.size()) + 3;
+  Big r(n);
+  __int128 carry = 0;
+  for (size_t i = 0; i < n; ++i) {
+    __int128 t = carry;
+    if (i < a.size()) t += X * (__int128)a[i];
+    if (i < b.size()) t += Y * (__int128)b[i];
+    r[i] = (uint32_t)((u128)t & 0xffffffffu);
+    carry = t >> 32;  // arithmetic shift (floor division by 2^32)
+  }
+  trim(r);
+  return r;
+}
+
+// gcd of magnitudes by Lehmer's method (D. H. Lehmer, "Euclid's algorithm
+// for large numbers", Amer. Math. Monthly 45, 1938; Knuth 4.5.2, Algorithm
+// L): the leading 62 bits of a and b drive single-precision Euclid steps for
+// as long as the quotients are certain (the quotients from (a' + A)/(b' + C)
+// and (a' + B)/(b' + D) agree); the accumulated 2x2 matrix is then applied
+// to the full numbers at once.  A full division step when no single-precision
+// step was certain.
+Big big_gcd_lehmer(Big a, Big b) {
+  if (cmp(a, b) < 0) std::swap(a, b);
+  while (b.size() > 2) {
+    const int sh = std::max(0, bitlen(a) - 62);
+    __int128 ah = (__int128)top_bits(a, sh), bh = (__int128)top_bits(b, sh);
+    __int128 A = 1, B = 0, C = 0, D = 1;
+    while (bh + C != 0 && bh + D != 0) {
+      const __int128 q1 = (ah + A) / (bh + C), q2 = (ah + B) / (bh + D);
+      if (q1 != q2) break;
+      __int128 t = A - q1 * C;
+      A = C;
+      C = t;
+      t = B - q1 * D;
+      B = D;
+      D = t;
+      t = ah - q1 * bh;
+      ah = bh;
+      bh = t;
+    }
+    if (B == 0) {
+      Big r;
+      big_divmod(a, b, &r);
+      a = std::move(b);
+      b = std::move(r);
+      continue;
+    }
+    // a' = A a + B b, b' = C a + D b (both non-negative)
+    Big na = lin_comb(a, A, b, B), nb = lin_comb(a, C, b, D);
+    a = std::move(na);
+    b = std::move(nb);
+    if (cmp(a, b) < 0) std::swap(a, b);
+  }
+  if (b.empty()) return a;
+  Big r;  // b has at most two limbs: one division, then the binary gcd
+  big_divmod(a, b, &r);
+  return big_gcd(b, r);
+}
+
+// Content of the integers c[0..n) (magnitudes, c[n-1] non-zero) and, when
+// quot is given, every c[j] divided by it.  Starts from |c[n-1]| and takes a
+// gcd only when a division leaves a remainder (then the quotients so far are
+// recomputed), so a content that is found early costs one long division per
+// coefficient.
+Big content_of(const std::vector<Big> &c, std::vector<Big> *quot) {
+  Big g = c.back();
+  if (quot) quot->assign(c.size(), Big());
+  for (size_t j = 0; j < c.size(); ++j) {
+    if (g.size() == 1 && g[0] == 1u) {
+      if (!quot) return g;
+      for (size_t k = j; k < c.size(); ++k) (*quot)[k] = c[k];
+      return g;
+    }
+    if (c[j].empty()) continue;
+    Big r;
+    Big q = big_divmod(c[j], g, &r);
+    if (!r.empty()) {
+      g = big_gcd_lehmer(g, r);
+      if (quot)
+        for (size_t k = 0; k < j; ++k) {  // the earlier quotients were by a multiple of g
+          Big r2;
+          (*quot)[k] = big_divmod(c[k], g, &r2);
+        }
+      q = big_divmod(c[j], g, &r);
+    }
+    if (quot) (*quot)[j] = std::move(q);
+  }
+  return g;
+}
+
 }  // namespace
+
+extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
+                                   int32_t max_mult, rs_upoly *content, rs_upoly *factors, int32_t *nmult,
+                                   int32_t *status) {
+  if (!ctx || n < 0 || max_mult < 1 || (n > 0 && (!f || !g || !content || !factors || !nmult)))
+    return rs_fail(ctx, RS_ERR_ARG, "NULL argument, negative n or max_mult < 1");
+  if (n == 0) return RS_OK;
+  const auto t_start = std::chrono::steady_clock::now();
+  rs_sqf_info info;
+  memset(&info, 0, sizeof(info));
+  std::vector<PairPlan> plans;
+  int first = RS_OK;
+  rs_plan_all(ctx, n, f, g, plans, nullptr, &first);
+  std::vector<int> st(n, RS_OK);
+  std::vector<std::string> why(n);
+  std::vector<int> KH(n, 0), bitsH(n, 0);
+  int valid = 0;
+  for (int i = 0; i < n; ++i) {
+    PairPlan &p = plans[i];
+    st[i] = p.status;
+    if (st[i] != RS_OK) {
+      why[i] = "rejected by the planner";
+      continue;
+    }
+    if (p.trivial_zero) {
+      st[i] = RS_ERR_ARG;
+      why[i] = "R = 0 has no square-free factorisation";
+      p.status = RS_ERR_ARG;
+      continue;
+    }
+    // primes for the factors: coefficients of H_i below 2^bitsH
+    bitsH[i] = 2 * p.bits + p.D + (int)std::ceil(0.5 * std::log2((double)p.D + 1.0)) + 2;
+    double acc = 0.0;
+    while (KH[i] < (int)ctx->log2p.size() && acc < bitsH[i] + 2) acc += ctx->log2p[KH[i]++];
+    if (acc < bitsH[i] + 2) {
+      st[i] = RS_ERR_LIMIT;
+      why[i] = "factor bound needs more primes than RS_MAX_PRIMES";
+      p.status = RS_ERR_LIMIT;
+      continue;
+    }
+    p.K = std::min((int)ctx->log2p.size(), std::max(p.K, KH[i]) + 4);  // a few spare primes
+    ++valid;
+  }
+  const int M = max_mult;
+  std::vector<int> K(n, 0);
+  for (int i = 0; i < n; ++i) K[i] = plans[i].K;
+  rs_batch *b = nullptr;
+  std::vector<uint32_t> hdr;  // per Yun task: deg R mod p, overflow flag, d_1 .. d_M
+  const int hw = 2 + M;
+  if (valid) {
+    RsBatchOpts o;
+    o.use_graph = false;
+    o.persistent = ctx->cfg.persistent != 0;
+    o.fork = true;
+    o.yun_maxm = M;
+    o.timing = true;
+    int rc = rs_build_batch(ctx, n, f, g, std::move(plans), o, &b);
+    if (rc != RS_OK) return rc;
+    DevGuard dg(ctx->device);
+    rc = rs_upload(b, f, g);
+    if (rc == RS_OK) rc = rs_run(b);
+    if (rc == RS_OK) rc = rs_fetch_async(b);
+    hdr.resize((size_t)b->nyun * hw);
+    if (rc == RS_OK && b->nyun) {
+      cudaError_t e = cudaMemcpy2DAsync(hdr.data(), hw * 4, b->d_yun_out, (size_t)b->yun_ostride * 4, hw * 4,
+                                        b->nyun, cudaMemcpyDeviceToHost, b->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+      if (e != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("square-free: ") + cudaGetErrorString(e));
+    }
+    if (rc == RS_OK) rc = rs_batch_info_get(b, &info.batch);
+    if (rc != RS_OK) {
+      rs_free_batch(b);
+      return rc;
+    }
+    info.yun_tasks = b->nyun;
+  }
+  const auto t_host0 = std::chrono::steady_clock::now();
+  auto put = [&](rs_upoly &out, const std::vector<Big> &mag, const std::vector<char> &neg) -> int {
+    int L = 1;
+    for (size_t j = 0; j < mag.size(); ++j) L = std::max(L, twos_limbs(mag[j], neg[j] != 0));
+    const int deg = (int)mag.size() - 1;
+    out.deg = deg;
+    out.limbs = L;
+    if ((int64_t)(deg + 1) * L > out.capacity_words || (!out.coeffs && deg >= 0)) return RS_ERR_CAPACITY;
+    for (int j = 0; j <= deg; ++j) to_twos(mag[j], neg[j] != 0, out.coeffs + (size_t)j * L, L);
+    return RS_OK;
+  };
+  const std::vector<Big> one_m{Big{1u}};
+  const std::vector<char> one_s{0};
+  // Per pair, on host threads: R, its content, the usable primes and the
+  // pattern of factor degrees.
+  struct PairRes {
+    int degR = -1;
+    Big content;
+    bool lc_neg = false;
+    std::vector<int> pattern;
+  };
+  std::vector<PairRes> pr(n);
+  std::vector<int64_t> t0v(n, 0);
+  {
+    int64_t task0 = 0;
+    for (int i = 0; i < n; ++i)
+      if (st[i] == RS_OK) {
+        t0v[i] = task0;
+        task0 += K[i];
+      }
+  }
+  auto analyse = [&](int i) {
+    PairRes &q = pr[i];
+    std::vector<uint32_t> Rw;
+    int LR = 1;
+    st[i] = rs_unpack_one(b, i, Rw, &q.degR, &LR);
+    if (st[i] != RS_OK) {
+      why[i] = "resultant failed";
+      return;
+    }
+    if (q.degR < 0) {
+      st[i] = RS_ERR_ARG;
+      why[i] = "R = 0 has no square-free factorisation";
+      return;
+    }
+    std::vector<Big> Rm(q.degR + 1);
+    for (int j = 0; j <= q.degR; ++j) {
+      bool ng;
+      Rm[j] = from_twos(&Rw[(size_t)j * LR], LR, &ng);
+      if (j == q.degR) q.lc_neg = ng;
+    }
+    q.content = content_of(Rm, nullptr);
+    if (q.degR == 0) return;
+    // usable primes: R keeps its degree mod p, square-free part of largest degree
+    auto task = [&](int k) { return &hdr[(size_t)(t0v[i] + k) * hw]; };
+    int best_sf = -1;
+    for (int k = 0; k < K[i]; ++k) {
+      const uint32_t *t = task(k);
+      if ((int)t[0] != q.degR || t[1]) continue;
+      int sf = 0;
+      for (int m = 0; m < M; ++m) sf += (int)t[2 + m];
+      best_sf = std::max(best_sf, sf);
+    }
+    bool over = false;
+    for (int k = 0; k < KH[i]; ++k) over = over || ((int)task(k)[0] == q.degR && task(k)[1]);
+    if (over) {  // Yun ran past max_mult on a prime that keeps deg R
+      st[i] = RS_ERR_CAPACITY;
+      why[i] = "a factor's multiplicity exceeds max_mult";
+      return;
+    }
+    q.pattern.assign(M, 0);
+    int good = 0;  // length of the prefix of usable primes with the same pattern
+    for (int k = 0; k < K[i]; ++k) {
+      const uint32_t *t = task(k);
+      if ((int)t[0] != q.degR || t[1]) break;
+      int sf = 0;
+      for (int m = 0; m < M; ++m) sf += (int)t[2 + m];
+      if (sf != best_sf) break;
+      if (k == 0)
+        for (int m = 0; m < M; ++m) q.pattern[m] = (int)t[2 + m];
+      bool same = true;
+      for (int m = 0; m < M; ++m) same = same && (int)t[2 + m] == q.pattern[m];
+      if (!same) break;
+      ++good;
+    }
+    if (good < KH[i]) {
+      st[i] = RS_ERR_LIMIT;
+      why[i] = "an unlucky prime for the square-free factorisation lies among the first " + std::to_string(KH[i]) +
+               " primes (prime index " + std::to_string(good) + ")";
+    }
+  };
+  auto parallel_for = [](int count, const std::function<void(int)> &fn) {
+    const int nt = std::max(1, std::min({count, 16, (int)std::thread::hardware_concurrency()}));
+    if (nt <= 1) {
+      for (int i = 0; i < count; ++i) fn(i);
+      return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&] {
+        for (int i = next++; i < count; i = next++) fn(i);
+      });
+    for (auto &x : th) x.join();
+  };
+  {
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i)
+      if (st[i] == RS_OK) todo.push_back(i);
+    parallel_for((int)todo.size(), [&](int t) { analyse(todo[t]); });
+  }
+  // Outputs that are known now, and the factors to lift.
+  struct Lift {
+    int pair, mult;
+    PairDesc pd;
+  };
+  std::vector<Lift> lifts;
+  int64_t xl = 0, cy = 0, outw = 0;
+  int kmax = 0;
+  std::vector<int> out_rc(n, RS_OK);
+  for (int i = 0; i < n; ++i) {
+    if (st[i] != RS_OK) continue;
+    const PairRes &q = pr[i];
+    out_rc[i] = put(content[i], {q.content}, {(char)q.lc_neg});
+    for (int m = 0; m < M; ++m) {  // R_i = 1 unless set below
+      const int r2 = put(factors[(size_t)i * M + m], one_m, one_s);
+      if (out_rc[i] == RS_OK) out_rc[i] = r2;
+    }
+    nmult[i] = 0;
+    if (q.degR == 0) continue;
+    // H_m = lc(R) R_m / lc(R_m) over the first KH primes, read in place from
+    // the Yun output (stride one task per prime)
+    const int LH = (bitsH[i] + 1 + 31) / 32;
+    int64_t off = t0v[i] * b->yun_ostride + 2 + M;
+    for (int m = 0; m < M; ++m) {
+      const int d = q.pattern[m];
+      if (d > 0) {
+        Lift lf;
+        lf.pair = i;
+        lf.mult = m;
+        PairDesc &pd = lf.pd;
+        memset(&pd, 0, sizeof(pd));
+        pd.N = d + 1;
+        pd.NI = (int32_t)b->yun_ostride;
+        pd.K = KH[i];
+        pd.Lout = LH;
+        pd.img_off = off;
+        const int64_t chunks = (LH + 15) / 16;
+        pd.xl_off = xl;
+        xl += (int64_t)pd.N * 16 * chunks;
+        pd.cy_off = cy;
+        cy += (int64_t)pd.N * chunks;
+        pd.out_off = outw;
+        outw += (int64_t)pd.N * LH;
+        lifts.push_back(lf);
+        kmax = std::max(kmax, KH[i]);
+      }
+      off += d + 1;
+    }
+  }
+  // One CRT pass over every factor of every pair.
+  const int nf = (int)lifts.size();
+  std::vector<uint32_t> hwords((size_t)outw);
+  if (nf) {
+    std::vector<PairDesc> descs(nf);
+    for (int fi = 0; fi < nf; ++fi) descs[fi] = lifts[fi].pd;
+    std::vector<int2> g3d, g3;
+    std::vector<int4> g3b;
+    for (int fi = 0; fi < nf; ++fi) {
+      const PairDesc &pd = descs[fi];
+      for (int j = 0; j < pd.N; j += 32) g3d.push_back(make_int2(fi, j));
+      for (int j = 0; j < pd.N; j += 128) g3.push_back(make_int2(fi, j));
+      for (int c = 0; c < (pd.Lout + 15) / 16; ++c)
+        for (int j = 0; j < pd.N; j += 128) g3b.push_back(make_int4(fi, j, c, 0));
+    }
+    const int64_t shape_off = outw;
+    auto round256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t piece[7] = {descs.size() * sizeof(PairDesc), g3d.size() * 8, g3.size() * 8, g3b.size() * 16,
+                             (size_t)xl * 4, (size_t)cy * 8, (size_t)(outw + 2 * (int64_t)nf) * 4};
+    size_t bytes = 0;
+    for (size_t x : piece) bytes += round256(x);
+    DevGuard dg(ctx->device);
+    void *arena = nullptr;
+    cudaError_t e = cudaMalloc(&arena, bytes);
+    char *cur = static_cast<char *>(arena);
+    auto carve = [&](size_t x) {
+      char *r = cur;
+      cur += round256(x);
+      return r;
+    };
+    cudaStream_t s = b->stream;
+    cudaEvent_t lev[2] = {nullptr, nullptr};
+    for (auto &x : lev)
+      if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e == cudaSuccess) {
+      PairDesc *d_desc = (PairDesc *)carve(piece[0]);
+      int2 *d_g3d = (int2 *)carve(piece[1]);
+      int2 *d_g3 = (int2 *)carve(piece[2]);
+      int4 *d_g3b = (int4 *)carve(piece[3]);
+      uint32_t *d_xl = (uint32_t *)carve(piece[4]);
+      int64_t *d_cy = (int64_t *)carve(piece[5]);
+      uint32_t *d_out = (uint32_t *)carve(piece[6]);
+      e = cudaMemcpyAsync(d_desc, descs.data(), piece[0], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3d, g3d.data(), piece[1], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3, g3.data(), piece[2], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3b, g3b.data(), piece[3], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_out + shape_off, 0, (size_t)nf * 8, s);
+      RsTables tab;
+      {
+        std::lock_guard<std::mutex> lock(ctx->tab_mu);
+        tab = ctx->tab;
+      }
+      if (e == cudaSuccess) {
+        G3Args a3;
+        memset(&a3, 0, sizeof(a3));
+        a3.pairs = d_desc;
+        a3.ctasks = d_g3b;
+        a3.mods = ctx->d_mods;
+        a3.crt = ctx->d_crt;
+        a3.wtab = tab.wtab;
+        a3.p16 = tab.p16;
+        a3.poff = tab.poff;
+        a3.nh = tab.nh;
+        a3.coef = b->d_yun_out;  // residues of H_m, stride one Yun task (= one prime)
+        a3.xl = d_xl;
+        a3.carry = d_cy;
+        a3.out = d_out;
+        a3.shape = reinterpret_cast<int32_t *>(d_out + shape_off);
+        a3.kmax = kmax;
+        e = cudaEventRecord(lev[0], s);
+        if (e == cudaSuccess) e = launch_g3t((int)g3d.size(), a3, d_g3d, s);
+        if (e == cudaSuccess) e = launch_g3bc((int)g3b.size(), (int)g3.size(), a3, d_g3, s);
+        if (e == cudaSuccess) e = cudaEventRecord(lev[1], s);
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hwords.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&info.ms_lift, lev[0], lev[1]);
+    }
+    for (auto &x : lev)
+      if (x) cudaEventDestroy(x);
+    if (arena) cudaFree(arena);
+    if (e != cudaSuccess) {
+      rs_free_batch(b);
+      return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
+    }
+  }
+  if (b) rs_free_batch(b);
+  // R_m = H_m / content(H_m), leading coefficient made positive; factors on
+  // host threads
+  std::vector<int> lift_rc(nf, RS_OK);
+  std::vector<int> order(nf);  // largest factors first
+  for (int fi = 0; fi < nf; ++fi) order[fi] = fi;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return lifts[x].pd.N > lifts[y].pd.N; });
+  parallel_for(nf, [&](int t) {
+    const int fi = order[t];
+    const Lift &lf = lifts[fi];
+    const PairDesc &pd = lf.pd;
+    std::vector<Big> mag(pd.N), q;
+    std::vector<char> neg(pd.N);
+    for (int j = 0; j < pd.N; ++j) {
+      bool ng;
+      mag[j] = from_twos(&hwords[(size_t)(pd.out_off + (int64_t)j * pd.Lout)], pd.Lout, &ng);
+      neg[j] = ng;
+    }
+    content_of(mag, &q);
+    const bool flip = neg[pd.N - 1] != 0;
+    for (int j = 0; j < pd.N; ++j) neg[j] = q[j].empty() ? 0 : (char)((neg[j] != 0) != flip);
+    lift_rc[fi] = put(factors[(size_t)lf.pair * M + lf.mult], q, neg);
+  });
+  for (int fi = 0; fi < nf; ++fi) {
+    const Lift &lf = lifts[fi];
+    if (out_rc[lf.pair] == RS_OK) out_rc[lf.pair] = lift_rc[fi];
+    nmult[lf.pair] = std::max(nmult[lf.pair], lf.mult + 1);
+  }
+  const auto t_end = std::chrono::steady_clock::now();
+  auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point z) {
+    return (float)std::chrono::duration<double, std::milli>(z - a).count();
+  };
+  info.factors = nf;
+  info.ms_host = ms(t_host0, t_end) - info.ms_lift;
+  info.ms_total = ms(t_start, t_end);
+  ctx->sqf_info = info;
+  int ret = RS_OK;
+  for (int i = 0; i < n; ++i) {
+    if (st[i] == RS_OK && out_rc[i] != RS_OK) {
+      st[i] = out_rc[i];
+      why[i] = "output capacity too small";
+    }
+    if (status) status[i] = st[i];
+    if (st[i] != RS_OK && ret == RS_OK) {
+      ret = st[i];
+      rs_fail(ctx, st[i], n == 1 ? why[i] : "pair " + std::to_string(i) + ": " + why[i]);
+    }
+  }
+  return ret;
+}
 
 extern "C" int rs_squarefree_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
                                rs_upoly *content, rs_upoly *factors, int32_t *nmult) {
   if (!ctx || !f || !g || !content || !factors || !nmult || max_mult < 1)
     return rs_fail(ctx, RS_ERR_ARG, "NULL argument or max_mult < 1");
-  std::vector<PairPlan> plans;
-  int first = RS_OK;
-  rs_plan_all(ctx, 1, f, g, plans, nullptr, &first);
-  if (first != RS_OK) return first;
-  PairPlan &p = plans[0];
-  if (p.trivial_zero) return rs_fail(ctx, RS_ERR_ARG, "R = 0 has no square-free factorisation");
-  // primes for the factors: coefficients of H_i below 2^bitsH
-  const int bitsH = 2 * p.bits + p.D + (int)std::ceil(0.5 * std::log2((double)p.D + 1.0)) + 2;
-  int KH = 0;
-  {
-    double acc = 0.0;
-    while (KH < (int)ctx->log2p.size() && acc < bitsH + 2) acc += ctx->log2p[KH++];
-    if (acc < bitsH + 2) return rs_fail(ctx, RS_ERR_LIMIT, "factor bound needs more primes than RS_MAX_PRIMES");
-  }
-  const int Kall = std::min((int)ctx->log2p.size(), std::max(p.K, KH) + 4);  // a few spare primes
-  p.K = Kall;
-  RsBatchOpts o;
-  o.use_graph = false;
-  o.persistent = ctx->cfg.persistent != 0;
-  o.fork = true;
-  o.yun_maxm = max_mult;
-  rs_batch *b = nullptr;
-  int rc = rs_build_batch(ctx, 1, f, g, std::move(plans), o, &b);
-  if (rc != RS_OK) return rc;
-  DevGuard dg(ctx->device);
-  rc = rs_upload(b, f, g);
-  if (rc == RS_OK) rc = rs_run(b);
-  if (rc == RS_OK) rc = rs_fetch_async(b);
-  std::vector<uint32_t> yun((size_t)b->nyun * b->yun_ostride);
-  if (rc == RS_OK && !yun.empty()) {
-    cudaError_t e = cudaMemcpyAsync(yun.data(), b->d_yun_out, yun.size() * 4, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("square-free: ") + cudaGetErrorString(e));
-  }
-  std::vector<uint32_t> Rw;
-  int degR = -1, LR = 1;
-  if (rc == RS_OK) rc = rs_unpack_one(b, 0, Rw, &degR, &LR);
-  if (rc != RS_OK) {
-    rs_free_batch(b);
-    return rc;
-  }
-  if (degR < 0) {
-    rs_free_batch(b);
-    return rs_fail(ctx, RS_ERR_ARG, "R = 0 has no square-free factorisation");
-  }
-  // content c = sign(lc R) gcd(coefficients of R)
-  Big cg;
-  bool lc_neg = false;
-  for (int j = 0; j <= degR; ++j) {
-    bool neg;
-    const Big v = from_twos(&Rw[(size_t)j * LR], LR, &neg);
-    if (j == degR) lc_neg = neg;
-    cg = big_gcd(cg, v);
-  }
-  auto put = [&](rs_upoly &out, const std::vector<std::pair<Big, bool>> &coefs) -> int {
-    int L = 1;
-    for (const auto &cv : coefs) L = std::max(L, twos_limbs(cv.first, cv.second));
-    const int deg = (int)coefs.size() - 1;
-    out.deg = deg;
-    out.limbs = L;
-    if ((int64_t)(deg + 1) * L > out.capacity_words || (!out.coeffs && deg >= 0)) return RS_ERR_CAPACITY;
-    for (int j = 0; j <= deg; ++j) to_twos(coefs[j].first, coefs[j].second, out.coeffs + (size_t)j * L, L);
-    return RS_OK;
-  };
-  int out_rc = put(*content, {{cg, lc_neg}});
-  for (int i = 0; i < max_mult; ++i) {  // R_i = 1 unless set below
-    std::vector<std::pair<Big, bool>> one{{Big{1u}, false}};
-    const int r2 = put(factors[i], one);
-    if (out_rc == RS_OK) out_rc = r2;
-  }
-  *nmult = 0;
-  if (degR <= 0) {
-    rs_free_batch(b);
-    return out_rc != RS_OK ? rs_fail(ctx, out_rc, "output capacity too small") : RS_OK;
-  }
-  // usable primes: R keeps its degree mod p, square-free part of largest degree
-  const int M = max_mult;
-  auto task = [&](int k) { return &yun[(size_t)k * b->yun_ostride]; };
-  int best_sf = -1;
-  for (int k = 0; k < b->nyun; ++k) {
-    const uint32_t *t = task(k);
-    if ((int)t[0] != degR || t[1]) continue;
-    int sf = 0;
-    for (int i = 0; i < M; ++i) sf += (int)t[2 + i];
-    best_sf = std::max(best_sf, sf);
-  }
-  for (int k = 0; k < KH && k < b->nyun; ++k)
-    if ((int)task(k)[0] == degR && task(k)[1]) {  // Yun ran past max_mult on a prime that keeps deg R
-      rs_free_batch(b);
-      return rs_fail(ctx, RS_ERR_CAPACITY, "a factor's multiplicity exceeds max_mult");
-    }
-  std::vector<int> pattern(M, 0);
-  int good = 0;  // length of the prefix of usable primes with the same pattern
-  for (int k = 0; k < b->nyun; ++k) {
-    const uint32_t *t = task(k);
-    if ((int)t[0] != degR || t[1]) break;
-    int sf = 0;
-    for (int i = 0; i < M; ++i) sf += (int)t[2 + i];
-    if (sf != best_sf) break;
-    if (k == 0)
-      for (int i = 0; i < M; ++i) pattern[i] = (int)t[2 + i];
-    bool same = true;
-    for (int i = 0; i < M; ++i) same = same && (int)t[2 + i] == pattern[i];
-    if (!same) break;
-    ++good;
-  }
-  if (good < KH) {
-    rs_free_batch(b);
-    return rs_fail(ctx, RS_ERR_LIMIT,
-                   "an unlucky prime for the square-free factorisation lies among the first " +
-                       std::to_string(KH) + " primes (prime index " + std::to_string(good) + ")");
-  }
-  // Lift H_i = lc(R) R_i / lc(R_i) over the first KH primes with the CRT kernels.
-  std::vector<int> fidx;  // multiplicities with a non-constant factor
-  std::vector<PairDesc> descs;
-  int64_t off = 2 + M, xl = 0, cy = 0, outw = 0;
-  const int LH = (bitsH + 1 + 31) / 32;
-  for (int i = 0; i < M; ++i) {
-    const int d = pattern[i];
-    if (d > 0) {
-      PairDesc pd;
-      memset(&pd, 0, sizeof(pd));
-      pd.N = d + 1;
-      pd.NI = (int32_t)b->yun_ostride;
-      pd.K = KH;
-      pd.Lout = LH;
-      pd.img_off = off;
-      const int64_t chunks = (LH + 15) / 16;
-      pd.xl_off = xl;
-      xl += (int64_t)pd.N * 16 * chunks;
-      pd.cy_off = cy;
-      cy += (int64_t)pd.N * chunks;
-      pd.out_off = outw;
-      outw += (int64_t)pd.N * LH;
-      descs.push_back(pd);
-      fidx.push_back(i);
-    }
-    off += d + 1;
-  }
-  const int nf = (int)descs.size();
-  std::vector<int2> g3d, g3;
-  std::vector<int4> g3b;
-  for (int fi = 0; fi < nf; ++fi) {
-    const PairDesc &pd = descs[fi];
-    for (int j = 0; j < pd.N; j += 32) g3d.push_back(make_int2(fi, j));
-    for (int j = 0; j < pd.N; j += 128) g3.push_back(make_int2(fi, j));
-    for (int c = 0; c < (pd.Lout + 15) / 16; ++c)
-      for (int j = 0; j < pd.N; j += 128) g3b.push_back(make_int4(fi, j, c, 0));
-  }
-  const int64_t shape_off = outw;
-  outw += 2 * (int64_t)nf;
-  auto round256 = [](size_t n) { return (n + 255) & ~(size_t)255; };
-  const size_t piece[7] = {descs.size() * sizeof(PairDesc), g3d.size() * 8, g3.size() * 8, g3b.size() * 16,
-                           (size_t)xl * 4, (size_t)cy * 8, (size_t)outw * 4};
-  size_t bytes = 0;
-  for (size_t n : piece) bytes += round256(n);
-  void *arena = nullptr;
-  cudaError_t e = cudaMalloc(&arena, bytes);
-  char *cur = static_cast<char *>(arena);
-  auto carve = [&](size_t n) {
-    char *r = cur;
-    cur += round256(n);
-    return r;
-  };
-  PairDesc *d_desc = nullptr;
-  int2 *d_g3d = nullptr, *d_g3 = nullptr;
-  int4 *d_g3b = nullptr;
-  uint32_t *d_xl = nullptr, *d_out = nullptr;
-  int64_t *d_cy = nullptr;
-  if (e == cudaSuccess) {
-    d_desc = (PairDesc *)carve(descs.size() * sizeof(PairDesc));
-    d_g3d = (int2 *)carve(g3d.size() * 8);
-    d_g3 = (int2 *)carve(g3.size() * 8);
-    d_g3b = (int4 *)carve(g3b.size() * 16);
-    d_xl = (uint32_t *)carve((size_t)xl * 4);
-    d_cy = (int64_t *)carve((size_t)cy * 8);
-    d_out = (uint32_t *)carve((size_t)outw * 4);
-  }
-  cudaStream_t s = b->stream;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_desc, descs.data(), descs.size() * sizeof(PairDesc), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3d, g3d.data(), g3d.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3, g3.data(), g3.size() * 8, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3b, g3b.data(), g3b.size() * 16, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_out + shape_off, 0, (size_t)nf * 8, s);
-  RsTables tab;
-  {
-    std::lock_guard<std::mutex> lock(ctx->tab_mu);
-    tab = ctx->tab;
-  }
-  if (e == cudaSuccess && nf) {
-    G3Args a3;
-    memset(&a3, 0, sizeof(a3));
-    a3.pairs = d_desc;
-    a3.ctasks = d_g3b;
-    a3.mods = ctx->d_mods;
-    a3.crt = ctx->d_crt;
-    a3.wtab = tab.wtab;
-    a3.p16 = tab.p16;
-    a3.poff = tab.poff;
-    a3.nh = tab.nh;
-    a3.coef = b->d_yun_out;  // the residues, stride yun_ostride per prime (task k = prime k)
-    a3.xl = d_xl;
-    a3.carry = d_cy;
-    a3.out = d_out;
-    a3.shape = reinterpret_cast<int32_t *>(d_out + shape_off);
-    a3.kmax = KH;
-    e = launch_g3t((int)g3d.size(), a3, d_g3d, s);
-    if (e == cudaSuccess) e = launch_g3bc((int)g3b.size(), (int)g3.size(), a3, d_g3, s);
-  }
-  std::vector<uint32_t> hw((size_t)outw);
-  if (e == cudaSuccess && outw) e = cudaMemcpyAsync(hw.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (arena) cudaFree(arena);
-  rs_free_batch(b);
-  if (e != cudaSuccess) return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
-  // R_i = H_i / content(H_i), leading coefficient made positive
-  for (int fi = 0; fi < nf; ++fi) {
-    const PairDesc &pd = descs[fi];
-    std::vector<std::pair<Big, bool>> co(pd.N);
-    Big gg;
-    for (int j = 0; j < pd.N; ++j) {
-      bool neg;
-      co[j].first = from_twos(&hw[(size_t)(pd.out_off + (int64_t)j * LH)], LH, &neg);
-      co[j].second = neg;
-      gg = big_gcd(gg, co[j].first);
-    }
-    const bool flip = co[pd.N - 1].second;
-    for (auto &cv : co) {
-      if (!cv.first.empty()) cv.first = big_divexact(cv.first, gg);
-      cv.second = cv.first.empty() ? false : (cv.second != flip);
-    }
-    const int r2 = put(factors[fidx[fi]], co);
-    if (out_rc == RS_OK) out_rc = r2;
-    *nmult = std::max(*nmult, fidx[fi] + 1);
-  }
-  if (out_rc != RS_OK) return rs_fail(ctx, out_rc, "output capacity too small");
+  return rs_squarefree_batch(ctx, 1, f, g, max_mult, content, factors, nmult, nullptr);
+}
+
+extern "C" int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info) {
+  if (!ctx || !info) return RS_ERR_ARG;
+  *info = ctx->sqf_info;
   return RS_OK;
 }

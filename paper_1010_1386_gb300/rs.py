@@ -5,6 +5,7 @@ Python polynomials to the C structs and results back.  There is no fallback:
 if ``librs.so`` is missing or cannot be loaded, ``load()`` raises.
 """
 import ctypes
+import math
 import os
 from ctypes import POINTER, c_char_p, c_double, c_float, c_int32, c_int64, c_uint32, c_void_p
 
@@ -54,7 +55,13 @@ class rs_batch_info(ctypes.Structure):
                 ("output_bytes", c_int64), ("ms_images", c_float), ("ms_interp", c_float),
                 ("ms_crt", c_float), ("ms_total", c_float), ("unlucky_points", c_int64),
                 ("degenerate_images", c_int64), ("unlucky_primes", c_int64),
-                ("kernel_launches", c_int64)]
+                ("kernel_launches", c_int64), ("ms_yun", c_float), ("reserved", c_int32)]
+
+
+class rs_sqf_info(ctypes.Structure):
+    _fields_ = [("batch", rs_batch_info), ("yun_tasks", c_int64), ("factors", c_int64),
+                ("ms_lift", c_float), ("ms_host", c_float), ("ms_total", c_float),
+                ("reserved", c_int32)]
 
 
 class rs_server_stats(ctypes.Structure):
@@ -98,6 +105,9 @@ _SIGS = {
                                  _P(rs_upoly), _P(c_int32)]),
     "rs_squarefree_y": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), c_int32, _P(rs_upoly),
                                   _P(rs_upoly), _P(c_int32)]),
+    "rs_squarefree_batch": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), c_int32,
+                                      _P(rs_upoly), _P(rs_upoly), _P(c_int32), _P(c_int32)]),
+    "rs_squarefree_info_get": (c_int32, [c_void_p, _P(rs_sqf_info)]),
     "rs_autotune": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
     "rs_autotune_entries": (c_int32, [_P(rs_tune_entry), c_int32, _P(c_int32)]),
     "rs_autotune_save": (c_int32, [c_char_p]),
@@ -290,33 +300,91 @@ class Context:
         """Square-free factorisation of Res_y(f, g): (c, [(i, R_i), ...]) with
         Res_y = c * prod R_i^i (R_i as lists of Python ints, ascending; only
         the non-constant factors, in increasing multiplicity)."""
-        P = _Polys([f, g])
-        b = result_bound(f, g)
-        words = [max(1, b["limbs"]), max(1, (b["deg"] + 1) * (2 * b["limbs"] + 2))]
+        out = self.squarefree_batch([(f, g)], max_mult)[0]
+        if isinstance(out, RsError):
+            raise out
+        return out
+
+    def squarefree_batch(self, pairs, max_mult=8, raw=False):
+        """Square-free factorisations of Res_y(f, g) for every (f, g) in pairs
+        in one GPU pass: per pair (c, [(i, R_i), ...]) as squarefree()
+        returns, or the RsError of a pair that failed (``raw``: only the
+        per-pair status codes; the limbs stay in the host buffers)."""
+        n = len(pairs)
+        if n == 0:
+            return []
+        F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        # output room from the planner's bounds: R_i has degree <= D / i and
+        # coefficients below the bound of the lifted factors
+        cw, fw = [], []
+        for f, g in pairs:
+            try:
+                b = result_bound(f, g)
+            except RsError:
+                b = {"deg": 0, "limbs": 1, "bits": 0}
+            D = max(b["deg"], 0)
+            lh = (2 * b["bits"] + D + int(math.ceil(0.5 * math.log2(D + 1))) + 3 + 31) // 32 + 1
+            cw.append(max(1, b["limbs"]))
+            fw.append([max(1, (D // m + 1) * lh) for m in range(1, max_mult + 1)])
         for _ in range(2):  # the second call has the exact sizes the first reported
-            content = rs_upoly()
-            cbuf = np.zeros(words[0], dtype=np.uint32)
-            content.capacity_words, content.coeffs = words[0], cbuf.ctypes.data_as(POINTER(c_uint32))
-            facs = (rs_upoly * max_mult)()
-            fbufs = []
-            for fs in facs:
-                fb = np.zeros(words[1], dtype=np.uint32)
-                fbufs.append(fb)
-                fs.capacity_words, fs.coeffs = words[1], fb.ctypes.data_as(POINTER(c_uint32))
-            nm = c_int32()
-            rc = self.lib.rs_squarefree_y(self.h, ctypes.byref(P.structs[0]), ctypes.byref(P.structs[1]),
-                                          max_mult, ctypes.byref(content), facs, ctypes.byref(nm))
-            if rc != -2:
+            content = (rs_upoly * n)()
+            facs = (rs_upoly * (n * max_mult))()
+            cbuf = np.empty(sum(cw), dtype=np.uint32)
+            fbuf = np.empty(sum(sum(w) for w in fw), dtype=np.uint32)
+            base, co, fo = cbuf.ctypes.data, [], []
+            off = 0
+            for i in range(n):
+                content[i].capacity_words = cw[i]
+                content[i].coeffs = ctypes.cast(base + 4 * off, POINTER(c_uint32))
+                co.append(off)
+                off += cw[i]
+            fbase, off = fbuf.ctypes.data, 0
+            for i in range(n):
+                for m in range(max_mult):
+                    u = facs[i * max_mult + m]
+                    u.capacity_words = fw[i][m]
+                    u.coeffs = ctypes.cast(fbase + 4 * off, POINTER(c_uint32))
+                    fo.append(off)
+                    off += fw[i][m]
+            nm = (c_int32 * n)()
+            st = (c_int32 * n)()
+            rc = self.lib.rs_squarefree_batch(self.h, n, F.structs, G.structs, max_mult, content, facs, nm, st)
+            grow = False
+            for i in range(n):
+                if st[i] != -2:
+                    continue
+                need_c = max(1, (content[i].deg + 1) * content[i].limbs)
+                need_f = [max(1, (u.deg + 1) * u.limbs) for u in facs[i * max_mult:(i + 1) * max_mult]]
+                if need_c > cw[i] or any(a > b for a, b in zip(need_f, fw[i])):
+                    cw[i] = max(cw[i], need_c)
+                    fw[i] = [max(a, b) for a, b in zip(need_f, fw[i])]
+                    grow = True
+            if not grow:
                 break
-            words = [max(1, (content.deg + 1) * content.limbs),
-                     max(max(1, (fs.deg + 1) * fs.limbs) for fs in facs)]
-        _check(rc, self.h)
-        c = limbs_to_ints(cbuf, content.deg, content.limbs)[0]
+        if raw:
+            return list(st)
+        msg = (self.lib.rs_last_error(self.h) or b"").decode() if rc < 0 else ""
         out = []
-        for i, (fs, fb) in enumerate(zip(facs, fbufs), start=1):
-            if fs.deg > 0:
-                out.append((i, limbs_to_ints(fb, fs.deg, fs.limbs)))
-        return c, out
+        for i in range(n):
+            if st[i] != 0:
+                out.append(RsError(st[i], msg if n == 1 else f"pair {i} failed"))
+                continue
+            c = limbs_to_ints(cbuf[co[i]:], content[i].deg, content[i].limbs)[0]
+            r = []
+            for m in range(max_mult):
+                u = facs[i * max_mult + m]
+                if u.deg > 0:
+                    r.append((m + 1, limbs_to_ints(fbuf[fo[i * max_mult + m]:], u.deg, u.limbs)))
+            out.append((c, r))
+        return out
+
+    def squarefree_info(self):
+        """Stage times and counts of the last square-free call (dict)."""
+        si = rs_sqf_info()
+        _check(self.lib.rs_squarefree_info_get(self.h, ctypes.byref(si)), self.h)
+        out = {k: getattr(si, k) for k, _ in rs_sqf_info._fields_ if k not in ("batch", "reserved")}
+        out["batch"] = {k: getattr(si.batch, k) for k, _ in rs_batch_info._fields_ if k != "reserved"}
+        return out
 
     def images(self, f, g, nprimes, npoints):
         """(primes[K], points[K, N], images[K, N]): images[k, i] =

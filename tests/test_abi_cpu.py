@@ -1,6 +1,7 @@
 """CPU-only checks of the C ABI: the library loads, exports every function
 include/rs.h declares, and its host-side planner returns bounds that hold
 for the oracle's exact results.  No GPU compute is called."""
+import ctypes
 import os
 import random
 import re
@@ -137,3 +138,31 @@ def test_config_layout(lib):
     assert cfg.mem_limit_bytes == 0 and cfg.autotune_cache is None
     assert cfg.g2_form == 0
     assert rs.rs_config.mem_limit_bytes.offset == 32 and rs.rs_config.autotune_cache.offset == 40
+
+
+def test_info_struct_layouts(tmp_path):
+    """The binding's ctypes structs match the header as a C compiler lays it
+    out (sizes and field offsets)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    checks = [("rs_batch_info", rs.rs_batch_info), ("rs_sqf_info", rs.rs_sqf_info)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rs.h"', "int main(void) {"]
+    for name, st in checks:
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in st._fields_:
+            lines.append(f'  printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("  return 0;\n}")
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for name, st in checks:
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for fname, _ in st._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(st, fname).offset, (name, fname)

@@ -69,10 +69,28 @@ def test_constant_zero_and_multiplicity_limit(ctx):
 def test_nongeneric_workload_full_size(ctx):
     """The first pair of the coprime topology workload (f = p q^2, g =
     d(pq)/dy, total degrees 48 and 35): the factors multiply back to the GPU
-    resultant, and a factor of multiplicity 2 carries Res_y(q, g)."""
+    resultant.  By multiplicativity R = Res_y(p, g) Res_y(q, g)^2, which is
+    disc_y(p) disc_y(q)^2 Res_y(p, q)^3 up to a constant, so factors of
+    multiplicities 1, 2 and 3 appear."""
     (f, g), = inputs.workload_nongeneric(3, n=1, coprime=True)
     R = ctx.resultant_y(f, g)
     c, facs = ctx.squarefree(f, g)
     assert sq.expand(c, facs) == R
     assert all(P[-1] > 0 for _, P in facs) and [m for m, _ in facs] == sorted(m for m, _ in facs)
-    assert any(m >= 2 for m, _ in facs)
+    assert [m for m, _ in facs] == [1, 2, 3]
+
+
+def test_batch_mixed_pairs(ctx):
+    """One pass over planted, random, constant and zero resultants: every
+    pair matches the oracle, the zero one fails alone with RS_ERR_ARG."""
+    rng = random.Random(73)
+    pairs = [planted(rng, dp, dq, bits) for dp, dq, bits in [(2, 1, 9), (1, 2, 3), (3, 2, 12)]]
+    pairs += [(rand_bipoly(rng, 3, 3, bits=40), rand_bipoly(rng, 2, 4, bits=5)) for _ in range(3)]
+    pairs += [([[3]], [[0, 1]]), ([[0, 1]], [[0, 2]]), ([[0, 1]], [[0, 0, 0, 1], [0], [0], [-1]])]
+    got = ctx.squarefree_batch(pairs)
+    for i, ((f, g), r) in enumerate(zip(pairs, got)):
+        R = exact.resultant_y(f, g)
+        if not R:
+            assert isinstance(r, rs.RsError) and r.code == -1, i
+        else:
+            assert r == sq.squarefree(R), i
