@@ -205,7 +205,7 @@ int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *
                    rs_upoly *out_y, rs_upoly *out_x, int32_t *status);
 
 /* Square-free factorisation of R = R^{(y)} = res(f, g, y) (the paper's
- * solver computes R^{(y)} "and a corresponding square-free factorization",
+ * solver computes R^{(y)} together with its square-free factorisation,
  * Section 5, PROJECT): R = c * prod_{i >= 1} R_i^i with c an integer and
  * every R_i in Z[x] primitive, square-free, pairwise coprime, with a
  * positive leading coefficient.  One GPU pass computes R over enough primes

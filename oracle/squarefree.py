@@ -1,8 +1,7 @@
 """Square-free factorisation of a polynomial in Z[x] -- test infrastructure only.
 
 The paper's solver computes, for each resultant polynomial R, a square-free
-factorisation (Section 5, the PROJECT phase: R^{(y)} and "a corresponding
-square-free factorization").  The plain definition: R = c * prod_i R_i^i
+factorisation of it (Section 5, the PROJECT phase).  The plain definition: R = c * prod_i R_i^i
 with c in Z, every R_i in Z[x] primitive with positive leading coefficient,
 square-free, and the R_i pairwise coprime; constant factors are omitted.
 

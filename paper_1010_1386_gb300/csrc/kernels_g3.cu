@@ -1,5 +1,5 @@
 // G3: Chinese remaindering (paper, Section 4.1: the residues R mod p are
-// "lifted to an integer solution via Chinese remaindering").
+// combined into the integer result by the Chinese remainder theorem).
 //
 // Garner's mixed-radix form R_j = v_0 + p_0 (v_1 + p_1 (v_2 + ...)) with
 // digits v_k in the symmetric range (-p_k/2, p_k/2) gives the symmetric

@@ -1,17 +1,19 @@
-// Square-free factorisation of R mod p (the paper's solver, Section 5,
-// PROJECT: R^{(y)} "and a corresponding square-free factorization"), one
-// thread block per (pair, prime), between the interpolation (G2) and the
-// Chinese remaindering (G3): Yun's algorithm (D. Y. Y. Yun, SYMSAC 1976) over
-// Z_p on the interpolated residues of R,
+// Square-free factorisation of R mod p (the paper's solver computes R^{(y)}
+// together with its square-free factorisation, Section 5, PROJECT), one warp
+// per (pair, prime), between the interpolation (G2) and the Chinese
+// remaindering (G3): Yun's algorithm (D. Y. Y. Yun, SYMSAC 1976) over Z_p on
+// the interpolated residues of R,
 //   A = gcd(F, F'), B = F / A, C = F' / A, D = C - B';
 //   repeat: R_i = gcd(B, D), B = B / R_i, C = D / R_i, D = C - B'
 // with monic R_i.  Remainders for the gcds are division-free (X <- lc(Y) X -
 // lc(X) x^s Y, the degree drops by one per step; a gcd is only defined up to
 // a unit), exact divisions use one inverse of the divisor's leading
-// coefficient, and every step is spread over the block's threads with a
-// barrier.  The polynomials live in global scratch, except the two that every
-// remainder and division step rewrites (the gcd operands and the division
-// remainder), which live in shared memory when they fit.
+// coefficient.  Each step is spread over the warp's lanes; a remainder step
+// reads the new leading coefficient once (it is non-zero unless p divides it,
+// and only then is the polynomial scanned for its degree), so a step costs one
+// warp barrier.  The polynomials live in global scratch, except the two that
+// every remainder and division step rewrites (the gcd operands and the
+// division remainder), which live in shared memory when they fit.
 //
 // Output per task (word offsets from out + task * ostride):
 //   [0]            degree of R mod p (-1 if R = 0 mod p)
@@ -25,90 +27,94 @@
 
 namespace {
 
+constexpr unsigned FULL = 0xffffffffu;
+
 struct Poly {
-  uint32_t *c;  // Montgomery form, c[0 .. deg]
+  uint32_t *c;  // Montgomery form, c[0 .. deg]; words above deg are don't-care
   int deg;      // -1 for the zero polynomial
 };
 
-// Highest j <= from with p[j] != 0, or -1 (all threads return the same value).
-__device__ int top_degree(const uint32_t *p, int from, int *s_min) {
-  const int T = blockDim.x;
-  for (int hi = from; hi >= 0; hi -= T) {
-    const int j = hi - (int)threadIdx.x;
-    const bool nz = j >= 0 && p[j] != 0u;
-    if (__syncthreads_or(nz)) {
-      if (threadIdx.x == 0) *s_min = T;
-      __syncthreads();
-      if (nz) atomicMin(s_min, (int)threadIdx.x);
-      __syncthreads();
-      const int r = hi - *s_min;
-      __syncthreads();
-      return r;
-    }
+__device__ __forceinline__ int lane_id() { return (int)(threadIdx.x & 31u); }
+
+// Highest j <= from with p[j] != 0, or -1 (the same value in every lane).
+__device__ int top_degree(const uint32_t *p, int from) {
+  for (int hi = from; hi >= 0; hi -= 32) {
+    const int j = hi - lane_id();
+    const unsigned m = __ballot_sync(FULL, j >= 0 && p[j] != 0u);
+    if (m) return hi - (__ffs(m) - 1);  // the lowest lane holds the highest index
   }
   return -1;
 }
 
 __device__ void copy_poly(Poly &dst, const Poly &src) {
-  for (int j = threadIdx.x; j <= src.deg; j += blockDim.x) dst.c[j] = src.c[j];
+  for (int j = lane_id(); j <= src.deg; j += 32) dst.c[j] = src.c[j];
   dst.deg = src.deg;
-  __syncthreads();
+  __syncwarp();
 }
 
 // d = p' (d may not alias p).
 __device__ void derivative(Poly &d, const Poly &p, const ModP &m) {
-  for (int j = threadIdx.x; j < p.deg; j += blockDim.x) d.c[j] = mmul(p.c[j + 1], to_mont((uint32_t)(j + 1), m), m);
-  __syncthreads();
-  d.deg = p.deg - 1;
-  if (d.deg >= 0) {
-    __shared__ int s_min;
-    d.deg = top_degree(d.c, d.deg, &s_min);
-  }
+  for (int j = lane_id(); j < p.deg; j += 32) d.c[j] = mmul(p.c[j + 1], to_mont((uint32_t)(j + 1), m), m);
+  __syncwarp();
+  d.deg = p.deg >= 1 ? top_degree(d.c, p.deg - 1) : -1;
 }
 
 // x <- x - y (in place).
 __device__ void sub_in_place(Poly &x, const Poly &y, const ModP &m) {
   const int n = max(x.deg, y.deg);
-  for (int j = threadIdx.x; j <= n; j += blockDim.x) {
+  for (int j = lane_id(); j <= n; j += 32) {
     const uint32_t a = j <= x.deg ? x.c[j] : 0u, b = j <= y.deg ? y.c[j] : 0u;
     x.c[j] = msub(a, b, m.p);
   }
-  __syncthreads();
-  __shared__ int s_min;
-  x.deg = n >= 0 ? top_degree(x.c, n, &s_min) : -1;
+  __syncwarp();
+  x.deg = n >= 0 ? top_degree(x.c, n) : -1;
 }
 
-// x <- x mod y up to a unit factor (division-free), y non-zero.
+// x <- x mod y up to a unit factor (division-free), y non-zero.  A step
+// rewrites x[0 .. deg) and never its leading coefficient, and each step ends
+// with a warp barrier, so the next step's reads of the leading coefficients
+// follow the writes.  In the normal case deg x = deg y + 1 one pass takes two
+// division steps at once:
+//   x <- lc(y)^2 x - (a t + b) y,  a = lc(y) x_n,  b = lc(y) x_{n-1} - x_n y_{n-2},
+// whose coefficients n and n - 1 vanish; otherwise one step
+//   x <- lc(y) x - lc(x) t^s y.
 __device__ void rem_in_place(Poly &x, const Poly &y, const ModP &m) {
-  __shared__ int s_min;
-  while (x.deg >= y.deg && x.deg >= 0) {
-    const int s = x.deg - y.deg;
-    const uint32_t lx = x.c[x.deg], ly = y.c[y.deg];
-    __syncthreads();
-    const uint32_t nlx = mneg(lx, m.p);
-    for (int j = threadIdx.x; j < x.deg; j += blockDim.x)
-      x.c[j] = j >= s ? mmul2(ly, x.c[j], nlx, y.c[j - s], m) : mmul(ly, x.c[j], m);
-    if (threadIdx.x == 0) x.c[x.deg] = 0u;
-    __syncthreads();
-    x.deg = x.deg > 0 ? top_degree(x.c, x.deg - 1, &s_min) : -1;
+  uint32_t *__restrict__ xc = x.c;
+  const uint32_t *__restrict__ yc = y.c;
+  const int dy = y.deg;
+  const uint32_t ly = yc[dy];
+  const uint32_t c2 = mmul(ly, ly, m);
+  while (x.deg >= dy) {
+    const int n = x.deg, s = n - dy;
+    if (s == 1 && dy >= 1) {
+      const uint32_t xn = xc[n], xn1 = xc[n - 1];
+      const uint32_t na = mneg(mmul(ly, xn, m), m.p);
+      const uint32_t nb = msub(mmul(xn, yc[dy - 1], m), mmul(ly, xn1, m), m.p);
+      for (int j = lane_id(); j < n - 1; j += 32) {
+        const uint32_t t1 = j >= 1 ? mmul2(c2, xc[j], na, yc[j - 1], m) : mmul(c2, xc[j], m);
+        xc[j] = madd(t1, mmul(nb, yc[j], m), m.p);
+      }
+      __syncwarp();
+      const int nd = n - 2;
+      x.deg = (nd < 0 || xc[nd] != 0u) ? nd : top_degree(xc, nd);
+    } else {
+      const uint32_t nlx = mneg(xc[n], m.p);
+      for (int j = lane_id(); j < n; j += 32)
+        xc[j] = j >= s ? mmul2(ly, xc[j], nlx, yc[j - s], m) : mmul(ly, xc[j], m);
+      __syncwarp();
+      const int nd = n - 1;
+      x.deg = (nd < 0 || xc[nd] != 0u) ? nd : top_degree(xc, nd);
+    }
   }
-}
-
-__device__ uint32_t block_inverse(uint32_t v, const ModP &m) {
-  __shared__ uint32_t s_inv;
-  if (threadIdx.x == 0) s_inv = minv(v, m);
-  __syncthreads();
-  const uint32_t r = s_inv;
-  __syncthreads();
-  return r;
 }
 
 // x <- x / lc(x).
 __device__ void make_monic(Poly &x, const ModP &m) {
   if (x.deg < 0) return;
-  const uint32_t inv = block_inverse(x.c[x.deg], m);
-  for (int j = threadIdx.x; j <= x.deg; j += blockDim.x) x.c[j] = mmul(x.c[j], inv, m);
-  __syncthreads();
+  const uint32_t inv = minv(x.c[x.deg], m);  // every lane computes the same inverse
+  __syncwarp();
+  for (int j = lane_id(); j <= x.deg; j += 32) x.c[j] = mmul(x.c[j], inv, m);
+  __syncwarp();
 }
 
 // g <- monic gcd(a, b), copied into g's own buffer; a and b (distinct from
@@ -129,23 +135,48 @@ __device__ void gcd_monic(Poly &g, Poly a, Poly b, const ModP &m) {
   copy_poly(g, a);
 }
 
-// q <- x / y exactly (y non-zero and dividing x); r is scratch holding x's copy.
+// q <- x / y exactly (y non-zero and dividing x); r is scratch holding x's
+// copy.  One pass takes two quotient coefficients q_t, q_{t-1} (the second
+// after the first's correction of r[deg y + t - 1]) and subtracts
+// (q_t t^t + q_{t-1} t^{t-1}) y from r; a pass reads the top two words of r,
+// which the previous pass wrote, and writes below them, with one barrier per
+// pass.
 __device__ void divexact(Poly &q, const Poly &x, const Poly &y, Poly &r, const ModP &m) {
   copy_poly(r, x);
-  const int dq = x.deg - y.deg;
-  const uint32_t inv = block_inverse(y.c[y.deg], m);
-  for (int t = dq; t >= 0; --t) {
-    const uint32_t qt = mmul(r.c[y.deg + t], inv, m);
-    __syncthreads();
-    const uint32_t nq = mneg(qt, m.p);
-    for (int j = threadIdx.x; j < y.deg; j += blockDim.x) r.c[j + t] = madd(r.c[j + t], mmul(nq, y.c[j], m), m.p);
-    if (threadIdx.x == 0) q.c[t] = qt;
-    __syncthreads();
-  }
+  const int dq = x.deg - y.deg, n = y.deg;
+  const uint32_t inv = minv(y.c[n], m);
+  uint32_t *__restrict__ rc = r.c;
+  const uint32_t *__restrict__ yc = y.c;
   q.deg = max(dq, -1);
+  if (n == 0) {  // a constant divisor
+    for (int t = lane_id(); t <= dq; t += 32) q.c[t] = mmul(rc[t], inv, m);
+    __syncwarp();
+    return;
+  }
+  int t = dq;
+  for (; t >= 1; t -= 2) {
+    const uint32_t qt = mmul(rc[n + t], inv, m);
+    const uint32_t qt1 = mmul(msub(rc[n + t - 1], mmul(qt, yc[n - 1], m), m.p), inv, m);
+    const uint32_t nq = mneg(qt, m.p), nq1 = mneg(qt1, m.p);
+    for (int i = t - 1 + lane_id(); i < n + t - 1; i += 32) {
+      const int k = i - t;  // y index of the q_t term
+      const uint32_t v = k >= 0 ? mmul2(nq, yc[k], nq1, yc[k + 1], m) : mmul(nq1, yc[0], m);
+      rc[i] = madd(rc[i], v, m.p);
+    }
+    if (lane_id() == 0) {
+      q.c[t] = qt;
+      q.c[t - 1] = qt1;
+    }
+    __syncwarp();
+  }
+  if (t == 0) {
+    const uint32_t q0 = mmul(rc[n], inv, m);
+    if (lane_id() == 0) q.c[0] = q0;
+    __syncwarp();
+  }
 }
 
-__global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
+__global__ void __launch_bounds__(32) yun_kernel(YunArgs a) {
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const ModP m = a.mods[task.y];
@@ -161,15 +192,14 @@ __global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
   }
   Poly &F = P[0], &Fd = P[1], &A = P[2], &B = P[3], &C = P[4], &D = P[5], &T1 = P[6], &T2 = P[7];
   const uint32_t *res = a.coef + pd.img_off + (size_t)task.y * pd.NI;
-  for (int j = threadIdx.x; j < N; j += blockDim.x) F.c[j] = to_mont(res[j], m);
-  __syncthreads();
-  __shared__ int s_min;
-  F.deg = top_degree(F.c, N - 1, &s_min);
-  if (threadIdx.x == 0) {
+  for (int j = lane_id(); j < N; j += 32) F.c[j] = to_mont(res[j], m);
+  __syncwarp();
+  F.deg = top_degree(F.c, N - 1);
+  if (lane_id() == 0) {
     o[0] = (uint32_t)F.deg;
     o[1] = 0u;
   }
-  for (int i = threadIdx.x; i < a.maxm; i += blockDim.x) o[2 + i] = 0u;
+  for (int i = lane_id(); i < a.maxm; i += 32) o[2 + i] = 0u;
   if (F.deg <= 0) return;  // R = 0 or a constant mod p: no factors
   const uint32_t lcR = F.c[F.deg];
   derivative(Fd, F, m);
@@ -185,7 +215,7 @@ __global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
   int i = 1;
   while (B.deg > 0) {
     if (i > a.maxm) {
-      if (threadIdx.x == 0) o[1] = 1u;
+      if (lane_id() == 0) o[1] = 1u;
       return;
     }
     // R_i = gcd(B, D) into the buffer of F' (free after the first step),
@@ -195,8 +225,8 @@ __global__ void __launch_bounds__(256) yun_kernel(YunArgs a) {
     copy_poly(T2, D);
     gcd_monic(Ri, T1, T2, m);
     // emit lc(R) R_i (plain) and its degree
-    for (int j = threadIdx.x; j <= Ri.deg; j += blockDim.x) dst[j] = from_mont(mmul(Ri.c[j], lcR, m), m);
-    if (threadIdx.x == 0) o[1 + i] = (uint32_t)Ri.deg;
+    for (int j = lane_id(); j <= Ri.deg; j += 32) dst[j] = from_mont(mmul(Ri.c[j], lcR, m), m);
+    if (lane_id() == 0) o[1 + i] = (uint32_t)Ri.deg;
     dst += Ri.deg + 1;
     // B = B / R_i, C = D / R_i, D = C - B'
     divexact(A, B, Ri, T1, m);  // A is free now: the new B
@@ -223,6 +253,6 @@ cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s) {
     dyn = smem;
     b.shared_scratch = 1;
   }
-  yun_kernel<<<ntasks, 256, dyn, s>>>(b);
+  yun_kernel<<<ntasks, 32, dyn, s>>>(b);
   return cudaGetLastError();
 }

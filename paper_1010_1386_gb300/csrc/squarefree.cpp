@@ -1,7 +1,7 @@
-// Square-free factorisation of R^{(y)} = res(f, g, y) (the paper's solver,
-// Section 5, PROJECT: R^{(y)} "and a corresponding square-free
-// factorization"): R = c prod_i R_i^i with R_i primitive, square-free,
-// pairwise coprime, leading coefficient > 0.
+// Square-free factorisation of R^{(y)} = res(f, g, y) (the paper's solver
+// computes R^{(y)} together with its square-free factorisation, Section 5,
+// PROJECT): R = c prod_i R_i^i with R_i primitive, square-free, pairwise
+// coprime, leading coefficient > 0.
 //
 // One batch computes R over K primes chosen for the factors' bound (below),
 // and Yun's algorithm mod every prime after G2 (kernels_yun.cu).  A prime is
