@@ -247,11 +247,11 @@ def max_over_ranks(dist, local, value):
     return mor(value, dist, device=f"cuda:{local}")
 
 
-def roofline(info, g1_ms, clk):
+def roofline(info, g1_ms, clk, kernel="G1 (reduce + evaluate + univariate resultant)"):
     sm_max = clk["sm_max_mhz"] or 2070.0
     peak = SM_COUNT * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
     achieved = 4.0 * (info["modmul_eval"] + info["modmul_prs"]) / (g1_ms * 1e-3) / 1e12
-    return {"bound": "alu", "kernel": "G1 (reduce + evaluate + univariate resultant)",
+    return {"bound": "alu", "kernel": kernel,
             "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
             "traffic": None,
             "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
@@ -320,7 +320,8 @@ def batch_main(args, world, rank, local, dist):
     torch.cuda.set_device(local)
     pairs = load_pairs(args.workload, args.pairs, rank, args)
     npairs = len(pairs)
-    ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache)
+    ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache,
+                     univariate=args.univariate)
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     t_tune = time.perf_counter()
     batch = ctx.batch(pairs)  # tunes the G1 launch of every class of the batch first
@@ -356,7 +357,7 @@ def batch_main(args, world, rank, local, dist):
 
     per_inst = None
     if npairs > 1 and not args.no_per_instance:
-        ctx1 = rs.Context(device=local, use_graphs=False, persistent=False)
+        ctx1 = rs.Context(device=local, use_graphs=False, persistent=False, univariate=args.univariate)
         singles = [ctx1.batch([p]) for p in pairs]
         for b in singles:
             b.run()
@@ -397,12 +398,19 @@ def batch_main(args, world, rank, local, dist):
 
     clk = clocks.summary()
     g1 = statistics.mean(stage["images"])
-    rf = roofline(info, g1, clk)
-    if args.workload == "batch" and npairs == 512:
+    if args.univariate == "schur":
+        rf = roofline(info, g1, clk, "G1, Schur variant (reduce + evaluate + Schur on generators + "
+                                     "elimination fallback)")
+    else:
+        rf = roofline(info, g1, clk)
+    if args.workload == "batch" and npairs == 512 and args.univariate == "prs":
         rf["traffic"] = g1_traffic()
     desc = WORKLOADS[args.workload] + ("" if args.pairs is None else f" (first {npairs} pairs)")
     line = base_line(args, world, value, ms, desc,
                      {"pairs_per_gpu": npairs, "images_per_step": info["images"],
+                      "univariate": ("Schur algorithm on displacement generators, one warp per image"
+                                     if args.univariate == "schur" else
+                                     "division-free remainder sequence, one thread per image"),
                       "l2": "256 MiB written before every timed step (outside its events); per-step "
                             "working set (num/den images) %.0f MB" % (info["images"] * 8 / 1e6)})
     line.update({
@@ -596,6 +604,9 @@ def main():
     ap.add_argument("--shift-deg", type=int, default=15, help="shift workload: total degree (9 or 15)")
     ap.add_argument("--shift-k", type=int, default=512, help="shift workload: coefficients times 2^k")
     ap.add_argument("--shift-sparse", action="store_true", help="shift workload: sparse curves")
+    ap.add_argument("--univariate", default="prs", choices=["prs", "schur"],
+                    help="univariate resultants mod p: remainder sequence (default) or the Schur "
+                         "algorithm on displacement generators (comparison variant)")
     ap.add_argument("--autotune-cache", default=None,
                     help="tuner cache file read before and written after the run")
     ap.add_argument("--pairs", type=int, default=None,

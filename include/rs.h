@@ -96,7 +96,10 @@ typedef struct {
   int32_t g2_form;           /* interpolation convolutions: 0 = per pair by a cost model, 1 = direct
                                 (lazily reduced dot products) only, 2 = number-theoretic transforms
                                 wherever D + 1 <= 4096 */
-  int32_t reserved;
+  int32_t univariate;        /* univariate resultants mod p (G1): 0 = division-free remainder
+                                sequence, one thread per image; 1 = the generalised Schur algorithm
+                                on displacement generators of the Sylvester matrix (the paper's
+                                Section 4.1 kernel), one warp per image, for comparison */
   int64_t mem_limit_bytes;   /* serving: device bytes admitted requests may hold; 0 = auto */
   const char *autotune_cache;  /* tuner cache file merged at rs_create (a missing file is not an
                                   error) and rewritten at rs_destroy; NULL = none.  The string

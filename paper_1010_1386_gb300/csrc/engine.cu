@@ -417,8 +417,14 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     const double imgs = (double)p.K * d.NI;
     // per image: half of the evaluation (the two images of a point pair share
     // the even and odd parts) plus one product per coefficient to combine them
-    b->info.modmul_eval += imgs * (0.5 * (p.f.nc + p.g.nc) + (p.f.my + 1) + (p.g.my + 1));
-    b->info.modmul_prs += imgs * 2.0 * prs_updates(p.f.my, p.g.my);
+    if (ctx->cfg.univariate == 1) {  // Schur variant: Horner per coefficient, 4 r (r + 1) products
+      const double r = (double)p.f.my + p.g.my;
+      b->info.modmul_eval += imgs * ((double)(p.f.my + 1) * (p.f.mx + 1) + (double)(p.g.my + 1) * (p.g.mx + 1));
+      b->info.modmul_prs += imgs * 4.0 * r * (r + 1.0);
+    } else {
+      b->info.modmul_eval += imgs * (0.5 * (p.f.nc + p.g.nc) + (p.f.my + 1) + (p.g.my + 1));
+      b->info.modmul_prs += imgs * 2.0 * prs_updates(p.f.my, p.g.my);
+    }
     b->info.modmul_interp += (double)p.K * ((double)d.NI * d.NI / 2 + 8.0 * d.NI);  // two interpolations of NI / 2
     b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
   }
@@ -455,7 +461,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       ch.threads = ctx->cfg.tile_points;
     } else {
       const int64_t key = rs_tune_key(ctx->sms, cap, cmaxN, cimages);
-      if (!rs_tune_find(key, &ch) && opt.tune && ctx->cfg.autotune) {
+      if (!rs_tune_find(key, &ch) && opt.tune && ctx->cfg.autotune && ctx->cfg.univariate == 0) {
         const int rc = rs_tune_g1(ctx, f, g, b->plans, members, key, &ch);
         if (rc != RS_OK) {
           rs_free_batch(b);
@@ -484,6 +490,26 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   }
   std::stable_sort(b->classes.begin(), b->classes.end(),
                    [](const RsClassLaunch &x, const RsClassLaunch &y) { return x.cost > y.cost; });
+  if (ctx->cfg.univariate == 1 && !tiles.empty()) {
+    b->schur = true;
+    b->ntiles_all = (int)tiles.size();
+    int rmax = 0;
+    size_t staged = 0, fb = 0;
+    for (int i : order) {
+      const PairPlan &p = b->plans[i];
+      const int r = p.f.my + p.g.my;
+      rmax = std::max(rmax, r);
+      staged = std::max(staged, (size_t)((p.f.my + 1) * (p.f.mx + 1) + (p.g.my + 1) * (p.g.mx + 1)) * 4);
+      fb = std::max(fb, (size_t)((size_t)r * r + r + r + 2) * 4);
+    }
+    b->schur_slots = std::max(1, (rmax + 31) / 32);
+    b->schur_smem = staged;
+    b->schur_fb_smem = fb;
+    if (b->schur_slots > RS_G1S_MAX_SLOTS || staged > 227 * 1024 || fb > 227 * 1024) {
+      rs_free_batch(b);
+      return rs_fail(ctx, RS_ERR_LIMIT, "Schur variant: m_y + n_y or the staged coefficients exceed its limits");
+    }
+  }
   std::vector<int2> g2, g3;
   std::vector<int> byN(order);
   std::sort(byN.begin(), byN.end(), [&](int x, int y) { return b->plans[x].N > b->plans[y].N; });
@@ -607,7 +633,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->g2smem = (size_t)4 * (maxM + 2 * RS_G2_PAD) * 4;
   b->info.input_bytes = b->in_words * 4;
   b->info.output_bytes = b->out_words * 4;
-  b->info.kernel_launches = (int64_t)b->classes.size() + (int64_t)b->g2cls.size() + (b->ng3d > 0) + (b->nyun > 0) +
+  b->info.kernel_launches = (b->schur ? 2 : (int64_t)b->classes.size()) + (int64_t)b->g2cls.size() + (b->ng3d > 0) +
+                            (b->nyun > 0) +
                             (b->ng3b > 0) +
                             (b->ng3 > 0);
 
@@ -634,7 +661,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                o_st = carve(ST_COUNT * sizeof(unsigned long long)), o_cy = carve(b->cy_words * 8),
                o_g3d = carve(g3d.size() * sizeof(int2)), o_yt = carve(yun.size() * sizeof(int2)),
                o_yo = carve((size_t)b->nyun * b->yun_ostride * 4), o_yw = carve((size_t)b->nyun * 8 * b->yun_wstride * 4),
-               o_g3b = carve(g3b.size() * sizeof(int4));
+               o_g3b = carve(g3b.size() * sizeof(int4)), o_fail = carve(b->schur ? b->img_words * sizeof(int2) : 0);
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
     b->arena = nullptr;
@@ -660,6 +687,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_yun_out = (uint32_t *)(base + o_yo);
   b->d_yun_work = (uint32_t *)(base + o_yw);
   b->d_g3b = (int4 *)(base + o_g3b);
+  b->d_fail = b->schur ? (int2 *)(base + o_fail) : nullptr;
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
     b->h_in = opt.h_in;
@@ -812,8 +840,26 @@ static int enqueue(rs_batch *b, bool capturing) {
   RS_CUDA(ctx, cudaMemsetAsync(b->d_counters, 0, 16 * sizeof(int32_t), s));
   RS_CUDA(ctx, cudaMemsetAsync(b->d_stats, 0, ST_COUNT * sizeof(unsigned long long), s));
   if (timing) RS_CUDA(ctx, record(b->ev[0], s, capturing));
+  if (b->schur) {  // Schur variant of G1 over every tile, then the elimination fallback
+    G1sArgs a;
+    a.pairs = b->d_pairs;
+    a.tiles = b->d_tiles;
+    a.limbs = b->d_in;
+    a.mods = ctx->d_mods;
+    a.vtab = ctx->d_vtab;
+    a.qp = tab.qp;
+    a.tstride = tab.cstride;
+    a.num = b->d_num;
+    a.den = b->d_den;
+    a.fail = b->d_fail;
+    a.fail_count = b->d_counters + 15;
+    a.stats = b->d_stats;
+    RS_CUDA(ctx, launch_g1s(b->schur_slots, b->ntiles_all, b->schur_smem, a, s));
+    RS_CUDA(ctx, launch_g1s_fallback(2 * ctx->sms, b->schur_fb_smem, a, s));
+  }
   int ci = 0;
   for (const auto &cl : b->classes) {
+    if (b->schur) break;
     G1Args a;
     a.pairs = b->d_pairs;
     a.tiles = b->d_tiles + cl.tile_off;
@@ -840,7 +886,7 @@ static int enqueue(rs_batch *b, bool capturing) {
   }
   {
     cudaError_t fe = cudaSuccess;
-    join_all(b, 0, 0, (int)b->classes.size(), s, &fe);
+    if (!b->schur) join_all(b, 0, 0, (int)b->classes.size(), s, &fe);
     RS_CUDA(ctx, fe);
   }
   if (timing) RS_CUDA(ctx, record(b->ev[1], s, capturing));
@@ -1119,6 +1165,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   if (c.tile_points != 0 && c.tile_points != 32 && c.tile_points != 64 && c.tile_points != 128)
     return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
   if (c.g2_form < 0 || c.g2_form > 2) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1 or 2");
+  if (c.univariate < 0 || c.univariate > 1) return rs_fail(nullptr, RS_ERR_ARG, "univariate must be 0 or 1");
   int dev = c.device;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);

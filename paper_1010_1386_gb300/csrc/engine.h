@@ -125,6 +125,12 @@ struct rs_batch {
   std::vector<int64_t> in_f, in_g;  // word offsets of each pair's inputs in the staging buffer
   std::vector<RsClassLaunch> classes;
   std::vector<RsG2Class> g2cls;
+  // Schur variant of G1 (rs_config.univariate = 1): one launch over every
+  // tile, then the elimination fallback over the listed images.
+  bool schur = false;
+  int schur_slots = 0, ntiles_all = 0;
+  size_t schur_smem = 0, schur_fb_smem = 0;
+  int2 *d_fail = nullptr;
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int64_t shape_off = 0;  // word offset of the per-pair result shapes in the output buffer
   int ng2 = 0, ng3 = 0, g2_threads = 256;

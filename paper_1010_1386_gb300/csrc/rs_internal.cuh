@@ -68,6 +68,25 @@ struct G1Args {
   unsigned long long *stats;
 };
 
+// Schur variant of G1 (kernels_schur.cu): the same tiles, points and image
+// layout; images whose recurrence meets a zero pivot are listed as (tile,
+// image within the tile) for the elimination fallback.
+struct G1sArgs {
+  const PairDesc *pairs;
+  const Tile *tiles;
+  const uint32_t *limbs;
+  const ModP *mods;
+  const uint32_t *vtab;
+  const uint32_t *qp;      // [prime][tstride] q^t (Montgomery)
+  int32_t tstride;
+  uint32_t *num, *den;
+  int2 *fail;              // capacity: every image of the batch
+  int32_t *fail_count;     // zeroed before the launch
+  unsigned long long *stats;
+};
+
+#define RS_G1S_MAX_SLOTS 5  // Schur variant: m_y + n_y <= 32 x this
+
 struct G2Args {
   const PairDesc *pairs;
   const int2 *tasks;       // (pair, prime)
@@ -155,6 +174,11 @@ cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int 
 // CRT digits by tiles of 32 coefficients (tasks step by 32), any prime count.
 cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s);
 cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s);
+// Schur variant of G1: one block per tile, `slots` = ceil((m_y + n_y) / 32)
+// over the batch, smem = staged residues of the largest pair; then the
+// elimination fallback over the listed images (grid-stride).
+cudaError_t launch_g1s(int slots, int ntiles, size_t smem, const G1sArgs &a, cudaStream_t s);
+cudaError_t launch_g1s_fallback(int blocks, size_t smem, const G1sArgs &a, cudaStream_t s);
 cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
 cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,

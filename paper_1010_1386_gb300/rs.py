@@ -38,7 +38,7 @@ class rs_upoly(ctypes.Structure):
 class rs_config(ctypes.Structure):
     _fields_ = [("device", c_int32), ("tile_points", c_int32), ("use_graphs", c_int32),
                 ("persistent", c_int32), ("timing", c_int32), ("autotune", c_int32),
-                ("g2_form", c_int32), ("reserved", c_int32),
+                ("g2_form", c_int32), ("univariate", c_int32),
                 ("mem_limit_bytes", c_int64), ("autotune_cache", c_char_p)]
 
 
@@ -223,7 +223,10 @@ class Context:
     """One librs context (device memory, stream, prime tables) on one GPU."""
 
     def __init__(self, device=-1, tile_points=0, use_graphs=True, persistent=True, timing=False,
-                 mem_limit_bytes=0, autotune=True, autotune_cache=None, g2_form=0):
+                 mem_limit_bytes=0, autotune=True, autotune_cache=None, g2_form=0, univariate="prs"):
+        """univariate: "prs" (division-free remainder sequence, one thread per
+        image) or "schur" (Schur algorithm on displacement generators, one
+        warp per image)."""
         lib = load()
         cfg = rs_config()
         _check(lib.rs_config_default(ctypes.byref(cfg)))
@@ -232,6 +235,9 @@ class Context:
         cfg.mem_limit_bytes = mem_limit_bytes
         cfg.autotune = int(autotune)
         cfg.g2_form = int(g2_form)
+        if univariate not in ("prs", "schur"):
+            raise ValueError("univariate must be 'prs' or 'schur'")
+        cfg.univariate = 1 if univariate == "schur" else 0
         cfg.autotune_cache = os.fsencode(autotune_cache) if autotune_cache else None
         h = c_void_p()
         _check(lib.rs_create(ctypes.byref(h), ctypes.byref(cfg)))
