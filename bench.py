@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "resultants/s batched vs per-instance launch, same GB300; % of INT32 IMAD peak"
+INTERP = {"auto": 0, "direct": 1, "transforms": 2, "triangular": 3}
 SQF_METRIC = "square-free factorisations of Res_y(f, g) per second (R = c prod R_i^i), one GB300"
 SM_COUNT = 152
 IMAD_PER_SM_CLK = 64  # 32-bit integer multiply-add results per clock per SM
@@ -321,7 +322,7 @@ def batch_main(args, world, rank, local, dist):
     pairs = load_pairs(args.workload, args.pairs, rank, args)
     npairs = len(pairs)
     ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache,
-                     univariate=args.univariate)
+                     univariate=args.univariate, g2_form=INTERP[args.interp])
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     t_tune = time.perf_counter()
     batch = ctx.batch(pairs)  # tunes the G1 launch of every class of the batch first
@@ -357,7 +358,8 @@ def batch_main(args, world, rank, local, dist):
 
     per_inst = None
     if npairs > 1 and not args.no_per_instance:
-        ctx1 = rs.Context(device=local, use_graphs=False, persistent=False, univariate=args.univariate)
+        ctx1 = rs.Context(device=local, use_graphs=False, persistent=False, univariate=args.univariate,
+                          g2_form=INTERP[args.interp])
         singles = [ctx1.batch([p]) for p in pairs]
         for b in singles:
             b.run()
@@ -411,6 +413,10 @@ def batch_main(args, world, rank, local, dist):
                       "univariate": ("Schur algorithm on displacement generators, one warp per image"
                                      if args.univariate == "schur" else
                                      "division-free remainder sequence, one thread per image"),
+                      "interpolation": {"auto": "convolutions (direct or transforms per pair)",
+                                        "direct": "direct convolutions", "transforms": "transforms",
+                                        "triangular": "triangular factorisation of the Vandermonde "
+                                                      "system (Bjorck-Pereyra stages)"}[args.interp],
                       "l2": "256 MiB written before every timed step (outside its events); per-step "
                             "working set (num/den images) %.0f MB" % (info["images"] * 8 / 1e6)})
     line.update({
@@ -607,6 +613,9 @@ def main():
     ap.add_argument("--univariate", default="prs", choices=["prs", "schur"],
                     help="univariate resultants mod p: remainder sequence (default) or the Schur "
                          "algorithm on displacement generators (comparison variant)")
+    ap.add_argument("--interp", default="auto", choices=sorted(INTERP),
+                    help="interpolation form: convolutions chosen per pair (auto), direct, transforms, "
+                         "or the triangular factorisation of the Vandermonde system (comparison)")
     ap.add_argument("--autotune-cache", default=None,
                     help="tuner cache file read before and written after the run")
     ap.add_argument("--pairs", type=int, default=None,

@@ -93,9 +93,11 @@ typedef struct {
   int32_t autotune;          /* 1 = a batch whose workload class is not in the tuner cache times
                                 the G1 candidates first; 0 = cached choices or the built-in
                                 default (128 points, persistent) */
-  int32_t g2_form;           /* interpolation convolutions: 0 = per pair by a cost model, 1 = direct
-                                (lazily reduced dot products) only, 2 = number-theoretic transforms
-                                wherever D + 1 <= 4096 */
+  int32_t g2_form;           /* interpolation: 0 = convolutions, per pair by a cost model, 1 = direct
+                                convolutions (lazily reduced dot products) only, 2 = number-theoretic
+                                transforms wherever D + 1 <= 4096, 3 = triangular factorisation of the
+                                Vandermonde system (the paper's Section 4.1 solve; comparison form,
+                                D + 1 <= 14,000) */
   int32_t univariate;        /* univariate resultants mod p (G1): 0 = division-free remainder
                                 sequence, one thread per image; 1 = the generalised Schur algorithm
                                 on displacement generators of the Sylvester matrix (the paper's

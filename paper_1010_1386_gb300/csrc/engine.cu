@@ -524,7 +524,25 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // allowed; groups with lg < 9 keep the model's choice), else the model.
   std::vector<int> g2lg(n, 0);
   int bhatK[RS_NTT_LGMAX + 1] = {};
-  if (!images_only) {
+  const bool g2tri = ctx->cfg.g2_form == 3;  // triangular factorisation of the Vandermonde system
+  if (g2tri && !images_only && !order.empty()) {
+    RsG2Class gc;
+    gc.lg = -1;
+    gc.off = (int64_t)g2.size();
+    int cmaxN = 0;
+    for (int i : byN) {
+      cmaxN = std::max(cmaxN, b->plans[i].N);
+      for (int k = 0; k < b->plans[i].K; ++k) g2.push_back(make_int2(b->dev_index[i], k));
+    }
+    gc.count = (int)((int64_t)g2.size() - gc.off);
+    gc.smem = (size_t)(4 * cmaxN + 97) * 4;
+    if (gc.smem > 227 * 1024) {
+      rs_free_batch(b);
+      return rs_fail(ctx, RS_ERR_LIMIT, "g2_form 3: D + 1 above the shared-memory limit of the form (14,000)");
+    }
+    b->g2cls.push_back(gc);
+  }
+  if (!images_only && !g2tri) {
     std::vector<std::vector<int>> bylg(RS_NTT_LGMAX + 1);
     for (int i : byN) {
       const int lg = rs_g2_len((b->plans[i].N + 1) / 2);
@@ -582,7 +600,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     b->g2cls.push_back(gc);
   }
   const int nlg = (int)b->g2cls.size();
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < 8 && !g2tri; ++c) {
     RsG2Class gc;
     gc.threads = 32 * (c + 1);
     gc.off = (int64_t)g2.size();
@@ -897,6 +915,26 @@ static int enqueue(rs_batch *b, bool capturing) {
   }
   int gi = 0;
   for (const auto &gc : b->g2cls) {
+    if (gc.lg < 0) {
+      G2sArgs as;
+      as.pairs = b->d_pairs;
+      as.tasks = b->d_g2 + gc.off;
+      as.mods = ctx->d_mods;
+      as.num = b->d_num;
+      as.den = b->d_den;
+      as.coef = b->d_num;
+      as.qp = tab.qp;
+      as.tstride = tab.cstride;
+      const int j = (int)b->classes.size() + gi;
+      cudaError_t fe = cudaSuccess;
+      cudaStream_t si = branch_begin(b, 1, gi, s, &fe);
+      RS_CUDA(ctx, fe);
+      RS_CUDA(ctx, launch_g2s(gc.count, gc.smem, as, si));
+      branch_end(b, 1, j, si, &fe);
+      RS_CUDA(ctx, fe);
+      ++gi;
+      continue;
+    }
     if (gc.lg > 0) {
       G2nArgs an;
       an.pairs = b->d_pairs;
@@ -1164,7 +1202,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
     rs_config_default(&c);
   if (c.tile_points != 0 && c.tile_points != 32 && c.tile_points != 64 && c.tile_points != 128)
     return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
-  if (c.g2_form < 0 || c.g2_form > 2) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1 or 2");
+  if (c.g2_form < 0 || c.g2_form > 3) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1, 2 or 3");
   if (c.univariate < 0 || c.univariate > 1) return rs_fail(nullptr, RS_ERR_ARG, "univariate must be 0 or 1");
   int dev = c.device;
   int ndev = 0;

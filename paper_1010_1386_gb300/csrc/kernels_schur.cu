@@ -25,6 +25,7 @@
 // point where lc_y f vanishes) stops the recurrence: the image goes to a list
 // that a second kernel finishes by Gaussian elimination with row pivoting on
 // the Sylvester matrix, so every image is exact.
+#include "blockinv.cuh"
 #include "rs_internal.cuh"
 
 namespace {
@@ -249,7 +250,87 @@ __global__ void __launch_bounds__(256) g1s_fallback_kernel(G1sArgs a) {
   }
 }
 
+// Interpolation (a5) by the triangular factorisation of the Vandermonde
+// system V c = z, V[j][i] = x_j^i (the paper solves it with the Schur
+// algorithm, exploiting its structure; this is the comparison variant of
+// G2).  The displacement V - D V Z^T (D = diag x_j) has rank one, and its
+// Schur recursion yields V's triangular factors; applying their inverses as
+// bidiagonal stages is the method of A. Bjorck and V. Pereyra ("Solution of
+// Vandermonde systems of equations", Math. Comp. 24, 1970):
+//   stage 1 (divided differences): for k = 0 .. N-2, for j > k:
+//     c_j <- (c_j - c_{j-1}) / (x_j - x_{j-k-1});
+//   stage 2 (Newton to monomial):  for k = N-2 .. 0, for k <= j < N-1:
+//     c_j <- c_j - x_k c_{j+1}.
+// Each stage is one parallel step over j (O(N) parallel time, O(N^2) work).
+// Stage 1 runs on fractions (numerator, denominator), starting from G1's
+// num/den images, so no division is taken until one simultaneous inversion
+// of the N denominators between the stages.  Thread t owns the contiguous
+// indices [t E, t E + E); it walks them downward in stage 1 and upward in
+// stage 2, reading the one old value it needs from a neighbour's range
+// before the stage's barrier.  Points: the first N images, x_j =
+// (-1)^j q^{floor(j/2)}.
+__global__ void __launch_bounds__(256) g2s_kernel(G2sArgs a) {
+  extern __shared__ __align__(16) uint32_t sv[];
+  const int2 task = a.tasks[blockIdx.x];
+  const PairDesc pd = a.pairs[task.x];
+  const ModP m = a.mods[task.y];
+  const int N = pd.N, T = (int)blockDim.x, tid = (int)threadIdx.x;
+  uint32_t *A = sv, *Bd = sv + N, *X = sv + 2 * N, *Inv = sv + 3 * N, *scratch = sv + 4 * N;
+  const size_t base = (size_t)pd.img_off + (size_t)task.y * pd.NI;
+  const uint32_t *qp = a.qp + (size_t)task.y * a.tstride;
+  for (int j = tid; j < N; j += T) {
+    A[j] = a.num[base + j];
+    Bd[j] = a.den[base + j];
+    const uint32_t q = qp[j >> 1];
+    X[j] = (j & 1) ? mneg(q, m.p) : q;
+  }
+  __syncthreads();
+  const int E = (N + T - 1) / T;
+  const int beg = min(tid * E, N), end = min(beg + E, N);
+  for (int k = 0; k + 1 < N; ++k) {
+    const int lo = max(beg, k + 1);
+    uint32_t pa = 0u, pb = 0u;
+    if (lo < end) {
+      pa = A[lo - 1];
+      pb = Bd[lo - 1];
+    }
+    __syncthreads();
+    for (int j = end - 1; j >= lo; --j) {
+      const uint32_t aj = A[j], bj = Bd[j];
+      const uint32_t am = j > lo ? A[j - 1] : pa, bm = j > lo ? Bd[j - 1] : pb;
+      const uint32_t e = msub(X[j], X[j - k - 1], m.p);
+      A[j] = mmul2(aj, bm, mneg(am, m.p), bj, m);
+      Bd[j] = mmul(mmul(bj, bm, m), e, m);
+    }
+    __syncthreads();
+  }
+  batch_invert(Bd, Inv, N, m, scratch);
+  __syncthreads();
+  for (int j = tid; j < N; j += T) A[j] = mmul(A[j], Inv[j], m);
+  __syncthreads();
+  for (int k = N - 2; k >= 0; --k) {
+    const int lo = max(beg, k), hi = min(end, N - 1);
+    const uint32_t nx = lo < hi ? A[hi] : 0u;
+    __syncthreads();
+    const uint32_t xk = X[k];
+    for (int j = lo; j < hi; ++j) {
+      const uint32_t cn = j + 1 < hi ? A[j + 1] : nx;
+      A[j] = msub(A[j], mmul(xk, cn, m), m.p);
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < N; j += T) a.coef[base + j] = from_mont(A[j], m);
+}
+
 }  // namespace
+
+cudaError_t launch_g2s(int ntasks, size_t smem, const G2sArgs &a, cudaStream_t s) {
+  if (!ntasks) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(g2s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  g2s_kernel<<<ntasks, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_g1s(int slots, int ntiles, size_t smem, const G1sArgs &a, cudaStream_t s) {
   if (!ntiles) return cudaSuccess;

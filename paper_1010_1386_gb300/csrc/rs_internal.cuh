@@ -87,6 +87,18 @@ struct G1sArgs {
 
 #define RS_G1S_MAX_SLOTS 5  // Schur variant: m_y + n_y <= 32 x this
 
+// Triangular-factorisation variant of G2 (kernels_schur.cu): one block per
+// (pair, prime), shared memory 4 N + 97 words.
+struct G2sArgs {
+  const PairDesc *pairs;
+  const int2 *tasks;       // (pair, prime)
+  const ModP *mods;
+  const uint32_t *num, *den;
+  uint32_t *coef;          // out: R mod p (plain), may alias num
+  const uint32_t *qp;      // [prime][tstride] q^t (Montgomery)
+  int32_t tstride;
+};
+
 struct G2Args {
   const PairDesc *pairs;
   const int2 *tasks;       // (pair, prime)
@@ -179,6 +191,7 @@ cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s);
 // elimination fallback over the listed images (grid-stride).
 cudaError_t launch_g1s(int slots, int ntiles, size_t smem, const G1sArgs &a, cudaStream_t s);
 cudaError_t launch_g1s_fallback(int blocks, size_t smem, const G1sArgs &a, cudaStream_t s);
+cudaError_t launch_g2s(int ntasks, size_t smem, const G2sArgs &a, cudaStream_t s);
 cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
 cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,

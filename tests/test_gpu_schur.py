@@ -1,8 +1,10 @@
-"""The Schur variant of the univariate resultants (rs_config.univariate = 1:
-the generalised Schur algorithm on displacement generators of the Sylvester
-matrix, one warp per image, elimination fallback on zero pivots) against the
-oracle and against the remainder-sequence path: every image and every
-resultant must agree bit for bit."""
+"""The paper's own structured solvers, built as comparison variants: the
+Schur variant of the univariate resultants (rs_config.univariate = 1: the
+generalised Schur algorithm on displacement generators of the Sylvester
+matrix, one warp per image, elimination fallback on zero pivots) and the
+interpolation by the triangular factorisation of the Vandermonde system
+(rs_config.g2_form = 3), against the oracle and against the default path:
+every image and every resultant must agree bit for bit."""
 import random
 
 import pytest
@@ -134,3 +136,43 @@ def test_largest_generators(schur, prs):
         f = rand_bipoly(rng, 1, dy_f, bits=12)
         g = rand_bipoly(rng, 1, dy_g, bits=12)
         assert schur.resultant_y(f, g) == prs.resultant_y(f, g)
+
+
+# ---------------------------------------- interpolation by triangular factorisation
+
+@pytest.fixture(scope="module")
+def tri():
+    c = rs.Context(device=0, timing=True, g2_form=3)
+    yield c
+    c.close()
+
+
+def test_triangular_interpolation_exact(tri):
+    rng = random.Random(38)
+    pairs = []
+    for _ in range(30):
+        f = rand_bipoly(rng, rng.randint(0, 5), rng.randint(0, 6), bits=rng.choice([4, 30, 70]))
+        g = rand_bipoly(rng, rng.randint(0, 5), rng.randint(0, 6), bits=rng.choice([4, 30, 70]))
+        pairs.append((f, g))
+    for (f, g), R in zip(pairs, tri.resultant_batch(pairs)):
+        assert R == exact.resultant_y(f, g)
+    from tests.test_oracle_pins import GOLDEN, load_golden
+    for path in GOLDEN:
+        f, g, R = load_golden(path)
+        assert tri.resultant_y(f, g) == R
+
+
+def test_triangular_interpolation_full_size(tri, prs):
+    [(f, g)] = inputs.workload_single(1)  # D + 1 = 901 points, 76 primes
+    assert tri.resultant_y(f, g) == prs.resultant_y(f, g)
+    pairs = inputs.workload_batch(2, n=512)[:24]
+    assert tri.resultant_batch(pairs) == prs.resultant_batch(pairs)
+
+
+def test_paper_design_end_to_end(prs):
+    """Both of the paper's structured solvers at once: Schur on the
+    generators for the images and the triangular factorisation for the
+    interpolation."""
+    pairs = inputs.workload_batch(2, n=512)[:12] + inputs.workload_small(0)
+    with rs.Context(device=0, univariate="schur", g2_form=3) as c:
+        assert c.resultant_batch(pairs) == prs.resultant_batch(pairs)
