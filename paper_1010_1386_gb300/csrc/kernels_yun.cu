@@ -11,9 +11,9 @@
 // coefficient.  Each step is spread over the warp's lanes; a remainder step
 // reads the new leading coefficient once (it is non-zero unless p divides it,
 // and only then is the polynomial scanned for its degree), so a step costs one
-// warp barrier.  The polynomials live in global scratch, except the two that
-// every remainder and division step rewrites (the gcd operands and the
-// division remainder), which live in shared memory when they fit.
+// warp barrier.  The polynomials live in global scratch, except two buffers
+// in shared memory (when they fit) that hold what every pass touches: the
+// gcd operands, then the division remainder and the divisor.
 //
 // Output per task (word offsets from out + task * ostride):
 //   [0]            degree of R mod p (-1 if R = 0 mod p)
@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(32) yun_kernel(YunArgs a) {
   copy_poly(T1, F);
   copy_poly(T2, Fd);
   gcd_monic(A, T1, T2, m);       // A = gcd(F, F')
-  divexact(B, F, A, T1, m);      // B = F / A
-  divexact(C, Fd, A, T1, m);     // C = F' / A
+  copy_poly(T2, A);              // the divisor, read by every division pass
+  divexact(B, F, T2, T1, m);     // B = F / A
+  divexact(C, Fd, T2, T1, m);    // C = F' / A
   derivative(T2, B, m);
   copy_poly(D, C);
   sub_in_place(D, T2, m);        // D = C - B'
@@ -229,8 +230,9 @@ __global__ void __launch_bounds__(32) yun_kernel(YunArgs a) {
     if (lane_id() == 0) o[1 + i] = (uint32_t)Ri.deg;
     dst += Ri.deg + 1;
     // B = B / R_i, C = D / R_i, D = C - B'
-    divexact(A, B, Ri, T1, m);  // A is free now: the new B
-    divexact(C, D, Ri, T1, m);
+    copy_poly(T2, Ri);          // the divisor, read by every division pass
+    divexact(A, B, T2, T1, m);  // A is free now: the new B
+    divexact(C, D, T2, T1, m);
     copy_poly(B, A);
     derivative(T2, B, m);
     copy_poly(D, C);

@@ -59,6 +59,7 @@ struct RsServer {
   int64_t mem_limit = 0, mem_used = 0;
   int max_inflight = 4, max_batch = 256;
   int min_batch = 32;                                  // launch early once this many wait
+  int64_t max_images = int64_t(1) << 22;               // images per micro-batch (about 5 ms of G1)
   std::chrono::microseconds max_wait{1000};            // or once the oldest waited this long
   std::vector<cudaStream_t> streams;
   std::vector<uint32_t *> h_in, h_out;
@@ -121,9 +122,13 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
     }
   if (slot < 0 || s->pending.empty()) return;
   std::vector<Request *> take;
-  int64_t bytes = 0;
+  int64_t bytes = 0, images = 0;
   while (!s->pending.empty() && (int)take.size() < s->max_batch) {
     Request *r = s->pending.front();
+    // a micro-batch holds at most max_images images (K N), so that one large
+    // request does not hold up many small ones behind it
+    const int64_t im = (int64_t)r->plan.K * r->plan.N;
+    if (!take.empty() && images + im > s->max_images) break;
     if (r->footprint > s->mem_limit) {  // can never fit: fail it
       s->pending.pop_front();
       r->status = RS_ERR_NOMEM;
@@ -135,6 +140,7 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
     }
     if (s->mem_used + bytes + r->footprint > s->mem_limit) break;
     bytes += r->footprint;
+    images += im;
     take.push_back(r);
     s->pending.pop_front();
   }
