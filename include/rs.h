@@ -359,6 +359,14 @@ int rs_server_poll(rs_ctx *ctx, uint64_t ticket, rs_upoly *out, double *latency_
 int rs_server_wait(rs_ctx *ctx, uint64_t ticket, rs_upoly *out, double *latency_ms,
                    int64_t timeout_us);
 int rs_server_stats_get(rs_ctx *ctx, rs_server_stats *stats);
+/* Per-request log of the running server: from now on every finished request
+ * appends one JSON line to the file at path (created or truncated) —
+ * {"ticket", "status", "submit_us", "admit_us" (-1 if never admitted),
+ * "done_us" (microseconds since the server started), "K" (primes), "D"
+ * (degree bound), "footprint" (device bytes), "deg", "limbs"}.  NULL closes
+ * the log; rs_server_stop closes it too.  RS_ERR_STATE without a server,
+ * RS_ERR_ARG if the file cannot be opened. */
+int rs_server_set_log(rs_ctx *ctx, const char *path);
 /* Finish every admitted and pending request, then stop the scheduler
  * thread and release its streams (results not yet polled are dropped). */
 int rs_server_stop(rs_ctx *ctx);

@@ -9,6 +9,7 @@
 // others run is admitted as soon as a stream slot and memory are free, so the
 // device never waits for a whole "epoch" to drain.  Results stay on the
 // device until their micro-batch finishes, then are copied back once.
+#include <stdio.h>
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -34,7 +35,8 @@ struct Request {
   int status = RS_OK;
   std::vector<uint32_t> words;
   int deg = -1, limbs = 1;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_done;
+  bool admitted = false;
 };
 
 struct Flight {
@@ -67,6 +69,8 @@ struct RsServer {
   std::vector<bool> slot_busy;
   std::vector<Flight> flights;
   rs_server_stats st;
+  FILE *log = nullptr;  // one JSON line per finished request (rs_server_set_log)
+  Clock::time_point t0 = Clock::now();
 };
 
 namespace {
@@ -80,6 +84,20 @@ int grow_pinned(uint32_t *&buf, int64_t &have, int64_t need) {
   if (cudaMallocHost((void **)&buf, words * 4) != cudaSuccess) return RS_ERR_NOMEM;
   have = words;
   return RS_OK;
+}
+
+// Called with the lock held when a request is done: its JSON line, times in
+// microseconds since the server started (admit_us -1: never admitted).
+void log_request(RsServer *s, const Request *r) {
+  if (!s->log) return;
+  auto us = [&](Clock::time_point t) {
+    return (long long)std::chrono::duration_cast<std::chrono::microseconds>(t - s->t0).count();
+  };
+  fprintf(s->log,
+          "{\"ticket\": %llu, \"status\": %d, \"submit_us\": %lld, \"admit_us\": %lld, \"done_us\": %lld, "
+          "\"K\": %d, \"D\": %d, \"footprint\": %lld, \"deg\": %d, \"limbs\": %d}\n",
+          (unsigned long long)r->ticket, r->status, us(r->t_submit), r->admitted ? us(r->t_admit) : -1LL,
+          us(r->t_done), r->plan.K, r->plan.D, (long long)r->footprint, r->deg, r->limbs);
 }
 
 // Called with the lock held: finish flights whose event has completed.
@@ -98,6 +116,7 @@ void reap(RsServer *s) {
                                      : RS_ERR_CUDA;
       req->state = REQ_DONE;
       req->t_done = now;
+      log_request(s, req);
       if (req->status == RS_OK)
         s->st.completed++;
       else
@@ -134,6 +153,7 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
       r->status = RS_ERR_NOMEM;
       r->state = REQ_DONE;
       r->t_done = Clock::now();
+      log_request(s, r);
       s->st.failed++;
       s->cv_done.notify_all();
       continue;
@@ -147,7 +167,12 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
   if (take.empty()) return;
   s->slot_busy[slot] = true;
   s->mem_used += bytes;
-  for (Request *r : take) r->state = REQ_RUNNING;
+  const auto t_admit = Clock::now();
+  for (Request *r : take) {
+    r->state = REQ_RUNNING;
+    r->t_admit = t_admit;
+    r->admitted = true;
+  }
   lk.unlock();
 
   const int n = (int)take.size();
@@ -193,6 +218,7 @@ void launch(RsServer *s, std::unique_lock<std::mutex> &lk) {
       r->status = rc;
       r->state = REQ_DONE;
       r->t_done = Clock::now();
+      log_request(s, r);
       s->st.failed++;
     }
     s->mem_used -= bytes;
@@ -318,6 +344,7 @@ void rs_server_shutdown(rs_ctx *ctx) {
   for (auto p : s->h_out)
     if (p) cudaFreeHost(p);
   for (auto &kv : s->reqs) delete kv.second;
+  if (s->log) fclose(s->log);
   delete s;
   ctx->server = nullptr;
 }
@@ -405,6 +432,18 @@ int rs_server_stats_get(rs_ctx *ctx, rs_server_stats *out) {
   out->mem_used = s->mem_used;
   out->running = 0;
   for (auto &f : s->flights) out->running += (int64_t)f.reqs.size();
+  return RS_OK;
+}
+
+int rs_server_set_log(rs_ctx *ctx, const char *path) {
+  if (!ctx) return rs_fail(ctx, RS_ERR_ARG, "NULL argument");
+  RsServer *s = ctx->server;
+  if (!s) return rs_fail(ctx, RS_ERR_STATE, "no server running");
+  FILE *f = nullptr;
+  if (path && !(f = fopen(path, "w"))) return rs_fail(ctx, RS_ERR_ARG, std::string("cannot open ") + path);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->log) fclose(s->log);
+  s->log = f;
   return RS_OK;
 }
 

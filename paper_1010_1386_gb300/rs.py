@@ -100,6 +100,7 @@ _SIGS = {
     "rs_server_wait": (c_int32, [c_void_p, ctypes.c_uint64, _P(rs_upoly), _P(c_double), c_int64]),
     "rs_server_stats_get": (c_int32, [c_void_p, _P(rs_server_stats)]),
     "rs_server_stop": (c_int32, [c_void_p]),
+    "rs_server_set_log": (c_int32, [c_void_p, c_char_p]),
     "rs_resultant_x": (c_int32, [c_void_p, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly)]),
     "rs_projections": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), _P(rs_upoly),
                                  _P(rs_upoly), _P(c_int32)]),
@@ -482,6 +483,10 @@ class Server:
     def __init__(self, ctx, max_inflight=0, max_batch=0, mem_limit_bytes=0):
         self.ctx, self.lib = ctx, ctx.lib
         _check(self.lib.rs_server_start(ctx.h, max_inflight, max_batch, mem_limit_bytes), ctx.h)
+
+    def set_log(self, path):
+        """Append one JSON line per finished request to path (None: stop)."""
+        _check(self.lib.rs_server_set_log(self.ctx.h, os.fsencode(path) if path else None), self.ctx.h)
 
     def submit(self, f, g):
         P = _Polys([f, g])

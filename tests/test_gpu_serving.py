@@ -11,7 +11,7 @@ import pytest
 
 from oracle import exact
 from paper_1010_1386_gb300 import inputs, rs
-from tests.helpers import check_sampled_31, exact_points
+from tests.helpers import check_sampled_31, exact_points, rand_bipoly
 
 pytestmark = pytest.mark.gpu
 
@@ -141,3 +141,26 @@ def test_serving_workload_sample_through_the_server():
         check_sampled_31(F, G, R, rng, samples=1)
         if i in small:
             exact_points(F, G, R, points=(0,))
+
+
+def test_request_log(tmp_path):
+    """rs_server_set_log: one JSON line per finished request, with ordered
+    times and the planner's K and D."""
+    import json
+    rng = random.Random(61)
+    pairs = [(rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 4), bits=30),
+              rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 4), bits=30)) for _ in range(20)]
+    path = tmp_path / "requests.jsonl"
+    with rs.Context(device=0) as c:
+        srv = rs.Server(c)
+        srv.set_log(str(path))
+        tickets = [srv.submit(f, g) for f, g in pairs]
+        for t in tickets:
+            srv.wait(t)
+        srv.stop()
+    recs = {r["ticket"]: r for r in map(json.loads, path.read_text().splitlines())}
+    assert sorted(recs) == sorted(tickets)
+    for t, (f, g) in zip(tickets, pairs):
+        r, b = recs[t], rs.result_bound(f, g)
+        assert r["status"] == 0 and 0 <= r["submit_us"] <= r["admit_us"] <= r["done_us"]
+        assert (r["K"], r["D"]) == (b["primes"], b["deg"]) and r["footprint"] > 0

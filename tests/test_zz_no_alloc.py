@@ -62,3 +62,36 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     assert lib.rs_crt_noalloc(ctypes.c_void_p(256), 4096, 10, 1, ctypes.c_void_p(256), None) == -6
     assert lib.rs_crt_noalloc(ctypes.c_void_p(256), 100, 30000, 100, ctypes.c_void_p(256), None) == -6
     assert lib.rs_crt_noalloc(None, 1, 1, 1, None, None) == -1
+
+
+def test_noalloc_crt_random_residues_vs_python():
+    """The CRT kernels on arbitrary residues (not images of a resultant):
+    the output is the unique integer in the symmetric range (-P/2, P/2)
+    congruent to every residue, P the product of the first K table primes;
+    residues 0, p - 1 and (p +- 1)/2 included, K from 1 to 1000."""
+    torch = pytest.importorskip("torch")
+    lib = rs.load()
+    ctx = rs.Context(device=0)
+    rng = random.Random(32)
+    table, _, _ = ctx.images([[0, 1]], [[1, 1], [1]], 1000, 1)
+    table = [int(p) for p in table]
+    for K, N in [(1, 5), (2, 9), (7, 33), (64, 40), (65, 17), (200, 64), (1000, 6)]:
+        primes = table[:K]
+        P = 1
+        for p in primes:
+            P *= p
+        L = (P.bit_length() + 1 + 31) // 32
+        res = np.zeros((K, N), dtype=np.uint32)
+        for j in range(N):
+            for k, p in enumerate(primes):
+                res[k, j] = rng.choice([0, p - 1, (p - 1) // 2, (p + 1) // 2, rng.randrange(p)])
+        got = _run_noalloc(lib, torch, res, L)
+        for j in range(N):
+            x = 0
+            for k, p in enumerate(primes):  # Garner-free CRT by the explicit formula
+                Pk = P // p
+                x = (x + int(res[k, j]) * Pk * pow(Pk, -1, p)) % P
+            if x > P // 2:
+                x -= P
+            assert got[j] == x, (K, j)
+    ctx.close()
