@@ -621,13 +621,20 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   }
   // CRT digits in tiles of 32 coefficients; limbs in blocks of 128
   // coefficients by chunks of 16 output limbs.
+  // Digit tiles hold 32 coefficients, or 16 when 32-wide tiles would be
+  // fewer than two per SM (few coefficients with many primes each).
   std::vector<int2> g3d;
   std::vector<int4> g3b;  // CRT limb chunks: 128 coefficients x one chunk per block
+  {
+    int64_t nt32 = 0;
+    for (int i : order) nt32 += (b->plans[i].N + 31) / 32;
+    b->g3_jt = nt32 < 2 * (int64_t)ctx->sms ? 16 : 32;
+  }
   for (int i : order) {
     const PairPlan &p = b->plans[i];
     const int di = b->dev_index[i], chunks = (p.Lout + 15) / 16;
     for (int j = 0; j < p.N; j += 128) g3.push_back(make_int2(di, j));
-    for (int j = 0; j < p.N; j += 32) g3d.push_back(make_int2(di, j));  // digit tiles of 32 coefficients
+    for (int j = 0; j < p.N; j += b->g3_jt) g3d.push_back(make_int2(di, j));  // digit tiles
     for (int c = 0; c < chunks; ++c)
       for (int j = 0; j < p.N; j += 128) g3b.push_back(make_int4(di, j, c, 0));
   }
@@ -1020,7 +1027,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.shape = reinterpret_cast<int32_t *>(b->d_out + b->shape_off);
     RS_CUDA(ctx, cudaMemsetAsync(a3.shape, 0, b->descs.size() * 2 * sizeof(int32_t), s));
     a3.kmax = b->kmax;
-    RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s));
+    RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
     RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));

@@ -31,34 +31,36 @@ __device__ __forceinline__ uint32_t finish64_3(int64_t s, const ModP &m) {
   return redc((uint64_t)(s + ((int64_t)m.p << 22)), m.p, m.pinv);  // 0 <= . < 2^54 < p 2^32
 }
 
-#define G3T_JT 32  // coefficients per tile
 #define G3T_BK 64  // digits per digit block
 #define G3T_LC 32  // earlier digits per staged chunk
 
-// Digits by tiles: a block of 256 threads owns 32 consecutive coefficients
-// of one pair and produces their digits 64 at a time.  For the digit block
+// Digits by tiles: a block of 256 threads owns JT (32, or 16 when there are
+// few coefficients to spread over the SMs) consecutive coefficients of one
+// pair and produces their digits 64 at a time.  For the digit block
 // [k0, k0 + 64) the contribution of every earlier digit,
 //   A[k][j] = sum_{l < k0} W[k][l] v_l(j),
 // is the product of a 64 x k0 slice of W and a k0 x 32 slice of digits:
 // chunks of both are staged in shared memory and each thread accumulates a
-// 4 x 2 block lazily in int64 (a fold with its row's 2^32 mod p_k every 7
-// products).  The 64 digits of the block then follow one by one (one warp,
-// lane = coefficient) from the triangle of W inside the block, with the
+// 4 x JT/16 block lazily in int64 (a fold with its row's 2^32 mod p_k every 7
+// products).  The 64 digits of the block then follow one by one (JT lanes of
+// one warp, lane = coefficient) from the triangle of W inside the block, with the
 // residues, constants and that triangle prefetched into shared memory.
 // The work per coefficient is still K^2 / 2 products, but W and the digits
 // come from shared memory, each value reused 32 and 64 times.
+template <int JT>
 __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
+  constexpr int CJ = JT / 16;              // columns per thread
   __shared__ int32_t Ws[G3T_LC][G3T_BK + 1];  // W[k0 + r][l0 + c] at Ws[c][r]
-  __shared__ int32_t Vs[G3T_LC][G3T_JT];      // digit l0 + c of coefficient j0 + jj
+  __shared__ int32_t Vs[G3T_LC][JT];          // digit l0 + c of coefficient j0 + jj
   __shared__ int32_t Wt[G3T_BK][G3T_BK + 1];  // W[k0 + r][k0 + c], c < r
-  __shared__ uint32_t Ds[G3T_BK][G3T_JT];     // r_k(j) - A[k][j] mod p_k
-  __shared__ int32_t Vb[G3T_BK][G3T_JT];      // the block's digits
+  __shared__ uint32_t Ds[G3T_BK][JT];         // r_k(j) - A[k][j] mod p_k
+  __shared__ int32_t Vb[G3T_BK][JT];          // the block's digits
   __shared__ ModP Ms[G3T_BK];
   __shared__ uint32_t Cs[G3T_BK];
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const int K = pd.K, N = pd.N, S = pd.NI, j0 = task.y, tid = threadIdx.x;
-  const int rg = tid >> 4, cg = tid & 15;  // rows 4 rg .. 4 rg + 3, columns 2 cg, 2 cg + 1
+  const int rg = tid >> 4, cg = tid & 15;  // rows 4 rg .. 4 rg + 3, columns CJ cg .. CJ cg + CJ - 1
   uint32_t *col = a.coef + pd.img_off;     // residue, then digit, of (k, j) at col[k S + j]
   for (int k0 = 0; k0 < K; k0 += G3T_BK) {
     const int bk = min(G3T_BK, K - k0);
@@ -70,13 +72,15 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
     uint32_t c32[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) c32[i] = 4 * rg + i < bk ? Ms[4 * rg + i].r1 : 0u;
-    int64_t acc[4][2];
+    int64_t acc[4][CJ];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < CJ; ++c) acc[i][c] = 0;
     int cnt = 0;
     // Chunks of W (8 values per thread) and digits (4 per thread) are loaded
     // into registers one chunk ahead, so their latency overlaps the products.
-    constexpr int NW = G3T_LC * G3T_BK / 256, NV = G3T_LC * G3T_JT / 256;
+    constexpr int NW = G3T_LC * G3T_BK / 256, NV = G3T_LC * JT / 256;
     int32_t wreg[NW], vreg[NV];
     auto fetch = [&](int l0) {
 #pragma unroll
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
       }
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const int e = tid + 256 * q, c = e >> 5, jj = e & 31, j = j0 + jj;
+        const int e = tid + 256 * q, c = e / JT, jj = e % JT, j = j0 + jj;
         vreg[q] = j < N ? (int32_t)col[(size_t)(l0 + c) * S + j] : 0;
       }
     };
@@ -100,27 +104,26 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         const int e = tid + 256 * q;
-        Vs[e >> 5][e & 31] = vreg[q];
+        Vs[e / JT][e % JT] = vreg[q];
       }
       __syncthreads();
       if (l0 + G3T_LC < k0) fetch(l0 + G3T_LC);
 #pragma unroll 4
       for (int c = 0; c < G3T_LC; ++c) {
-        int32_t w[4];
+        int32_t w[4], v[CJ];
 #pragma unroll
         for (int i = 0; i < 4; ++i) w[i] = Ws[c][4 * rg + i];
-        const int32_t v0 = Vs[c][2 * cg], v1 = Vs[c][2 * cg + 1];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          acc[i][0] = rs_mac_s32(acc[i][0], w[i], v0);
-          acc[i][1] = rs_mac_s32(acc[i][1], w[i], v1);
-        }
+        for (int cc = 0; cc < CJ; ++cc) v[cc] = Vs[c][CJ * cg + cc];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int cc = 0; cc < CJ; ++cc) acc[i][cc] = rs_mac_s32(acc[i][cc], w[i], v[cc]);
         if (++cnt == 7) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            acc[i][0] = rs_fold64(acc[i][0], c32[i]);
-            acc[i][1] = rs_fold64(acc[i][1], c32[i]);
-          }
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int cc = 0; cc < CJ; ++cc) acc[i][cc] = rs_fold64(acc[i][cc], c32[i]);
           cnt = 0;
         }
       }
@@ -133,8 +136,8 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
       if (r >= bk) continue;
       const ModP m = Ms[r];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int jj = 2 * cg + c, j = j0 + jj;
+      for (int c = 0; c < CJ; ++c) {
+        const int jj = CJ * cg + c, j = j0 + jj;
         const uint32_t tA = finish64_3(rs_fold64(acc[i][c], m.r1), m);
         const uint32_t res = j < N ? col[(size_t)(k0 + r) * S + j] : 0u;
         Ds[r][jj] = msub(res, tA, m.p);
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
       Wt[r][c] = (c < r && r < bk) ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + k0 + c) : 0;
     }
     __syncthreads();
-    if (tid < 32) {  // the block's digits in order, lane = coefficient
+    if (tid < JT) {  // the block's digits in order, lane = coefficient
       const int jj = tid, j = j0 + jj;
       for (int r = 0; r < bk; ++r) {
         const ModP m = Ms[r];
@@ -287,10 +290,15 @@ __global__ void crt_w_kernel(const ModP *mods, int K, int32_t *wtab) {
 
 }  // namespace
 
-cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s) {
+cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s, int jt) {
   G3Args at = a;
   at.tasks = ttasks;
-  if (nt) g3t_kernel<<<nt, 256, 0, s>>>(at);
+  if (nt) {
+    if (jt == 16)
+      g3t_kernel<16><<<nt, 256, 0, s>>>(at);
+    else
+      g3t_kernel<32><<<nt, 256, 0, s>>>(at);
+  }
   return cudaGetLastError();
 }
 

@@ -183,8 +183,9 @@ cudaError_t g2n_prepare();
 cudaError_t launch_g2n(int blocks, size_t smem, const G2nArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
-// CRT digits by tiles of 32 coefficients (tasks step by 32), any prime count.
-cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s);
+// CRT digits by tiles of jt (32 or 16) coefficients (tasks step by jt), any
+// prime count.
+cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s, int jt = 32);
 cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s);
 // Schur variant of G1: one block per tile, `slots` = ceil((m_y + n_y) / 32)
 // over the batch, smem = staged residues of the largest pair; then the
