@@ -1275,6 +1275,8 @@ int rs_destroy(rs_ctx *ctx) {
     DevGuard dg(ctx->device);
     for (rs_batch *b : ctx->batches) rs_free_batch(b);
     if (ctx->cache) rs_free_batch(ctx->cache);
+    if (ctx->sqf_cache) rs_free_batch(ctx->sqf_cache);
+    if (ctx->sqf_arena) cudaFree(ctx->sqf_arena);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_tables(ctx->tab);
     for (auto &t : ctx->retired) free_tables(t);

@@ -57,6 +57,9 @@ struct rs_ctx {
   std::string err;
   std::vector<rs_batch *> batches;
   rs_batch *cache = nullptr;
+  rs_batch *sqf_cache = nullptr;  // the last square-free batch, reused for the same shapes
+  void *sqf_arena = nullptr;      // the factor CRT's device arena, grown on demand
+  size_t sqf_arena_bytes = 0;
   std::mutex tab_mu;
   RsTables tab;
   std::vector<RsTables> retired;

@@ -90,7 +90,17 @@ __device__ void rem_in_place(Poly &x, const Poly &y, const ModP &m) {
       const uint32_t xn = xc[n], xn1 = xc[n - 1];
       const uint32_t na = mneg(mmul(ly, xn, m), m.p);
       const uint32_t nb = msub(mmul(xn, yc[dy - 1], m), mmul(ly, xn1, m), m.p);
-      for (int j = lane_id(); j < n - 1; j += 32) {
+      // two coefficients per iteration, loads first
+      const int e = n - 1;
+      int j = lane_id();
+      for (; j + 32 < e; j += 64) {
+        const uint32_t x0 = xc[j], x1 = xc[j + 32];
+        const uint32_t y0 = yc[j], y1 = yc[j + 32], z0 = j >= 1 ? yc[j - 1] : 0u, z1 = yc[j + 31];
+        const uint32_t t0 = mmul2(c2, x0, na, z0, m), t1 = mmul2(c2, x1, na, z1, m);
+        xc[j] = madd(t0, mmul(nb, y0, m), m.p);
+        xc[j + 32] = madd(t1, mmul(nb, y1, m), m.p);
+      }
+      if (j < e) {
         const uint32_t t1 = j >= 1 ? mmul2(c2, xc[j], na, yc[j - 1], m) : mmul(c2, xc[j], m);
         xc[j] = madd(t1, mmul(nb, yc[j], m), m.p);
       }
@@ -158,8 +168,17 @@ __device__ void divexact(Poly &q, const Poly &x, const Poly &y, Poly &r, const M
     const uint32_t qt = mmul(rc[n + t], inv, m);
     const uint32_t qt1 = mmul(msub(rc[n + t - 1], mmul(qt, yc[n - 1], m), m.p), inv, m);
     const uint32_t nq = mneg(qt, m.p), nq1 = mneg(qt1, m.p);
-    for (int i = t - 1 + lane_id(); i < n + t - 1; i += 32) {
-      const int k = i - t;  // y index of the q_t term
+    const int e = n + t - 1;
+    int i = t - 1 + lane_id();
+    for (; i + 32 < e; i += 64) {  // two coefficients per iteration, loads first
+      const int k = i - t;          // y index of the q_t term
+      const uint32_t r0 = rc[i], r1 = rc[i + 32];
+      const uint32_t a0 = k >= 0 ? yc[k] : 0u, b0 = yc[k + 1], a1 = yc[k + 32], b1 = yc[k + 33];
+      rc[i] = madd(r0, mmul2(nq, a0, nq1, b0, m), m.p);
+      rc[i + 32] = madd(r1, mmul2(nq, a1, nq1, b1, m), m.p);
+    }
+    if (i < e) {
+      const int k = i - t;
       const uint32_t v = k >= 0 ? mmul2(nq, yc[k], nq1, yc[k + 1], m) : mmul(nq1, yc[0], m);
       rc[i] = madd(rc[i], v, m.p);
     }

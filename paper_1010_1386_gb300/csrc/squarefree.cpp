@@ -480,8 +480,20 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     o.fork = true;
     o.yun_maxm = M;
     o.timing = true;
-    int rc = rs_build_batch(ctx, n, f, g, std::move(plans), o, &b);
-    if (rc != RS_OK) return rc;
+    // the batch of the previous call is reused when every pair has the same shape
+    rs_batch *cb = ctx->sqf_cache;
+    bool reuse = cb && cb->n == n && cb->opt.yun_maxm == M;
+    for (int i = 0; reuse && i < n; ++i) reuse = rs_same_shape(plans[i], cb->plans[i]);
+    int rc = RS_OK;
+    if (reuse) {
+      b = cb;
+    } else {
+      if (cb) rs_free_batch(cb);
+      ctx->sqf_cache = nullptr;
+      rc = rs_build_batch(ctx, n, f, g, std::move(plans), o, &b);
+      if (rc != RS_OK) return rc;
+      ctx->sqf_cache = b;
+    }
     DevGuard dg(ctx->device);
     rc = rs_upload(b, f, g);
     if (rc == RS_OK) rc = rs_run(b);
@@ -496,6 +508,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     if (rc == RS_OK) rc = rs_batch_info_get(b, &info.batch);
     if (rc != RS_OK) {
       rs_free_batch(b);
+      ctx->sqf_cache = nullptr;
       return rc;
     }
     info.yun_tasks = b->nyun;
@@ -682,9 +695,16 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     size_t bytes = 0;
     for (size_t x : piece) bytes += round256(x);
     DevGuard dg(ctx->device);
-    void *arena = nullptr;
-    cudaError_t e = cudaMalloc(&arena, bytes);
-    char *cur = static_cast<char *>(arena);
+    cudaError_t e = cudaSuccess;
+    if (bytes > ctx->sqf_arena_bytes) {  // grown on demand, kept by the context
+      if (ctx->sqf_arena) cudaFree(ctx->sqf_arena);
+      ctx->sqf_arena = nullptr;
+      ctx->sqf_arena_bytes = 0;
+      e = cudaMalloc(&ctx->sqf_arena, bytes);
+      if (e == cudaSuccess) ctx->sqf_arena_bytes = bytes;
+      else ctx->sqf_arena = nullptr;
+    }
+    char *cur = static_cast<char *>(ctx->sqf_arena);
     auto carve = [&](size_t x) {
       char *r = cur;
       cur += round256(x);
@@ -741,13 +761,12 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     }
     for (auto &x : lev)
       if (x) cudaEventDestroy(x);
-    if (arena) cudaFree(arena);
     if (e != cudaSuccess) {
       rs_free_batch(b);
+      ctx->sqf_cache = nullptr;
       return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
     }
   }
-  if (b) rs_free_batch(b);
   // R_m = H_m / content(H_m), leading coefficient made positive; factors on
   // host threads
   std::vector<int> lift_rc(nf, RS_OK);
