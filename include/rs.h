@@ -153,11 +153,18 @@ int rs_resultant_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipo
                        rs_upoly *out, int32_t *status);
 
 /* Prepared batches: plan once and keep the inputs resident on the device,
- * then run as often as wanted.  rs_batch_run only enqueues on the context's
+ * then run as often as wanted.  rs_batch_run only enqueues on the batch's
  * stream (a CUDA graph when enabled); rs_batch_sync waits for it;
  * rs_batch_results copies the last run's results to the host. */
 int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g,
                     rs_batch **batch);
+/* As rs_batch_create, with every copy and launch of the batch enqueued on
+ * the caller's CUDA stream (a cudaStream_t of the context's device; NULL =
+ * the context's stream).  Batches on different streams overlap: while one
+ * runs, another's results can be copied back and its next inputs uploaded.
+ * The stream must outlive the batch. */
+int rs_batch_create_on(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, void *stream,
+                       rs_batch **batch);
 int rs_batch_upload(rs_batch *batch, int32_t n, const rs_bipoly *f, const rs_bipoly *g);
 int rs_batch_run(rs_batch *batch);
 int rs_batch_sync(rs_batch *batch);

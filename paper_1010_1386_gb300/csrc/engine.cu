@@ -1321,14 +1321,17 @@ int rs_result_bound(const rs_bipoly *f, const rs_bipoly *g, int32_t *deg_bound, 
   return RS_OK;
 }
 
-int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_batch **batch) {
+int rs_batch_create_on(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, void *stream,
+                       rs_batch **batch) {
   if (!ctx || !batch || n < 0 || (n > 0 && (!f || !g))) return rs_fail(ctx, RS_ERR_ARG, "NULL argument or negative n");
   *batch = nullptr;
   std::vector<PairPlan> plans;
   int first = RS_OK;
   rs_plan_all(ctx, n, f, g, plans, nullptr, &first);
   rs_batch *b = nullptr;
-  int rc = rs_build_batch(ctx, n, f, g, std::move(plans), default_opts(ctx), &b);
+  RsBatchOpts o = default_opts(ctx);
+  o.stream = static_cast<cudaStream_t>(stream);
+  int rc = rs_build_batch(ctx, n, f, g, std::move(plans), o, &b);
   if (rc != RS_OK) return rc;
   DevGuard dg(ctx->device);
   rc = rs_upload(b, f, g);
@@ -1339,6 +1342,10 @@ int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly 
   ctx->batches.push_back(b);
   *batch = b;
   return RS_OK;
+}
+
+int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_batch **batch) {
+  return rs_batch_create_on(ctx, n, f, g, nullptr, batch);
 }
 
 int rs_batch_upload(rs_batch *b, int32_t n, const rs_bipoly *f, const rs_bipoly *g) {

@@ -85,6 +85,8 @@ _SIGS = {
     "rs_resultant_batch": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly),
                                      _P(rs_upoly), _P(c_int32)]),
     "rs_batch_create": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), _P(c_void_p)]),
+    "rs_batch_create_on": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), c_void_p,
+                                     _P(c_void_p)]),
     "rs_batch_upload": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
     "rs_batch_run": (c_int32, [c_void_p]),
     "rs_batch_sync": (c_int32, [c_void_p]),
@@ -161,19 +163,31 @@ _BIPOLY_DT = np.dtype([("deg_x", "<i4"), ("deg_y", "<i4"), ("limbs", "<i4"), ("p
                        ("coeffs", "<u8")])
 
 
+def _abi_record(b):
+    """(limb array, deg_x, deg_y, limbs, 0, data pointer) of a BiPoly, kept on
+    the instance while its coefficient array stays the same object, so that
+    marshalling the same inputs again costs one attribute lookup each."""
+    rec = getattr(b, "_rs_abi", None)
+    if rec is None or rec[0] is not b.coeffs:
+        a = b.coeffs
+        if not (a.dtype == np.uint32 and a.flags.c_contiguous):
+            a = np.ascontiguousarray(a, dtype=np.uint32)
+            b.coeffs = a
+        rec = (a, a.shape[0] - 1, a.shape[1] - 1, a.shape[2], 0, a.__array_interface__["data"][0])
+        b._rs_abi = rec
+    return rec
+
+
 class _Polys:
     """Keeps the limb arrays alive while C structs point at them."""
 
     def __init__(self, polys):
-        self.arrays = [np.ascontiguousarray(as_bipoly(p).coeffs, dtype=np.uint32) for p in polys]
-        n = len(self.arrays)
+        recs = [_abi_record(as_bipoly(p)) for p in polys]
+        n = len(recs)
+        self.arrays = [r[0] for r in recs]
         self.raw = np.zeros(max(n, 1), dtype=_BIPOLY_DT)
         if n:
-            shp = np.array([a.shape for a in self.arrays], dtype=np.int32)
-            self.raw["deg_x"][:n] = shp[:, 0] - 1
-            self.raw["deg_y"][:n] = shp[:, 1] - 1
-            self.raw["limbs"][:n] = shp[:, 2]
-            self.raw["coeffs"][:n] = [a.__array_interface__["data"][0] for a in self.arrays]
+            self.raw[:n] = np.array([r[1:] for r in recs], dtype=_BIPOLY_DT)
         self.structs = (rs_bipoly * max(n, 1)).from_buffer(self.raw)
 
 
@@ -406,8 +420,10 @@ class Context:
                                   imgs.ctypes.data_as(POINTER(c_uint32))), self.h)
         return primes, pts, imgs
 
-    def batch(self, pairs):
-        return Batch(self, pairs)
+    def batch(self, pairs, stream=None):
+        """A prepared batch; stream: a cudaStream_t handle (int) of this
+        device to enqueue it on, None for the context's stream."""
+        return Batch(self, pairs, stream)
 
     def autotune(self, pairs):
         """Tune the G1 launch for every workload class of these pairs that the
@@ -441,15 +457,16 @@ def autotune_clear():
 class Batch:
     """A prepared batch: inputs resident on the device, runs replayed."""
 
-    def __init__(self, ctx, pairs):
+    def __init__(self, ctx, pairs, stream=None):
         self.ctx, self.lib, self.n = ctx, ctx.lib, len(pairs)
         self.F, self.G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
         self.out = _Outputs(pairs)
         self.status = (c_int32 * max(self.n, 1))()
         h = c_void_p()
-        _check(self.lib.rs_batch_create(ctx.h, self.n, self.F.structs, self.G.structs,
-                                        ctypes.byref(h)), ctx.h)
+        _check(self.lib.rs_batch_create_on(ctx.h, self.n, self.F.structs, self.G.structs,
+                                           c_void_p(stream) if stream else None, ctypes.byref(h)), ctx.h)
         self.h = h
+        self.stream = stream or ctx.stream
 
     def upload(self, pairs=None):
         if pairs is not None:

@@ -289,3 +289,27 @@ def test_errors(ctx):
     rc = lib.rs_resultant_y(ctx.h, P.structs, rs.ctypes.byref(P.structs[1]), out)
     assert rc == -2 and out[0].deg >= 0
     assert lib.rs_resultant_y(ctx.h, None, None, out) == -1
+
+
+def test_batches_on_caller_streams_overlap_exactly(ctx):
+    """rs_batch_create_on: two prepared batches on two caller streams,
+    alternated with the result copy of one overlapping the other's run,
+    give the same results as the context's own path, step after step."""
+    torch = pytest.importorskip("torch")
+    rng = random.Random(9)
+    pairs = [(rand_bipoly(rng, rng.randint(1, 6), rng.randint(1, 6), bits=40),
+              rand_bipoly(rng, rng.randint(1, 6), rng.randint(1, 6), bits=40)) for _ in range(24)]
+    want = ctx.resultant_batch(pairs)
+    streams = [torch.cuda.Stream(device=0) for _ in range(2)]
+    bs = [ctx.batch(pairs, stream=st.cuda_stream) for st in streams]
+    prev = None
+    for s in range(5):
+        b = bs[s % 2]
+        b.upload(pairs)
+        b.run()
+        if prev is not None:
+            assert prev.results() == want
+        prev = b
+    assert prev.results() == want
+    for b in bs:
+        b.close()
