@@ -390,7 +390,7 @@ def batch_main(args, world, rank, local, dist):
     # one prepared batch, step after step.  Pipelined: two prepared batches
     # on two streams alternate, so step s's result copy and trim overlap step
     # s + 1's run (the same transfers, overlapped).
-    e2e_steps = max(4, min(args.steps, 8))
+    e2e_steps = max(8, min(2 * args.steps, 16))
     e2e_ms = []
     batch.upload(pairs)  # one untimed end-to-end pass (host buffers, staging pages)
     batch.run()
@@ -632,7 +632,7 @@ def serving_main(args, world, rank, local, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
