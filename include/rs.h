@@ -243,6 +243,17 @@ int rs_squarefree_y(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t
 int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
                         rs_upoly *content, rs_upoly *factors, int32_t *nmult, int32_t *status);
 
+/* Square-free factorisations of both projections of each pair (the PROJECT
+ * phase factors R^{(y)} and R^{(x)}, Section 5): for pair i, content_y[i],
+ * factors_y[i * max_mult + m - 1], nmult_y[i] describe res(f_i, g_i, y) as in
+ * rs_squarefree_y, and the _x outputs res(f_i, g_i, x) (coefficient k
+ * belongs to y^k), all 2n factorisations in one GPU pass.  status (may be
+ * NULL) receives 2n codes: the y-projections, then the x-projections.
+ * Returns the first failure, as rs_squarefree_batch. */
+int rs_squarefree_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
+                              rs_upoly *content_y, rs_upoly *factors_y, int32_t *nmult_y, rs_upoly *content_x,
+                              rs_upoly *factors_x, int32_t *nmult_x, int32_t *status);
+
 /* Where the last rs_squarefree_y / rs_squarefree_batch call of this context
  * spent its time. */
 typedef struct {

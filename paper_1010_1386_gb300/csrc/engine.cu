@@ -1467,6 +1467,45 @@ int rs_resultant_x(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, rs_upoly
   return rs_resultant_batch(ctx, 1, &ft, &gt, out, nullptr);
 }
 
+int rs_squarefree_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, int32_t max_mult,
+                              rs_upoly *content_y, rs_upoly *factors_y, int32_t *nmult_y, rs_upoly *content_x,
+                              rs_upoly *factors_x, int32_t *nmult_x, int32_t *status) {
+  if (!ctx || n < 0 || max_mult < 1 ||
+      (n > 0 && (!f || !g || !content_y || !factors_y || !nmult_y || !content_x || !factors_x || !nmult_x)))
+    return rs_fail(ctx, RS_ERR_ARG, "NULL argument, negative n or max_mult < 1");
+  if (n == 0) return RS_OK;
+  const size_t N2 = 2 * (size_t)n, M = (size_t)max_mult;
+  std::vector<std::vector<uint32_t>> bufs(N2);
+  std::vector<rs_bipoly> F(N2), G(N2);
+  std::vector<rs_upoly> C(N2), FA(N2 * M);
+  std::vector<int32_t> NM(N2, 0);
+  for (int i = 0; i < n; ++i) {
+    F[i] = f[i];
+    G[i] = g[i];
+    F[n + i] = transposed(f[i], bufs[2 * (size_t)i]);
+    G[n + i] = transposed(g[i], bufs[2 * (size_t)i + 1]);
+    C[i] = content_y[i];
+    C[n + i] = content_x[i];
+    for (size_t m = 0; m < M; ++m) {
+      FA[i * M + m] = factors_y[i * M + m];
+      FA[(n + i) * M + m] = factors_x[i * M + m];
+    }
+  }
+  const int rc = rs_squarefree_batch(ctx, 2 * n, F.data(), G.data(), max_mult, C.data(), FA.data(), NM.data(),
+                                     status);
+  for (int i = 0; i < n; ++i) {  // shapes (and data, through the caller's pointers) back
+    content_y[i] = C[i];
+    content_x[i] = C[n + i];
+    nmult_y[i] = NM[i];
+    nmult_x[i] = NM[n + i];
+    for (size_t m = 0; m < M; ++m) {
+      factors_y[i * M + m] = FA[i * M + m];
+      factors_x[i * M + m] = FA[(n + i) * M + m];
+    }
+  }
+  return rc;
+}
+
 int rs_projections(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, rs_upoly *out_y,
                    rs_upoly *out_x, int32_t *status) {
   if (!ctx || n < 0 || (n > 0 && (!f || !g || !out_y || !out_x)))

@@ -111,6 +111,9 @@ _SIGS = {
     "rs_squarefree_batch": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), c_int32,
                                       _P(rs_upoly), _P(rs_upoly), _P(c_int32), _P(c_int32)]),
     "rs_squarefree_info_get": (c_int32, [c_void_p, _P(rs_sqf_info)]),
+    "rs_squarefree_projections": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly), c_int32,
+                                            _P(rs_upoly), _P(rs_upoly), _P(c_int32), c_void_p, c_void_p,
+                                            c_void_p, _P(c_int32)]),
     "rs_autotune": (c_int32, [c_void_p, c_int32, _P(rs_bipoly), _P(rs_bipoly)]),
     "rs_autotune_entries": (c_int32, [_P(rs_tune_entry), c_int32, _P(c_int32)]),
     "rs_autotune_save": (c_int32, [c_char_p]),
@@ -335,8 +338,36 @@ class Context:
         if n == 0:
             return []
         F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
-        # output room from the planner's bounds: R_i has degree <= D / i and
-        # coefficients below the bound of the lifted factors
+
+        def call(content, facs, nm, st):
+            return self.lib.rs_squarefree_batch(self.h, n, F.structs, G.structs, max_mult, content, facs, nm, st)
+        return self._squarefree_call(list(pairs), max_mult, call, raw)
+
+    def squarefree_projections(self, pairs, max_mult=8):
+        """Square-free factorisations of both projections of every pair in one
+        GPU pass: per pair (sqf of Res_y, sqf of Res_x), each as squarefree()
+        returns (Res_x's coefficient k belongs to y^k) or an RsError."""
+        n = len(pairs)
+        if n == 0:
+            return []
+        F, G = _Polys([p[0] for p in pairs]), _Polys([p[1] for p in pairs])
+        sz_u, sz_i = ctypes.sizeof(rs_upoly), ctypes.sizeof(c_int32)
+
+        def call(content, facs, nm, st):
+            return self.lib.rs_squarefree_projections(
+                self.h, n, F.structs, G.structs, max_mult, content, facs, nm,
+                c_void_p(ctypes.addressof(content) + n * sz_u),
+                c_void_p(ctypes.addressof(facs) + n * max_mult * sz_u),
+                c_void_p(ctypes.addressof(nm) + n * sz_i), st)
+        sizing = list(pairs) + [(swap_xy(f), swap_xy(g)) for f, g in pairs]
+        out = self._squarefree_call(sizing, max_mult, call, False)
+        return list(zip(out[:n], out[n:]))
+
+    def _squarefree_call(self, pairs, max_mult, call, raw):
+        """Size the output buffers of len(pairs) factorisations from the
+        planner's bounds (R_i has degree <= D / i and coefficients below the
+        bound of the lifted factors), call, grow on RS_ERR_CAPACITY, decode."""
+        n = len(pairs)
         cw, fw = [], []
         for f, g in pairs:
             try:
@@ -369,7 +400,7 @@ class Context:
                     off += fw[i][m]
             nm = (c_int32 * n)()
             st = (c_int32 * n)()
-            rc = self.lib.rs_squarefree_batch(self.h, n, F.structs, G.structs, max_mult, content, facs, nm, st)
+            rc = call(content, facs, nm, st)
             grow = False
             for i in range(n):
                 if st[i] != -2:
@@ -388,7 +419,7 @@ class Context:
         out = []
         for i in range(n):
             if st[i] != 0:
-                out.append(RsError(st[i], msg if n == 1 else f"pair {i} failed"))
+                out.append(RsError(st[i], msg if n == 1 else f"factorisation {i} failed"))
                 continue
             c = limbs_to_ints(cbuf[co[i]:], content[i].deg, content[i].limbs)[0]
             r = []

@@ -94,3 +94,16 @@ def test_batch_mixed_pairs(ctx):
             assert isinstance(r, rs.RsError) and r.code == -1, i
         else:
             assert r == sq.squarefree(R), i
+
+
+def test_both_projections_in_one_pass(ctx):
+    """rs_squarefree_projections: Res_y and Res_x of each pair factored in one
+    pass, each equal to the oracle's factorisation of the oracle's
+    resultant in that variable."""
+    rng = random.Random(74)
+    pairs = [planted(rng, 2, 1, 7), planted(rng, 1, 1, 5)]
+    pairs += [(rand_bipoly(rng, 3, 2, bits=20), rand_bipoly(rng, 2, 3, bits=9))]
+    got = ctx.squarefree_projections(pairs)
+    for (f, g), (sy, sx) in zip(pairs, got):
+        assert sy == sq.squarefree(exact.resultant_y(f, g))
+        assert sx == sq.squarefree(exact.resultant_x(f, g))
