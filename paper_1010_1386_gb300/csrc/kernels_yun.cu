@@ -90,17 +90,21 @@ __device__ void rem_in_place(Poly &x, const Poly &y, const ModP &m) {
       const uint32_t xn = xc[n], xn1 = xc[n - 1];
       const uint32_t na = mneg(mmul(ly, xn, m), m.p);
       const uint32_t nb = msub(mmul(xn, yc[dy - 1], m), mmul(ly, xn1, m), m.p);
-      // two coefficients per iteration, loads first
+      // four coefficients per iteration, loads first
       const int e = n - 1;
       int j = lane_id();
-      for (; j + 32 < e; j += 64) {
-        const uint32_t x0 = xc[j], x1 = xc[j + 32];
-        const uint32_t y0 = yc[j], y1 = yc[j + 32], z0 = j >= 1 ? yc[j - 1] : 0u, z1 = yc[j + 31];
-        const uint32_t t0 = mmul2(c2, x0, na, z0, m), t1 = mmul2(c2, x1, na, z1, m);
-        xc[j] = madd(t0, mmul(nb, y0, m), m.p);
-        xc[j + 32] = madd(t1, mmul(nb, y1, m), m.p);
+      for (; j + 96 < e; j += 128) {
+        uint32_t xv[4], yv[4], zv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          xv[u] = xc[j + 32 * u];
+          yv[u] = yc[j + 32 * u];
+          zv[u] = (u > 0 || j >= 1) ? yc[j + 32 * u - 1] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xc[j + 32 * u] = madd(mmul2(c2, xv[u], na, zv[u], m), mmul(nb, yv[u], m), m.p);
       }
-      if (j < e) {
+      for (; j < e; j += 32) {
         const uint32_t t1 = j >= 1 ? mmul2(c2, xc[j], na, yc[j - 1], m) : mmul(c2, xc[j], m);
         xc[j] = madd(t1, mmul(nb, yc[j], m), m.p);
       }
@@ -170,14 +174,19 @@ __device__ void divexact(Poly &q, const Poly &x, const Poly &y, Poly &r, const M
     const uint32_t nq = mneg(qt, m.p), nq1 = mneg(qt1, m.p);
     const int e = n + t - 1;
     int i = t - 1 + lane_id();
-    for (; i + 32 < e; i += 64) {  // two coefficients per iteration, loads first
-      const int k = i - t;          // y index of the q_t term
-      const uint32_t r0 = rc[i], r1 = rc[i + 32];
-      const uint32_t a0 = k >= 0 ? yc[k] : 0u, b0 = yc[k + 1], a1 = yc[k + 32], b1 = yc[k + 33];
-      rc[i] = madd(r0, mmul2(nq, a0, nq1, b0, m), m.p);
-      rc[i + 32] = madd(r1, mmul2(nq, a1, nq1, b1, m), m.p);
+    for (; i + 96 < e; i += 128) {  // four coefficients per iteration, loads first
+      const int k = i - t;           // y index of the q_t term
+      uint32_t rv[4], av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        rv[u] = rc[i + 32 * u];
+        av[u] = (u > 0 || k >= 0) ? yc[k + 32 * u] : 0u;
+        bv[u] = yc[k + 32 * u + 1];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rc[i + 32 * u] = madd(rv[u], mmul2(nq, av[u], nq1, bv[u], m), m.p);
     }
-    if (i < e) {
+    for (; i < e; i += 32) {
       const int k = i - t;
       const uint32_t v = k >= 0 ? mmul2(nq, yc[k], nq1, yc[k + 1], m) : mmul(nq1, yc[0], m);
       rc[i] = madd(rc[i], v, m.p);
