@@ -526,10 +526,12 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   };
   const std::vector<Big> one_m{Big{1u}};
   const std::vector<char> one_s{0};
-  // Per pair, on host threads: R, its content, the usable primes and the
-  // pattern of factor degrees.
+  // Per pair, on host threads: R, the usable primes and the pattern of
+  // factor degrees (R's content is taken later, while the GPU lifts the
+  // factors).
   struct PairRes {
-    int degR = -1;
+    int degR = -1, LR = 1;
+    std::vector<uint32_t> Rw;  // R's limbs until its content is taken
     Big content;
     bool lc_neg = false;
     std::vector<int> pattern;
@@ -546,9 +548,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   }
   auto analyse = [&](int i) {
     PairRes &q = pr[i];
-    std::vector<uint32_t> Rw;
-    int LR = 1;
-    st[i] = rs_unpack_one(b, i, Rw, &q.degR, &LR);
+    st[i] = rs_unpack_one(b, i, q.Rw, &q.degR, &q.LR);
     if (st[i] != RS_OK) {
       why[i] = "resultant failed";
       return;
@@ -558,13 +558,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       why[i] = "R = 0 has no square-free factorisation";
       return;
     }
-    std::vector<Big> Rm(q.degR + 1);
-    for (int j = 0; j <= q.degR; ++j) {
-      bool ng;
-      Rm[j] = from_twos(&Rw[(size_t)j * LR], LR, &ng);
-      if (j == q.degR) q.lc_neg = ng;
-    }
-    q.content = content_of(Rm, nullptr);
+    q.lc_neg = (q.Rw[(size_t)q.degR * q.LR + q.LR - 1] >> 31) != 0;
     if (q.degR == 0) return;
     // usable primes: R keeps its degree mod p, square-free part of largest degree
     auto task = [&](int k) { return &hdr[(size_t)(t0v[i] + k) * hw]; };
@@ -636,7 +630,6 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   for (int i = 0; i < n; ++i) {
     if (st[i] != RS_OK) continue;
     const PairRes &q = pr[i];
-    out_rc[i] = put(content[i], {q.content}, {(char)q.lc_neg});
     for (int m = 0; m < M; ++m) {  // R_i = 1 unless set below
       const int r2 = put(factors[(size_t)i * M + m], one_m, one_s);
       if (out_rc[i] == RS_OK) out_rc[i] = r2;
@@ -673,6 +666,24 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       off += d + 1;
     }
   }
+  // R's content c = sign(lc R) gcd(coefficients of R), per pair on host
+  // threads (run while the GPU lifts the factors).
+  auto contents = [&] {
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i)
+      if (st[i] == RS_OK && pr[i].degR >= 0) todo.push_back(i);
+    parallel_for((int)todo.size(), [&](int t) {
+      PairRes &q = pr[todo[t]];
+      std::vector<Big> Rm(q.degR + 1);
+      for (int j = 0; j <= q.degR; ++j) {
+        bool ng;
+        Rm[j] = from_twos(&q.Rw[(size_t)j * q.LR], q.LR, &ng);
+      }
+      q.content = content_of(Rm, nullptr);
+      std::vector<uint32_t>().swap(q.Rw);
+    });
+  };
+  bool contents_done = false;
   // One CRT pass over every factor of every pair.
   const int nf = (int)lifts.size();
   std::vector<uint32_t> hwords((size_t)outw);
@@ -754,6 +765,10 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
         if (e == cudaSuccess) e = launch_g3bc((int)g3b.size(), (int)g3.size(), a3, d_g3, s);
         if (e == cudaSuccess) e = cudaEventRecord(lev[1], s);
       }
+      if (e == cudaSuccess) {  // host work while the lift runs
+        contents();
+        contents_done = true;
+      }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hwords.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -766,6 +781,12 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       ctx->sqf_cache = nullptr;
       return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
     }
+  }
+  if (!contents_done) contents();
+  for (int i = 0; i < n; ++i) {
+    if (st[i] != RS_OK) continue;
+    const int r2 = put(content[i], {pr[i].content}, {(char)pr[i].lc_neg});
+    if (out_rc[i] == RS_OK) out_rc[i] = r2;
   }
   // R_m = H_m / content(H_m), leading coefficient made positive; factors on
   // host threads
