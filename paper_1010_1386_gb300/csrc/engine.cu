@@ -94,6 +94,7 @@ int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
 
 bool rs_same_shape(const PairPlan &a, const PairPlan &b) {
   return a.status == b.status && a.trivial_zero == b.trivial_zero && a.N == b.N && a.K == b.K &&
+         a.Kcrt == b.Kcrt &&
          a.Lout == b.Lout && a.f.my == b.f.my && a.g.my == b.g.my && a.f.mx == b.f.mx &&
          a.g.mx == b.g.mx && a.f.L == b.f.L && a.g.L == b.g.L && a.f.stride == b.f.stride &&
          a.g.stride == b.g.stride && a.f.dx == b.f.dx && a.g.dx == b.g.dx;
@@ -374,7 +375,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     d.ny = p.g.my;
     d.N = p.N;
     d.NI = 2 * ((p.N + 1) / 2);
-    d.K = p.K;
+    d.K = p.Kcrt > 0 ? std::min(p.Kcrt, p.K) : p.K;  // read by the CRT kernels only
     d.Lf = p.f.L;
     d.Lg = p.g.L;
     d.fstride = p.f.stride;
@@ -426,7 +427,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       b->info.modmul_prs += imgs * 2.0 * prs_updates(p.f.my, p.g.my);
     }
     b->info.modmul_interp += (double)p.K * ((double)d.NI * d.NI / 2 + 8.0 * d.NI);  // two interpolations of NI / 2
-    b->info.modmul_crt += (double)p.N * ((double)p.K * (p.K - 1) + p.K);
+    b->info.modmul_crt += (double)p.N * ((double)d.K * (d.K - 1) + d.K);
   }
   b->shape_off = b->out_words;  // per pair (1 + degree, limbs), written by the last CRT kernel
   if (!images_only) b->out_words += 2 * (int64_t)b->descs.size();

@@ -26,7 +26,9 @@ struct PairPlan {
   int D = 0;      // degree bound of R
   int N = 0;      // points = D + 1
   int bits = 0;   // |coef R| < 2^bits
-  int K = 0;      // primes
+  int K = 0;      // primes (images are taken for the first K)
+  int Kcrt = 0;   // primes R's Chinese remaindering uses (0: all K); a square-free
+                  // batch draws more primes than R needs, for its factors
   int Lout = 0;   // output limbs
   int cap = 0;    // compiled register capacity class for G1
   int staged = 0; // shared-memory words G1 stages per tile

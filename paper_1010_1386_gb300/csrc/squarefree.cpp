@@ -464,6 +464,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       p.status = RS_ERR_LIMIT;
       continue;
     }
+    p.Kcrt = p.K;  // R itself needs only its own primes
     p.K = std::min((int)ctx->log2p.size(), std::max(p.K, KH[i]) + 4);  // a few spare primes
     ++valid;
   }
