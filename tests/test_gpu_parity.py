@@ -313,3 +313,25 @@ def test_batches_on_caller_streams_overlap_exactly(ctx):
     assert prev.results() == want
     for b in bs:
         b.close()
+
+
+def test_product_formula_full_size(ctx):
+    """Every coefficient of a large resultant against the closed form
+    Res_y(f, g) = a^{n_y} prod_i g(x, alpha_i(x)) for f = a prod_{i<30}
+    (y - alpha_i(x)) (plain Z[x] arithmetic, no determinant): m_y = 30,
+    n_y = 20, deg R = 1000, coefficients of up to about 3,700 bits."""
+    from oracle.exact import zx_mul, zx_trim
+    from tests.test_oracle_pins import _from_factors, _subst_y
+    rng = random.Random(11)
+    a = [rng.randint(-40, 40) for _ in range(3)]
+    a[-1] = a[-1] or 7
+    alphas = [[rng.randint(-40, 40), rng.randint(-40, 40) or 1] for _ in range(30)]
+    f = _from_factors(a, alphas)
+    g = rand_bipoly(rng, 12, 20, bits=20)
+    expect = [1]
+    for _ in range(20):
+        expect = zx_mul(expect, zx_trim(a))
+    for al in alphas:
+        expect = zx_mul(expect, _subst_y(g, al))
+    got = ctx.resultant_y(f, g)
+    assert len(got) == 1001 and got == expect
