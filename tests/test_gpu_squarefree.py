@@ -23,6 +23,31 @@ def ctx():
     c.close()
 
 
+def _trim_mod(a):
+    while a and a[-1] == 0:
+        a.pop()
+    return a
+
+
+def _deriv_mod(a, q):
+    return _trim_mod([i * a[i] % q for i in range(1, len(a))])
+
+
+def _gcd_mod(a, b, q):
+    """Monic gcd of polynomials mod a prime q (ascending lists)."""
+    a, b = _trim_mod(list(a)), _trim_mod(list(b))
+    while b:
+        inv = pow(b[-1], q - 2, q)
+        while len(a) >= len(b):
+            t, s = a[-1] * inv % q, len(a) - len(b)
+            for i, v in enumerate(b):
+                a[s + i] = (a[s + i] - t * v) % q
+            _trim_mod(a)
+        a, b = b, a
+    inv = pow(a[-1], q - 2, q)
+    return [v * inv % q for v in a]
+
+
 def planted(rng, dp, dq, bits):
     p = rand_bipoly(rng, dp, dp, bits=bits)
     q = rand_bipoly(rng, dq, dq, bits=bits)
@@ -76,6 +101,15 @@ def test_nongeneric_workload_full_size(ctx):
     R = ctx.resultant_y(f, g)
     c, facs = ctx.squarefree(f, g)
     assert sq.expand(c, facs) == R
+    # square-free and pairwise coprime: a common factor over Z would survive
+    # reduction mod a prime that divides no leading coefficient
+    q = (1 << 61) - 1
+    assert all(P[-1] % q for _, P in facs)
+    red = [[v % q for v in P] for _, P in facs]
+    for i, A in enumerate(red):
+        assert len(_gcd_mod(A, _deriv_mod(A, q), q)) == 1
+        for B in red[i + 1:]:
+            assert len(_gcd_mod(A, B, q)) == 1
     assert all(P[-1] > 0 for _, P in facs) and [m for m, _ in facs] == sorted(m for m, _ in facs)
     assert [m for m, _ in facs] == [1, 2, 3]
 
