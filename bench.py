@@ -652,7 +652,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=None,
                     help="time only the first PAIRS pairs / requests (profiling)")
     ap.add_argument("--load", type=float, default=0.8, help="serving: arrival rate / saturation")
-    ap.add_argument("--inflight", type=int, default=4, help="serving: concurrent micro-batches")
+    ap.add_argument("--inflight", type=int, default=3, help="serving: concurrent micro-batches")
     ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per micro-batch")
     args = ap.parse_args()
     global SHIFT

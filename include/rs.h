@@ -360,7 +360,7 @@ typedef struct {
 } rs_server_stats;
 
 /* Start the server (optional: the first submit starts it with defaults).
- * max_inflight: concurrent micro-batches (streams), 0 = 4; max_batch:
+ * max_inflight: concurrent micro-batches (streams), 0 = 3; max_batch:
  * requests per micro-batch, 0 = 256; mem_limit_bytes: admission budget,
  * 0 = rs_config.mem_limit_bytes or half of the free device memory. */
 int rs_server_start(rs_ctx *ctx, int32_t max_inflight, int32_t max_batch, int64_t mem_limit_bytes);

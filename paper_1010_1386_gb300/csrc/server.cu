@@ -59,7 +59,7 @@ struct RsServer {
   std::unordered_map<uint64_t, Request *> reqs;
   uint64_t next_ticket = 1;
   int64_t mem_limit = 0, mem_used = 0;
-  int max_inflight = 4, max_batch = 256;
+  int max_inflight = 3, max_batch = 256;
   int min_batch = 32;                                  // launch early once this many wait
   int64_t max_images = int64_t(1) << 22;               // images per micro-batch (about 5 ms of G1)
   std::chrono::microseconds max_wait{1000};            // or once the oldest waited this long
@@ -273,7 +273,7 @@ int start(rs_ctx *ctx, int32_t max_inflight, int32_t max_batch, int64_t mem_limi
   RsServer *s = new RsServer();
   s->ctx = ctx;
   memset(&s->st, 0, sizeof(s->st));
-  s->max_inflight = max_inflight > 0 ? max_inflight : 4;
+  s->max_inflight = max_inflight > 0 ? max_inflight : 3;
   s->max_batch = max_batch > 0 ? max_batch : 256;
   s->min_batch = std::max(1, std::min(32, s->max_batch / 4));
   if (mem_limit <= 0) mem_limit = ctx->cfg.mem_limit_bytes;
