@@ -534,6 +534,7 @@ def squarefree_main(args, world, rank, local, dist):
         "stage_ms": {"G1": bmean("ms_images"), "G2": bmean("ms_interp"), "yun": bmean("ms_yun"),
                      "G3 (R)": bmean("ms_crt"), "lift (factor CRT)": mean("ms_lift"),
                      "host (selection, contents, primitive parts)": mean("ms_host"),
+                     "host: primitive parts": mean("ms_primitive"),
                      "call": mean("ms_total")},
         "resultant_only": {"ms_per_step": statistics.mean(res_ms),
                            "value": npairs / (statistics.mean(res_ms) * 1e-3), "unit": "resultants/s",

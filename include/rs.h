@@ -263,7 +263,7 @@ typedef struct {
   float ms_lift;        /* CRT of the factors on the device */
   float ms_host;        /* host work after the GPU pass: prime selection, contents, primitive parts */
   float ms_total;       /* wall time of the call */
-  int32_t reserved;
+  float ms_primitive;   /* of ms_host: the primitive parts of the lifted factors */
 } rs_sqf_info;
 
 int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info);

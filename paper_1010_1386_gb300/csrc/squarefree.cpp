@@ -791,6 +791,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   }
   // R_m = H_m / content(H_m), leading coefficient made positive; factors on
   // host threads
+  const auto t_prim0 = std::chrono::steady_clock::now();
   std::vector<int> lift_rc(nf, RS_OK);
   std::vector<int> order(nf);  // largest factors first
   for (int fi = 0; fi < nf; ++fi) order[fi] = fi;
@@ -821,6 +822,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     return (float)std::chrono::duration<double, std::milli>(z - a).count();
   };
   info.factors = nf;
+  info.ms_primitive = ms(t_prim0, t_end);
   info.ms_host = ms(t_host0, t_end) - info.ms_lift;
   info.ms_total = ms(t_start, t_end);
   ctx->sqf_info = info;
