@@ -165,6 +165,10 @@ int rs_batch_create(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly 
  * The stream must outlive the batch. */
 int rs_batch_create_on(rs_ctx *ctx, int32_t n, const rs_bipoly *f, const rs_bipoly *g, void *stream,
                        rs_batch **batch);
+/* New inputs for a prepared batch (copied into its pinned staging and sent
+ * to the device on its stream).  The inputs are planned again: if any pair's
+ * plan (degrees, prime count, output limbs) differs from the batch's, the
+ * call returns RS_ERR_STATE and uploads nothing. */
 int rs_batch_upload(rs_batch *batch, int32_t n, const rs_bipoly *f, const rs_bipoly *g);
 int rs_batch_run(rs_batch *batch);
 int rs_batch_sync(rs_batch *batch);
