@@ -141,3 +141,15 @@ def test_both_projections_in_one_pass(ctx):
     for (f, g), (sy, sx) in zip(pairs, got):
         assert sy == sq.squarefree(exact.resultant_y(f, g))
         assert sx == sq.squarefree(exact.resultant_x(f, g))
+
+
+def test_hand_derived_content_sign_and_factors(ctx):
+    """Res_y(y - x, g) = g(x, x); with g = -6 (y - 1)^2 (x + 2) this is
+    R = -6 (x - 1)^2 (x + 2): content -6 (the sign of lc R), x + 2 with
+    multiplicity 1 and x - 1 with multiplicity 2."""
+    f = [[0, 1], [-1, 0]]  # y - x  (f[i][j]: coefficient of x^i y^j)
+    # -6 (y^2 - 2y + 1)(x + 2) = -12 + 24 y - 12 y^2 - 6 x + 12 x y - 6 x y^2
+    g = [[-12, 24, -12], [-6, 12, -6]]
+    want = (-6, [(1, [2, 1]), (2, [-1, 1])])
+    assert sq.squarefree(exact.resultant_y(f, g)) == want
+    assert ctx.squarefree(f, g) == want
