@@ -259,6 +259,20 @@ def roofline(info, g1_ms, clk, kernel="G1 (reduce + evaluate + univariate result
                            "(no integer peak in MEASURED_PEAKS.json)"}
 
 
+def whole_path_work(info, npairs, ms, peak):
+    """Algorithmic modular products of one step by stage (a3 evaluation, a4
+    univariate resultants, a5 interpolation counted in its direct
+    convolution form, a6 Garner digits) and the whole path's rate at 4 IMAD
+    per product against the same derived peak as the G1 roofline."""
+    parts = {"eval": info["modmul_eval"], "prs": info["modmul_prs"], "interp": info["modmul_interp"],
+             "crt": info["modmul_crt"]}
+    total = sum(parts.values())
+    rate = 4.0 * total / (ms * 1e-3) / 1e12
+    return {"unit": "modular products per step (interp: direct-convolution count)", **parts,
+            "total": total, "per_resultant": total / max(npairs, 1),
+            "whole_path_timad_s": rate, "whole_path_frac": rate / peak}
+
+
 def base_line(args, world, value, ms, workload_desc, extra_cfg):
     return {"metric": METRIC, "value": value, "unit": "resultants/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -453,6 +467,7 @@ def batch_main(args, world, rank, local, dist):
         "batched_over_per_instance": (value / world / per_inst["value"]) if per_inst else None,
         "imad_frac_g1": rf["frac"],
         "roofline": rf,
+        "work": whole_path_work(info, npairs, ms, rf["peak"]),
         "gpu_launches": args.steps * info["kernel_launches"],
         "clocks": clk,
         "e2e": {"value": e2e_val, "unit": "resultants/s", "h2d_bytes_per_step": info["input_bytes"],
