@@ -62,15 +62,20 @@ int rs_plan_all(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   auto plan_range = [&](int lo, int hi) {
     for (int i = lo; i < hi; ++i) plans[i].status = rs_plan_pair(&f[i], &g[i], ctx->log2p, plans[i], &why[i]);
   };
-  // Planning reads every input coefficient once; large batches are split
-  // over host threads in contiguous ranges of pairs.
+  // Planning reads every input coefficient once and takes one summed
+  // autocorrelation per polynomial ((deg_x + 1)^2 (deg_y + 1) / 2 products);
+  // large batches are split over host threads in contiguous ranges of pairs.
   auto sane = [](const rs_bipoly &p) {
     return p.coeffs && p.deg_x >= 0 && p.deg_y >= 0 && p.deg_x < (1 << 26) && p.deg_y < (1 << 26) &&
            p.limbs >= 1 && p.limbs <= RS_MAX_LIMBS;
   };
   int64_t words = 0;  // only steers the thread count
+  auto corr = [](const rs_bipoly &p) {  // sane p: (deg_x + 1)^2 (deg_y + 1) < 2^78 would overflow
+    const int64_t c = (int64_t)(p.deg_x + 1) * (p.deg_y + 1);
+    return c <= ((int64_t)1 << 26) ? c * (p.deg_x + 1) / 16 : 0;
+  };
   for (int i = 0; i < n; ++i)
-    if (sane(f[i]) && sane(g[i])) words += rs_input_words(f[i]) + rs_input_words(g[i]);
+    if (sane(f[i]) && sane(g[i])) words += rs_input_words(f[i]) + rs_input_words(g[i]) + corr(f[i]) + corr(g[i]);
   const int hw = std::max(1, (int)std::thread::hardware_concurrency());
   const int nt = (int)std::min<int64_t>({(int64_t)std::min(hw, 16), (int64_t)n, words / (int64_t(1) << 18) + 1});
   if (nt <= 1) {

@@ -6,10 +6,15 @@
 // deg R <= m n (total degrees).  D is the smaller of the two.
 //
 // Coefficient bound: R(x) = det S(x) and |coef_k R| <= max_{|x|=1} |R(x)|.
-// On |x| = 1, |f_j(x)| <= ||f_j||_1 (sum of |coefficients|), so by
-// Hadamard's inequality on the rows of S,
-//   |coef_k R| <= (sum_j ||f_j||_1^2)^{n_y/2} (sum_j ||g_j||_1^2)^{m_y/2}.
-// The same row-norm idea is the one the paper uses for its inclusion
+// An f-row of S at x = e^{it} has squared Euclidean norm
+//   T_f(t) = sum_j |f_j(e^{it})|^2 = a_0 + 2 sum_{k>=1} a_k cos(k t),
+//   a_k = sum_j sum_i f_{j,i} f_{j,i+k}   (the summed autocorrelation),
+// so T_f(t) <= a_0 + 2 sum_{k>=1} |a_k| =: H_f, and Hadamard's inequality on
+// the rows of S gives
+//   |coef_k R| <= H_f^{n_y/2} H_g^{m_y/2}.
+// H_f never exceeds sum_j ||f_j||_1^2 (the bound with |f_j(x)| <= ||f_j||_1,
+// ||.||_1 the sum of |coefficients|), which is also computed; the smaller
+// is used.  Both are the row-norm idea the paper uses for its inclusion
 // predicate (Section 3.2).  Logarithms are taken with upward margins.
 #include "planner.h"
 
@@ -69,6 +74,73 @@ double lse2(const std::vector<double> &xs) {
   return mx + log2(s) * (1.0 + 1e-12) + 1e-12;
 }
 
+// floor(c / 2^S) for a two's-complement limb integer c whose quotient fits
+// in an int64 (an arithmetic shift right by S bits).
+int64_t shr_floor(const uint32_t *c, int L, int S) {
+  const uint32_t ext = (c[L - 1] >> 31) ? 0xffffffffu : 0u;
+  const int w = S >> 5, o = S & 31;
+  auto limb = [&](int i) { return i < L ? c[i] : ext; };
+  const uint64_t u = ((uint64_t)limb(w + 1) << 32) | limb(w);
+  const uint64_t r = o ? (u >> o) | ((uint64_t)limb(w + 2) << (64 - o)) : u;
+  return (int64_t)r;
+}
+
+// log2 of H_f = a_0 + 2 sum_{k>=1} |a_k| (see the top of this file), rounded
+// up.  Every coefficient is cut to a = floor(c / 2^S) with |a| <= 2^20 + 1
+// (S from the largest magnitude, 2^maxbits), so c = 2^S (a + r), 0 <= r < 1,
+// and each product f_{j,i} f_{j,i+k} differs from 2^{2S} a a' by less than
+// 2^{2S} (|a| + |a'| + 1); summed over the products of a_k (weight 2 for
+// k >= 1) that is at most 2^{2S} sum_j 2 n_j (2 s_j + n_j) with s_j =
+// sum_i |a_{j,i}| and n_j the entries of row j.  Everything up to the final
+// logarithm is exact integer arithmetic: products below 2^42, row sums of at
+// most 2^14 of them in int64, sums over rows in 128 bits.
+double log2_autocorr_bound(const rs_bipoly *f, const std::vector<int> &dx, int maxbits) {
+  const int L = f->limbs, nx = f->deg_x + 1, ny = f->deg_y + 1, my = (int)dx.size() - 1;
+  const int S = std::max(0, maxbits - 20);
+  std::vector<int> len(my + 1, 0);  // row j holds f_{j,0..dx_j}
+  double work = 0.0;
+  int nmax = 0;
+  for (int j = 0; j <= my; ++j) {
+    len[j] = dx[j] + 1;
+    nmax = std::max(nmax, len[j]);
+    work += 0.5 * len[j] * len[j];
+  }
+  // long rows: keep the l1 bound (planning stays near linear in the input)
+  if (work > 0x1p27 || nmax > (1 << 14)) return INFINITY;
+  // rows padded with at least 4 zeros, so the products run in whole groups of 4
+  const int stride = ((nmax + 3) & ~3) + 4;
+  std::vector<int32_t> a((size_t)(my + 1) * stride, 0);
+  for (int i = 0; i < nmax; ++i)
+    for (int j = 0; j <= my; ++j)
+      if (i < len[j]) a[(size_t)j * stride + i] = (int32_t)shr_floor(f->coeffs + ((size_t)i * ny + j) * L, L, S);
+  std::vector<__int128> ac(nmax, 0);
+  __int128 trunc = 0;
+  for (int j = 0; j <= my; ++j) {
+    const int n = len[j];
+    if (n == 0) continue;
+    const int32_t *r = &a[(size_t)j * stride];
+    int64_t s1 = 0;
+    for (int i = 0; i < n; ++i) s1 += r[i] < 0 ? -(int64_t)r[i] : (int64_t)r[i];
+    if (S > 0) trunc += (__int128)(2 * (int64_t)n) * (2 * s1 + n);
+    for (int k = 0; k < n; ++k) {
+      const int m = n - k;  // terms i < m; r[i + k] = 0 for i >= m (padding)
+      int64_t u0 = 0, u1 = 0, u2 = 0, u3 = 0;  // four independent chains
+      for (int i = 0; i < m; i += 4) {
+        u0 += (int64_t)r[i] * r[i + k];
+        u1 += (int64_t)r[i + 1] * r[i + 1 + k];
+        u2 += (int64_t)r[i + 2] * r[i + 2 + k];
+        u3 += (int64_t)r[i + 3] * r[i + 3 + k];
+      }
+      ac[k] += (__int128)u0 + u1 + u2 + u3;
+    }
+  }
+  __int128 h = ac[0] + trunc;
+  for (int k = 1; k < nmax; ++k) h += 2 * (ac[k] < 0 ? -ac[k] : ac[k]);
+  if (h <= 0) return -INFINITY;
+  // (double) h errs by at most 2^-53 relative: inside the margins below
+  return 2.0 * S + log2((double)h) * (1.0 + 1e-12) + 1e-12;
+}
+
 int analyze(const rs_bipoly *f, PolyInfo &pi, const char **why) {
   if (!f || !f->coeffs) {
     *why = "NULL polynomial or coefficient pointer";
@@ -95,12 +167,16 @@ int analyze(const rs_bipoly *f, PolyInfo &pi, const char **why) {
   // at most 2^26 terms: the sums stay far below the double range).
   std::vector<double> acc((size_t)ny * (RS_MAX_LIMBS + 1), 0.0);
   std::vector<int> tmax(ny, -1);
+  int maxbits = 0;  // |c| <= 2^maxbits for every coefficient
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < ny; ++j) {
       const uint32_t *c = f->coeffs + ((size_t)i * ny + j) * L;
       double hi;
       const int t = abs_upper(c, L, &hi);
       if (t < 0) continue;
+      int e;  // hi < 2^e (hi >= 1)
+      frexp(hi, &e);
+      maxbits = std::max(maxbits, 32 * (t > 0 ? t - 1 : 0) + e);
       dx[j] = i;
       pi.mx = std::max(pi.mx, i);
       pi.tdeg = std::max(pi.tdeg, i + j);
@@ -119,7 +195,7 @@ int analyze(const rs_bipoly *f, PolyInfo &pi, const char **why) {
     pi.nc += pi.dx[j] + 1;
     if (tmax[j] >= 0) rows.push_back(2.0 * log2_scaled_sum(&acc[(size_t)j * (RS_MAX_LIMBS + 1)], tmax[j], rel));
   }
-  pi.log2_rownorm2 = lse2(rows);
+  pi.log2_rownorm2 = std::min(lse2(rows), log2_autocorr_bound(f, pi.dx, maxbits));
   return RS_OK;
 }
 

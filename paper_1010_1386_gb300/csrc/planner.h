@@ -16,7 +16,7 @@ struct PolyInfo {
   int stride = 1;  // row stride of the input array (deg_y extent + 1)
   int nc = 0;      // coefficients kept: sum_j (dx_j + 1)
   std::vector<int> dx;  // x-degree of f_j, j = 0..my (-1 for f_j = 0)
-  double log2_rownorm2 = 0.0;  // log2 of sum_j ||f_j||_1^2 (rounded up)
+  double log2_rownorm2 = 0.0;  // log2 of a bound on max_{|x|=1} sum_j |f_j(x)|^2 (rounded up)
 };
 
 struct PairPlan {
