@@ -559,8 +559,10 @@ def squarefree_main(args, world, rank, local, dist):
         "gpu_launches": args.steps * (bi["kernel_launches"] + 3),
         "clocks": clk,
         "e2e": {"value": value, "unit": "factorisations/s",
-                "h2d_bytes_per_step": bi["input_bytes"], "d2h_bytes_per_step": None,
-                "note": "the call is end to end (host inputs, host outputs); value is the same number"},
+                "h2d_bytes_per_step": last["h2d_bytes"], "d2h_bytes_per_step": last["d2h_bytes"],
+                "note": "the call is end to end (host inputs, host outputs); value is the same number; "
+                        "bytes are the call's own copies (inputs and CRT descriptors in; R's limbs, "
+                        "Yun headers and lifted factors out)"},
     })
     add_cpu_baseline(line, args, rank)
     if rank == 0:
@@ -600,22 +602,23 @@ def serving_main(args, world, rank, local, dist):
         t_start = time.perf_counter()
         th = threading.Thread(target=producer)
         th.start()
-        lat = []
+        lat, out_bytes = [], 0
         for i in range(n):
             while tickets[i] is None:
                 time.sleep(0.0001)
-            _, ms = srv.wait(tickets[i], raw=True)  # limbs into a host buffer, no Python ints
+            (deg, limbs, _), ms = srv.wait(tickets[i], raw=True)  # limbs into a host buffer, no Python ints
             lat.append(ms)
+            out_bytes += 4 * max(deg + 1, 0) * limbs
         th.join()
-        return time.perf_counter() - t_start, lat
+        return time.perf_counter() - t_start, lat, out_bytes
 
     barrier(dist, local)
     with ClockSampler(local) as clocks:
-        sat_s, sat_lat = run_stream(None)
+        sat_s, sat_lat, _ = run_stream(None)
         sat = n / sat_s
         rate = args.load * sat
         arrivals = np.cumsum(gaps) / rate
-        wall, lat = run_stream(arrivals)
+        wall, lat, out_bytes = run_stream(arrivals)
         barrier(dist, local)
     st = srv.stats()
     srv.stop()
@@ -637,8 +640,9 @@ def serving_main(args, world, rank, local, dist):
         "clocks": clocks.summary(),
         "e2e": {"value": value, "unit": "resultants/s",
                 "h2d_bytes_per_step": int(sum(f.coeffs.nbytes + g.coeffs.nbytes for f, g in pairs)),
-                "d2h_bytes_per_step": None,
-                "note": "every request crosses the C ABI with host buffers; latency is submit to result"},
+                "d2h_bytes_per_step": out_bytes,
+                "note": "every request crosses the C ABI with host buffers; latency is submit to result; "
+                        "the step is the whole stream, d2h the result limbs handed back"},
     })
     add_cpu_baseline(line, args, rank)
     if rank == 0:

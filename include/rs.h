@@ -268,6 +268,8 @@ typedef struct {
   float ms_host;        /* host work after the GPU pass: prime selection, contents, primitive parts */
   float ms_total;       /* wall time of the call */
   float ms_primitive;   /* of ms_host: the primitive parts of the lifted factors */
+  int64_t h2d_bytes;    /* host-to-device bytes the call copied (inputs, CRT descriptors) */
+  int64_t d2h_bytes;    /* device-to-host bytes the call copied (R's limbs, Yun headers, lifted factors) */
 } rs_sqf_info;
 
 int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info);

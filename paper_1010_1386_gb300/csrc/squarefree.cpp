@@ -500,6 +500,8 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     if (rc == RS_OK) rc = rs_run(b);
     if (rc == RS_OK) rc = rs_fetch_async(b);
     hdr.resize((size_t)b->nyun * hw);
+    info.h2d_bytes += b->in_words * 4;
+    info.d2h_bytes += b->out_words * 4 + (int64_t)b->nyun * hw * 4;
     if (rc == RS_OK && b->nyun) {
       cudaError_t e = cudaMemcpy2DAsync(hdr.data(), hw * 4, b->d_yun_out, (size_t)b->yun_ostride * 4, hw * 4,
                                         b->nyun, cudaMemcpyDeviceToHost, b->stream);
@@ -772,6 +774,8 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hwords.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
+      info.h2d_bytes += (int64_t)(piece[0] + piece[1] + piece[2] + piece[3]);
+      info.d2h_bytes += (int64_t)outw * 4;
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&info.ms_lift, lev[0], lev[1]);
     }
