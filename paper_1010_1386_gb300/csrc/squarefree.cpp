@@ -7,15 +7,17 @@
 // and Yun's algorithm mod every prime after G2 (kernels_yun.cu).  A prime is
 // used if R keeps its degree mod p and the square-free part mod p has the
 // largest degree seen (a smaller one means p divides a discriminant and
-// merged factors).  Every R_i divides F = pp(R), so by Mignotte's bound
-// (M. Mignotte, "An inequality about factors of polynomials", Math. Comp. 28,
-// 1974) |coef R_i| <= 2^{deg R_i} ||R||_2, and H_i = lc(R) R_i / lc(R_i) (the
-// residues lc(R) monic(R_i mod p) lift to it) has coefficients below
-// |lc R| 2^{deg R} ||R||_2 <= 2^{2 B + D + log2(D + 1) / 2}, B the resultant's
-// coefficient bits and D its degree bound.  The H_i are lifted by the CRT
-// kernels over the first K_H primes, then R_i = H_i / content(H_i) on the
-// host (binary gcd and exact division by Hensel's method), and c = sign(lc R)
-// content(R).
+// merged factors).  Every R_i divides R in Z[x], so by the Landau-Mignotte
+// bound (M. Mignotte, "An inequality about factors of polynomials", Math.
+// Comp. 28, 1974: with R = R_i G, M(R_i) = M(R) / M(G) <= M(R) |lc R_i| /
+// |lc R| since M(G) >= |lc G|, and ||h||_1 <= 2^{deg h} M(h), M(R) <=
+// ||R||_2)  ||R_i||_1 <= 2^{deg R_i} |lc R_i / lc R| ||R||_2.  So
+// H_i = lc(R) R_i / lc(R_i), the integer polynomial the residues
+// lc(R) monic(R_i mod p) lift to, has ||H_i||_1 <= 2^{deg R_i} ||R||_2
+// <= 2^{B + D + log2(D + 1) / 2}, B the resultant's coefficient bits and D its
+// degree bound.  The H_i are lifted by the CRT kernels over the first K_H
+// primes, then R_i = H_i / content(H_i) on the host (long division and
+// Lehmer's gcd), and c = sign(lc R) content(R).
 #include <string.h>
 
 #include <algorithm>
@@ -454,8 +456,9 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       p.status = RS_ERR_ARG;
       continue;
     }
-    // primes for the factors: coefficients of H_i below 2^bitsH
-    bitsH[i] = 2 * p.bits + p.D + (int)std::ceil(0.5 * std::log2((double)p.D + 1.0)) + 2;
+    // primes for the factors: coefficients of H_i below 2^bitsH (|coef R| < 2^bits,
+    // so ||R||_2 < 2^{bits + log2(D + 1) / 2}; one bit of margin)
+    bitsH[i] = p.bits + p.D + (int)std::ceil(0.5 * std::log2((double)p.D + 1.0)) + 1;
     double acc = 0.0;
     while (KH[i] < (int)ctx->log2p.size() && acc < bitsH[i] + 2) acc += ctx->log2p[KH[i]++];
     if (acc < bitsH[i] + 2) {

@@ -375,7 +375,7 @@ class Context:
             except RsError:
                 b = {"deg": 0, "limbs": 1, "bits": 0}
             D = max(b["deg"], 0)
-            lh = (2 * b["bits"] + D + int(math.ceil(0.5 * math.log2(D + 1))) + 3 + 31) // 32 + 1
+            lh = (b["bits"] + D + int(math.ceil(0.5 * math.log2(D + 1))) + 2 + 31) // 32 + 1
             cw.append(max(1, b["limbs"]))
             fw.append([max(1, (D // m + 1) * lh) for m in range(1, max_mult + 1)])
         for _ in range(2):  # the second call has the exact sizes the first reported

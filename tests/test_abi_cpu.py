@@ -2,6 +2,7 @@
 include/rs.h declares, and its host-side planner returns bounds that hold
 for the oracle's exact results.  No GPU compute is called."""
 import ctypes
+import math
 import os
 import random
 import re
@@ -131,6 +132,57 @@ def test_row_norm_bound_holds_on_adversarial_pairs(lib):
         R = exact.resultant_y(f, g)
         b = rs.result_bound(f, g)
         assert all(abs(c) < (1 << (b["bits"] - 1)) for c in R), case
+
+
+def test_factor_bound_holds_for_oracle_factorisations(lib):
+    """The square-free path lifts H_i = lc(R) R_i / lc(R_i) with primes for
+    coefficients below 2^(bits + D + ceil(log2(D + 1) / 2) + 1) (the
+    Landau-Mignotte bound with the leading-coefficient ratio, from the
+    planner's bits and D).  On resultants with planted repeated factors
+    (f = y - x, so Res_y(f, g) is g(x) up to sign, with g built from a square
+    and a cyclotomic-rich product; and Res_y(p q^2, (pq)_y) of small random
+    p, q) every H_i of the oracle's exact factorisation satisfies
+    ||H_i||_1 <= 2^(deg R_i) ||R||_2 and stays below that bound."""
+    from oracle import squarefree as sq
+    from oracle.exact import zx_mul
+    from paper_1010_1386_gb300.inputs import _dy, _from_dict, _mul_dict, _to_dict
+    rng = random.Random(26)
+
+    def poly_pow(a, k):
+        out = [1]
+        for _ in range(k):
+            out = zx_mul(out, a)
+        return out
+
+    cases = []
+    for gy in ([-1] + [0] * 14 + [1],                                         # y^15 - 1
+               zx_mul(poly_pow([1, 1], 3), poly_pow([-1, 0, 1], 2)),           # (y+1)^3 (y^2-1)^2
+               zx_mul(poly_pow([2, -3, 1], 2), [-1] + [0] * 20 + [1]),         # (y^2-3y+2)^2 (y^21-1)
+               zx_mul(poly_pow([rng.randint(-9, 9), rng.randint(-9, 9), 3], 2), [5, 0, 7, 1])):
+        cases.append(([[0, 1], [-1, 0]], [list(gy)]))  # f = y - x, g = gy(y)
+    for _ in range(4):
+        p = [[rng.randint(-4, 4) for _ in range(3)] for _ in range(2)]
+        q = [[rng.randint(-4, 4) for _ in range(2)] for _ in range(2)]
+        p[1][2] = q[1][1] = 1
+        pq = _mul_dict(_to_dict(p), _to_dict(q))
+        cases.append((_from_dict(_mul_dict(pq, _to_dict(q))), _from_dict(_dy(pq))))
+    checked = 0
+    for f, g in cases:
+        R = exact.resultant_y(f, g)
+        if len(R) < 2:
+            continue
+        b = rs.result_bound(f, g)
+        D = b["deg"]
+        bitsH = b["bits"] + D + math.ceil(0.5 * math.log2(D + 1)) + 1
+        norm2 = math.isqrt(sum(c * c for c in R)) + 1
+        c, facs = sq.squarefree(R)
+        for _, Ri in facs:
+            H = [R[-1] * v // Ri[-1] for v in Ri]
+            assert all(R[-1] * v % Ri[-1] == 0 for v in Ri)
+            assert sum(abs(v) for v in H) <= (1 << (len(Ri) - 1)) * norm2
+            assert max(abs(v) for v in H) < (1 << bitsH)
+            checked += 1
+    assert checked >= 10
 
 
 def test_planner_errors(lib):
