@@ -550,6 +550,9 @@ def squarefree_main(args, world, rank, local, dist):
                      "G3 (R)": bmean("ms_crt"), "lift (factor CRT)": mean("ms_lift"),
                      "host (selection, contents, primitive parts)": mean("ms_host"),
                      "host: primitive parts": mean("ms_primitive"),
+                     "host: analyse": mean("ms_analyse"),
+                     "host: R's contents": mean("ms_contents"),
+                     "host: lifted limbs fetch": mean("ms_fetch"),
                      "call": mean("ms_total")},
         "resultant_only": {"ms_per_step": statistics.mean(res_ms),
                            "value": npairs / (statistics.mean(res_ms) * 1e-3), "unit": "resultants/s",

@@ -270,6 +270,11 @@ typedef struct {
   float ms_primitive;   /* of ms_host: the primitive parts of the lifted factors */
   int64_t h2d_bytes;    /* host-to-device bytes the call copied (inputs, CRT descriptors) */
   int64_t d2h_bytes;    /* device-to-host bytes the call copied (R's limbs, Yun headers, lifted factors) */
+  float ms_analyse;     /* of ms_host: R unpacked, usable primes and factor degrees per pair */
+  float ms_contents;    /* of ms_host: R's contents, lc(R) / prod_i lc(R_i)^i (gcd of R's coefficients
+                           if that division is not exact) */
+  float ms_fetch;       /* of ms_host: waiting for the lifted factors' limbs after the contents */
+  float reserved;
 } rs_sqf_info;
 
 int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info);

@@ -17,7 +17,8 @@
 // <= 2^{B + D + log2(D + 1) / 2}, B the resultant's coefficient bits and D its
 // degree bound.  The H_i are lifted by the CRT kernels over the first K_H
 // primes, then R_i = H_i / content(H_i) on the host (long division and
-// Lehmer's gcd), and c = sign(lc R) content(R).
+// Lehmer's gcd), and c = lc(R) / prod_i lc(R_i)^i (an exact division, since
+// lc R = c prod_i lc(R_i)^i; the gcd of R's coefficients if it is not).
 #include <string.h>
 
 #include <algorithm>
@@ -206,6 +207,23 @@ Big big_divexact(Big a, Big b) {
   }
   trim(q);
   return q;
+}
+
+// a * b of magnitudes (schoolbook, 64-bit column sums).
+Big big_mul(const Big &a, const Big &b) {
+  if (a.empty() || b.empty()) return Big();
+  Big r(a.size() + b.size(), 0u);
+  for (size_t i = 0; i < a.size(); ++i) {
+    uint64_t carry = 0;
+    for (size_t j = 0; j < b.size(); ++j) {
+      const uint64_t t = (uint64_t)a[i] * b[j] + r[i + j] + carry;
+      r[i + j] = (uint32_t)t;
+      carry = t >> 32;
+    }
+    r[i + b.size()] = (uint32_t)carry;
+  }
+  trim(r);
+  return r;
 }
 
 // Quotient and remainder of magnitudes, b non-zero (D. E. Knuth, The Art of
@@ -538,6 +556,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   struct PairRes {
     int degR = -1, LR = 1;
     std::vector<uint32_t> Rw;  // R's limbs until its content is taken
+    Big lcR;                   // |lc R|
     Big content;
     bool lc_neg = false;
     std::vector<int> pattern;
@@ -565,6 +584,10 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       return;
     }
     q.lc_neg = (q.Rw[(size_t)q.degR * q.LR + q.LR - 1] >> 31) != 0;
+    {
+      bool ng;
+      q.lcR = from_twos(&q.Rw[(size_t)q.degR * q.LR], q.LR, &ng);
+    }
     if (q.degR == 0) return;
     // usable primes: R keeps its degree mod p, square-free part of largest degree
     auto task = [&](int k) { return &hdr[(size_t)(t0v[i] + k) * hw]; };
@@ -622,7 +645,9 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     std::vector<int> todo;
     for (int i = 0; i < n; ++i)
       if (st[i] == RS_OK) todo.push_back(i);
+    const auto ta = std::chrono::steady_clock::now();
     parallel_for((int)todo.size(), [&](int t) { analyse(todo[t]); });
+    info.ms_analyse = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ta).count();
   }
   // Outputs that are known now, and the factors to lift.
   struct Lift {
@@ -672,24 +697,16 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       off += d + 1;
     }
   }
-  // R's content c = sign(lc R) gcd(coefficients of R), per pair on host
-  // threads (run while the GPU lifts the factors).
-  auto contents = [&] {
-    std::vector<int> todo;
-    for (int i = 0; i < n; ++i)
-      if (st[i] == RS_OK && pr[i].degR >= 0) todo.push_back(i);
-    parallel_for((int)todo.size(), [&](int t) {
-      PairRes &q = pr[todo[t]];
-      std::vector<Big> Rm(q.degR + 1);
-      for (int j = 0; j <= q.degR; ++j) {
-        bool ng;
-        Rm[j] = from_twos(&q.Rw[(size_t)j * q.LR], q.LR, &ng);
-      }
-      q.content = content_of(Rm, nullptr);
-      std::vector<uint32_t>().swap(q.Rw);
-    });
+  // R's content as the gcd of its coefficients: the fallback of the content
+  // from the factors' leading coefficients (below).
+  auto content_by_gcd = [&](PairRes &q) {
+    std::vector<Big> Rm(q.degR + 1);
+    for (int j = 0; j <= q.degR; ++j) {
+      bool ng;
+      Rm[j] = from_twos(&q.Rw[(size_t)j * q.LR], q.LR, &ng);
+    }
+    q.content = content_of(Rm, nullptr);
   };
-  bool contents_done = false;
   // One CRT pass over every factor of every pair.
   const int nf = (int)lifts.size();
   std::vector<uint32_t> hwords((size_t)outw);
@@ -771,15 +788,13 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
         if (e == cudaSuccess) e = launch_g3bc((int)g3b.size(), (int)g3.size(), a3, d_g3, s);
         if (e == cudaSuccess) e = cudaEventRecord(lev[1], s);
       }
-      if (e == cudaSuccess) {  // host work while the lift runs
-        contents();
-        contents_done = true;
-      }
+      const auto tf = std::chrono::steady_clock::now();
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hwords.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
       info.h2d_bytes += (int64_t)(piece[0] + piece[1] + piece[2] + piece[3]);
       info.d2h_bytes += (int64_t)outw * 4;
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      info.ms_fetch = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf).count();
       if (e == cudaSuccess) e = cudaEventElapsedTime(&info.ms_lift, lev[0], lev[1]);
     }
     for (auto &x : lev)
@@ -790,16 +805,11 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
     }
   }
-  if (!contents_done) contents();
-  for (int i = 0; i < n; ++i) {
-    if (st[i] != RS_OK) continue;
-    const int r2 = put(content[i], {pr[i].content}, {(char)pr[i].lc_neg});
-    if (out_rc[i] == RS_OK) out_rc[i] = r2;
-  }
   // R_m = H_m / content(H_m), leading coefficient made positive; factors on
   // host threads
   const auto t_prim0 = std::chrono::steady_clock::now();
   std::vector<int> lift_rc(nf, RS_OK);
+  std::vector<Big> lcq(nf);  // lc of each primitive factor
   std::vector<int> order(nf);  // largest factors first
   for (int fi = 0; fi < nf; ++fi) order[fi] = fi;
   std::sort(order.begin(), order.end(), [&](int x, int y) { return lifts[x].pd.N > lifts[y].pd.N; });
@@ -815,23 +825,49 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       neg[j] = ng;
     }
     content_of(mag, &q);
+    lcq[fi] = q[pd.N - 1];
     const bool flip = neg[pd.N - 1] != 0;
     for (int j = 0; j < pd.N; ++j) neg[j] = q[j].empty() ? 0 : (char)((neg[j] != 0) != flip);
     lift_rc[fi] = put(factors[(size_t)lf.pair * M + lf.mult], q, neg);
   });
+  std::vector<Big> lcprod(n, Big{1u});  // prod_i lc(R_i)^i per pair
   for (int fi = 0; fi < nf; ++fi) {
     const Lift &lf = lifts[fi];
     if (out_rc[lf.pair] == RS_OK) out_rc[lf.pair] = lift_rc[fi];
     nmult[lf.pair] = std::max(nmult[lf.pair], lf.mult + 1);
+    for (int r = 0; r <= lf.mult; ++r) lcprod[lf.pair] = big_mul(lcprod[lf.pair], lcq[fi]);
   }
   const auto t_end = std::chrono::steady_clock::now();
+  // R's content: R = c prod_i R_i^i with R_i primitive and lc R_i > 0, so
+  // c = lc(R) / prod_i lc(R_i)^i, sign(c) = sign(lc R).  The division must be
+  // exact; if it is not (or a factor was not produced), the gcd of R's
+  // coefficients is taken instead.
+  {
+    std::vector<int> todo;
+    for (int i = 0; i < n; ++i)
+      if (st[i] == RS_OK) todo.push_back(i);
+    parallel_for((int)todo.size(), [&](int t) {
+      const int i = todo[t];
+      PairRes &q = pr[i];
+      Big r;
+      q.content = out_rc[i] == RS_OK ? big_divmod(q.lcR, lcprod[i], &r) : Big();
+      if (out_rc[i] != RS_OK || !r.empty() || q.content.empty()) content_by_gcd(q);
+      std::vector<uint32_t>().swap(q.Rw);
+    });
+    for (int i : todo) {
+      const int r2 = put(content[i], {pr[i].content}, {(char)pr[i].lc_neg});
+      if (out_rc[i] == RS_OK) out_rc[i] = r2;
+    }
+  }
+  const auto t_end2 = std::chrono::steady_clock::now();
+  info.ms_contents = (float)std::chrono::duration<double, std::milli>(t_end2 - t_end).count();
   auto ms = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point z) {
     return (float)std::chrono::duration<double, std::milli>(z - a).count();
   };
   info.factors = nf;
   info.ms_primitive = ms(t_prim0, t_end);
-  info.ms_host = ms(t_host0, t_end) - info.ms_lift;
-  info.ms_total = ms(t_start, t_end);
+  info.ms_host = ms(t_host0, t_end2) - info.ms_lift;
+  info.ms_total = ms(t_start, t_end2);
   ctx->sqf_info = info;
   int ret = RS_OK;
   for (int i = 0; i < n; ++i) {

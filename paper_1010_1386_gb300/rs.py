@@ -61,7 +61,9 @@ class rs_batch_info(ctypes.Structure):
 class rs_sqf_info(ctypes.Structure):
     _fields_ = [("batch", rs_batch_info), ("yun_tasks", c_int64), ("factors", c_int64),
                 ("ms_lift", c_float), ("ms_host", c_float), ("ms_total", c_float),
-                ("ms_primitive", c_float), ("h2d_bytes", c_int64), ("d2h_bytes", c_int64)]
+                ("ms_primitive", c_float), ("h2d_bytes", c_int64), ("d2h_bytes", c_int64),
+                ("ms_analyse", c_float), ("ms_contents", c_float), ("ms_fetch", c_float),
+                ("reserved", c_float)]
 
 
 class rs_server_stats(ctypes.Structure):
