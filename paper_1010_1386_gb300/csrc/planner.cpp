@@ -95,7 +95,7 @@ int64_t shr_floor(const uint32_t *c, int L, int S) {
 // logarithm is exact integer arithmetic: products below 2^42, row sums of at
 // most 2^14 of them in int64, sums over rows in 128 bits.
 double log2_autocorr_bound(const rs_bipoly *f, const std::vector<int> &dx, int maxbits) {
-  const int L = f->limbs, nx = f->deg_x + 1, ny = f->deg_y + 1, my = (int)dx.size() - 1;
+  const int L = f->limbs, ny = f->deg_y + 1, my = (int)dx.size() - 1;
   const int S = std::max(0, maxbits - 20);
   std::vector<int> len(my + 1, 0);  // row j holds f_{j,0..dx_j}
   double work = 0.0;

@@ -178,37 +178,6 @@ Big big_gcd(Big a, Big b) {
   return b;
 }
 
-// a / b for b dividing a exactly (Hensel division from the low limb).
-Big big_divexact(Big a, Big b) {
-  const int z = ctz(b);
-  shr_in_place(a, z);
-  shr_in_place(b, z);
-  if (b.size() == 1 && b[0] == 1u) return a;
-  uint32_t inv = b[0];  // b odd: Newton's iteration for b^-1 mod 2^32
-  for (int i = 0; i < 5; ++i) inv *= 2u - b[0] * inv;
-  const size_t nq = a.size() >= b.size() ? a.size() - b.size() + 1 : 0;
-  Big q(nq, 0u);
-  a.resize(std::max(a.size(), nq + b.size()) + 1, 0u);
-  for (size_t i = 0; i < nq; ++i) {
-    const uint32_t qi = a[i] * inv;
-    q[i] = qi;
-    uint64_t borrow = 0;  // a -= qi * b << (32 i)
-    for (size_t j = 0; j < b.size(); ++j) {
-      const uint64_t prod = (uint64_t)qi * b[j] + borrow;
-      const uint32_t lo = (uint32_t)prod;
-      borrow = (prod >> 32) + (a[i + j] < lo ? 1u : 0u);
-      a[i + j] -= lo;
-    }
-    for (size_t j = i + b.size(); borrow && j < a.size(); ++j) {
-      const uint32_t prev = a[j];
-      a[j] -= (uint32_t)borrow;
-      borrow = prev < (uint32_t)borrow ? 1u : 0u;
-    }
-  }
-  trim(q);
-  return q;
-}
-
 // a * b of magnitudes (schoolbook, 64-bit column sums).
 Big big_mul(const Big &a, const Big &b) {
   if (a.empty() || b.empty()) return Big();
