@@ -106,6 +106,12 @@ def test_row_norm_bound_matches_exact_integers(lib):
         b = rs.result_bound(f, g)
         want = _bits_exact(f, g)
         assert want <= b["bits"] <= want + 1, (case, want, b["bits"])
+    # the widest coefficients the ABI takes (128 limbs), negative ones among them
+    f = rand_bipoly(rng, 5, 3, bits=4000)
+    g = rand_bipoly(rng, 4, 2, bits=2000)
+    f[2][1] = -(1 << 4090) + 12345
+    want = _bits_exact(f, g)
+    assert want <= rs.result_bound(f, g)["bits"] <= want + 1
 
 
 def test_row_norm_bound_holds_on_adversarial_pairs(lib):
