@@ -264,7 +264,7 @@ typedef struct {
   rs_batch_info batch;  /* the GPU pass over the factors' primes (stage times, ms_yun) */
   int64_t yun_tasks;    /* (pair, prime) factorisations mod p */
   int64_t factors;      /* non-constant factors lifted */
-  float ms_lift;        /* CRT of the factors on the device */
+  float ms_lift;        /* CRT of the factors on the device (the lifted H_i, then the scaled primitive parts) */
   float ms_host;        /* host work after the GPU pass: prime selection, contents, primitive parts */
   float ms_total;       /* wall time of the call */
   float ms_primitive;   /* of ms_host: the primitive parts of the lifted factors */

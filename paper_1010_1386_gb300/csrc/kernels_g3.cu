@@ -288,7 +288,39 @@ __global__ void crt_w_kernel(const ModP *mods, int K, int32_t *wtab) {
   }
 }
 
+// One warp per (factor, prime): g mod p by Horner over g's limbs
+// (r <- r 2^32 + limb, with 2^32 = R mod p taken as mmul by R^2 mod p), its
+// inverse by Fermat, then the factor's residues times that inverse (plain
+// residues times a Montgomery-form value stay plain).  g = 0 mod p gives 0.
+__global__ void scale_kernel(const ScaleDesc *sd, int nf, int kmax, const ModP *mods, const uint32_t *gw,
+                             const uint32_t *in, uint32_t *out) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (int64_t)nf * kmax) return;
+  const int fi = (int)(warp / kmax), k = (int)(warp - (int64_t)fi * kmax);
+  const ScaleDesc d = sd[fi];
+  if (k >= d.k) return;
+  const ModP m = mods[k];
+  uint32_t r = 0u;
+  for (int l = d.g_len - 1; l >= 0; --l) {
+    uint32_t limb = gw[d.g_off + l];  // < 2^32 < 4p
+    while (limb >= m.p) limb -= m.p;
+    r = madd(mmul(r, m.r2, m), limb, m.p);
+  }
+  const uint32_t inv = minv(to_mont(r, m), m);
+  const uint32_t *src = in + d.src_off + (int64_t)k * d.src_stride;
+  uint32_t *dst = out + d.dst_off + (int64_t)k * d.n;
+  for (int j = lane; j < d.n; j += 32) dst[j] = mmul(src[j], inv, m);
+}
+
 }  // namespace
+
+cudaError_t launch_scale(const ScaleDesc *sd, int nf, int kmax, const ModP *mods, const uint32_t *gw,
+                         const uint32_t *in, uint32_t *out, cudaStream_t s) {
+  const int64_t warps = (int64_t)nf * kmax;
+  if (warps > 0) scale_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(sd, nf, kmax, mods, gw, in, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s, int jt) {
   G3Args at = a;

@@ -194,6 +194,16 @@ cudaError_t launch_g1s(int slots, int ntiles, size_t smem, const G1sArgs &a, cud
 cudaError_t launch_g1s_fallback(int blocks, size_t smem, const G1sArgs &a, cudaStream_t s);
 cudaError_t launch_g2s(int ntasks, size_t smem, const G2sArgs &a, cudaStream_t s);
 cudaError_t launch_g3bc(int nb, int nc, const G3Args &a, const int2 *otasks, cudaStream_t s);
+// Residues of one lifted factor divided by an integer g, prime by prime:
+// out[dst_off + k n + j] = in[src_off + k src_stride + j] * (g mod p_k)^{-1}
+// mod p_k for k < this factor's primes, j < n; g's 32-bit limbs (least
+// significant first) at gw[g_off .. g_off + g_len).
+struct ScaleDesc {
+  int64_t src_off, dst_off, g_off;
+  int32_t src_stride, n, k, g_len;
+};
+cudaError_t launch_scale(const ScaleDesc *sd, int nf, int kmax, const ModP *mods, const uint32_t *gw,
+                         const uint32_t *in, uint32_t *out, cudaStream_t s);
 cudaError_t launch_crt_tables(const ModP *mods, int K, int32_t *wtab, cudaStream_t s);
 cudaError_t launch_init_primes(const uint32_t *primes, int n, ModP *mods, uint32_t *vtab,
                                uint32_t *crt, uint32_t *qbase, cudaStream_t s);

@@ -680,8 +680,29 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   const int nf = (int)lifts.size();
   std::vector<uint32_t> hwords((size_t)outw);
   if (nf) {
+    // The CRT's digit kernel overwrites its residues with the mixed-radix
+    // digits, and the device path of the primitive parts (below) reads the
+    // residues of H_m again: the residues are first gathered (scaled by g = 1)
+    // into a compact copy, prime-major with stride N, which this pass consumes.
     std::vector<PairDesc> descs(nf);
-    for (int fi = 0; fi < nf; ++fi) descs[fi] = lifts[fi].pd;
+    std::vector<ScaleDesc> gat(nf);
+    int64_t qwA = 0;
+    for (int fi = 0; fi < nf; ++fi) {
+      const PairDesc &pd = lifts[fi].pd;
+      descs[fi] = pd;
+      descs[fi].img_off = qwA;
+      descs[fi].NI = pd.N;
+      ScaleDesc &u = gat[fi];
+      u.src_off = pd.img_off;
+      u.src_stride = pd.NI;
+      u.dst_off = qwA;
+      u.n = pd.N;
+      u.k = pd.K;
+      u.g_off = 0;
+      u.g_len = 1;
+      qwA += (int64_t)pd.K * pd.N;
+    }
+    const uint32_t one = 1u;
     std::vector<int2> g3d, g3;
     std::vector<int4> g3b;
     for (int fi = 0; fi < nf; ++fi) {
@@ -693,8 +714,9 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     }
     const int64_t shape_off = outw;
     auto round256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t piece[7] = {descs.size() * sizeof(PairDesc), g3d.size() * 8, g3.size() * 8, g3b.size() * 16,
-                             (size_t)xl * 4, (size_t)cy * 8, (size_t)(outw + 2 * (int64_t)nf) * 4};
+    const size_t piece[10] = {descs.size() * sizeof(PairDesc), g3d.size() * 8, g3.size() * 8, g3b.size() * 16,
+                              (size_t)xl * 4, (size_t)cy * 8, (size_t)(outw + 2 * (int64_t)nf) * 4,
+                              (size_t)qwA * 4, gat.size() * sizeof(ScaleDesc), sizeof(one)};
     size_t bytes = 0;
     for (size_t x : piece) bytes += round256(x);
     DevGuard dg(ctx->device);
@@ -725,7 +747,12 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       uint32_t *d_xl = (uint32_t *)carve(piece[4]);
       int64_t *d_cy = (int64_t *)carve(piece[5]);
       uint32_t *d_out = (uint32_t *)carve(piece[6]);
+      uint32_t *d_qA = (uint32_t *)carve(piece[7]);
+      ScaleDesc *d_gat = (ScaleDesc *)carve(piece[8]);
+      uint32_t *d_one = (uint32_t *)carve(piece[9]);
       e = cudaMemcpyAsync(d_desc, descs.data(), piece[0], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_gat, gat.data(), piece[8], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_one, &one, piece[9], cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3d, g3d.data(), piece[1], cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3, g3.data(), piece[2], cudaMemcpyHostToDevice, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3b, g3b.data(), piece[3], cudaMemcpyHostToDevice, s);
@@ -746,13 +773,14 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
         a3.p16 = tab.p16;
         a3.poff = tab.poff;
         a3.nh = tab.nh;
-        a3.coef = b->d_yun_out;  // residues of H_m, stride one Yun task (= one prime)
+        a3.coef = d_qA;  // residues of H_m gathered from the Yun output
         a3.xl = d_xl;
         a3.carry = d_cy;
         a3.out = d_out;
         a3.shape = reinterpret_cast<int32_t *>(d_out + shape_off);
         a3.kmax = kmax;
         e = cudaEventRecord(lev[0], s);
+        if (e == cudaSuccess) e = launch_scale(d_gat, nf, kmax, ctx->d_mods, d_one, b->d_yun_out, d_qA, s);
         if (e == cudaSuccess) e = launch_g3t((int)g3d.size(), a3, d_g3d, s);
         if (e == cudaSuccess) e = launch_g3bc((int)g3b.size(), (int)g3.size(), a3, d_g3, s);
         if (e == cudaSuccess) e = cudaEventRecord(lev[1], s);
@@ -760,7 +788,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       const auto tf = std::chrono::steady_clock::now();
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hwords.data(), d_out, (size_t)outw * 4, cudaMemcpyDeviceToHost, s);
-      info.h2d_bytes += (int64_t)(piece[0] + piece[1] + piece[2] + piece[3]);
+      info.h2d_bytes += (int64_t)(piece[0] + piece[1] + piece[2] + piece[3] + piece[8] + piece[9]);
       info.d2h_bytes += (int64_t)outw * 4;
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       info.ms_fetch = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf).count();
@@ -774,9 +802,199 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
       return rs_fail(ctx, RS_ERR_CUDA, std::string("square-free CRT: ") + cudaGetErrorString(e));
     }
   }
-  // R_m = H_m / content(H_m), leading coefficient made positive; factors on
-  // host threads
+  // Primitive parts R_m = H_m / content(H_m), first on the device.  g = gcd of
+  // lc(H_m) and a few coefficients of H_m is a multiple of content(H_m) and
+  // divides lc(H_m) = lc(R), so it is invertible modulo every lifting prime
+  // (each keeps deg R).  The device takes V = H_m g^{-1} mod each prime and
+  // its CRT in the symmetric range, so g V = H_m (mod P).  Since |H_m| < P/4
+  // (the factor bound), |g V| <= P/4 forces g V = H_m: g then divides every
+  // coefficient, g = content(H_m) and V = +-R_m.  A factor that fails this
+  // check (or any device step) takes the host path: content by running gcd
+  // and long division of every coefficient.
   const auto t_prim0 = std::chrono::steady_clock::now();
+  std::vector<char> dev_ok(nf, 0);
+  std::vector<int> qneed(nf, 0);
+  std::vector<int64_t> qoffh(nf, 0);
+  std::vector<uint32_t> qh;
+  if (nf) {
+    std::vector<Big> gc(nf);
+    parallel_for(nf, [&](int fi) {
+      const PairDesc &pd = lifts[fi].pd;
+      auto coef = [&](int j) {
+        bool ng;
+        return from_twos(&hwords[(size_t)(pd.out_off + (int64_t)j * pd.Lout)], pd.Lout, &ng);
+      };
+      Big g = coef(pd.N - 1);
+      const int picks[8] = {0, 1, 2, pd.N / 4, pd.N / 2, (3 * pd.N) / 4, pd.N - 3, pd.N - 2};
+      for (int t = 0; t < 8 && !(g.size() == 1 && g[0] == 1u); ++t) {
+        const int j = picks[t];
+        if (j < 0 || j >= pd.N - 1) continue;
+        const Big c = coef(j);
+        if (c.empty()) continue;
+        Big r;
+        big_divmod(c, g, &r);
+        if (!r.empty()) g = big_gcd_lehmer(g, r);
+      }
+      gc[fi] = std::move(g);
+    });
+    // second CRT pass over the scaled residues (compact: prime-major, stride N)
+    std::vector<PairDesc> dB(nf);
+    std::vector<ScaleDesc> sd(nf);
+    std::vector<uint32_t> gw;
+    int64_t qw = 0, xlB = 0, cyB = 0, outB = 0;
+    int kmaxB = 0;
+    for (int fi = 0; fi < nf; ++fi) {
+      const PairDesc &pd = lifts[fi].pd;
+      PairDesc q = pd;
+      const int LQ = (31 * pd.K + 31) / 32 + 1;  // any symmetric residue mod P < 2^(31 K)
+      const int64_t chunks = (LQ + 15) / 16;
+      q.img_off = qw;
+      q.NI = pd.N;
+      q.Lout = LQ;
+      q.xl_off = xlB;
+      xlB += (int64_t)pd.N * 16 * chunks;
+      q.cy_off = cyB;
+      cyB += (int64_t)pd.N * chunks;
+      q.out_off = outB;
+      outB += (int64_t)pd.N * LQ;
+      dB[fi] = q;
+      ScaleDesc &u = sd[fi];
+      u.src_off = pd.img_off;
+      u.src_stride = pd.NI;
+      u.dst_off = qw;
+      u.n = pd.N;
+      u.k = pd.K;
+      u.g_off = (int64_t)gw.size();
+      u.g_len = (int32_t)gc[fi].size();
+      gw.insert(gw.end(), gc[fi].begin(), gc[fi].end());
+      qw += (int64_t)pd.K * pd.N;
+      kmaxB = std::max(kmaxB, pd.K);
+    }
+    if (gw.empty()) gw.push_back(0u);
+    std::vector<int2> g3dB, g3B;
+    std::vector<int4> g3bB;
+    for (int fi = 0; fi < nf; ++fi) {
+      const PairDesc &q = dB[fi];
+      for (int j = 0; j < q.N; j += 32) g3dB.push_back(make_int2(fi, j));
+      for (int j = 0; j < q.N; j += 128) g3B.push_back(make_int2(fi, j));
+      for (int c = 0; c < (q.Lout + 15) / 16; ++c)
+        for (int j = 0; j < q.N; j += 128) g3bB.push_back(make_int4(fi, j, c, 0));
+    }
+    auto round256 = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t pc[10] = {dB.size() * sizeof(PairDesc), g3dB.size() * 8, g3B.size() * 8, g3bB.size() * 16,
+                           (size_t)xlB * 4, (size_t)cyB * 8, (size_t)(outB + 2 * (int64_t)nf) * 4,
+                           (size_t)qw * 4, gw.size() * 4, sd.size() * sizeof(ScaleDesc)};
+    size_t bytes = 0;
+    for (size_t x : pc) bytes += round256(x);
+    DevGuard dg(ctx->device);
+    cudaError_t e = cudaSuccess;
+    if (bytes > ctx->sqf_arena_bytes) {
+      if (ctx->sqf_arena) cudaFree(ctx->sqf_arena);
+      ctx->sqf_arena = nullptr;
+      ctx->sqf_arena_bytes = 0;
+      e = cudaMalloc(&ctx->sqf_arena, bytes);
+      if (e == cudaSuccess) ctx->sqf_arena_bytes = bytes;
+      else ctx->sqf_arena = nullptr;
+    }
+    cudaStream_t s = b->stream;
+    cudaEvent_t qev[2] = {nullptr, nullptr};
+    for (auto &x : qev)
+      if (e == cudaSuccess) e = cudaEventCreate(&x);
+    std::vector<int32_t> shp(2 * (size_t)nf, 0);
+    uint32_t *d_outB = nullptr;
+    if (e == cudaSuccess) {
+      char *cur = static_cast<char *>(ctx->sqf_arena);
+      auto carve = [&](size_t x) {
+        char *r = cur;
+        cur += round256(x);
+        return r;
+      };
+      PairDesc *d_desc = (PairDesc *)carve(pc[0]);
+      int2 *d_g3d = (int2 *)carve(pc[1]);
+      int2 *d_g3 = (int2 *)carve(pc[2]);
+      int4 *d_g3b = (int4 *)carve(pc[3]);
+      uint32_t *d_xl = (uint32_t *)carve(pc[4]);
+      int64_t *d_cy = (int64_t *)carve(pc[5]);
+      d_outB = (uint32_t *)carve(pc[6]);
+      uint32_t *d_q = (uint32_t *)carve(pc[7]);
+      uint32_t *d_gw = (uint32_t *)carve(pc[8]);
+      ScaleDesc *d_sd = (ScaleDesc *)carve(pc[9]);
+      e = cudaMemcpyAsync(d_desc, dB.data(), pc[0], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3d, g3dB.data(), pc[1], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3, g3B.data(), pc[2], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_g3b, g3bB.data(), pc[3], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_gw, gw.data(), pc[8], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_sd, sd.data(), pc[9], cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_outB + outB, 0, (size_t)nf * 8, s);
+      info.h2d_bytes += (int64_t)(pc[0] + pc[1] + pc[2] + pc[3] + pc[8] + pc[9]);
+      RsTables tab;
+      {
+        std::lock_guard<std::mutex> lock(ctx->tab_mu);
+        tab = ctx->tab;
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(qev[0], s);
+      if (e == cudaSuccess) e = launch_scale(d_sd, nf, kmaxB, ctx->d_mods, d_gw, b->d_yun_out, d_q, s);
+      if (e == cudaSuccess) {
+        G3Args a3;
+        memset(&a3, 0, sizeof(a3));
+        a3.pairs = d_desc;
+        a3.ctasks = d_g3b;
+        a3.mods = ctx->d_mods;
+        a3.crt = ctx->d_crt;
+        a3.wtab = tab.wtab;
+        a3.p16 = tab.p16;
+        a3.poff = tab.poff;
+        a3.nh = tab.nh;
+        a3.coef = d_q;
+        a3.xl = d_xl;
+        a3.carry = d_cy;
+        a3.out = d_outB;
+        a3.shape = reinterpret_cast<int32_t *>(d_outB + outB);
+        a3.kmax = kmaxB;
+        e = launch_g3t((int)g3dB.size(), a3, d_g3d, s);
+        if (e == cudaSuccess) e = launch_g3bc((int)g3bB.size(), (int)g3B.size(), a3, d_g3, s);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(qev[1], s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(shp.data(), d_outB + outB, (size_t)nf * 8, cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      float msB = 0.0f;
+      if (e == cudaSuccess && cudaEventElapsedTime(&msB, qev[0], qev[1]) == cudaSuccess) info.ms_lift += msB;
+    }
+    if (e == cudaSuccess) {
+      int64_t words = 0;
+      for (int fi = 0; fi < nf; ++fi) {
+        const PairDesc &q = dB[fi];
+        double log2P = 0.0;
+        for (int k = 0; k < q.K; ++k) log2P += ctx->log2p[k];
+        const int need = shp[2 * (size_t)fi + 1];
+        const int gbits = bitlen(gc[fi]);
+        // |V| < 2^(32 need - 1); |g V| <= P / 4 when gbits + 32 need - 1 <= log2 P - 2
+        if (shp[2 * (size_t)fi] == q.N && need >= 1 && need <= q.Lout &&
+            (double)gbits + 32.0 * need - 1.0 <= std::floor(log2P - 1e-6) - 2.0) {
+          dev_ok[fi] = 1;
+          qneed[fi] = need;
+          qoffh[fi] = words;
+          words += (int64_t)q.N * need;
+        }
+      }
+      qh.assign((size_t)std::max<int64_t>(words, 1), 0u);
+      for (int fi = 0; fi < nf && e == cudaSuccess; ++fi) {
+        if (!dev_ok[fi]) continue;
+        const PairDesc &q = dB[fi];
+        e = cudaMemcpy2DAsync(qh.data() + qoffh[fi], (size_t)qneed[fi] * 4, d_outB + q.out_off, (size_t)q.Lout * 4,
+                              (size_t)qneed[fi] * 4, q.N, cudaMemcpyDeviceToHost, s);
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      info.d2h_bytes += (int64_t)nf * 8 + words * 4;
+    }
+    for (auto &x : qev)
+      if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // a non-sticky failure: every factor takes the host path
+      std::fill(dev_ok.begin(), dev_ok.end(), 0);
+    }
+  }
   std::vector<int> lift_rc(nf, RS_OK);
   std::vector<Big> lcq(nf);  // lc of each primitive factor
   std::vector<int> order(nf);  // largest factors first
@@ -788,12 +1006,20 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     const PairDesc &pd = lf.pd;
     std::vector<Big> mag(pd.N), q;
     std::vector<char> neg(pd.N);
-    for (int j = 0; j < pd.N; ++j) {
-      bool ng;
-      mag[j] = from_twos(&hwords[(size_t)(pd.out_off + (int64_t)j * pd.Lout)], pd.Lout, &ng);
-      neg[j] = ng;
+    if (dev_ok[fi]) {  // V = +-R_m from the device
+      for (int j = 0; j < pd.N; ++j) {
+        bool ng;
+        q.push_back(from_twos(&qh[(size_t)(qoffh[fi] + (int64_t)j * qneed[fi])], qneed[fi], &ng));
+        neg[j] = ng;
+      }
+    } else {
+      for (int j = 0; j < pd.N; ++j) {
+        bool ng;
+        mag[j] = from_twos(&hwords[(size_t)(pd.out_off + (int64_t)j * pd.Lout)], pd.Lout, &ng);
+        neg[j] = ng;
+      }
+      content_of(mag, &q);
     }
-    content_of(mag, &q);
     lcq[fi] = q[pd.N - 1];
     const bool flip = neg[pd.N - 1] != 0;
     for (int j = 0; j < pd.N; ++j) neg[j] = q[j].empty() ? 0 : (char)((neg[j] != 0) != flip);
