@@ -559,6 +559,7 @@ def squarefree_main(args, world, rank, local, dist):
                            "value": npairs / (statistics.mean(res_ms) * 1e-3), "unit": "resultants/s",
                            "note": "same pairs, device-resident inputs, resultant primes only"},
         "factor_degrees_pair0": [(m, len(r) - 1) for m, r in out[1]],
+        "primitive_parts_on_device": "%d of %d factors" % (last["factors_device"], last["factors"]),
         "roofline": rf,
         "gpu_launches": args.steps * (bi["kernel_launches"] + 3),
         "clocks": clk,

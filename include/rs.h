@@ -274,7 +274,7 @@ typedef struct {
   float ms_contents;    /* of ms_host: R's contents, lc(R) / prod_i lc(R_i)^i (gcd of R's coefficients
                            if that division is not exact) */
   float ms_fetch;       /* of ms_host: waiting for the lifted factors' limbs after the contents */
-  float reserved;
+  int32_t factors_device; /* of factors: primitive parts taken on the device (the rest by host division) */
 } rs_sqf_info;
 
 int rs_squarefree_info_get(const rs_ctx *ctx, rs_sqf_info *info);

@@ -813,7 +813,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
   // and long division of every coefficient.
   const auto t_prim0 = std::chrono::steady_clock::now();
   std::vector<char> dev_ok(nf, 0);
-  std::vector<int> qneed(nf, 0);
+  std::vector<int> qneed(nf, 0), gbitsv(nf, 0), limP(nf, 0);
   std::vector<int64_t> qoffh(nf, 0);
   std::vector<uint32_t> qh;
   if (nf) {
@@ -968,10 +968,14 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
         double log2P = 0.0;
         for (int k = 0; k < q.K; ++k) log2P += ctx->log2p[k];
         const int need = shp[2 * (size_t)fi + 1];
-        const int gbits = bitlen(gc[fi]);
-        // |V| < 2^(32 need - 1); |g V| <= P / 4 when gbits + 32 need - 1 <= log2 P - 2
+        gbitsv[fi] = bitlen(gc[fi]);
+        limP[fi] = (int)std::floor(log2P - 1e-6) - 2;  // 2^limP <= P / 4
+        // |g V| <= P / 4 holds when gbits + (bits of the largest |V_j|) <= limP,
+        // checked exactly on the host once V is read; a coefficient that needs
+        // `need` limbs has more than 32 (need - 1) - 1 bits, so this filter
+        // only drops factors that would fail
         if (shp[2 * (size_t)fi] == q.N && need >= 1 && need <= q.Lout &&
-            (double)gbits + 32.0 * need - 1.0 <= std::floor(log2P - 1e-6) - 2.0) {
+            gbitsv[fi] + 32 * (need - 1) - 1 <= limP[fi]) {
           dev_ok[fi] = 1;
           qneed[fi] = need;
           qoffh[fi] = words;
@@ -1006,13 +1010,20 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     const PairDesc &pd = lf.pd;
     std::vector<Big> mag(pd.N), q;
     std::vector<char> neg(pd.N);
-    if (dev_ok[fi]) {  // V = +-R_m from the device
+    if (dev_ok[fi]) {  // V = +-R_m from the device, if |g V| <= P / 4
+      int vbits = 0;
       for (int j = 0; j < pd.N; ++j) {
         bool ng;
         q.push_back(from_twos(&qh[(size_t)(qoffh[fi] + (int64_t)j * qneed[fi])], qneed[fi], &ng));
         neg[j] = ng;
+        vbits = std::max(vbits, bitlen(q.back()));
       }
-    } else {
+      if (gbitsv[fi] + vbits > limP[fi]) {
+        dev_ok[fi] = 0;
+        q.clear();
+      }
+    }
+    if (!dev_ok[fi]) {
       for (int j = 0; j < pd.N; ++j) {
         bool ng;
         mag[j] = from_twos(&hwords[(size_t)(pd.out_off + (int64_t)j * pd.Lout)], pd.Lout, &ng);
@@ -1025,6 +1036,7 @@ extern "C" int rs_squarefree_batch(rs_ctx *ctx, int32_t n, const rs_bipoly *f, c
     for (int j = 0; j < pd.N; ++j) neg[j] = q[j].empty() ? 0 : (char)((neg[j] != 0) != flip);
     lift_rc[fi] = put(factors[(size_t)lf.pair * M + lf.mult], q, neg);
   });
+  info.factors_device = (int32_t)std::count(dev_ok.begin(), dev_ok.end(), (char)1);
   std::vector<Big> lcprod(n, Big{1u});  // prod_i lc(R_i)^i per pair
   for (int fi = 0; fi < nf; ++fi) {
     const Lift &lf = lifts[fi];

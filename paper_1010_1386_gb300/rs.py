@@ -63,7 +63,7 @@ class rs_sqf_info(ctypes.Structure):
                 ("ms_lift", c_float), ("ms_host", c_float), ("ms_total", c_float),
                 ("ms_primitive", c_float), ("h2d_bytes", c_int64), ("d2h_bytes", c_int64),
                 ("ms_analyse", c_float), ("ms_contents", c_float), ("ms_fetch", c_float),
-                ("reserved", c_float)]
+                ("factors_device", c_int32)]
 
 
 class rs_server_stats(ctypes.Structure):

@@ -112,6 +112,8 @@ def test_nongeneric_workload_full_size(ctx):
             assert len(_gcd_mod(A, B, q)) == 1
     assert all(P[-1] > 0 for _, P in facs) and [m for m, _ in facs] == sorted(m for m, _ in facs)
     assert [m for m, _ in facs] == [1, 2, 3]
+    info = ctx.squarefree_info()  # every primitive part passed the device check
+    assert info["factors"] == 3 and info["factors_device"] == 3
 
 
 def test_batch_mixed_pairs(ctx):
@@ -122,6 +124,8 @@ def test_batch_mixed_pairs(ctx):
     pairs += [(rand_bipoly(rng, 3, 3, bits=40), rand_bipoly(rng, 2, 4, bits=5)) for _ in range(3)]
     pairs += [([[3]], [[0, 1]]), ([[0, 1]], [[0, 2]]), ([[0, 1]], [[0, 0, 0, 1], [0], [0], [-1]])]
     got = ctx.squarefree_batch(pairs)
+    info = ctx.squarefree_info()
+    assert info["factors"] > 0 and info["factors_device"] == info["factors"]
     for i, ((f, g), r) in enumerate(zip(pairs, got)):
         R = exact.resultant_y(f, g)
         if not R:
