@@ -1,7 +1,12 @@
 """Shared helpers of the test-suite (test infrastructure, not product code)."""
+import glob
+import os
 import random
 
 from oracle import exact, modp
+from oracle.exact import zx_add, zx_mul, zx_trim
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def rand_bipoly(rng, dx, dy, bits=20, density=1.0):
@@ -48,3 +53,99 @@ def exact_points(f, g, R, points=(0, 1, -1)):
 
 def coprime_rng(seed):
     return random.Random(seed)
+
+
+def golden_var(path):
+    """'y' for Res_y fixtures, 'x' for files with a `var: x` line."""
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line.startswith("var:"):
+            return line.split(":")[1].strip()
+    return "y"
+
+
+def load_golden(path):
+    f, g, R = {}, {}, {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line or line.startswith("var:"):
+            continue
+        tag, rest = line.split(":")
+        nums = [int(t) for t in rest.split()]
+        if tag == "R":
+            R[nums[0]] = nums[1]
+        else:
+            (f if tag == "f" else g)[(nums[0], nums[1])] = nums[2]
+
+    def dense(d):
+        nx = max(i for i, _ in d) + 1
+        ny = max(j for _, j in d) + 1
+        rows = [[0] * ny for _ in range(nx)]
+        for (i, j), c in d.items():
+            rows[i][j] = c
+        return rows
+
+    deg = max(R) if R else -1
+    return dense(f), dense(g), zx_trim([R.get(k, 0) for k in range(deg + 1)])
+
+
+ALL_GOLDEN = sorted(glob.glob(os.path.join(GOLDEN_DIR, "*.txt")))
+GOLDEN = [p for p in ALL_GOLDEN if golden_var(p) == "y"]
+GOLDEN_X = [p for p in ALL_GOLDEN if golden_var(p) == "x"]
+
+
+def subst_y(g, alpha):
+    """g(x, alpha(x)) in Z[x]."""
+    gy = exact.y_coefficients(g)
+    out, powa = [], [1]
+    for gj in gy:
+        out = zx_add(out, zx_mul(gj, powa))
+        powa = zx_mul(powa, alpha)
+    return out
+
+
+def from_factors(a, alphas):
+    """a(x) * prod (y - alpha_i(x)) as a dense f[i][j]."""
+    poly = [list(a)]  # list over y-degree of Z[x] polys
+    for al in alphas:
+        nxt = [[] for _ in range(len(poly) + 1)]
+        for j, c in enumerate(poly):
+            nxt[j + 1] = zx_add(nxt[j + 1], c)
+            nxt[j] = zx_add(nxt[j], zx_mul(c, [-t for t in al]))
+        poly = nxt
+    nx = max(len(c) for c in poly)
+    return [[(poly[j][i] if i < len(poly[j]) else 0) for j in range(len(poly))] for i in range(nx)]
+
+
+# ------------------------------------------------- full-size expected values
+
+_FULL = {}
+
+
+def full_size_records(name):
+    """Expected (degree, bits, SHA-256) of every instance of a full-size
+    workload, written by tests/golden/make_full_size.py from the oracle O2."""
+    import json
+    if not _FULL:
+        _FULL.update(json.load(open(os.path.join(GOLDEN_DIR, "full_size.json")))["workloads"])
+    return _FULL[name]["results"]
+
+
+def assert_full_size(name, results, pairs=None, offset=0):
+    """Every coefficient of every result equals the oracle's: the digest of
+    the exact coefficient list must match the stored one.  On a mismatch the
+    first failing instance is recomputed with O2 (when ``pairs`` is given)
+    to name the first differing coefficient."""
+    from oracle import modular
+    recs = full_size_records(name)[offset:offset + len(results)]
+    assert len(recs) == len(results), f"{name}: {len(results)} results, {len(recs)} expected values"
+    bad = [i for i, (R, rec) in enumerate(zip(results, recs)) if modular.digest(R) != rec["sha256"]]
+    if bad and pairs is not None:
+        i = bad[0]
+        want = modular.resultant(*pairs[i])
+        got = results[i]
+        first = next((k for k in range(max(len(want), len(got)))
+                      if (want[k] if k < len(want) else 0) != (got[k] if k < len(got) else 0)), None)
+        raise AssertionError(f"{name}: {len(bad)} of {len(results)} differ; instance {offset + i}: "
+                             f"degree {len(got) - 1} vs {len(want) - 1}, first differing coefficient {first}")
+    assert not bad, f"{name}: instances {[offset + i for i in bad[:10]]} differ from the oracle"

@@ -66,7 +66,7 @@ def test_random_small_pairs_exact(schur):
 
 
 def test_golden_examples(schur):
-    from tests.test_oracle_pins import GOLDEN, load_golden
+    from tests.helpers import GOLDEN, load_golden
     for path in GOLDEN:
         f, g, R = load_golden(path)
         assert schur.resultant_y(f, g) == R
@@ -156,7 +156,7 @@ def test_triangular_interpolation_exact(tri):
         pairs.append((f, g))
     for (f, g), R in zip(pairs, tri.resultant_batch(pairs)):
         assert R == exact.resultant_y(f, g)
-    from tests.test_oracle_pins import GOLDEN, load_golden
+    from tests.helpers import GOLDEN, load_golden
     for path in GOLDEN:
         f, g, R = load_golden(path)
         assert tri.resultant_y(f, g) == R

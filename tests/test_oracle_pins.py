@@ -13,6 +13,7 @@ import pytest
 
 from oracle import exact, modp
 from oracle.exact import zx_add, zx_mul, zx_trim
+from tests.helpers import ALL_GOLDEN, GOLDEN, GOLDEN_X, from_factors, golden_var, load_golden, subst_y  # noqa: F401
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -25,43 +26,7 @@ def rand_bipoly(rng, dx, dy, bound=20, density=1.0):
     return f
 
 
-def golden_var(path):
-    """'y' for Res_y fixtures, 'x' for files with a `var: x` line."""
-    for line in open(path):
-        line = line.split("#")[0].strip()
-        if line.startswith("var:"):
-            return line.split(":")[1].strip()
-    return "y"
 
-
-def load_golden(path):
-    f, g, R = {}, {}, {}
-    for line in open(path):
-        line = line.split("#")[0].strip()
-        if not line or line.startswith("var:"):
-            continue
-        tag, rest = line.split(":")
-        nums = [int(t) for t in rest.split()]
-        if tag == "R":
-            R[nums[0]] = nums[1]
-        else:
-            (f if tag == "f" else g)[(nums[0], nums[1])] = nums[2]
-
-    def dense(d):
-        nx = max(i for i, _ in d) + 1
-        ny = max(j for _, j in d) + 1
-        rows = [[0] * ny for _ in range(nx)]
-        for (i, j), c in d.items():
-            rows[i][j] = c
-        return rows
-
-    deg = max(R) if R else -1
-    return dense(f), dense(g), zx_trim([R.get(k, 0) for k in range(deg + 1)])
-
-
-ALL_GOLDEN = sorted(glob.glob(os.path.join(HERE, "golden", "*.txt")))
-GOLDEN = [p for p in ALL_GOLDEN if golden_var(p) == "y"]
-GOLDEN_X = [p for p in ALL_GOLDEN if golden_var(p) == "x"]
 
 
 @pytest.mark.parametrize("path", GOLDEN, ids=[os.path.basename(p) for p in GOLDEN])
@@ -140,29 +105,6 @@ def test_leibniz_bareiss_kronecker_interp_agree():
         assert exact.resultant_y_interp(f, g) == ref
 
 
-def _subst_y(g, alpha):
-    """g(x, alpha(x)) in Z[x]."""
-    gy = exact.y_coefficients(g)
-    out, powa = [], [1]
-    for gj in gy:
-        out = zx_add(out, zx_mul(gj, powa))
-        powa = zx_mul(powa, alpha)
-    return out
-
-
-def _from_factors(a, alphas):
-    """a(x) * prod (y - alpha_i(x)) as a dense f[i][j]."""
-    poly = [list(a)]  # list over y-degree of Z[x] polys
-    for al in alphas:
-        nxt = [[] for _ in range(len(poly) + 1)]
-        for j, c in enumerate(poly):
-            nxt[j + 1] = zx_add(nxt[j + 1], c)
-            nxt[j] = zx_add(nxt[j], zx_mul(c, [-t for t in al]))
-        poly = nxt
-    nx = max(len(c) for c in poly)
-    return [[(poly[j][i] if i < len(poly[j]) else 0) for j in range(len(poly))] for i in range(nx)]
-
-
 @pytest.mark.parametrize("seed", range(6))
 def test_product_formula(seed):
     """Res_y(f, g) = a^{n_y} prod_i g(x, alpha_i(x)) for f = a prod (y - alpha_i)."""
@@ -170,14 +112,14 @@ def test_product_formula(seed):
     a = [rng.randint(-5, 5) for _ in range(rng.randint(1, 3))]
     a[-1] = a[-1] or 2
     alphas = [[rng.randint(-4, 4) for _ in range(rng.randint(1, 3))] for _ in range(rng.randint(1, 4))]
-    f = _from_factors(a, alphas)
+    f = from_factors(a, alphas)
     g = rand_bipoly(rng, rng.randint(0, 3), rng.randint(1, 4), bound=9)
     ny = len(exact.y_coefficients(g)) - 1
     expect = [1]
     for _ in range(ny):
         expect = zx_mul(expect, zx_trim(a))
     for al in alphas:
-        expect = zx_mul(expect, _subst_y(g, al))
+        expect = zx_mul(expect, subst_y(g, al))
     assert exact.resultant_y(f, g) == expect
     assert exact.resultant_y_interp(f, g) == expect
     if len(alphas) + ny <= 6:
@@ -318,14 +260,14 @@ def test_planted_mistakes_are_caught(monkeypatch, bad):
         a[-1] = a[-1] or 2
         alphas = [[rng.randint(-4, 4) for _ in range(rng.randint(1, 3))]
                   for _ in range(rng.randint(1, 4))]
-        f = _from_factors(a, alphas)
+        f = from_factors(a, alphas)
         g = rand_bipoly(rng, rng.randint(0, 3), rng.randint(1, 4), bound=9)
         ny = len(exact.y_coefficients(g)) - 1
         expect = [1]
         for _ in range(ny):
             expect = zx_mul(expect, zx_trim(a))
         for al in alphas:
-            expect = zx_mul(expect, _subst_y(g, al))
+            expect = zx_mul(expect, subst_y(g, al))
         caught |= exact.resultant_y(f, g) != expect
     assert caught
 
