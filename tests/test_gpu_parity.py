@@ -1,11 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Small inputs are compared coefficient by coefficient with the exact oracle;
-full-size workloads are checked on sampled values the oracle computes one by
-one: R(0), R(1), R(-1) exactly (determinants of integer Sylvester matrices),
-R(x0) mod q for random x0 and primes q outside the library's table, every
-sampled modular image z_i^{(p)} against det S(x_i) mod p, the degree bound
-and the coefficient bound.  Expected values never come from the GPU.
+Small inputs are compared coefficient by coefficient with the exact oracle
+O1; every instance of the full-size workloads (configs[1], all 512 pairs of
+configs[2], all 32 pairs of configs[3] and its coprime variant, the first
+512 requests of configs[4]) is compared coefficient by coefficient with the
+independent modular oracle O2 through the stored digests of its exact
+results (tests/golden/full_size.json).  Sampled modular images are checked
+against det S(x_i) mod p at the library's own points.  Expected values never
+come from the GPU.
 """
 import random
 
@@ -14,7 +16,7 @@ import pytest
 
 from oracle import exact, modp
 from paper_1010_1386_gb300 import inputs, rs
-from tests.helpers import check_sampled_31, eval_mod, exact_points, rand_bipoly
+from tests.helpers import assert_full_size, check_sampled_31, eval_mod, rand_bipoly
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +55,7 @@ def test_random_small_pairs_exact(ctx):
 
 
 def test_golden_examples(ctx):
-    from tests.test_oracle_pins import GOLDEN, load_golden
+    from tests.helpers import GOLDEN, load_golden
     for path in GOLDEN:
         f, g, R = load_golden(path)
         assert ctx.resultant_y(f, g) == R
@@ -156,32 +158,29 @@ def test_images_against_oracle(ctx):
 # ---------------------------------------------------------- full-size configs
 
 def test_single_dense30_full_size(ctx):
+    """configs[1] (dense total degree 30, signed 32-bit): every coefficient
+    against the oracle O2, the planner's bounds, and sampled images against
+    the result reduced at the library's own points."""
     [(f, g)] = inputs.workload_single(1)
-    F, G = f.to_ints(), g.to_ints()
     R = ctx.resultant_y(f, g)
+    assert_full_size("c1_single", [R], [(f, g)])
     bound = rs.result_bound(f, g)
     assert len(R) - 1 <= bound["deg"] == 900
     assert max(abs(c) for c in R).bit_length() < bound["bits"]
-    exact_points(F, G, R, points=(0, 1, -1, 2))
-    check_sampled_31(F, G, R, random.Random(7), samples=3)
     primes, pts, imgs = ctx.images(f, g, 3, 901)
     for k in range(3):
         for i in (0, 1, 450, 900):
             assert int(imgs[k, i]) == eval_mod(R, int(pts[k, i]), int(primes[k]))
 
 
-def test_batch_full_size_sampled(ctx):
+def test_batch_full_size_exact(ctx):
+    """configs[2], all 512 pairs in one batch: every coefficient of every
+    resultant against the oracle O2, and the degree bound."""
     pairs = inputs.workload_batch(2, n=512)
     got = ctx.resultant_batch(pairs)
-    rng = random.Random(8)
-    small = sorted(range(512), key=lambda i: pairs[i][0].deg_x * pairs[i][0].deg_y)[:2]
-    for i, ((f, g), R) in enumerate(zip(pairs, got)):
-        b = rs.result_bound(f, g)
-        assert len(R) - 1 <= b["deg"]
-        F, G = f.to_ints(), g.to_ints()
-        check_sampled_31(F, G, R, rng, samples=1)
-        if i in small or i < 2:
-            exact_points(F, G, R, points=(0,))
+    assert_full_size("c2_batch", got, pairs)
+    for (f, g), R in zip(pairs, got):
+        assert len(R) - 1 <= rs.result_bound(f, g)["deg"]
 
 
 def test_nongeneric_literal_is_zero(ctx):
@@ -195,22 +194,23 @@ def test_nongeneric_literal_is_zero(ctx):
         info = b.info()
         b.close()
     assert all(R == [] for R in got)
+    assert_full_size("c3_nongeneric", got, pairs)
     assert info["degenerate_images"] == info["images"]
 
 
 def test_nongeneric_coprime_full_size(ctx):
     """The coprime topology workload at full size (f = p q^2, g = d(pq)/dy,
-    total degrees 48 and 35, 64-bit coefficients): sampled values against
-    the oracle for every pair, and for the first pair the exact identity
-    Res_y(p q^2, g) = Res_y(p, g) Res_y(q, g)^2 from three GPU resultants."""
+    total degrees 48 and 35, 64-bit coefficients): every coefficient of all
+    32 resultants against the oracle O2, and for the first pair the exact
+    identity Res_y(p q^2, g) = Res_y(p, g) Res_y(q, g)^2 from three GPU
+    resultants."""
     pairs = inputs.workload_nongeneric(3, n=32, coprime=True)
     got = ctx.resultant_batch(pairs)
-    rng = random.Random(31)
+    assert_full_size("c3p_nongeneric_coprime", got, pairs)
     for (f, g), R in zip(pairs, got):
         b = rs.result_bound(f, g)
         assert len(R) - 1 <= b["deg"]
         assert R and max(abs(c) for c in R).bit_length() < b["bits"]
-        check_sampled_31(f.to_ints(), g.to_ints(), R, rng, samples=1)
     # the generator's first draw, replayed: p and q of pair 0
     from paper_1010_1386_gb300.inputs import _dy, _from_dict, _mul_dict, _to_dict
     g0 = np.random.Generator(np.random.PCG64(3))
@@ -221,6 +221,15 @@ def test_nongeneric_coprime_full_size(ctx):
     assert f0 == pairs[0][0].to_ints() and gg == pairs[0][1].to_ints()
     Rp, Rq = ctx.resultant_batch([(p, gg), (q, gg)])
     assert got[0] == exact.zx_mul(Rp, exact.zx_mul(Rq, Rq))
+
+
+def test_serving_requests_batched_exact(ctx):
+    """The first 512 requests of the serving stream (total degrees 8..64,
+    16..128-bit coefficients) in one batch: every coefficient against the
+    oracle O2."""
+    pairs, _ = inputs.workload_serving(4, n=512)
+    got = ctx.resultant_batch(pairs)
+    assert_full_size("c4_serving_first512", got, pairs)
 
 
 def test_nongeneric_coprime_multiplicative(ctx):
@@ -321,17 +330,17 @@ def test_product_formula_full_size(ctx):
     (y - alpha_i(x)) (plain Z[x] arithmetic, no determinant): m_y = 30,
     n_y = 20, deg R = 1000, coefficients of up to about 3,700 bits."""
     from oracle.exact import zx_mul, zx_trim
-    from tests.test_oracle_pins import _from_factors, _subst_y
+    from tests.helpers import from_factors, subst_y
     rng = random.Random(11)
     a = [rng.randint(-40, 40) for _ in range(3)]
     a[-1] = a[-1] or 7
     alphas = [[rng.randint(-40, 40), rng.randint(-40, 40) or 1] for _ in range(30)]
-    f = _from_factors(a, alphas)
+    f = from_factors(a, alphas)
     g = rand_bipoly(rng, 12, 20, bits=20)
     expect = [1]
     for _ in range(20):
         expect = zx_mul(expect, zx_trim(a))
     for al in alphas:
-        expect = zx_mul(expect, _subst_y(g, al))
+        expect = zx_mul(expect, subst_y(g, al))
     got = ctx.resultant_y(f, g)
     assert len(got) == 1001 and got == expect

@@ -1,16 +1,17 @@
 """Both projections (Section 3.1): R^{(x)} = res(f, g, x) through
 rs_resultant_x and the paired call rs_projections, against the oracle's own
-x-resultant (exact on small inputs and the worked examples; sampled values
-on the random-curve workload with coefficients shifted by 2^k, whose
-resultants need up to ~2000 primes)."""
+x-resultant (exact on small inputs and the worked examples), and every
+coefficient of both projections of the random-curve workload with
+coefficients shifted by 2^k (up to ~2000 primes per resultant) against the
+independent modular oracle O2."""
 import random
 
 import pytest
 
-from oracle import exact, modp
+from oracle import exact
 from paper_1010_1386_gb300 import inputs, rs
-from tests.helpers import check_sampled_31, eval_mod, rand_bipoly
-from tests.test_oracle_pins import GOLDEN_X, load_golden
+from tests.helpers import assert_full_size, rand_bipoly
+from tests.helpers import GOLDEN_X, load_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -53,25 +54,18 @@ def test_projections_match_single_calls_and_oracle(ctx):
     assert exact.zx_eval(ry, 3) == 0 and exact.zx_eval(rx, -2) == 0
 
 
-@pytest.mark.parametrize("deg,sparse,k", [(9, False, 128), (9, True, 2048), (15, False, 512)])
+@pytest.mark.parametrize("deg,sparse,k", [(9, False, 128), (9, True, 2048), (15, False, 512), (15, False, 2048)])
 def test_shift_workload_projections(ctx, deg, sparse, k):
-    """All 10 pairs of five random curves scaled by 2^k (constant term + 1):
-    both projections within their bounds, R^{(y)} and R^{(x)} matching the
-    oracle's determinant at a random point modulo a prime outside the
-    library's table, and exactly at x = 0 (y = 0) for the first pair."""
+    """All 10 pairs of five random curves scaled by 2^k (constant term + 1),
+    up to about 2,000 primes per resultant: every coefficient of both
+    projections against the oracle O2, and the planner's bounds."""
     pairs = inputs.workload_shift(5, deg, sparse, k)
     Ry, Rx = ctx.projections(pairs)
-    rng = random.Random(53 + deg + k)
-    for i, ((f, g), ry, rx) in enumerate(zip(pairs, Ry, Rx)):
-        F, G = f.to_ints(), g.to_ints()
-        by, bx = rs.result_bound(f, g), rs.result_bound(rs.swap_xy(f), rs.swap_xy(g))
+    name = f"shift_{deg}_{'sparse' if sparse else 'dense'}_{k}"
+    swapped = [(inputs.swap_xy(f), inputs.swap_xy(g)) for f, g in pairs]
+    assert_full_size(name, Ry, pairs)
+    assert_full_size(name, Rx, swapped, offset=len(pairs))
+    for (f, g), (fs, gs), ry, rx in zip(pairs, swapped, Ry, Rx):
+        by, bx = rs.result_bound(f, g), rs.result_bound(fs, gs)
         assert len(ry) - 1 <= by["deg"] and max(abs(c) for c in ry).bit_length() < by["bits"]
         assert len(rx) - 1 <= bx["deg"] and max(abs(c) for c in rx).bit_length() < bx["bits"]
-        check_sampled_31(F, G, ry, rng, samples=1)
-        FT, GT = exact.transpose(F), exact.transpose(G)
-        q = 998244353
-        y0 = rng.randrange(q)
-        assert eval_mod(rx, y0, q) == modp.resultant_image(FT, GT, q, y0)
-        if i == 0:
-            assert exact.zx_eval(ry, 0) == exact.resultant_y_at(F, G, 0)
-            assert exact.zx_eval(rx, 0) == exact.resultant_y_at(FT, GT, 0)
