@@ -62,13 +62,14 @@ SHIFT = (15, 512, False)  # shift workload (degree, k, sparse); main() sets it f
 
 def load_pairs(workload, npairs=None, rank=0, args=None):
     """The workload's pairs; under weak scaling rank r > 0 draws its own
-    batch of the same distribution (seed + 1000 r)."""
-    from paper_1010_1386_gb300 import inputs, rs
+    batch of the same distribution (seed + 1000 r).  Uses the seeded
+    generators only (no library)."""
+    from paper_1010_1386_gb300 import inputs
     from paper_1010_1386_gb300.sharding import rank_seed
     if workload == "shift":
         deg, k, sparse = (args.shift_deg, args.shift_k, args.shift_sparse) if args else SHIFT
         base = inputs.workload_shift(rank_seed(5, rank), deg, sparse, k)
-        pairs = base + [(rs.swap_xy(f), rs.swap_xy(g)) for f, g in base]  # R^{(y)}, then R^{(x)}
+        pairs = base + [(inputs.swap_xy(f), inputs.swap_xy(g)) for f, g in base]  # R^{(y)}, then R^{(x)}
         return pairs[:npairs] if npairs else pairs
     if workload == "batch":
         pairs = inputs.workload_batch(rank_seed(2, rank), n=512)
@@ -81,45 +82,47 @@ def load_pairs(workload, npairs=None, rank=0, args=None):
     elif workload == "nongeneric-coprime":
         pairs = inputs.workload_nongeneric(rank_seed(3, rank), n=32, coprime=True)
     else:
-        pairs = inputs.workload_serving(4, n=10000)[0]
+        pairs = inputs.workload_serving(4, n=npairs or 10000)[0]
     return pairs[:npairs] if npairs else pairs
 
 
 # ------------------------------------------------------------ CPU oracle leg
 
-def _oracle_point(args):
-    f, g, x0 = args
-    from oracle import exact
-    t = time.perf_counter()
-    exact.resultant_y_at(f, g, x0)
-    return time.perf_counter() - t
+def cpu_threads():
+    return os.cpu_count() or 1
 
 
-def oracle_sample(workload, npairs, seed, cores):
-    """Time the oracle's exact Sylvester determinant at the middle evaluation
-    point for ``npairs`` sampled pairs (one process each) and extrapolate to
-    its full evaluation-interpolation resultant: (D + 1) determinants per pair
-    (interpolation not counted).  Returns (resultants/s over ``cores``
-    processes, description)."""
+def oracle_sample(workload, seconds, seed, threads, args=None):
+    """Time the independent modular oracle O2 (``oracle.modular``: its own
+    plan, every image, interpolation and CRT -- the whole algorithm) on a
+    seeded random sample of the workload's pairs, on ``threads`` host
+    threads.  Chunks of ``threads`` pairs are drawn without replacement and
+    run until ``seconds`` of wall time are spent (the whole workload if it
+    is done first; a one-pair workload is repeated).  Returns
+    (resultants/s, pairs timed, description)."""
     import random
-    from paper_1010_1386_gb300 import rs
-    pairs = load_pairs(workload, 512 if workload == "serving" else None)
-    idx = random.Random(seed).sample(range(len(pairs)), min(npairs, len(pairs)))
-    jobs, points = [], []
-    for i in idx:
-        f, g = pairs[i]
-        d = rs.result_bound(f, g)["deg"]
-        points.append(d + 1)
-        jobs.append((f.to_ints(), g.to_ints(), d // 2))
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(min(cores, len(jobs))) as pool:
-        times = pool.map(_oracle_point, jobs)
-    per_pair = statistics.mean(t * n for t, n in zip(times, points))
-    value = cores / per_pair
-    desc = (f"exact integer Sylvester determinant at x = D/2 for {len(jobs)} random pairs "
-            f"(mean {statistics.mean(times):.2f} s each), scaled by D+1 points per pair, "
-            f"interpolation not counted; {cores} processes")
-    return value, desc
+    from oracle import modular
+    modular.load()
+    pairs = load_pairs(workload, 512 if workload == "serving" else None, 0, args)
+    order = list(range(len(pairs)))
+    random.Random(seed).shuffle(order)
+    done, wall, pos = 0, 0.0, 0
+    while wall < seconds:
+        if pos >= len(order):
+            if len(pairs) > 1:
+                break
+            pos = 0
+        chunk = order[pos:pos + threads]
+        pos += len(chunk)
+        t = time.perf_counter()
+        modular.resultants([pairs[i] for i in chunk], threads=threads)
+        wall += time.perf_counter() - t
+        done += len(chunk)
+    total = len(pairs) if workload != "serving" else 10000
+    desc = (f"measured: oracle O2 (C, whole algorithm: plan, Euclid/Sylvester images at x = 0..D, "
+            f"Lagrange interpolation, CRT) on {done} {'random ' if len(pairs) > 1 else ''}pair(s) "
+            f"of the {total} in {wall:.1f} s wall, {threads} threads")
+    return done / wall, done, desc
 
 
 def _oracle_sqf(args):
@@ -283,45 +286,70 @@ def base_line(args, world, value, ms, workload_desc, extra_cfg):
 
 
 def add_cpu_baseline(line, args, rank):
-    if rank != 0 or args.no_baseline:
+    """``cpu_baseline``: the oracle as it stands, timed on this host's cores
+    (rank 0 at N = 1 only; about args.baseline_seconds of CPU work)."""
+    if rank != 0 or args.no_baseline or int(os.environ.get("WORLD_SIZE", "1")) > 1:
         return
-    cores = min(os.cpu_count() or 1, 8)
+    threads = cpu_threads()
     if args.workload == "squarefree":
-        v, desc = oracle_sqf_sample(8, 7, cores)
-        line["cpu_baseline"] = {"value": v, "unit": "factorisations/s", "cores": cores, "kind": "oracle",
+        v, desc = oracle_sqf_sample(threads, 7, threads)
+        line["cpu_baseline"] = {"value": v, "unit": "factorisations/s", "cores": threads, "kind": "oracle",
                                 "sample": desc}
         return
-    n = 8 if args.workload in ("batch", "serving", "nongeneric", "nongeneric-coprime") else 1
-    v, desc = oracle_sample(args.workload, n, 7, cores)
-    line["cpu_baseline"] = {"value": v, "unit": "resultants/s", "cores": cores, "kind": "oracle",
-                            "sample": desc}
+    v, n, desc = oracle_sample(args.workload, args.baseline_seconds, 7, threads, args)
+    line["cpu_baseline"] = {"value": v, "unit": "resultants/s", "cores": threads, "kind": "oracle",
+                            "sample": desc, "pairs": n}
 
 
 # ------------------------------------------------------------------ legs
 
 def reference_main(args, world, rank, dist):
+    """The reference arm: the oracle O2 on this host's cores, the same
+    workload, metric and unit as the GPU arm.  Each step is a seeded random
+    sample of the workload (``threads`` pairs, or the whole workload if it
+    is smaller; a one-pair workload runs once per step); value = pairs timed
+    / wall time of the timed steps.  Loads no GPU library.  Under torchrun
+    only rank 0 works."""
     if rank != 0:
         return
-    cores = min(os.cpu_count() or 1, 2)
-    vals, t0 = [], time.perf_counter()
-    desc = ""
+    import random
+    from oracle import modular
+    threads = cpu_threads()
     sqf = args.workload == "squarefree"
     unit = "factorisations/s" if sqf else "resultants/s"
-    for s in range(args.warmup + args.steps):
-        if sqf:
-            v, desc = oracle_sqf_sample(2, 1000 + s, cores)
-        else:
-            v, desc = oracle_sample(args.workload, 2, 1000 + s, cores)
-        if s >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
-    wall = time.perf_counter() - t0
-    line = base_line(args, 1, value, 1000.0 * wall / (args.steps + args.warmup),
-                     WORKLOADS[args.workload], {})
+    if sqf:
+        vals = []
+        desc = ""
+        t0 = time.perf_counter()
+        for s in range(args.warmup + args.steps):
+            v, desc = oracle_sqf_sample(threads, 1000 + s, threads)
+            if s >= args.warmup:
+                vals.append(v)
+        value = statistics.mean(vals)
+        ms = 1000.0 * (time.perf_counter() - t0) / (args.steps + args.warmup)
+    else:
+        modular.load()
+        pairs = load_pairs(args.workload, 512 if args.workload == "serving" else None, 0, args)
+        per_step = min(len(pairs), threads)
+        done, wall = 0, 0.0
+        for s in range(args.warmup + args.steps):
+            idx = random.Random(1000 + s).sample(range(len(pairs)), per_step)
+            t = time.perf_counter()
+            modular.resultants([pairs[i] for i in idx], threads=threads)
+            dt = time.perf_counter() - t
+            if s >= args.warmup:
+                done += per_step
+                wall += dt
+        value = done / wall
+        ms = 1000.0 * wall / args.steps
+        desc = (f"measured: oracle O2 (C, whole algorithm: plan, Euclid/Sylvester images at x = 0..D, "
+                f"Lagrange interpolation, CRT), {args.steps} timed steps of {per_step} seeded random "
+                f"pair(s) each ({done} pairs, {wall:.1f} s wall), {threads} threads")
+    line = base_line(args, 1, value, ms, WORKLOADS[args.workload], {})
     if sqf:
         line.update({"metric": SQF_METRIC, "unit": unit})
-    line.update({"impl": "reference", "dtype": "int (Python big integers)",
-                 "cpu_baseline": {"value": value, "unit": unit, "cores": cores,
+    line.update({"impl": "reference", "dtype": "u32 modular (64-bit products), bignum CRT",
+                 "cpu_baseline": {"value": value, "unit": unit, "cores": threads,
                                   "kind": "oracle", "sample": desc},
                  "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0}})
@@ -663,6 +691,8 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
+    ap.add_argument("--baseline-seconds", type=float, default=15.0,
+                    help="wall seconds of oracle work for cpu_baseline")
     ap.add_argument("--shift-deg", type=int, default=15, help="shift workload: total degree (9 or 15)")
     ap.add_argument("--shift-k", type=int, default=512, help="shift workload: coefficients times 2^k")
     ap.add_argument("--shift-sparse", action="store_true", help="shift workload: sparse curves")

@@ -58,6 +58,11 @@ class BiPoly:
         return BiPoly(out)
 
 
+def swap_xy(f):
+    """The same polynomial with x and y exchanged (a layout change only)."""
+    return BiPoly(np.ascontiguousarray(f.coeffs.transpose(1, 0, 2)))
+
+
 def signed_uniform_limbs(rng, shape, bits, limbs):
     """Uniform integers in [-2^(bits-1), 2^(bits-1)) as two's-complement
     limbs, shape ``shape + (limbs,)``; needs limbs * 32 >= bits."""
