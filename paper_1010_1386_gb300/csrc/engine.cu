@@ -246,20 +246,23 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
     e = launch_tables(ctx->d_mods, ctx->d_qbase, nt.K, nt.N, nt.cstride, nt.finv, nt.gtab, nt.btab,
                       nt.hq, nt.qc, nt.qn, nt.qp, ctx->stream);
   // Chinese-remaindering tables for the same primes.
-  std::vector<int32_t> poff(nt.K + 1, 0);
-  for (int k = 0; k < nt.K; ++k) poff[k + 1] = poff[k] + p16_row(k);
+  // Rows 0..K of the prefix products: row K (the product of all K primes of
+  // a pair that uses every table prime) gives floor(P / 2) to the limb kernel.
+  std::vector<int32_t> poff(nt.K + 2, 0);
+  for (int k = 0; k <= nt.K; ++k) poff[k + 1] = poff[k] + p16_row(k);
   if (e == cudaSuccess) e = cudaMalloc(&nt.wtab, std::max<size_t>(1, (size_t)nt.K * (nt.K - 1) / 2) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&nt.p16, (size_t)poff[nt.K] * 2);
-  if (e == cudaSuccess) e = cudaMalloc(&nt.poff, (size_t)(nt.K + 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&nt.nh, (size_t)nt.K * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.p16, (size_t)poff[nt.K + 1] * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.poff, (size_t)(nt.K + 2) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&nt.nh, (size_t)(nt.K + 1) * 4);
   // Prefix products P_k = p_0 ... p_{k-1} as 16-bit digits (row k at poff[k],
-  // zero padded to its reserved length) and nh[k] = digits up to the top
-  // non-zero one, built on the host: P_{k+1} = P_k p_k on 32-bit limbs.
-  std::vector<uint16_t> p16((size_t)poff[nt.K], 0);
-  std::vector<int32_t> nh(nt.K, 0);
+  // zero padded to its reserved length; read as 32-bit limbs by the limb
+  // kernels) and nh[k] = digits up to the top non-zero one, built on the
+  // host: P_{k+1} = P_k p_k on 32-bit limbs.
+  std::vector<uint16_t> p16((size_t)poff[nt.K + 1], 0);
+  std::vector<int32_t> nh(nt.K + 1, 0);
   {
     std::vector<uint32_t> limbs(1, 1u);
-    for (int k = 0; k < nt.K; ++k) {
+    for (int k = 0; k <= nt.K; ++k) {
       uint16_t *row = p16.data() + poff[k];
       const int reserved = poff[k + 1] - poff[k];
       int top = 0;
@@ -269,6 +272,7 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
         if (d) top = i + 1;
       }
       nh[k] = top;
+      if (k == nt.K) break;
       uint64_t carry = 0;
       for (uint32_t &l : limbs) {
         const uint64_t v = (uint64_t)l * ctx->primes[k] + carry;

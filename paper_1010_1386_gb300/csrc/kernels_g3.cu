@@ -11,11 +11,12 @@
 // G3t: the digits, in tiles of 32 coefficients by blocks of 64 digits (a
 //      rectangular update from the earlier digits, then a small triangular
 //      solve), every dot product lazily accumulated in int64.
-// G3b: one thread per (coefficient, chunk of 32 sixteen-bit digits of R_j)
-//      accumulates sum_k v_k P_k[h] exactly in int64 (|v_k P_k[h]| < 2^46)
-//      and normalises the chunk, keeping its carry.
-// G3c: one thread per coefficient ripples the chunk carries and writes the
-//      two's-complement 32-bit limbs.
+// G3b: one thread per (coefficient, chunk of 16 limbs of R_j) accumulates
+//      sum_k w_k P_k[h] with the offset digits w_k = v_k + (p_k - 1)/2 >= 0
+//      in 96-bit carry chains and normalises the chunk, keeping its carry.
+// G3c: one block per 128 coefficients ripples the chunk carries, subtracts
+//      floor(P/2) = sum_k (p_k - 1)/2 P_k and writes the two's-complement
+//      32-bit limbs through shared memory in coalesced runs.
 #include <algorithm>
 
 #include "../../include/rs.h"
@@ -175,15 +176,30 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
   }
 }
 
-// Limb chunks: blockDim = 128 coefficients of one pair, one 32-digit chunk.
-__global__ void g3b_kernel(G3Args a) {
+// a2:a1:a0 += x * y (96-bit accumulator, one carry chain).
+__device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t x, uint32_t y) {
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(a0), "+r"(a1), "+r"(a2)
+      : "r"(x), "r"(y));
+}
+
+// Limb chunks: blockDim = 128 coefficients of one pair, one chunk of 16
+// output limbs.  With the offset digits w_k = v_k + (p_k - 1)/2 in [0, p_k)
+// the limb sums S[h] = sum_k w_k P_k[16 c + h] (P_k's 32-bit limbs) are
+// unsigned and below K 2^63, so each is kept in a 96-bit carry chain; the
+// chunk is then normalised into 16 limbs and a carry (< 2^47).  Only primes
+// whose prefix product reaches this chunk contribute to it directly; lower
+// terms arrive through the previous chunk's carry.
+__global__ void __launch_bounds__(128) g3b_kernel(G3Args a) {
   const int4 task = a.ctasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const int c = task.z;
   const int j = task.y + (int)threadIdx.x;
   if (j >= pd.N) return;
   const int K = pd.K, N = pd.N;
-  // first k whose prefix product has a digit in this chunk (nh is increasing)
+  // first k whose prefix product has a limb in this chunk (nh is increasing)
   int lo = 0, hi = K;
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
@@ -192,80 +208,97 @@ __global__ void g3b_kernel(G3Args a) {
     else
       lo = mid + 1;
   }
-  int64_t acc[32];
+  uint32_t a0[16], a1[16], a2[16];
 #pragma unroll
-  for (int h = 0; h < 32; ++h) acc[h] = 0;
+  for (int h = 0; h < 16; ++h) a0[h] = a1[h] = a2[h] = 0u;
   const uint32_t *col = a.coef + pd.img_off + j;
+#pragma unroll 2
   for (int k = lo; k < K; ++k) {
-    const int32_t v = (int32_t)col[(size_t)k * pd.NI];
-    const uint4 *row = reinterpret_cast<const uint4 *>(a.p16 + a.poff[k] + 32 * c);
+    const uint32_t half = (__ldg(&a.mods[k].p) - 1u) >> 1;
+    const uint32_t w = (uint32_t)((int32_t)col[(size_t)k * pd.NI] + (int32_t)half);
+    const uint4 *row = reinterpret_cast<const uint4 *>(a.p16 + __ldg(a.poff + k) + 32 * c);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const uint4 w = row[q];
-      const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        acc[8 * q + 2 * e] = rs_mac_s32(acc[8 * q + 2 * e], v, (int32_t)(ws[e] & 0xffffu));
-        acc[8 * q + 2 * e + 1] = rs_mac_s32(acc[8 * q + 2 * e + 1], v, (int32_t)(ws[e] >> 16));
-      }
+      const uint4 l4 = __ldg(row + q);
+      mac96(a0[4 * q], a1[4 * q], a2[4 * q], w, l4.x);
+      mac96(a0[4 * q + 1], a1[4 * q + 1], a2[4 * q + 1], w, l4.y);
+      mac96(a0[4 * q + 2], a1[4 * q + 2], a2[4 * q + 2], w, l4.z);
+      mac96(a0[4 * q + 3], a1[4 * q + 3], a2[4 * q + 3], w, l4.w);
     }
   }
-  int64_t carry = 0;
+  uint64_t carry = 0;
   uint32_t *xl = a.xl + pd.xl_off + j;
 #pragma unroll
-  for (int w = 0; w < 16; ++w) {
-    const int64_t t0 = acc[2 * w] + carry;
-    const uint32_t d0 = (uint32_t)t0 & 0xffffu;
-    carry = (t0 - (int64_t)d0) >> 16;
-    const int64_t t1 = acc[2 * w + 1] + carry;
-    const uint32_t d1 = (uint32_t)t1 & 0xffffu;
-    carry = (t1 - (int64_t)d1) >> 16;
-    xl[(size_t)(16 * c + w) * N] = d0 | (d1 << 16);
+  for (int h = 0; h < 16; ++h) {
+    const uint64_t lo64 = ((uint64_t)a1[h] << 32) | a0[h];
+    const uint64_t t = lo64 + carry;
+    const uint64_t ovf = t < lo64 ? 1u : 0u;
+    xl[(size_t)(16 * c + h) * N] = (uint32_t)t;
+    carry = (t >> 32) + (((uint64_t)a2[h] + ovf) << 32);
   }
-  a.carry[pd.cy_off + (size_t)c * N + j] = carry;
+  a.carry[pd.cy_off + (size_t)c * N + j] = (int64_t)carry;
 }
 
-// Carries and output: one thread per coefficient.  Also records the shape of
-// each pair's result: shape[2 pair] = 1 + the largest index of a non-zero
-// coefficient (0 for R = 0) and shape[2 pair + 1] = the most two's-complement
-// limbs any coefficient needs (both by atomicMax on zeroed words).
-__global__ void g3c_kernel(G3Args a) {
+// Carries and output: one thread per coefficient adds the chunk carries to
+// the chunk limbs and subtracts floor(P / 2), P = p_0 ... p_{K-1} (the offset
+// digits added sum_k (p_k - 1)/2 P_k = (P - 1)/2), giving the symmetric
+// representative in two's complement; only the Lout low limbs are formed,
+// which is exact because the result fits in them.  Each chunk's 16 limbs of
+// the block's 128 coefficients are staged in shared memory and written back
+// as runs of 16 consecutive limbs of one coefficient (out is
+// [coefficient][limb], so a warp's store covers two 64-byte runs instead of
+// 32 words Lout apart).  Also records the shape of each pair's result:
+// shape[2 pair] = 1 + the largest index of a non-zero coefficient (0 for
+// R = 0) and shape[2 pair + 1] = the most two's-complement limbs any
+// coefficient needs (both by atomicMax on zeroed words).
+__global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
+  __shared__ uint32_t T[128 * 17];  // T[t * 17 + w]: limb 16 c + w of coefficient j0 + t
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
-  const int j = task.y + (int)threadIdx.x;
-  if (j >= pd.N) return;
+  const int t = (int)threadIdx.x, j0 = task.y, j = j0 + t;
+  const bool live = j < pd.N;
   const int N = pd.N, L = pd.Lout, C = (L + 15) / 16;
   const uint32_t *xl = a.xl + pd.xl_off + j;
-  uint32_t *o = a.out + pd.out_off + (size_t)j * L;
+  const int p0 = __ldg(a.poff + pd.K);
+  const uint32_t *PK = reinterpret_cast<const uint32_t *>(a.p16 + p0);  // P's 32-bit limbs
+  const int plen = (__ldg(a.poff + pd.K + 1) - p0) / 2;
+  uint32_t *o = a.out + pd.out_off;
   int64_t r = 0;
   int last_nz = -1, last_nf = -1;  // last limb != 0, last limb != 0xffffffff
   uint32_t top_nz = 0u, top_nf = 0u, top = 0u;
   for (int c = 0; c < C; ++c) {
-    for (int w = 0; w < 16; ++w) {
-      const uint32_t word = xl[(size_t)(16 * c + w) * N];
-      const int64_t t0 = (int64_t)(word & 0xffffu) + r;
-      const uint32_t e0 = (uint32_t)t0 & 0xffffu;
-      r = (t0 - (int64_t)e0) >> 16;
-      const int64_t t1 = (int64_t)(word >> 16) + r;
-      const uint32_t e1 = (uint32_t)t1 & 0xffffu;
-      r = (t1 - (int64_t)e1) >> 16;
-      const int l = 16 * c + w;
-      if (l < L) {
-        const uint32_t limb = e0 | (e1 << 16);
-        o[l] = limb;
-        if (limb != 0u) {
-          last_nz = l;
-          top_nz = limb;
+    if (live) {
+      for (int w = 0; w < 16; ++w) {
+        const int l = 16 * c + w;
+        const uint32_t h = (l < plen ? (__ldg(PK + l) >> 1) : 0u) | (l + 1 < plen ? (__ldg(PK + l + 1) << 31) : 0u);
+        const int64_t v = (int64_t)xl[(size_t)l * N] + r - (int64_t)h;
+        const uint32_t limb = (uint32_t)v;
+        r = v >> 32;
+        T[t * 17 + w] = limb;
+        if (l < L) {
+          if (limb != 0u) {
+            last_nz = l;
+            top_nz = limb;
+          }
+          if (limb != 0xffffffffu) {
+            last_nf = l;
+            top_nf = limb;
+          }
+          top = limb;
         }
-        if (limb != 0xffffffffu) {
-          last_nf = l;
-          top_nf = limb;
-        }
-        top = limb;
       }
+      r += a.carry[pd.cy_off + (size_t)c * N + j];
     }
-    r += a.carry[pd.cy_off + (size_t)c * N + j];
+    __syncthreads();
+    const int nl = min(16, L - 16 * c);  // limbs of this chunk that exist
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+      const int e = q * 128 + t, jj = e >> 4, w = e & 15;
+      if (j0 + jj < N && w < nl) o[(size_t)(j0 + jj) * L + 16 * c + w] = T[jj * 17 + w];
+    }
+    __syncthreads();
   }
+  if (!live) return;
   // fewest limbs whose two's-complement value is this coefficient
   const bool neg = (top >> 31) != 0u;
   if (!neg && last_nz < 0) return;  // a zero coefficient
