@@ -425,8 +425,13 @@ int rs_server_stop(rs_ctx *ctx);
  * calls on a device share the one array: calls whose kernels overlap on the
  * GPU (other streams, other host threads) race and must be serialised by the
  * caller.  No cudaMalloc, cudaFree or other allocating routine is called.
+ * Cost: one thread per coefficient runs the whole O(nprimes^2) digit
+ * recurrence and writes its limbs with a stride of `limbs` words, so at
+ * nprimes near 2048 it is far slower than the resultant pipeline's CRT.
  * Returns RS_OK, RS_ERR_ARG, RS_ERR_LIMIT or RS_ERR_CUDA (rs_last_error is
- * not updated by this call). */
+ * not updated by this call).  RS_ERR_CUDA is returned only for a launch
+ * error that appears during this call; a CUDA error already pending on the
+ * calling thread from earlier work is left pending for its owner. */
 int rs_crt_noalloc(const uint32_t *residues, int32_t nprimes, int32_t ncoeffs, int32_t limbs,
                    uint32_t *out, void *stream);
 

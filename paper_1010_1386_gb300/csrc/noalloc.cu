@@ -13,9 +13,12 @@
 // radix digits in the symmetric range, then two's-complement limbs), with its
 // digits and its limb accumulator in that array instead of the pipeline's
 // buffers, and its own per-prime constants in fixed device tables.
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "../../include/rs.h"
+#include "planner.h"
 #include "rs_internal.cuh"
 
 #define RS_NOALLOC_SCRATCH_WORDS (1u << 21)  // 8 MiB of scratch per GPU
@@ -30,7 +33,8 @@ static __device__ uint32_t g_noalloc_primes[RS_NOALLOC_MAX_PRIMES];
 static __device__ ModP g_noalloc_mods[RS_NOALLOC_MAX_PRIMES];
 static __device__ uint32_t g_noalloc_crt[RS_NOALLOC_MAX_PRIMES];
 
-// Host-side set-up state: static storage only, nothing is allocated.
+// Host-side set-up state: static storage only, nothing is allocated on the
+// device.
 struct NoallocDevice {
   bool ready;
   uint32_t *scratch;  // device address of g_noalloc_scratch on that device
@@ -40,26 +44,6 @@ struct NoallocDevice {
 static NoallocDevice g_dev[RS_NOALLOC_MAX_DEVICES];
 static std::mutex g_mu;
 static uint32_t h_primes[RS_NOALLOC_MAX_PRIMES];
-static unsigned char h_composite[1u << 20];
-
-// The same prime table as the library's contexts: primes in
-// (2^31 - 2^20, 2^31), descending, by a sieve of Eratosthenes.
-void sieve_primes() {
-  const uint64_t hi = (uint64_t)1 << 31, lo = hi - ((uint64_t)1 << 20);
-  for (uint32_t q = 2; (uint64_t)q * q < hi; ++q) {
-    bool prime = true;
-    for (uint32_t d = 2; d * d <= q; ++d)
-      if (q % d == 0) {
-        prime = false;
-        break;
-      }
-    if (!prime) continue;
-    for (uint64_t v = ((lo + q - 1) / q) * q; v < hi; v += q) h_composite[v - lo] = 1;
-  }
-  int n = 0;
-  for (uint64_t v = hi - 1; v >= lo && n < RS_NOALLOC_MAX_PRIMES; --v)
-    if (!h_composite[v - lo]) h_primes[n++] = (uint32_t)v;
-}
 
 __global__ void noalloc_init_kernel(int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -126,7 +110,11 @@ int noalloc_setup(int dev) {
   std::lock_guard<std::mutex> lock(g_mu);
   NoallocDevice &d = g_dev[dev];
   if (d.ready) return RS_OK;
-  if (h_primes[0] == 0) sieve_primes();
+  if (h_primes[0] == 0) {  // the first primes of the library's own table (host memory only)
+    const std::vector<uint32_t> t = rs_prime_table(RS_NOALLOC_MAX_PRIMES);
+    if ((int)t.size() < RS_NOALLOC_MAX_PRIMES) return RS_ERR_LIMIT;
+    std::copy(t.begin(), t.end(), h_primes);
+  }
   if (cudaMemcpyToSymbol(g_noalloc_primes, h_primes, sizeof(h_primes)) != cudaSuccess)
     return RS_ERR_CUDA;
   noalloc_init_kernel<<<(RS_NOALLOC_MAX_PRIMES + 127) / 128, 128>>>(RS_NOALLOC_MAX_PRIMES);
@@ -157,7 +145,16 @@ extern "C" int rs_crt_noalloc(const uint32_t *residues, int32_t nprimes, int32_t
   const int rc = noalloc_setup(dev);
   if (rc != RS_OK) return rc;
   const NoallocDevice &d = g_dev[dev];
+  // An error left pending by earlier, unrelated work on this thread is not
+  // this call's: only a launch error that appears here is consumed and
+  // reported, so the caller can still read its own.
+  const cudaError_t before = cudaPeekAtLastError();
   crt_noalloc_kernel<<<(ncoeffs + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
       residues, nprimes, ncoeffs, limbs, out, d.scratch, d.mods, d.crt);
-  return cudaGetLastError() == cudaSuccess ? RS_OK : RS_ERR_CUDA;
+  const cudaError_t after = cudaPeekAtLastError();
+  if (after != cudaSuccess && after != before) {
+    (void)cudaGetLastError();
+    return RS_ERR_CUDA;
+  }
+  return RS_OK;
 }

@@ -3,8 +3,8 @@ that may not allocate device memory themselves or through the library (a
 plugin handed fixed buffers, code where cudaMalloc/cudaFree could
 synchronise the device or fail).  Its output must equal the regular
 resultant path's, bit for bit, on two calls in a row that share its fixed
-scratch array.  The test itself allocates the input and output buffers with
-torch, as such a caller's host application would."""
+scratch array, and equal the oracle's.  The test itself allocates the input
+and output buffers with torch, as such a caller's host application would."""
 import ctypes
 import random
 
@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_1010_1386_gb300 import rs
+from oracle import exact
 from tests.helpers import rand_bipoly
 
 pytestmark = pytest.mark.gpu
@@ -39,20 +40,24 @@ def _run_noalloc(lib, torch, res, L):
     return [int.from_bytes(row.astype("<u4").tobytes(), "little", signed=True) for row in out]
 
 
-def test_noalloc_crt_matches_resultant_path():
+def test_noalloc_crt_matches_resultant_path_and_oracle():
+    """Two calls in a row (different sizes, one shared scratch array): the
+    residues of the oracle's R modulo the library's primes come back as R,
+    equal to the regular resultant path's output."""
     torch = pytest.importorskip("torch")
     lib = rs.load()
     ctx = rs.Context(device=0)
     rng = random.Random(31)
     cases = [(rand_bipoly(rng, 4, 5, bits=40), rand_bipoly(rng, 3, 6, bits=40)),
              (rand_bipoly(rng, 6, 3, bits=100), rand_bipoly(rng, 5, 4, bits=100))]
-    for f, g in cases:  # two calls in a row, different sizes, one shared scratch array
-        R = ctx.resultant_y(f, g)
+    for f, g in cases:
+        R = exact.resultant_y(f, g)
         b = rs.result_bound(f, g)
         K, N, L = b["primes"], b["deg"] + 1, b["limbs"]
         primes, _, _ = ctx.images(f, g, K, 1)
         got = _run_noalloc(lib, torch, _residues(R, [int(p) for p in primes], N), L)
         assert got == list(R) + [0] * (N - len(R))
+        assert ctx.resultant_y(f, g) == R
     ctx.close()
 
 
@@ -94,4 +99,31 @@ def test_noalloc_crt_random_residues_vs_python():
             if x > P // 2:
                 x -= P
             assert got[j] == x, (K, j)
+    ctx.close()
+
+
+def test_noalloc_at_the_scratch_limit_and_the_prime_limit():
+    """nprimes * ncoeffs + ncoeffs * limbs exactly 2^21 (the last limb lands
+    on the scratch array's last word), then nprimes = 2048, the largest
+    table prefix: known integers in the symmetric range come back exactly."""
+    torch = pytest.importorskip("torch")
+    lib = rs.load()
+    ctx = rs.Context(device=0)
+    rng = random.Random(33)
+    table, _, _ = ctx.images([[0, 1]], [[1, 1], [1]], 2048, 1)
+    table = [int(p) for p in table]
+    for K, N, L in [(1000, 1024, 1048), (2048, 8, 1990)]:
+        assert K * N + N * L <= 1 << 21
+        P = 1
+        for p in table[:K]:
+            P *= p
+        vals = [rng.randrange(-(P // 2), P // 2 + 1) for _ in range(13)] + [0, 1, -1, P // 2, -(P // 2)]
+        pick = [vals[(7 * j + 3) % len(vals)] for j in range(N)]
+        rows = {v: [v % p for p in table[:K]] for v in vals}
+        res = np.zeros((K, N), dtype=np.uint32)
+        for j, v in enumerate(pick):
+            res[:, j] = rows[v]
+        got = _run_noalloc(lib, torch, res, L)
+        assert got == pick, K
+    assert 1000 * 1024 + 1024 * 1048 == 1 << 21
     ctx.close()
