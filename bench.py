@@ -34,8 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "resultants/s batched vs per-instance launch, same GB300; % of INT32 IMAD peak"
 INTERP = {"auto": 0, "direct": 1, "transforms": 2, "triangular": 3}
 SQF_METRIC = "square-free factorisations of Res_y(f, g) per second (R = c prod R_i^i), one GB300"
-SM_COUNT = 152
-IMAD_PER_SM_CLK = 64  # 32-bit integer multiply-add results per clock per SM
+IMAD_PER_SM_CLK = 64  # nominal 32-bit integer multiply-add results per clock per SM
 WORKLOADS = {
     "batch": "batched: 512 pairs in one run, per-pair deg_x, deg_y ~ U[8,40] shared by f and g, "
              "bidegree-dense, coefficient bits per pair in {16,32,64}, seed 2",
@@ -209,21 +208,57 @@ class ClockSampler:
 
 # -------------------------------------------------------------- profiles
 
+def _traffic_paths():
+    return (os.path.join(ROOT, "profiles", "g1_traffic.json"),
+            os.path.join(ROOT, "paper_1010_1386_gb300", "csrc", "kernels_g1.cu"))
+
+
+def _sha256(path):
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
 def g1_traffic():
-    """DRAM bytes per G1 stage of the default workload from the committed ncu
-    summary, if it was taken on the current G1 source; else None."""
-    path = os.path.join(ROOT, "profiles", "g1_images_batch512.md")
-    src = os.path.join(ROOT, "paper_1010_1386_gb300", "csrc", "kernels_g1.cu")
+    """DRAM bytes of one G1 stage of the default workload from the record
+    that ``--record-traffic`` wrote from an ncu capture, if that capture was
+    taken on the current G1 source; else None."""
+    path, src = _traffic_paths()
     try:
-        text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        rec = json.load(open(path))
+        if rec["kernels_g1_sha256"] != _sha256(src):
+            return None
+        return float(rec["dram_bytes_per_stage"])
+    except (OSError, KeyError, ValueError):
         return None
-    m_sha = re.search(r"kernels_g1\.cu sha256:\s*([0-9a-f]{64})", text)
-    m_tr = re.search(r"dram bytes per G1 stage:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_tr or m_sha.group(1) != sha:
-        return None
-    return float(m_tr.group(1))
+
+
+def record_traffic(csv_path, command):
+    """Write profiles/g1_traffic.json from an ncu --csv log of the G1 launches
+    (metrics dram__bytes_read.sum and dram__bytes_write.sum, one value per
+    launch): the DRAM bytes of the last complete step, i.e. the last launch
+    of each G1 kernel instance name."""
+    import csv
+    rows = [r for r in csv.reader(open(csv_path)) if r]
+    hdr = next(i for i, r in enumerate(rows) if "Metric Name" in r)
+    h = rows[hdr]
+    ki, mi, vi, ui = h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Value"), h.index("Metric Unit")
+    idi = h.index("ID")
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[hdr + 1:]:
+        if "g1_kernel" not in r[ki] or not r[mi].startswith("dram__bytes_"):
+            continue
+        per.setdefault(r[ki], {}).setdefault(int(r[idi]), 0.0)
+        per[r[ki]][int(r[idi])] += float(r[vi].replace(",", "")) * scale.get(r[ui], 1)
+    last = {k: v[max(v)] for k, v in per.items()}
+    path, src = _traffic_paths()
+    rec = {"kernel": "G1 (all register-capacity launches of one step)",
+           "dram_bytes_per_stage": sum(last.values()), "per_launch": last,
+           "kernels_g1_sha256": _sha256(src), "command": command,
+           "note": "dram__bytes_read.sum + dram__bytes_write.sum of the last launch of each G1 kernel"}
+    with open(path, "w") as fh:
+        json.dump(rec, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+    print(json.dumps(rec))
 
 
 # -------------------------------------------------------------- helpers
@@ -251,15 +286,39 @@ def max_over_ranks(dist, local, value):
     return mor(value, dist, device=f"cuda:{local}")
 
 
+_PEAK = {}
+
+
+def int_peak():
+    """The device's integer multiply-add throughputs, measured once per
+    process by the library's probe (rs_measure_int_peak) before any timed
+    region."""
+    if not _PEAK:
+        from paper_1010_1386_gb300 import rs
+        _PEAK.update(rs.measure_int_peak())
+    return _PEAK
+
+
 def roofline(info, g1_ms, clk, kernel="G1 (reduce + evaluate + univariate resultant)"):
-    sm_max = clk["sm_max_mhz"] or 2070.0
-    peak = SM_COUNT * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
+    """G1's algorithmic IMAD rate (4 multiply-adds per modular product of
+    the evaluation and the remainder sequence) against the measured
+    mad.lo.u32 peak of this device."""
+    pk = int_peak()
+    peak = pk["mad_lo_u32"] / 1e12
     achieved = 4.0 * (info["modmul_eval"] + info["modmul_prs"]) / (g1_ms * 1e-3) / 1e12
+    sm_max = clk["sm_max_mhz"] or pk["clock_max_mhz"]
+    derived = pk["sms"] * IMAD_PER_SM_CLK * sm_max * 1e6 / 1e12
     return {"bound": "alu", "kernel": kernel,
             "achieved": achieved, "peak": peak, "unit": "TIMAD/s", "frac": achieved / peak,
             "traffic": None,
-            "peak_source": f"derived: {SM_COUNT} SMs x {IMAD_PER_SM_CLK} IMAD/clk x {sm_max:.0f} MHz "
-                           "(no integer peak in MEASURED_PEAKS.json)"}
+            "peak_source": "measured: rs_measure_int_peak, independent mad.lo.u32 chains on all %d SMs "
+                           "(%.1f per clock per SM at the %.0f MHz maximum clock)"
+                           % (pk["sms"], pk["mad_lo_u32"] / (pk["sms"] * pk["clock_max_mhz"] * 1e6),
+                              pk["clock_max_mhz"]),
+            "probe": {"mad_lo_u32_T": pk["mad_lo_u32"] / 1e12, "mad_wide_u32_T": pk["mad_wide_u32"] / 1e12,
+                      "mad_hi_u32_T": pk["mad_hi_u32"] / 1e12, "mad_wide_s32_T": pk["mad_wide_s32"] / 1e12,
+                      "montgomery_step_T": pk["mont_update"] / 1e12, "sms": pk["sms"]},
+            "derived_peak": derived, "frac_of_derived": achieved / derived}
 
 
 def whole_path_work(info, npairs, ms, peak):
@@ -365,6 +424,7 @@ def batch_main(args, world, rank, local, dist):
     npairs = len(pairs)
     ctx = rs.Context(device=local, timing=True, autotune_cache=args.autotune_cache,
                      univariate=args.univariate, g2_form=INTERP[args.interp])
+    int_peak()  # the integer-pipe probe runs before anything is timed
     stream = torch.cuda.ExternalStream(ctx.stream, device=local)
     t_tune = time.perf_counter()
     batch = ctx.batch(pairs)  # tunes the G1 launch of every class of the batch first
@@ -691,6 +751,9 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
+    ap.add_argument("--record-traffic", default=None, metavar="CSV",
+                    help="write profiles/g1_traffic.json from an ncu --csv log of the G1 launches and exit")
+    ap.add_argument("--record-command", default="", help="the ncu command that wrote CSV (stored with it)")
     ap.add_argument("--baseline-seconds", type=float, default=15.0,
                     help="wall seconds of oracle work for cpu_baseline")
     ap.add_argument("--shift-deg", type=int, default=15, help="shift workload: total degree (9 or 15)")
@@ -710,6 +773,9 @@ def main():
     ap.add_argument("--inflight", type=int, default=3, help="serving: concurrent micro-batches")
     ap.add_argument("--max-batch", type=int, default=256, help="serving: requests per micro-batch")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.record_command)
+        return
     global SHIFT
     SHIFT = (args.shift_deg, args.shift_k, args.shift_sparse)
     world, rank, local, dist = dist_setup(args)

@@ -400,6 +400,24 @@ int rs_server_set_log(rs_ctx *ctx, const char *path);
  * thread and release its streams (results not yet polled are dropped). */
 int rs_server_stop(rs_ctx *ctx);
 
+/* Throughput of the integer multiply-add forms the kernels use, measured on
+ * the current CUDA device (a measurement facility; the paper has no
+ * counterpart).  Each rate is operations per second over all SMs at the
+ * clock the device runs at during the call: independent chains of
+ * mad.lo.u32, mad.wide.u32 (64-bit accumulate), mad.hi.u32, mad.wide.s32,
+ * and of the remainder sequence's Montgomery step x <- (x w1 + y w2) R^-1
+ * mod p.  The mad.lo.u32 rate is the measured integer multiply-add peak.
+ * Runs `launches` short kernels (about 20 ms in all) on the legacy default
+ * stream and synchronises; allocates and frees a small device buffer.
+ * Returns RS_OK, RS_ERR_ARG (out NULL), RS_ERR_NOMEM or RS_ERR_CUDA. */
+typedef struct {
+  double mad_lo_u32, mad_wide_u32, mad_hi_u32, mad_wide_s32, mont_update;
+  double clock_max_mhz;  /* the device's maximum SM clock */
+  int32_t sms;           /* streaming multiprocessors */
+  int32_t launches;
+} rs_int_peak;
+int rs_measure_int_peak(rs_int_peak *out);
+
 /* Chinese remaindering that allocates nothing, for callers that may not
  * allocate device memory (a plugin handed fixed buffers by its host
  * application, code that must not call cudaMalloc/cudaFree because they can

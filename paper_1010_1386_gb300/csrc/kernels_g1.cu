@@ -37,7 +37,7 @@
 #include "rs_internal.cuh"
 
 #ifndef RS_G1_PSTEP
-#define RS_G1_PSTEP 8  // register capacity dropped per phase
+#define RS_G1_PSTEP 12  // register capacity dropped per phase
 #endif
 // Minimum resident 128-thread blocks per SM requested from ptxas per register
 // capacity (caps registers at 65536 / (128 * MINB) per thread).
@@ -69,12 +69,35 @@ __device__ __forceinline__ void settle(Prs &s, int e, uint32_t c, const ModP &m)
   s.eprev = e;
 }
 
-// P[i] <- w1 P[i+1] + w2 V[i+1]; the top entry (which cancels) is dropped.
+// Entries I .. C - 2 of a reduction whose result has `live` entries: entry
+// I is computed while I < live, entry `live` (the old constant term shifted
+// out) becomes zero, and the zero padding beyond it is left alone.  The
+// degrees are the same for every image of a tile, so these branches are
+// uniform across the warp and skip the padding instead of multiplying zeros.
+template <int C, int I>
+__device__ __forceinline__ void reduce_tail(uint32_t (&P)[C], const uint32_t (&V)[C], uint32_t w1, uint32_t w2,
+                                            const ModP &m, int live) {
+  if constexpr (I < C - 1) {
+    if (live > I) {
+      P[I] = mmul2(P[I + 1], w1, V[I + 1], w2, m);
+      reduce_tail<C, I + 1>(P, V, w1, w2, m, live);
+    } else {
+      P[I] = 0u;
+    }
+  }
+}
+
+// P[i] <- w1 P[i+1] + w2 V[i+1] for i < live (the reduced polynomial's
+// entries); the top entry (which cancels) is dropped.  Every caller reduces
+// an array whose degree is at least C - 8 (the phase condition), so the
+// first C - 8 entries are always live and only the last 7 are checked.
 template <int C>
 __device__ __forceinline__ void reduce_into(uint32_t (&P)[C], const uint32_t (&V)[C], uint32_t w1,
-                                            uint32_t w2, const ModP &m) {
+                                            uint32_t w2, const ModP &m, int live) {
+  constexpr int H = C > RS_G1_PSTEP ? C - RS_G1_PSTEP : 0;
 #pragma unroll
-  for (int i = 0; i < C - 1; ++i) P[i] = mmul2(P[i + 1], w1, V[i + 1], w2, m);
+  for (int i = 0; i < H; ++i) P[i] = mmul2(P[i + 1], w1, V[i + 1], w2, m);
+  reduce_tail<C, H>(P, V, w1, w2, m, live);
   P[C - 1] = 0u;
 }
 
@@ -90,7 +113,7 @@ template <int C>
 __device__ __forceinline__ void step_a(uint32_t (&A)[C], const uint32_t (&B)[C], Prs &s, const ModP &m) {
   const uint32_t lb = B[0], la = A[0];
   settle(s, s.b - 1, lb, m);
-  reduce_into<C>(A, B, lb, mneg(la, m.p), m);
+  reduce_into<C>(A, B, lb, mneg(la, m.p), m, s.a);
   s.sign ^= (uint32_t)(s.b & 1);
   --s.a;
 }
@@ -99,7 +122,7 @@ template <int C>
 __device__ __forceinline__ void step_b(const uint32_t (&A)[C], uint32_t (&B)[C], Prs &s, const ModP &m) {
   const uint32_t la = A[0], lb = B[0];
   settle(s, s.a - 1, la, m);
-  reduce_into<C>(B, A, la, mneg(lb, m.p), m);
+  reduce_into<C>(B, A, la, mneg(lb, m.p), m, s.b);
   --s.b;
 }
 
@@ -124,7 +147,7 @@ __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs 
       if (lb != 0u) {
         const uint32_t la = A[0];
         settle(s, s.b - 1, lb, m);
-        reduce_into<C>(A, B, lb, mneg(la, m.p), m);
+        reduce_into<C>(A, B, lb, mneg(la, m.p), m, s.a);
         s.sign ^= (uint32_t)(s.b & 1);
         --s.a;
       } else {
@@ -138,7 +161,7 @@ __device__ __forceinline__ void prs_run(uint32_t (&A)[C], uint32_t (&B)[C], Prs 
       if (la != 0u) {
         const uint32_t lb = B[0];
         settle(s, s.a - 1, la, m);
-        reduce_into<C>(B, A, la, mneg(lb, m.p), m);
+        reduce_into<C>(B, A, la, mneg(lb, m.p), m, s.b);
         --s.b;
       } else {
         s.num = mmul(s.num, B[0], m);

@@ -73,8 +73,15 @@ class rs_server_stats(ctypes.Structure):
                                         "kernel_launches")]
 
 
+class rs_int_peak(ctypes.Structure):
+    _fields_ = [(n, c_double) for n in ("mad_lo_u32", "mad_wide_u32", "mad_hi_u32", "mad_wide_s32",
+                                         "mont_update", "clock_max_mhz")] + \
+               [("sms", c_int32), ("launches", c_int32)]
+
+
 _P = POINTER
 _SIGS = {
+    "rs_measure_int_peak": (c_int32, [_P(rs_int_peak)]),
     "rs_config_default": (c_int32, [_P(rs_config)]),
     "rs_create": (c_int32, [_P(c_void_p), _P(rs_config)]),
     "rs_destroy": (c_int32, [c_void_p]),
@@ -143,6 +150,17 @@ def load(path=None):
     if path is None:
         _lib = lib
     return lib
+
+
+def measure_int_peak():
+    """Integer multiply-add throughputs of the current device (operations per
+    second over all SMs): mad.lo.u32, mad.wide.u32, mad.hi.u32, mad.wide.s32
+    and the Montgomery remainder step; plus the SM count and max clock."""
+    out = rs_int_peak()
+    rc = load().rs_measure_int_peak(ctypes.byref(out))
+    if rc:
+        raise RsError(rc, "rs_measure_int_peak")
+    return {n: getattr(out, n) for n, _ in rs_int_peak._fields_}
 
 
 class RsError(RuntimeError):

@@ -278,7 +278,8 @@ def test_info_struct_layouts(tmp_path):
         pytest.skip("no C compiler")
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     src = tmp_path / "layout.c"
-    checks = [("rs_batch_info", rs.rs_batch_info), ("rs_sqf_info", rs.rs_sqf_info)]
+    checks = [("rs_batch_info", rs.rs_batch_info), ("rs_sqf_info", rs.rs_sqf_info),
+              ("rs_int_peak", rs.rs_int_peak)]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rs.h"', "int main(void) {"]
     for name, st in checks:
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
