@@ -577,6 +577,8 @@ def batch_main(args, world, rank, local, dist):
                        "degenerate_images": info["degenerate_images"],
                        "unlucky_primes": info["unlucky_primes"]},
     })
+    if args.workload == "batch" and not args.no_other_configs and world == 1 and args.pairs is None:
+        line["configs"] = other_configs(ctx, local, args.steps, flush, stream)
     add_cpu_baseline(line, args, rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -663,20 +665,18 @@ def squarefree_main(args, world, rank, local, dist):
     ctx.close()
 
 
-def serving_main(args, world, rank, local, dist):
-    """Closed-loop saturation pass, then a Poisson stream at --load x that
-    throughput through the continuous-batching server."""
+def measure_serving(local, n, load, inflight, max_batch, dist=None, clocks=None):
+    """Closed-loop saturation pass, then a Poisson stream at ``load`` x that
+    throughput through the continuous-batching server; every request crosses
+    the C ABI with host buffers.  Returns the measurements as a dict."""
     import numpy as np
-    import torch
     from paper_1010_1386_gb300 import inputs, rs
 
-    torch.cuda.set_device(local)
-    n = args.pairs or 10000
     pairs, gaps = inputs.workload_serving(4, n=n)
     ctx = rs.Context(device=local)
     for k in (16, 64, 256):  # the server never tunes: warm the tuner cache with batches of a mix
         ctx.autotune(pairs[:k])
-    srv = rs.Server(ctx, max_inflight=args.inflight, max_batch=args.max_batch)
+    srv = rs.Server(ctx, max_inflight=inflight, max_batch=max_batch)
     for f, g in pairs[: min(n, 256)]:  # warm-up: tables, streams, pinned staging
         srv.wait(srv.submit(f, g))
 
@@ -706,40 +706,122 @@ def serving_main(args, world, rank, local, dist):
         return time.perf_counter() - t_start, lat, out_bytes
 
     barrier(dist, local)
-    with ClockSampler(local) as clocks:
-        sat_s, sat_lat, _ = run_stream(None)
-        sat = n / sat_s
-        rate = args.load * sat
-        arrivals = np.cumsum(gaps) / rate
-        wall, lat, out_bytes = run_stream(arrivals)
-        barrier(dist, local)
+    sat_s, sat_lat, _ = run_stream(None)
+    sat = n / sat_s
+    rate = load * sat
+    arrivals = np.cumsum(gaps) / rate
+    wall, lat, out_bytes = run_stream(arrivals)
+    barrier(dist, local)
     st = srv.stats()
     srv.stop()
     ctx.close()
-    wall = max_over_ranks(dist, local, wall)
-    value = world * n / wall
     lat_sorted = sorted(lat)
-    p50 = lat_sorted[len(lat) // 2]
-    p99 = lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]
+    return {"requests": n, "wall_s": wall, "value": n / wall, "unit": "resultants/s",
+            "arrival_rate_per_s": rate, "load_vs_saturation": load,
+            "latency_ms": {"p50": lat_sorted[len(lat) // 2],
+                           "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "mean": statistics.mean(lat)},
+            "saturation": {"value": sat, "unit": "resultants/s", "p50_ms": sorted(sat_lat)[n // 2]},
+            "server": {k: st[k] for k in ("batches", "peak_inflight_batches", "peak_running", "failed")},
+            "kernel_launches": st["kernel_launches"],
+            "h2d_bytes": int(sum(f.coeffs.nbytes + g.coeffs.nbytes for f, g in pairs)),
+            "d2h_bytes": out_bytes, "max_inflight_batches": inflight, "max_batch": max_batch}
+
+
+def serving_main(args, world, rank, local, dist):
+    """Closed-loop saturation pass, then a Poisson stream at --load x that
+    throughput through the continuous-batching server."""
+    import torch
+
+    torch.cuda.set_device(local)
+    with ClockSampler(local) as clocks:
+        r = measure_serving(local, args.pairs or 10000, args.load, args.inflight, args.max_batch, dist)
+    wall = max_over_ranks(dist, local, r["wall_s"])
+    n = r["requests"]
+    value = world * n / wall
     line = base_line(args, world, value, 1e3 * wall, WORKLOADS["serving"],
-                     {"requests": n, "arrival_rate_per_s": rate, "load_vs_saturation": args.load,
-                      "max_inflight_batches": args.inflight, "max_batch": args.max_batch})
+                     {"requests": n, "arrival_rate_per_s": r["arrival_rate_per_s"],
+                      "load_vs_saturation": args.load, "max_inflight_batches": args.inflight,
+                      "max_batch": args.max_batch})
     line.update({
         "steps": 1,
-        "latency_ms": {"p50": p50, "p99": p99, "mean": statistics.mean(lat)},
-        "saturation": {"value": sat, "unit": "resultants/s", "p50_ms": sorted(sat_lat)[n // 2]},
-        "server": {k: st[k] for k in ("batches", "peak_inflight_batches", "peak_running", "failed")},
-        "gpu_launches": st["kernel_launches"],
+        "latency_ms": r["latency_ms"],
+        "saturation": r["saturation"],
+        "server": r["server"],
+        "gpu_launches": r["kernel_launches"],
         "clocks": clocks.summary(),
-        "e2e": {"value": value, "unit": "resultants/s",
-                "h2d_bytes_per_step": int(sum(f.coeffs.nbytes + g.coeffs.nbytes for f, g in pairs)),
-                "d2h_bytes_per_step": out_bytes,
+        "e2e": {"value": value, "unit": "resultants/s", "h2d_bytes_per_step": r["h2d_bytes"],
+                "d2h_bytes_per_step": r["d2h_bytes"],
                 "note": "every request crosses the C ABI with host buffers; latency is submit to result; "
                         "the step is the whole stream, d2h the result limbs handed back"},
     })
     add_cpu_baseline(line, args, rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_batch(ctx, pairs, steps, warmup, stream, flush, e2e_steps=0):
+    """Device-timed steps of one prepared batch (inputs resident, L2 flushed
+    before each step outside its events), then ``e2e_steps`` end-to-end
+    steps through the C ABI with host buffers (upload, run, results)."""
+    import torch
+    b = ctx.batch(pairs)
+    for _ in range(warmup):
+        b.run()
+        b.sync()
+    ms, stage = [], {"images": [], "interp": [], "crt": []}
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0.record(stream)
+        b.run()
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        b.sync()
+        ms.append(e0.elapsed_time(e1))
+        i = b.info()
+        for k, key in (("images", "ms_images"), ("interp", "ms_interp"), ("crt", "ms_crt")):
+            stage[k].append(i[key])
+    info = b.info()
+    out = {"value": len(pairs) / (statistics.mean(ms) * 1e-3), "unit": "resultants/s",
+           "ms_per_step": statistics.mean(ms), "stage_ms": {k: statistics.mean(v) for k, v in stage.items()},
+           "images_per_step": info["images"], "steps": steps, "gpu_launches": steps * info["kernel_launches"]}
+    if e2e_steps:
+        b.upload(pairs)
+        b.run()
+        b.results(raw=True)
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            b.upload(pairs)
+            b.run()
+            b.results(raw=True)
+        e2e_ms = 1e3 * (time.perf_counter() - t) / e2e_steps
+        out["e2e"] = {"value": len(pairs) / (e2e_ms * 1e-3), "unit": "resultants/s",
+                      "h2d_bytes_per_step": info["input_bytes"], "d2h_bytes_per_step": info["output_bytes"],
+                      "form": "one prepared batch: upload, run, results, step after step"}
+    b.close()
+    return out
+
+
+def other_configs(ctx, local, steps, flush, stream):
+    """Compact records of the other configurations, on the same GPU right
+    after the headline workload: configs[1] (one dense degree-30 pair, with
+    its end-to-end rate), the coprime non-generic batch of 32 (configs[3]'s
+    non-zero variant) and the serving stream of configs[4] (10,000 requests
+    at 0.8 of the measured saturation rate)."""
+    from paper_1010_1386_gb300 import inputs
+    out = {}
+    out["c1_single_dense30"] = measure_batch(ctx, inputs.workload_single(1), max(steps, 10), 3, stream, flush,
+                                             e2e_steps=20)
+    out["c3p_nongeneric_coprime_32"] = measure_batch(ctx, inputs.workload_nongeneric(3, n=32, coprime=True),
+                                                     max(3, min(steps, 5)), 2, stream, flush)
+    srv = measure_serving(local, 10000, 0.8, 3, 256)
+    out["c4_serving_10000"] = {k: srv[k] for k in ("value", "unit", "latency_ms", "saturation",
+                                                   "arrival_rate_per_s", "load_vs_saturation", "wall_s")}
+    out["c4_serving_10000"]["form"] = ("Poisson arrivals at 0.8 of the closed-loop saturation rate, every "
+                                       "request through the C ABI with host buffers (value is end to end)")
+    return out
 
 
 def main():
@@ -751,6 +833,8 @@ def main():
     ap.add_argument("--workload", default="batch", choices=sorted(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="batch workload: skip the compact records of configs[1], [3'] and [4]")
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write profiles/g1_traffic.json from an ncu --csv log of the G1 launches and exit")
     ap.add_argument("--record-command", default="", help="the ncu command that wrote CSV (stored with it)")

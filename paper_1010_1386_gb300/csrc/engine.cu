@@ -635,10 +635,17 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // fewer than two per SM (few coefficients with many primes each).
   std::vector<int2> g3d;
   std::vector<int4> g3b;  // CRT limb chunks: 128 coefficients x one chunk per block
+  // With enough coefficients for one thread each to fill the GPU, the digits
+  // take one thread per coefficient (no warp waits on a serial triangle);
+  // otherwise the tiled kernel spreads each coefficient's work over a block.
   {
-    int64_t nt32 = 0;
-    for (int i : order) nt32 += (b->plans[i].N + 31) / 32;
+    int64_t nt32 = 0, ncoef = 0;
+    for (int i : order) {
+      nt32 += (b->plans[i].N + 31) / 32;
+      ncoef += b->plans[i].N;
+    }
     b->g3_jt = nt32 < 2 * (int64_t)ctx->sms ? 16 : 32;
+    b->g3_perthread = ncoef >= (int64_t)RS_G3P_MIN_COEF_PER_SM * ctx->sms;
   }
   for (int i : order) {
     const PairPlan &p = b->plans[i];
@@ -1037,7 +1044,10 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.shape = reinterpret_cast<int32_t *>(b->d_out + b->shape_off);
     RS_CUDA(ctx, cudaMemsetAsync(a3.shape, 0, b->descs.size() * 2 * sizeof(int32_t), s));
     a3.kmax = b->kmax;
-    RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
+    if (b->g3_perthread)
+      RS_CUDA(ctx, launch_g3p(b->ng3, a3, b->d_g3, s));
+    else
+      RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
     RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));

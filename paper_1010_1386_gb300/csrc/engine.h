@@ -139,6 +139,7 @@ struct rs_batch {
   int ng2 = 0, ng3 = 0, g2_threads = 256;
   int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int g3_jt = 32;                    // coefficients per CRT digit tile (32 or 16)
+  bool g3_perthread = false;         // CRT digits with one thread per coefficient
   int64_t xl_words = 0, cy_words = 0;
   int2 *d_g3d = nullptr;
   int nyun = 0;                         // square-free tasks (pair, prime)

@@ -34,6 +34,139 @@ __device__ __forceinline__ uint32_t add_p(uint32_t a, uint32_t b, uint32_t P) {
   return rs_umin(s, s - P);
 }
 
+// A twiddle pair of stage row l (w_{2^l}^j): shared-memory rows 1 .. lg-1,
+// the top row lg from global memory.
+__device__ __forceinline__ uint2 twiddle(const uint2 *rows, const uint2 *top, int l, int lg, int j) {
+  return l == lg ? __ldg(top + j) : rows[(1 << (l - 1)) - 1 + j];
+}
+
+// A 16-entry group of shared memory in registers and back.  Thread t moves
+// its group's four 16-byte chunks starting with chunk (t / 2) mod 4, so the
+// eight threads of a quarter warp (groups 64 bytes apart) always touch eight
+// different 16-byte bank groups.
+#ifndef RS_G2N_ROTATE
+#define RS_G2N_ROTATE 1
+#endif
+__device__ __forceinline__ void load16(const uint32_t *g, uint32_t (&x)[16]) {
+  const int h = RS_G2N_ROTATE ? (threadIdx.x >> 1) & 3 : 0;
+  const uint4 *g4 = reinterpret_cast<const uint4 *>(g);
+  uint4 v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = g4[(q + h) & 3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {  // chunk c is v[(c - h) mod 4]
+    const uint4 a0 = v[(c + 4) & 3], a1 = v[(c + 3) & 3], a2 = v[(c + 2) & 3], a3 = v[(c + 1) & 3];
+    const uint4 u = h == 0 ? a0 : h == 1 ? a1 : h == 2 ? a2 : a3;
+    x[4 * c] = u.x;
+    x[4 * c + 1] = u.y;
+    x[4 * c + 2] = u.z;
+    x[4 * c + 3] = u.w;
+  }
+}
+
+__device__ __forceinline__ void store16(uint32_t *g, const uint32_t (&x)[16]) {
+  const int h = RS_G2N_ROTATE ? (threadIdx.x >> 1) & 3 : 0;
+  uint4 *g4 = reinterpret_cast<uint4 *>(g);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {  // chunk (q + h) mod 4
+    const uint4 c0 = make_uint4(x[(4 * q) & 15], x[(4 * q + 1) & 15], x[(4 * q + 2) & 15], x[(4 * q + 3) & 15]);
+    const uint4 c1 = make_uint4(x[(4 * q + 4) & 15], x[(4 * q + 5) & 15], x[(4 * q + 6) & 15], x[(4 * q + 7) & 15]);
+    const uint4 c2 = make_uint4(x[(4 * q + 8) & 15], x[(4 * q + 9) & 15], x[(4 * q + 10) & 15], x[(4 * q + 11) & 15]);
+    const uint4 c3 = make_uint4(x[(4 * q + 12) & 15], x[(4 * q + 13) & 15], x[(4 * q + 14) & 15], x[(4 * q + 15) & 15]);
+    g4[(q + h) & 3] = h == 0 ? c0 : h == 1 ? c1 : h == 2 ? c2 : c3;
+  }
+}
+
+// The two radix-4 passes with the smallest strides (quarter sizes 4 and 1)
+// only combine entries inside aligned groups of 16, so one thread takes a
+// whole group: four 16-byte shared loads, both passes in registers with the
+// 14 twiddles every group shares, four 16-byte stores.  (Done pass by pass,
+// those strides made 2- to 4-way shared-memory bank conflicts.)
+__device__ __forceinline__ void dif16_tail(uint32_t *a, int lg, const uint2 *rows, const uint2 *top, uint32_t P) {
+  uint2 w16[8], w8[4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) w16[j] = twiddle(rows, top, 4, lg, j);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) w8[j] = twiddle(rows, top, 3, lg, j);
+  const uint2 w4a = twiddle(rows, top, 2, lg, 0), w4b = twiddle(rows, top, 2, lg, 1);
+  const uint2 w2 = twiddle(rows, top, 1, lg, 0);
+  const int groups = 1 << (lg - 4);
+  for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+    uint32_t x[16];
+    load16(a + 16 * gi, x);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // half-sizes 8 and 4: entries j, j + 4, j + 8, j + 12
+      const uint32_t x0 = x[j], x1 = x[j + 4], x2 = x[j + 8], x3 = x[j + 12];
+      const uint32_t y0 = add_p(x0, x2, P), y1 = add_p(x1, x3, P);
+      const uint32_t y2 = shoup_mul(x0 + P - x2, w16[j], P);
+      const uint32_t y3 = shoup_mul(x1 + P - x3, w16[j + 4], P);
+      x[j] = add_p(y0, y1, P);
+      x[j + 4] = shoup_mul(y0 + P - y1, w8[j], P);
+      x[j + 8] = add_p(y2, y3, P);
+      x[j + 12] = shoup_mul(y2 + P - y3, w8[j], P);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {  // half-sizes 2 and 1: entries 4 m .. 4 m + 3
+      const uint32_t x0 = x[4 * m], x1 = x[4 * m + 1], x2 = x[4 * m + 2], x3 = x[4 * m + 3];
+      const uint32_t y0 = add_p(x0, x2, P), y1 = add_p(x1, x3, P);
+      const uint32_t y2 = shoup_mul(x0 + P - x2, w4a, P);
+      const uint32_t y3 = shoup_mul(x1 + P - x3, w4b, P);
+      x[4 * m] = add_p(y0, y1, P);
+      x[4 * m + 1] = shoup_mul(y0 + P - y1, w2, P);
+      x[4 * m + 2] = add_p(y2, y3, P);
+      x[4 * m + 3] = shoup_mul(y2 + P - y3, w2, P);
+    }
+    store16(a + 16 * gi, x);
+  }
+  __syncthreads();
+}
+
+// The inverse's first two passes (quarter sizes 1 and 4) the same way.
+__device__ __forceinline__ void dit16_head(uint32_t *a, int lg, const uint2 *irows, const uint2 *top, uint32_t P) {
+  uint2 w16[8], w8[4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) w16[j] = twiddle(irows, top, 4, lg, j);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) w8[j] = twiddle(irows, top, 3, lg, j);
+  const uint2 w4a = twiddle(irows, top, 2, lg, 0), w4b = twiddle(irows, top, 2, lg, 1);
+  const uint2 w2 = twiddle(irows, top, 1, lg, 0);
+  const int groups = 1 << (lg - 4);
+  for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+    uint32_t x[16];
+    load16(a + 16 * gi, x);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {  // half-sizes 1 and 2: entries 4 m .. 4 m + 3
+      const uint32_t v1 = shoup_mul(x[4 * m + 1], w2, P), v3 = shoup_mul(x[4 * m + 3], w2, P);
+      const uint32_t x0 = x[4 * m], x2 = x[4 * m + 2];
+      const uint32_t y0 = add_p(x0, v1, P), y1 = x0 + P - v1;
+      const uint32_t y2 = add_p(x2, v3, P), y3 = x2 + P - v3;
+      const uint32_t u2 = shoup_mul(y2, w4a, P);
+      const uint32_t u3 = shoup_mul(y3, w4b, P);
+      const uint32_t z1 = rs_umin(y1, y1 - P);
+      x[4 * m] = add_p(y0, u2, P);
+      x[4 * m + 2] = y0 + P - u2 - (y0 + P - u2 >= P ? P : 0);
+      x[4 * m + 1] = add_p(z1, u3, P);
+      x[4 * m + 3] = z1 + P - u3 - (z1 + P - u3 >= P ? P : 0);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // half-sizes 4 and 8: entries j, j + 4, j + 8, j + 12
+      const uint32_t v1 = shoup_mul(x[j + 4], w8[j], P), v3 = shoup_mul(x[j + 12], w8[j], P);
+      const uint32_t x0 = x[j], x2 = x[j + 8];
+      const uint32_t y0 = add_p(x0, v1, P), y1 = x0 + P - v1;
+      const uint32_t y2 = add_p(x2, v3, P), y3 = x2 + P - v3;
+      const uint32_t u2 = shoup_mul(y2, w16[j], P);
+      const uint32_t u3 = shoup_mul(y3, w16[j + 4], P);
+      const uint32_t z1 = rs_umin(y1, y1 - P);
+      x[j] = add_p(y0, u2, P);
+      x[j + 8] = y0 + P - u2 - (y0 + P - u2 >= P ? P : 0);
+      x[j + 4] = add_p(z1, u3, P);
+      x[j + 12] = z1 + P - u3 - (z1 + P - u3 >= P ? P : 0);
+    }
+    store16(a + 16 * gi, x);
+  }
+  __syncthreads();
+}
+
 // Forward transform of a[0, L), L = 2^lg, in shared memory: decimation in
 // frequency, two stages per pass (radix 4) plus one radix-2 pass when lg is
 // odd.  Twiddle row l holds (w_{2^l}^j, Shoup quotient) for j < 2^(l-1); a
@@ -53,7 +186,8 @@ __device__ void ntt_dif(uint32_t *a, int lg, const uint2 *rows, const uint2 *top
     __syncthreads();
     --s;
   }
-  for (; s >= 1; s -= 2) {  // stages with half-sizes h = 2^s and q = h/2
+  const int s_end = lg >= 4 ? 3 : 0;  // with lg >= 4 the last two passes run as 16-entry groups
+  for (; s > s_end; s -= 2) {  // stages with half-sizes h = 2^s and q = h/2
     const int q = 1 << (s - 1), h = q << 1;
     const bool gtop = s + 1 == lg;  // w_{2h}^j from the global top row (block-uniform)
     const uint2 *r1 = rows + (h - 1), *r0 = rows + (q - 1);  // w_{2h}^j and w_h^j in shared memory
@@ -73,6 +207,7 @@ __device__ void ntt_dif(uint32_t *a, int lg, const uint2 *rows, const uint2 *top
     }
     __syncthreads();
   }
+  if (lg >= 4) dif16_tail(a, lg, rows, top, P);
 }
 
 // Inverse transform (without the 1/L factor) of a bit-reversed a: decimation
@@ -81,6 +216,10 @@ __device__ void ntt_dif(uint32_t *a, int lg, const uint2 *rows, const uint2 *top
 __device__ void ntt_dit_inv(uint32_t *a, int lg, const uint2 *irows, const uint2 *top, uint32_t P) {
   const int L = 1 << lg;
   int s = 0;
+  if (lg >= 4) {  // the first two passes as 16-entry groups
+    dit16_head(a, lg, irows, top, P);
+    s = 4;
+  }
   for (; s + 1 < lg; s += 2) {  // stages with half-sizes q = 2^s and h = 2q
     const int q = 1 << s, h = q << 1;
     const bool gtop = s + 2 == lg;  // w_{4q}^-j from the global top row (block-uniform)
@@ -120,6 +259,7 @@ __device__ void ntt_dit_inv(uint32_t *a, int lg, const uint2 *irows, const uint2
 // start of the compact table) into shared memory.
 __device__ __forceinline__ void stage_twiddles(uint2 *dst, const uint2 *table, int lg) {
   const int n = (1 << (lg - 1)) - 1;
+#pragma unroll 4
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = __ldg(table + i);
 }
 
@@ -142,6 +282,7 @@ __device__ void conv_ntt(const int32_t *x, int N, int lg, const uint32_t *bhat, 
     __syncthreads();
     ntt_dif(W, lg, TWS, fw + ((L >> 1) - 1), P.p);
     const uint32_t *bh = bhat + (size_t)q * L;
+#pragma unroll 4
     for (int i = threadIdx.x; i < L; i += T) W[i] = mmul(W[i], __ldg(bh + i), P);
     stage_twiddles(TWS, iw, lg);
     __syncthreads();
@@ -175,7 +316,7 @@ __device__ __forceinline__ int32_t srep(uint32_t v, uint32_t p) {
 // images give E(Q^i) and O(Q^i), interpolated in turn into the even and the
 // odd coefficients.  Shared memory: X, V0, V1, Oh (M words each), W (2^lg
 // words), twiddle rows 1 .. lg-1 (2^(lg-1) - 1 pairs).
-__global__ void __launch_bounds__(256) g2n_kernel(G2nArgs a) {
+__global__ void __launch_bounds__(256, 3) g2n_kernel(G2nArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t scratch[128];
   const int2 task = a.tasks[blockIdx.x];

@@ -33,6 +33,9 @@ __device__ __forceinline__ uint32_t finish64_3(int64_t s, const ModP &m) {
 }
 
 #define G3T_BK 64  // digits per digit block
+#ifndef RS_G3T_LS16
+#define RS_G3T_LS16 1  // thread groups per 16-coefficient tile (1 or 2)
+#endif
 #define G3T_LC 32  // earlier digits per staged chunk
 
 // Digits by tiles: a block of 256 threads owns JT (32, or 16 when there are
@@ -48,21 +51,29 @@ __device__ __forceinline__ uint32_t finish64_3(int64_t s, const ModP &m) {
 // residues, constants and that triangle prefetched into shared memory.
 // The work per coefficient is still K^2 / 2 products, but W and the digits
 // come from shared memory, each value reused 32 and 64 times.
-template <int JT>
-__global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
-  constexpr int CJ = JT / 16;              // columns per thread
-  __shared__ int32_t Ws[G3T_LC][G3T_BK + 1];  // W[k0 + r][l0 + c] at Ws[c][r]
-  __shared__ int32_t Vs[G3T_LC][JT];          // digit l0 + c of coefficient j0 + jj
-  __shared__ int32_t Wt[G3T_BK][G3T_BK + 1];  // W[k0 + r][k0 + c], c < r
-  __shared__ uint32_t Ds[G3T_BK][JT];         // r_k(j) - A[k][j] mod p_k
-  __shared__ int32_t Vb[G3T_BK][JT];          // the block's digits
+template <int JT, int LS>
+__global__ void __launch_bounds__(256 * LS, 4 / LS) g3t_kernel(G3Args a) {
+  constexpr int CJ = JT / 16;  // columns per thread
+  // LS thread groups of 256 share the earlier-digit chunks of a digit block
+  // (group q takes chunks q, q + LS, ...) and their partial sums are added
+  // through shared memory; with few tiles per SM this multiplies the warps
+  // without changing each thread's 4 x CJ register block.
+  // W[k0 + r][l0 + c] at Ws[q][c][r]: rows of 68 words keep each thread's four
+  // consecutive r 16-byte aligned, so they come in one shared load
+  __shared__ __align__(16) int32_t Ws[LS][G3T_LC][G3T_BK + 4];
+  __shared__ int32_t Vs[LS][G3T_LC][JT];                        // digit l0 + c of coefficient j0 + jj
+  __shared__ int32_t Wt[G3T_BK][G3T_BK + 1];                    // W[k0 + r][k0 + c], c < r
+  __shared__ uint32_t Ds[G3T_BK][JT];                           // r_k(j) - A[k][j] mod p_k
+  __shared__ int32_t Vb[G3T_BK][JT];                            // the block's digits
   __shared__ ModP Ms[G3T_BK];
   __shared__ uint32_t Cs[G3T_BK];
+  static_assert(LS == 1 || (size_t)(LS - 1) * 256 * 4 * CJ * 8 <= sizeof(Ws), "partial sums fit in Ws");
   const int2 task = a.tasks[blockIdx.x];
   const PairDesc pd = a.pairs[task.x];
   const int K = pd.K, N = pd.N, S = pd.NI, j0 = task.y, tid = threadIdx.x;
-  const int rg = tid >> 4, cg = tid & 15;  // rows 4 rg .. 4 rg + 3, columns CJ cg .. CJ cg + CJ - 1
-  uint32_t *col = a.coef + pd.img_off;     // residue, then digit, of (k, j) at col[k S + j]
+  const int grp = tid >> 8, ltid = tid & 255;
+  const int rg = ltid >> 4, cg = ltid & 15;  // rows 4 rg .. 4 rg + 3, columns CJ cg .. CJ cg + CJ - 1
+  uint32_t *col = a.coef + pd.img_off;       // residue, then digit, of (k, j) at col[k S + j]
   for (int k0 = 0; k0 < K; k0 += G3T_BK) {
     const int bk = min(G3T_BK, K - k0);
     for (int r = tid; r < bk; r += blockDim.x) {
@@ -78,70 +89,104 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int c = 0; c < CJ; ++c) acc[i][c] = 0;
-    int cnt = 0;
-    // Chunks of W (8 values per thread) and digits (4 per thread) are loaded
-    // into registers one chunk ahead, so their latency overlaps the products.
+    // Chunks of W (8 values per thread) and digits are loaded into registers
+    // one chunk ahead, so their latency overlaps the products.
     constexpr int NW = G3T_LC * G3T_BK / 256, NV = G3T_LC * JT / 256;
     int32_t wreg[NW], vreg[NV];
     auto fetch = [&](int l0) {
 #pragma unroll
       for (int q = 0; q < NW; ++q) {
-        const int e = tid + 256 * q, r = e >> 5, c = e & 31, k = k0 + r;
+        const int e = ltid + 256 * q, r = e >> 5, c = e & 31, k = k0 + r;
         wreg[q] = r < bk ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + l0 + c) : 0;
       }
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        const int e = tid + 256 * q, c = e / JT, jj = e % JT, j = j0 + jj;
+        const int e = ltid + 256 * q, c = e / JT, jj = e % JT, j = j0 + jj;
         vreg[q] = j < N ? (int32_t)col[(size_t)(l0 + c) * S + j] : 0;
       }
     };
-    if (k0 > 0) fetch(0);
-    for (int l0 = 0; l0 < k0; l0 += G3T_LC) {  // k0 is a multiple of G3T_LC: full chunks
+    const int nch = k0 / G3T_LC;  // k0 is a multiple of G3T_LC: full chunks
+    if (grp < nch) fetch(grp * G3T_LC);
+    for (int it = 0; it * LS < nch; ++it) {
+      const int ch = it * LS + grp, l0 = ch * G3T_LC;
+      const bool act = ch < nch;
+      if (act) {
 #pragma unroll
-      for (int q = 0; q < NW; ++q) {
-        const int e = tid + 256 * q;
-        Ws[e & 31][e >> 5] = wreg[q];
-      }
+        for (int q = 0; q < NW; ++q) {
+          const int e = ltid + 256 * q;
+          Ws[grp][e & 31][e >> 5] = wreg[q];
+        }
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int e = tid + 256 * q;
-        Vs[e / JT][e % JT] = vreg[q];
+        for (int q = 0; q < NV; ++q) {
+          const int e = ltid + 256 * q;
+          Vs[grp][e / JT][e % JT] = vreg[q];
+        }
       }
       __syncthreads();
-      if (l0 + G3T_LC < k0) fetch(l0 + G3T_LC);
-#pragma unroll 4
-      for (int c = 0; c < G3T_LC; ++c) {
-        int32_t w[4], v[CJ];
+      if (ch + LS < nch) fetch(l0 + LS * G3T_LC);
+      if (act) {
+        // |acc| < 2^53 after a fold and each product is below 2^60 in size, so
+        // 7 products may follow a fold: four groups of 7 steps and one of 4.
+        auto steps = [&](int c0, int n) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = Ws[c][4 * rg + i];
+          for (int c = c0; c < c0 + 7; ++c) {
+            if (c - c0 >= n) break;
+            const int4 w4 = *reinterpret_cast<const int4 *>(&Ws[grp][c][4 * rg]);
+            const int32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+            int32_t v[CJ];
 #pragma unroll
-        for (int cc = 0; cc < CJ; ++cc) v[cc] = Vs[c][CJ * cg + cc];
+            for (int cc = 0; cc < CJ; ++cc) v[cc] = Vs[grp][c][CJ * cg + cc];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int cc = 0; cc < CJ; ++cc) acc[i][cc] = rs_mac_s32(acc[i][cc], w[i], v[cc]);
-        if (++cnt == 7) {
+              for (int cc = 0; cc < CJ; ++cc) acc[i][cc] = rs_mac_s32(acc[i][cc], w[i], v[cc]);
+          }
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int cc = 0; cc < CJ; ++cc) acc[i][cc] = rs_fold64(acc[i][cc], c32[i]);
-          cnt = 0;
-        }
+        };
+#pragma unroll 1
+        for (int c0 = 0; c0 < 28; c0 += 7) steps(c0, 7);
+        steps(28, G3T_LC - 28);
       }
       __syncthreads();
     }
+    if constexpr (LS > 1) {  // the other groups' partial sums, through the (now unused) staging buffer
+      int64_t *part = reinterpret_cast<int64_t *>(&Ws[0][0][0]);
+      if (grp > 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < CJ; ++c)
+            part[(((size_t)(grp - 1) * 256 + ltid) * 4 + i) * CJ + c] = rs_fold64(acc[i][c], c32[i]);
+      }
+      __syncthreads();
+      if (grp == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < CJ; ++c) {
+            int64_t sum = rs_fold64(acc[i][c], c32[i]);  // |.| < 2^53 each: LS of them stay below 2^63
+            for (int q = 1; q < LS; ++q) sum += part[(((size_t)(q - 1) * 256 + ltid) * 4 + i) * CJ + c];
+            acc[i][c] = sum;
+          }
+      }
+    }
     // D = r - A mod p_k (plain: W is in Montgomery form, the finish removes R)
+    if (grp == 0) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = 4 * rg + i;
-      if (r >= bk) continue;
-      const ModP m = Ms[r];
+      for (int i = 0; i < 4; ++i) {
+        const int r = 4 * rg + i;
+        if (r >= bk) continue;
+        const ModP m = Ms[r];
 #pragma unroll
-      for (int c = 0; c < CJ; ++c) {
-        const int jj = CJ * cg + c, j = j0 + jj;
-        const uint32_t tA = finish64_3(rs_fold64(acc[i][c], m.r1), m);
-        const uint32_t res = j < N ? col[(size_t)(k0 + r) * S + j] : 0u;
-        Ds[r][jj] = msub(res, tA, m.p);
+        for (int c = 0; c < CJ; ++c) {
+          const int jj = CJ * cg + c, j = j0 + jj;
+          const uint32_t tA = finish64_3(rs_fold64(acc[i][c], m.r1), m);
+          const uint32_t res = j < N ? col[(size_t)(k0 + r) * S + j] : 0u;
+          Ds[r][jj] = msub(res, tA, m.p);
+        }
       }
     }
     for (int e = tid; e < G3T_BK * G3T_BK; e += blockDim.x) {
@@ -175,6 +220,94 @@ __global__ void __launch_bounds__(256, 4) g3t_kernel(G3Args a) {
     __syncthreads();  // this block's digits are read by the next digit blocks
   }
 }
+
+#define G3P_G 4     // digit rows per group
+#define G3P_LC 128  // earlier digits per staged chunk of W
+
+// Digits, one thread per coefficient: a block of 128 threads owns 128
+// consecutive coefficients of one pair (the same tasks as the output
+// kernel) and walks the digits in groups of 4 rows.  For the group
+// [k0, k0 + 4) each thread accumulates A[k0 + i] = sum_{l < k0} W[k0 + i][l] v_l
+// over its own earlier digits (re-read from the residue array they
+// overwrote, where they stay in L1) with the four W values of each l
+// broadcast from shared memory (one 16-byte load per l), lazily in int64 (a
+// fold every 7 products); then it finishes the group's four digits in turn
+// from the 4 x 4 triangle of W.  No warp waits for another: this is the form
+// for batches with many coefficients, where one thread per coefficient
+// fills the GPU (the tiled kernel serves batches with few coefficients and
+// many primes).
+__global__ void __launch_bounds__(128) g3p_kernel(G3Args a) {
+  __shared__ __align__(16) int32_t Ws[G3P_LC][G3P_G];  // W[k0 + i][l0 + c] at Ws[c][i]
+  __shared__ int32_t Wt[G3P_G][G3P_G];                 // W[k0 + i][k0 + c], c < i
+  __shared__ ModP Ms[G3P_G];
+  __shared__ uint32_t Cs[G3P_G];
+  const int2 task = a.tasks[blockIdx.x];
+  const PairDesc pd = a.pairs[task.x];
+  const int K = pd.K, N = pd.N, S = pd.NI, t = (int)threadIdx.x, j = task.y + t;
+  const bool live = j < N;
+  uint32_t *col = a.coef + pd.img_off + (live ? j : 0);  // residue, then digit, of row k at col[k S]
+  for (int k0 = 0; k0 < K; k0 += G3P_G) {
+    const int g = min(G3P_G, K - k0);
+    __syncthreads();  // the previous group's constants and triangle are no longer read
+    if (t < G3P_G) {
+      Ms[t] = a.mods[k0 + min(t, g - 1)];
+      Cs[t] = a.crt[k0 + min(t, g - 1)];
+    }
+    if (t < G3P_G * G3P_G) {
+      const int i = t >> 2, c = t & 3, k = k0 + i;
+      Wt[i][c] = (c < i && i < g) ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + k0 + c) : 0;
+    }
+    int64_t acc[G3P_G] = {0, 0, 0, 0};
+    uint32_t c32[G3P_G];
+    for (int l0 = 0; l0 < k0; l0 += G3P_LC) {
+      const int lc = min(G3P_LC, k0 - l0);
+      if (l0 > 0) __syncthreads();  // the previous chunk is no longer read
+#pragma unroll
+      for (int i = 0; i < G3P_G; ++i) {  // row k0 + i, entries l0 + t
+        const int k = k0 + i;
+        Ws[t][i] = (t < lc && i < g) ? __ldg(a.wtab + (size_t)k * (k - 1) / 2 + l0 + t) : 0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < G3P_G; ++i) c32[i] = Ms[i].r1;
+      int c = 0;
+      while (c < lc) {
+        const int cend = min(c + 7, lc);  // 7 products per fold
+#pragma unroll 7
+        for (; c < cend; ++c) {
+          const int32_t v = live ? (int32_t)col[(size_t)(l0 + c) * S] : 0;
+          const int4 w = *reinterpret_cast<const int4 *>(&Ws[c][0]);
+          acc[0] = rs_mac_s32(acc[0], w.x, v);
+          acc[1] = rs_mac_s32(acc[1], w.y, v);
+          acc[2] = rs_mac_s32(acc[2], w.z, v);
+          acc[3] = rs_mac_s32(acc[3], w.w, v);
+        }
+#pragma unroll
+        for (int i = 0; i < G3P_G; ++i) acc[i] = rs_fold64(acc[i], c32[i]);
+      }
+    }
+    __syncthreads();  // Ms, Cs, Wt of this group are in place
+    int32_t vg[G3P_G];
+#pragma unroll
+    for (int i = 0; i < G3P_G; ++i) {
+      if (i >= g) break;
+      const ModP m = Ms[i];
+      int64_t s2 = rs_fold64(acc[i], m.r1);  // |s2| < 2^53
+#pragma unroll
+      for (int c = 0; c < i; ++c) s2 = rs_mac_s32(s2, Wt[i][c], vg[c]);  // + at most 3 products < 2^60
+      s2 = rs_fold64(s2, m.r1);                                          // |s2| < 2^53 again
+      const uint32_t r = live ? col[(size_t)(k0 + i) * S] : 0u;
+      const uint32_t v = mmul(msub(r, finish64_3(s2, m), m.p), Cs[i], m);
+      vg[i] = signed_rep3(v, m.p);
+      if (live) col[(size_t)(k0 + i) * S] = (uint32_t)vg[i];
+    }
+  }
+}
+
+#ifndef RS_G3B_UNROLL
+#define RS_G3B_UNROLL 4
+#endif
+constexpr int kG3bUnroll = RS_G3B_UNROLL;  // prime rows of the limb kernel per loop iteration
 
 // a2:a1:a0 += x * y (96-bit accumulator, one carry chain).
 __device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t x, uint32_t y) {
@@ -212,7 +345,7 @@ __global__ void __launch_bounds__(128) g3b_kernel(G3Args a) {
 #pragma unroll
   for (int h = 0; h < 16; ++h) a0[h] = a1[h] = a2[h] = 0u;
   const uint32_t *col = a.coef + pd.img_off + j;
-#pragma unroll 2
+#pragma unroll kG3bUnroll
   for (int k = lo; k < K; ++k) {
     const uint32_t half = (__ldg(&a.mods[k].p) - 1u) >> 1;
     const uint32_t w = (uint32_t)((int32_t)col[(size_t)k * pd.NI] + (int32_t)half);
@@ -268,10 +401,18 @@ __global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
   uint32_t top_nz = 0u, top_nf = 0u, top = 0u;
   for (int c = 0; c < C; ++c) {
     if (live) {
+      // every load of the chunk first (they are independent), then the carry chain
+      uint32_t xw[16], pk[17];
+#pragma unroll
+      for (int w = 0; w < 16; ++w) xw[w] = xl[(size_t)(16 * c + w) * N];
+#pragma unroll
+      for (int w = 0; w < 17; ++w) pk[w] = 16 * c + w < plen ? __ldg(PK + 16 * c + w) : 0u;
+      const int64_t cy = a.carry[pd.cy_off + (size_t)c * N + j];
+#pragma unroll
       for (int w = 0; w < 16; ++w) {
         const int l = 16 * c + w;
-        const uint32_t h = (l < plen ? (__ldg(PK + l) >> 1) : 0u) | (l + 1 < plen ? (__ldg(PK + l + 1) << 31) : 0u);
-        const int64_t v = (int64_t)xl[(size_t)l * N] + r - (int64_t)h;
+        const uint32_t h = (pk[w] >> 1) | (pk[w + 1] << 31);
+        const int64_t v = (int64_t)xw[w] + r - (int64_t)h;
         const uint32_t limb = (uint32_t)v;
         r = v >> 32;
         T[t * 17 + w] = limb;
@@ -287,7 +428,7 @@ __global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
           top = limb;
         }
       }
-      r += a.carry[pd.cy_off + (size_t)c * N + j];
+      r += cy;
     }
     __syncthreads();
     const int nl = min(16, L - 16 * c);  // limbs of this chunk that exist
@@ -360,10 +501,17 @@ cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t
   at.tasks = ttasks;
   if (nt) {
     if (jt == 16)
-      g3t_kernel<16><<<nt, 256, 0, s>>>(at);
+      g3t_kernel<16, RS_G3T_LS16><<<nt, 256 * RS_G3T_LS16, 0, s>>>(at);
     else
-      g3t_kernel<32><<<nt, 256, 0, s>>>(at);
+      g3t_kernel<32, 1><<<nt, 256, 0, s>>>(at);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g3p(int nt, const G3Args &a, const int2 *tasks, cudaStream_t s) {
+  G3Args at = a;
+  at.tasks = tasks;
+  if (nt) g3p_kernel<<<nt, 128, 0, s>>>(at);
   return cudaGetLastError();
 }
 

@@ -186,6 +186,14 @@ cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int 
 // CRT digits by tiles of jt (32 or 16) coefficients (tasks step by jt), any
 // prime count.
 cudaError_t launch_g3t(int nt, const G3Args &a, const int2 *ttasks, cudaStream_t s, int jt = 32);
+// CRT digits with one thread per coefficient (tasks: (pair, first
+// coefficient) per block of 128 coefficients, the output kernel's tasks).
+cudaError_t launch_g3p(int nt, const G3Args &a, const int2 *tasks, cudaStream_t s);
+// Coefficients per SM from which a batch takes the one-thread-per-coefficient
+// digit kernel.
+#ifndef RS_G3P_MIN_COEF_PER_SM
+#define RS_G3P_MIN_COEF_PER_SM 1024
+#endif
 cudaError_t launch_yun(int ntasks, const YunArgs &a, cudaStream_t s);
 // Schur variant of G1: one block per tile, `slots` = ceil((m_y + n_y) / 32)
 // over the batch, smem = staged residues of the largest pair; then the

@@ -344,3 +344,24 @@ def test_product_formula_full_size(ctx):
         expect = zx_mul(expect, subst_y(g, al))
     got = ctx.resultant_y(f, g)
     assert len(got) == 1001 and got == expect
+
+
+def test_crt_one_thread_per_coefficient_small_prime_counts(ctx):
+    """A batch with enough coefficients (about 170,000) to take the CRT digit
+    kernel with one thread per coefficient, made of small pairs whose prime
+    counts run from 1 to about 25 (groups of four digit rows, partial ones
+    included): every result against the oracle O2, a sample against O1."""
+    from oracle import modular
+    rng = random.Random(71)
+    pairs = []
+    for i in range(4000):
+        bits = 2 + (i % 12) * 6
+        dx, dy = rng.randint(3, 6), rng.randint(3, 6)
+        pairs.append((rand_bipoly(rng, dx, dy, bits=bits), rand_bipoly(rng, dx, dy, bits=bits)))
+    nc = sum(rs.result_bound(f, g)["deg"] + 1 for f, g in pairs)
+    ks = {rs.result_bound(f, g)["primes"] for f, g in pairs[:24]}
+    assert nc >= 256 * 152 and {1, 2, 3, 5} <= ks, (nc, ks)
+    got = ctx.resultant_batch(pairs)
+    assert got == modular.resultants(pairs)
+    for i in range(0, 4000, 500):
+        assert got[i] == oracle(*pairs[i])
