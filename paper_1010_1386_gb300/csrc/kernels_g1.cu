@@ -45,7 +45,7 @@
 #define RS_G1_MINB RS_G1_MINB_SET  // tuning override for one capacity
 #endif
 #ifndef RS_G1_MINB
-#define RS_G1_MINB (RS_G1_CAP <= 16 ? 6 : RS_G1_CAP <= 24 ? 5 : RS_G1_CAP <= 40 ? 4 : 3)
+#define RS_G1_MINB (RS_G1_CAP <= 24 ? 6 : RS_G1_CAP <= 48 ? 4 : 3)
 #endif
 
 namespace {

@@ -47,6 +47,7 @@ __device__ __forceinline__ uint2 twiddle(const uint2 *rows, const uint2 *top, in
 #ifndef RS_G2N_ROTATE
 #define RS_G2N_ROTATE 1
 #endif
+
 __device__ __forceinline__ void load16(const uint32_t *g, uint32_t (&x)[16]) {
   const int h = RS_G2N_ROTATE ? (threadIdx.x >> 1) & 3 : 0;
   const uint4 *g4 = reinterpret_cast<const uint4 *>(g);

@@ -13,6 +13,7 @@ compiled with O2_PLANT = 1..7) must each fail the pins.
 import json
 import os
 import random
+import sys
 
 import numpy as np
 import pytest
@@ -137,11 +138,13 @@ def test_small_configs_and_stored_o1_digests():
     assert modular.resultant(f, g) == exact.resultant_y(f.to_ints(), g.to_ints())
     path = os.path.join(GOLDEN_DIR, "o1_pins.json")
     o1 = json.load(open(path))["workloads"]
+    sys.path.insert(0, GOLDEN_DIR)
+    from make_full_size import workloads
     checked = 0
-    for name, make in (("c1_single", lambda: inputs.workload_single(1)),
-                       ("c2_batch", lambda: inputs.workload_batch(2, n=512))):
-        done = o1.get(name, {})
-        pairs = make()
+    for name, done in o1.items():
+        if name == "c0_small":
+            continue
+        pairs = workloads()[name][1]()
         idx = sorted(int(i) for i in done)
         got = modular.resultants([pairs[i] for i in idx], threads=8)
         for i, R in zip(idx, got):
