@@ -4,10 +4,11 @@
 // (steps 1-2), then takes z_i^{(p)} = res(f(x_i, y), g(x_i, y), y) in Z_p.
 // The points come in pairs +-q^i (q of multiplicative order above the
 // largest point count, chosen per prime).  With f_j(x) = E_j(x^2) + x O_j(x^2)
-// (even and odd parts), both images of a pair need E_j and O_j at Q^i only,
-// Q = q^2: the two threads of a pair each evaluate one part, as a correlation
-// of chirp-scaled coefficients with the sequence Q^{C(t,2)} (accumulated
-// without per-term reduction), and exchange it with a shuffle:
+// (even and odd parts), both images of a pair need E_j(Q^i) and x O_j(Q^i)
+// only, Q = q^2, x = q^i: the sums of f_{j,k} q^{ik} over the even and over
+// the odd k.  The two threads of a pair each take one parity, as a
+// correlation of chirp-scaled coefficients with the sequence q^{C(t,2)}
+// (accumulated without per-term reduction), and exchange it with a shuffle:
 // f_j(+-q^i) = E_j(Q^i) +- q^i O_j(Q^i).  G2 splits the images back into
 // E and O and interpolates each with two convolutions.
 //
@@ -204,13 +205,18 @@ __device__ __forceinline__ int32_t signed_rep(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
 }
 
-// Evaluation of the even (par = 0) or odd (par = 1) part at Q^i by the chirp
-// identity i m = C(i+m,2) - C(i,2) - C(m,2):
-//   sum_m f_{j,2m+par} Q^{im} = Q^{-C(i,2)} sum_m (f_{j,2m+par} Q^{-C(m,2)}) Q^{C(i+m,2)}.
-// The staged coefficients a[k][r] = f_{deg-r,k} Q^{-C(k div 2,2)} (top-aligned
-// in r, zero past the degree) and the window w[t] = Q^{C(x0+t,2)} are signed
-// representatives (|v| < 2^30): 7 products accumulate exactly in an int64,
-// then one fold S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53.
+// Evaluation of the sum over the k of parity par (0 even, 1 odd) at x = q^i
+// by the chirp identity i k = C(i+k,2) - C(i,2) - C(k,2):
+//   sum_{k = par mod 2} f_{j,k} q^{ik} = q^{-C(i,2)} sum_{k = par mod 2} (f_{j,k} q^{-C(k,2)}) q^{C(i+k,2)},
+// which is E_j(Q^i) for par = 0 and x O_j(Q^i) for par = 1.  The factor
+// w_i = q^{-C(i,2)} is the same for every coefficient of f and g at the point
+// pair, and the Sylvester determinant is homogeneous of degree n_y in the
+// f-entries and m_y in the g-entries, so the coefficients are left without
+// it and the image is multiplied by w_i^(m_y + n_y) at the end.  The staged
+// coefficients a[k][r] = f_{deg-r,k} q^{-C(k,2)} (top-aligned in r, zero past
+// the degree) and the window w[t] = q^{C(x0+t,2)} are signed representatives
+// (|v| < 2^30): 7 products accumulate exactly in an int64, then one fold
+// S = hi 2^32 + lo -> hi (2^32 mod p) + lo keeps |S| < 2^53.
 __device__ __forceinline__ int64_t fold64(int64_t s, uint32_t c32) { return rs_fold64(s, c32); }
 
 __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
@@ -219,8 +225,7 @@ __device__ __forceinline__ uint32_t finish64(int64_t s, const ModP &m) {
 
 template <int C>
 __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, const int2 *meta,
-                                           int deg, const int32_t *win, uint32_t wi, int par,
-                                           const ModP &m) {
+                                           int deg, const int32_t *win, int par, const ModP &m) {
   const uint32_t c32 = m.r1;  // 2^32 mod p (<= 2^21 for every table prime)
 #pragma unroll
   for (int r0 = 0; r0 < C; r0 += 8) {
@@ -231,12 +236,12 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr)
       if (deg - (r0 + rr) >= 0) kmax = max(kmax, meta[deg - (r0 + rr)].y);
-    int k = par;  // rows par, par + 2, ...: window entry k / 2
+    int k = par;  // rows par, par + 2, ...: window entry k
     while (k <= kmax) {
       const int kend = min(k + 14, kmax + 1);  // 7 products per fold
 #pragma unroll 1
       for (; k < kend; k += 2) {
-        const int32_t c = win[k >> 1];
+        const int32_t c = win[k];
         const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
         const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
         acc[0] = rs_mac_s32(acc[0], lo.x, c);
@@ -252,23 +257,23 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
       for (int rr = 0; rr < 8; ++rr) acc[rr] = fold64(acc[rr], c32);
     }
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) P[r0 + rr] = kmax >= 0 ? mmul(finish64(acc[rr], m), wi, m) : 0u;
+    for (int rr = 0; rr < 8; ++rr) P[r0 + rr] = kmax >= 0 ? finish64(acc[rr], m) : 0u;
   }
 }
 
-// f_j(+-x) = E_j + (+-x) O_j from the partner lane's part: lane par = 0 holds
-// E_j and keeps +x, lane par = 1 holds O_j and takes -x (xs = +-x).
+// f_j(+-x) = E_j +- x O_j from the partner lane's part: lane par = 0 holds
+// E_j and keeps +x, lane par = 1 holds x O_j and takes -x.
 template <int C>
-__device__ __forceinline__ void combine_pm(uint32_t (&P)[C], int par, uint32_t xs, const ModP &m) {
+__device__ __forceinline__ void combine_pm(uint32_t (&P)[C], int par, const ModP &m) {
 #pragma unroll
   for (int r = 0; r < C; ++r) {
     const uint32_t other = __shfl_xor_sync(0xffffffffu, P[r], 1);
     const uint32_t e = par ? other : P[r], o = par ? P[r] : other;
-    P[r] = madd(e, mmul(o, xs, m), m.p);
+    P[r] = par ? msub(e, o, m.p) : madd(e, o, m.p);
   }
 }
 
-// a[k][r] for k <= dx (the largest x-degree), r < C; qn[t] = Q^{-C(t,2)}.
+// a[k][r] for k <= dx (the largest x-degree), r < C; qn[t] = q^{-C(t,2)}.
 template <int C>
 __device__ __forceinline__ void stage_chirp(int32_t *sa, const int2 *smeta, int deg, int dx,
                                             const uint32_t *limbs, int stride, int L,
@@ -278,7 +283,7 @@ __device__ __forceinline__ void stage_chirp(int32_t *sa, const int2 *smeta, int 
     const int k = idx / C, r = idx - k * C, j = deg - r;
     int32_t v = 0;
     if (j >= 0 && k <= smeta[j].y)
-      v = signed_rep(mmul(reduce_coef(limbs + ((size_t)k * stride + j) * L, L, V, m), qn[k >> 1], m), m.p);
+      v = signed_rep(mmul(reduce_coef(limbs + ((size_t)k * stride + j) * L, L, V, m), qn[k], m), m.p);
     sa[idx] = v;
   }
 }
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
     const size_t tb = (size_t)tl.prime * a.tstride;
 
     for (int i = threadIdx.x; i < nmeta; i += blockDim.x) smeta[i] = a.meta[pd.meta_off + i];
-    for (int t = threadIdx.x; t < (int)(blockDim.x >> 1) + (dxm >> 1) + 1; t += blockDim.x)
+    for (int t = threadIdx.x; t < (int)(blockDim.x >> 1) + dxm + 1; t += blockDim.x)
       swin[t] = a.qc[tb + tl.x0 + t];
     __syncthreads();
     stage_chirp<C>(saf, smeta, pd.my, pd.mxf, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, a.qn + tb, m);
@@ -333,13 +338,11 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
     const int i = tl.x0 + ti;  // point pair: this thread's image is at (-1)^par q^i
     // every thread evaluates (the shuffles need the whole warp); only the
     // threads of the tile's pairs run the remainder sequence
-    const uint32_t wi = a.qn[tb + i], x = a.qp[tb + i];  // Q^{-C(i,2)}, q^i
-    const uint32_t xs = par ? mneg(x, m.p) : x;
     uint32_t A[C], B[C];
-    eval_chirp<C>(A, saf, smeta, pd.my, swin + ti, wi, par, m);
-    eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + ti, wi, par, m);
-    combine_pm<C>(A, par, xs, m);
-    combine_pm<C>(B, par, xs, m);
+    eval_chirp<C>(A, saf, smeta, pd.my, swin + ti, par, m);
+    eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + ti, par, m);
+    combine_pm<C>(A, par, m);
+    combine_pm<C>(B, par, m);
     if (ti < tl.n) {
       unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
       Prs s;
@@ -350,6 +353,8 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
       s.sign = 0u;
       s.degen = 0u;
       prs_run<C>(A, B, s, m);
+      // the chirp factor left out of the coefficients (reloaded: no register held through the sequence)
+      s.num = mmul(s.num, mpow(a.qn[tb + i], (uint32_t)(pd.my + pd.ny), m), m);
       while (s.eprev > 0) {
         s.den = mmul(s.den, s.Q, m);
         --s.eprev;

@@ -166,7 +166,8 @@ __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, in
   const uint32_t qb = qbase[k], qbi = minv(qb, m);
   const uint32_t q = mmul(qb, qb, m), qi = minv(q, m);  // Q and 1/Q
   {
-    uint32_t up = m.r1, dn = m.r1, qt = m.r1, qit = m.r1, pw = m.r1;  // Q^{C(t,2)}, Q^{-C(t,2)}, Q^t, Q^{-t}, q^t
+    // the chirp tables of the evaluation, base q: q^{C(t,2)}, q^{-C(t,2)}, and q^t
+    uint32_t up = m.r1, dn = m.r1, pw = m.r1, piw = m.r1;  // q^{C(t,2)}, q^{-C(t,2)}, q^t, q^{-t}
     int32_t *qc = qct + (size_t)k * stride;
     uint32_t *qn = qnt + (size_t)k * stride;
     uint32_t *qp = qpt + (size_t)k * stride;
@@ -174,11 +175,10 @@ __global__ void tables_kernel(const ModP *mods, const uint32_t *qbase, int K, in
       qc[t] = signed_rep(up, m.p);
       qn[t] = dn;
       qp[t] = pw;
-      up = mmul(up, qt, m);  // C(t+1,2) = C(t,2) + t
-      dn = mmul(dn, qit, m);
-      qt = mmul(qt, q, m);
-      qit = mmul(qit, qi, m);
+      up = mmul(up, pw, m);  // C(t+1,2) = C(t,2) + t
+      dn = mmul(dn, piw, m);
       pw = mmul(pw, qb, m);
+      piw = mmul(piw, qbi, m);
     }
   }
   if (!finv) return;
