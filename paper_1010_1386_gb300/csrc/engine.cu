@@ -487,13 +487,26 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     cl.threads = T;
     cl.persistent = ch.persistent;
     cl.tile_off = (int64_t)tiles.size();
+    // Work items of `run` consecutive chunks of T / 2 point pairs: the block
+    // stages a (pair, prime)'s coefficients once per item and walks its
+    // chunks.  Runs are as long as the class allows while it keeps at least
+    // 16 items per SM for the scheduler to balance.
+    int64_t chunks = 0;
+    for (int i : members) chunks += (int64_t)b->plans[i].K * (((b->plans[i].N + 1) / 2 + T / 2 - 1) / (T / 2));
+    const int run = (int)std::max<int64_t>(1, chunks / (16 * (int64_t)ctx->sms));
     for (int i : members) {
       const PairPlan &p = b->plans[i];
       cl.cost += (double)p.K * p.N * (p.f.nc + p.g.nc + 2.0 * p.f.my * p.g.my);
       cl.smem = std::max(cl.smem, (size_t)rs_g1_staged_words(p, cap, T) * 4);
-      for (int k = 0; k < p.K; ++k)
-        for (int x0 = 0; x0 < (p.N + 1) / 2; x0 += T / 2)  // point pairs: two threads each
-          tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T / 2, (p.N + 1) / 2 - x0)});
+      const int M = (p.N + 1) / 2;  // point pairs: two threads each
+      for (int k = 0; k < p.K; ++k) {
+        if (ctx->cfg.univariate == 0) {
+          for (int x0 = 0; x0 < M; x0 += run * (T / 2))
+            tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(run * (T / 2), M - x0)});
+        } else {
+          for (int x0 = 0; x0 < M; x0 += T / 2) tiles.push_back(Tile{b->dev_index[i], k, x0, std::min(T / 2, M - x0)});
+        }
+      }
     }
     cl.ntiles = (int)((int64_t)tiles.size() - cl.tile_off);
     if (cl.ntiles > 0) b->classes.push_back(cl);

@@ -318,8 +318,6 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
     const size_t tb = (size_t)tl.prime * a.tstride;
 
     for (int i = threadIdx.x; i < nmeta; i += blockDim.x) smeta[i] = a.meta[pd.meta_off + i];
-    for (int t = threadIdx.x; t < (int)(blockDim.x >> 1) + dxm + 1; t += blockDim.x)
-      swin[t] = a.qc[tb + tl.x0 + t];
     __syncthreads();
     stage_chirp<C>(saf, smeta, pd.my, pd.mxf, a.limbs + pd.f_off, pd.fstride, pd.Lf, V, a.qn + tb, m);
     stage_chirp<C>(sag, smeta + pd.my + 1, pd.ny, pd.mxg, a.limbs + pd.g_off, pd.gstride, pd.Lg, V,
@@ -333,44 +331,52 @@ __global__ void __launch_bounds__(128, RS_G1_MINB) g1_kernel(G1Args a) {
       if (zf || zg) atomicAdd(a.stats + ST_UNLUCKY_PRIMES, 1ull);
     }
 
-    uint32_t unlucky = 0u, degen = 0u;
+    // The work item's point pairs [x0, x0 + n) in chunks of blockDim / 2: the
+    // staged coefficients serve every chunk, only the window is reloaded.
     const int ti = (int)threadIdx.x >> 1, par = (int)threadIdx.x & 1;
-    const int i = tl.x0 + ti;  // point pair: this thread's image is at (-1)^par q^i
-    // every thread evaluates (the shuffles need the whole warp); only the
-    // threads of the tile's pairs run the remainder sequence
-    uint32_t A[C], B[C];
-    eval_chirp<C>(A, saf, smeta, pd.my, swin + ti, par, m);
-    eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + ti, par, m);
-    combine_pm<C>(A, par, m);
-    combine_pm<C>(B, par, m);
-    if (ti < tl.n) {
-      unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
-      Prs s;
-      s.a = pd.my;
-      s.b = pd.ny;
-      s.num = s.den = s.Q = m.r1;
-      s.eprev = max(min(pd.my, pd.ny) - 1, 0);
-      s.sign = 0u;
-      s.degen = 0u;
-      prs_run<C>(A, B, s, m);
-      // the chirp factor left out of the coefficients (reloaded: no register held through the sequence)
-      s.num = mmul(s.num, mpow(a.qn[tb + i], (uint32_t)(pd.my + pd.ny), m), m);
-      while (s.eprev > 0) {
-        s.den = mmul(s.den, s.Q, m);
-        --s.eprev;
+    const int half = (int)(blockDim.x >> 1);
+    for (int cx = tl.x0; cx < tl.x0 + tl.n; cx += half) {
+      const int nn = min(half, tl.x0 + tl.n - cx);
+      for (int t = threadIdx.x; t < half + dxm + 1; t += blockDim.x) swin[t] = a.qc[tb + cx + t];
+      __syncthreads();
+      uint32_t unlucky = 0u, degen = 0u;
+      const int i = cx + ti;  // point pair: this thread's image is at (-1)^par q^i
+      // every thread evaluates (the shuffles need the whole warp); only the
+      // threads of the chunk's pairs run the remainder sequence
+      uint32_t A[C], B[C];
+      eval_chirp<C>(A, saf, smeta, pd.my, swin + ti, par, m);
+      eval_chirp<C>(B, sag, smeta + pd.my + 1, pd.ny, swin + ti, par, m);
+      combine_pm<C>(A, par, m);
+      combine_pm<C>(B, par, m);
+      if (ti < nn) {
+        unlucky = (A[0] == 0u || B[0] == 0u) ? 1u : 0u;
+        Prs s;
+        s.a = pd.my;
+        s.b = pd.ny;
+        s.num = s.den = s.Q = m.r1;
+        s.eprev = max(min(pd.my, pd.ny) - 1, 0);
+        s.sign = 0u;
+        s.degen = 0u;
+        prs_run<C>(A, B, s, m);
+        // the chirp factor left out of the coefficients (reloaded: no register held through the sequence)
+        s.num = mmul(s.num, mpow(a.qn[tb + i], (uint32_t)(pd.my + pd.ny), m), m);
+        while (s.eprev > 0) {
+          s.den = mmul(s.den, s.Q, m);
+          --s.eprev;
+        }
+        const size_t idx = (size_t)pd.img_off + (size_t)tl.prime * pd.NI + 2 * i + par;
+        a.num[idx] = s.sign ? mneg(s.num, m.p) : s.num;
+        a.den[idx] = s.den;
+        degen = s.degen;
       }
-      const size_t idx = (size_t)pd.img_off + (size_t)tl.prime * pd.NI + 2 * i + par;
-      a.num[idx] = s.sign ? mneg(s.num, m.p) : s.num;
-      a.den[idx] = s.den;
-      degen = s.degen;
+      const unsigned bu = __ballot_sync(0xffffffffu, unlucky);
+      const unsigned bd = __ballot_sync(0xffffffffu, degen);
+      if ((threadIdx.x & 31) == 0) {
+        if (bu) atomicAdd(a.stats + ST_UNLUCKY_POINTS, (unsigned long long)__popc(bu));
+        if (bd) atomicAdd(a.stats + ST_DEGENERATE, (unsigned long long)__popc(bd));
+      }
+      __syncthreads();  // the next chunk reloads the window (the next item restages everything)
     }
-    const unsigned bu = __ballot_sync(0xffffffffu, unlucky);
-    const unsigned bd = __ballot_sync(0xffffffffu, degen);
-    if ((threadIdx.x & 31) == 0) {
-      if (bu) atomicAdd(a.stats + ST_UNLUCKY_POINTS, (unsigned long long)__popc(bu));
-      if (bd) atomicAdd(a.stats + ST_DEGENERATE, (unsigned long long)__popc(bd));
-    }
-    __syncthreads();  // the next tile restages shared memory
   }
 }
 
