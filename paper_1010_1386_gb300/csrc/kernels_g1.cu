@@ -236,26 +236,33 @@ __device__ __forceinline__ void eval_chirp(uint32_t (&P)[C], const int32_t *sa, 
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr)
       if (deg - (r0 + rr) >= 0) kmax = max(kmax, meta[deg - (r0 + rr)].y);
-    int k = par;  // rows par, par + 2, ...: window entry k
-    while (k <= kmax) {
-      const int kend = min(k + 14, kmax + 1);  // 7 products per fold
+    auto step = [&](int k) {
+      const int32_t c = win[k];
+      const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
+      const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
+      acc[0] = rs_mac_s32(acc[0], lo.x, c);
+      acc[1] = rs_mac_s32(acc[1], lo.y, c);
+      acc[2] = rs_mac_s32(acc[2], lo.z, c);
+      acc[3] = rs_mac_s32(acc[3], lo.w, c);
+      acc[4] = rs_mac_s32(acc[4], hi.x, c);
+      acc[5] = rs_mac_s32(acc[5], hi.y, c);
+      acc[6] = rs_mac_s32(acc[6], hi.z, c);
+      acc[7] = rs_mac_s32(acc[7], hi.w, c);
+    };
+    // rows par, par + 2, ... (window entry k): full groups of 7 products per
+    // fold unrolled, then the rest
+    int k = par;
 #pragma unroll 1
-      for (; k < kend; k += 2) {
-        const int32_t c = win[k];
-        const int4 lo = *reinterpret_cast<const int4 *>(sa + k * C + r0);
-        const int4 hi = *reinterpret_cast<const int4 *>(sa + k * C + r0 + 4);
-        acc[0] = rs_mac_s32(acc[0], lo.x, c);
-        acc[1] = rs_mac_s32(acc[1], lo.y, c);
-        acc[2] = rs_mac_s32(acc[2], lo.z, c);
-        acc[3] = rs_mac_s32(acc[3], lo.w, c);
-        acc[4] = rs_mac_s32(acc[4], hi.x, c);
-        acc[5] = rs_mac_s32(acc[5], hi.y, c);
-        acc[6] = rs_mac_s32(acc[6], hi.z, c);
-        acc[7] = rs_mac_s32(acc[7], hi.w, c);
-      }
+    for (; k + 12 <= kmax; k += 14) {
+#pragma unroll
+      for (int u = 0; u < 7; ++u) step(k + 2 * u);
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) acc[rr] = fold64(acc[rr], c32);
     }
+#pragma unroll 1
+    for (; k <= kmax; k += 2) step(k);
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) acc[rr] = fold64(acc[rr], c32);
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr) P[r0 + rr] = kmax >= 0 ? finish64(acc[rr], m) : 0u;
   }
