@@ -47,6 +47,9 @@ __device__ __forceinline__ uint2 twiddle(const uint2 *rows, const uint2 *top, in
 #ifndef RS_G2N_ROTATE
 #define RS_G2N_ROTATE 1
 #endif
+#ifndef RS_G2N_MINB
+#define RS_G2N_MINB 3  // resident blocks per SM requested from ptxas (caps registers at 85)
+#endif
 
 __device__ __forceinline__ void load16(const uint32_t *g, uint32_t (&x)[16]) {
   const int h = RS_G2N_ROTATE ? (threadIdx.x >> 1) & 3 : 0;
@@ -317,7 +320,7 @@ __device__ __forceinline__ int32_t srep(uint32_t v, uint32_t p) {
 // images give E(Q^i) and O(Q^i), interpolated in turn into the even and the
 // odd coefficients.  Shared memory: X, V0, V1, Oh (M words each), W (2^lg
 // words), twiddle rows 1 .. lg-1 (2^(lg-1) - 1 pairs).
-__global__ void __launch_bounds__(256, 3) g2n_kernel(G2nArgs a) {
+__global__ void __launch_bounds__(256, RS_G2N_MINB) g2n_kernel(G2nArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   __shared__ uint32_t scratch[128];
   const int2 task = a.tasks[blockIdx.x];
