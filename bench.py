@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "resultants/s batched vs per-instance launch, same GB300; % of INT32 IMAD peak"
-INTERP = {"auto": 0, "direct": 1, "transforms": 2, "triangular": 3}
+INTERP = {"auto": 0, "direct": 1, "transforms": 2, "triangular": 3, "tensor": 4}
 SQF_METRIC = "square-free factorisations of Res_y(f, g) per second (R = c prod R_i^i), one GB300"
 IMAD_PER_SM_CLK = 64  # nominal 32-bit integer multiply-add results per clock per SM
 WORKLOADS = {
@@ -546,7 +546,10 @@ def batch_main(args, world, rank, local, dist):
                       "interpolation": {"auto": "convolutions (direct or transforms per pair)",
                                         "direct": "direct convolutions", "transforms": "transforms",
                                         "triangular": "triangular factorisation of the Vandermonde "
-                                                      "system (Bjorck-Pereyra stages)"}[args.interp],
+                                                      "system (Bjorck-Pereyra stages)",
+                                        "tensor": "convolutions of all pairs of a prime as exact matrix "
+                                                  "products on the tensor cores (bf16 digits, fp32 "
+                                                  "accumulation)"}[args.interp],
                       "l2": "256 MiB written before every timed step (outside its events); per-step "
                             "working set (num/den images) %.0f MB" % (info["images"] * 8 / 1e6)})
     line.update({

@@ -97,7 +97,9 @@ typedef struct {
                                 convolutions (lazily reduced dot products) only, 2 = number-theoretic
                                 transforms wherever D + 1 <= 4096, 3 = triangular factorisation of the
                                 Vandermonde system (the paper's Section 4.1 solve; comparison form,
-                                D + 1 <= 14,000) */
+                                D + 1 <= 14,000), 4 = the convolutions of all pairs of a prime as
+                                one exact matrix product on the tensor cores (bf16 digit products
+                                with fp32 accumulation) wherever D + 1 <= 8192 */
   int32_t univariate;        /* univariate resultants mod p (G1): 0 = division-free remainder
                                 sequence, one thread per image; 1 = the generalised Schur algorithm
                                 on displacement generators of the Sylvester matrix (the paper's

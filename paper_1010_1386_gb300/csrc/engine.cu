@@ -224,6 +224,29 @@ int rs_ensure_bhat(rs_ctx *ctx, int lg, int K) {
   return RS_OK;
 }
 
+int rs_ensure_g2t_btile(rs_ctx *ctx, int K, int tiles) {
+  std::lock_guard<std::mutex> lock(ctx->tab_mu);
+  if (ctx->g2t_K >= K && ctx->g2t_tiles >= tiles) return RS_OK;
+  const RsTables &t = ctx->tab;
+  const int nK = std::max(K, ctx->g2t_K), nt = std::max(tiles, ctx->g2t_tiles);
+  if (t.K < nK)
+    return rs_fail(ctx, RS_ERR_STATE, "tensor-core G2 tables: point tables not built for these primes");
+  DevGuard dg(ctx->device);
+  uint16_t *nb = nullptr;
+  cudaError_t e = cudaMalloc(&nb, (size_t)nK * nt * 8192 * sizeof(uint16_t));
+  if (e == cudaSuccess) e = launch_g2t_btile(t.btab, t.N, t.N, nK, nt, nb, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (nb) cudaFree(nb);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core G2 tables: ") + cudaGetErrorString(e));
+  }
+  if (ctx->g2t_bt) ctx->g2t_retired.push_back(ctx->g2t_bt);
+  ctx->g2t_bt = nb;
+  ctx->g2t_K = nK;
+  ctx->g2t_tiles = nt;
+  return RS_OK;
+}
+
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   std::lock_guard<std::mutex> lock(ctx->tab_mu);
   const int need_c = N + 128 + dx + 1;
@@ -325,6 +348,7 @@ void rs_free_batch(rs_batch *b) {
 void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, const rs_bipoly *g,
                     int64_t *in_words, int64_t *out_words, int64_t *device_bytes) {
   int64_t in = 0, out = 0, img = 0, meta = 0, tiles = 0, g2 = 0, g3 = 0, xl = 0, cy = 0, g3d = 0, g3b = 0;
+  int64_t t_items = 0, t_bytes = 0;  // tensor-core G2 work items and buffers, if every pair takes that form
   for (size_t i = 0; i < plans.size(); ++i) {
     in += rs_input_words(f[i]) + rs_input_words(g[i]);
     const PairPlan &p = plans[i];
@@ -337,6 +361,9 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     meta += p.f.my + p.g.my + 2;
     tiles += (int64_t)p.K * (((p.N + 1) / 2 + 15) / 16);
     g2 += p.K;
+    const int64_t mt = (((p.N + 1) / 2 + 63) / 64) * 64;
+    t_items += (int64_t)p.K * (mt / 64);
+    t_bytes += (int64_t)p.K * mt * 2 * (4 * 2 + 4);  // two rows: four bf16 digits and one product per input
     g3 += (p.N + 127) / 128;
     g3d += (p.N + 31) / 32;  // digit tiles
     g3b += (p.N + 127) / 128 * chunks;
@@ -344,13 +371,14 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
   // inputs plus room for the static tables (descriptors, tiles, task lists)
   // that rs_build_batch packs behind them in borrowed pinned staging
   const int64_t stat = meta * 2 + (int64_t)plans.size() * (int64_t)(sizeof(PairDesc) / 4) + tiles * 4 +
-                       g2 * 2 + g3 * 2 + g3d * 4 + g3b * 4 + 8 * 4;
+                       g2 * 2 + g3 * 2 + g3d * 4 + g3b * 4 + 8 * 4 + g2 * 4 + g2 * 8 + t_items * 2;
   *in_words = in + stat;
-  *out_words = out;
+  *out_words = out + 1;
   *device_bytes = (int64_t)(align_up(in * 4) + align_up(meta * 8) + align_up(plans.size() * sizeof(PairDesc)) +
                             align_up(tiles * sizeof(Tile)) + kAlign + 2 * align_up(img * 4) +
                             align_up(xl * 4) + align_up(out * 4) + align_up(cy * 8) + align_up(g2 * 8) +
-                            align_up(g3 * 8) + align_up(g3d * 8) + align_up(g3b * 16) + kAlign);
+                            align_up(g3 * 8) + align_up(g3d * 8) + align_up(g3b * 16) + kAlign +
+                            align_up(g2 * 16) + align_up(g2 * 32) + align_up(t_items * 8) + align_up(t_bytes));
 }
 
 int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
@@ -439,7 +467,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     b->info.modmul_crt += (double)p.N * ((double)d.K * (d.K - 1) + d.K);
   }
   b->shape_off = b->out_words;  // per pair (1 + degree, limbs), written by the last CRT kernel
-  if (!images_only) b->out_words += 2 * (int64_t)b->descs.size();
+  b->status_off = b->shape_off + 2 * (int64_t)b->descs.size();
+  if (!images_only) b->out_words += 2 * (int64_t)b->descs.size() + 1;  // + the device status word
   if (images_only) b->out_words = std::max(b->out_words, b->img_words);
 
   // G1 tiles grouped by register-capacity class; costliest pairs first.
@@ -545,7 +574,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // The form is chosen per transform-length group: forced by the context or
   // the options, else the tuner's cached choice (timed now when missing and
   // allowed; groups with lg < 9 keep the model's choice), else the model.
-  std::vector<int> g2lg(n, 0);
+  std::vector<int> g2lg(n, 0), g2t_lg(n, 0);  // transform / tensor-core length group per pair
   int bhatK[RS_NTT_LGMAX + 1] = {};
   const bool g2tri = ctx->cfg.g2_form == 3;  // triangular factorisation of the Vandermonde system
   if (g2tri && !images_only && !order.empty()) {
@@ -583,8 +612,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       }
       const int model = cn < cd ? 1 : 0;
       int form = model;
-      if (ctx->cfg.g2_form == 1 || ctx->cfg.g2_form == 2) {
-        form = ctx->cfg.g2_form == 2 ? 1 : 0;
+      if (ctx->cfg.g2_form == 1 || ctx->cfg.g2_form == 2 || ctx->cfg.g2_form == 4) {
+        form = ctx->cfg.g2_form == 2 ? 1 : ctx->cfg.g2_form == 4 ? 2 : 0;
       } else if (opt.g2_force >= 0) {
         form = opt.g2_force;
       } else if (lg >= 9) {
@@ -601,11 +630,81 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
         }
       }
       if (!form) continue;
+      if (form == 2) {
+        for (int i : bylg[lg]) g2t_lg[i] = lg;
+        continue;
+      }
       for (int i : bylg[lg]) {
         g2lg[i] = lg;
         bhatK[lg] = std::max(bhatK[lg], b->plans[i].K);
       }
     }
+  }
+  // Tensor-core classes, one per length group: for every prime k, the
+  // group's pairs with K > k in decreasing point count, 64 to a row tile
+  // (rows 2 slot, 2 slot + 1: even and odd part); a tile's length is its
+  // first pair's point-pair count rounded up to 64.  Work items: every 64
+  // outputs of every tile, tiles by decreasing length, outputs from the top
+  // (the longest items first; a tile's items run close together in time,
+  // so its operand digits are read from L2).
+  std::vector<G2tTask> g2t_tasks;
+  std::vector<G2tRowTile> g2t_rts;
+  std::vector<G2tItem> g2t_items;
+  int64_t g2t_y_words = 0;
+  int g2t_kmax = 0, g2t_tiles = 0;
+  b->g2t_x_elems = 0;
+  for (int lg = RS_NTT_LGMAX; lg > 0 && !images_only && !g2tri; --lg) {
+    std::vector<int> mem;
+    for (int i : byN)
+      if (g2t_lg[i] == lg) mem.push_back(i);
+    if (mem.empty()) continue;
+    RsG2Class gc;
+    gc.lg = lg;
+    gc.tensor = true;
+    gc.t_task_off = (int64_t)g2t_tasks.size();
+    gc.t_item_off = (int64_t)g2t_items.size();
+    const int rt0 = (int)g2t_rts.size();
+    int kmax = 0;
+    for (int i : mem) kmax = std::max(kmax, b->plans[i].K);
+    for (int k = 0; k < kmax; ++k) {
+      std::vector<int> rows;
+      for (int i : mem)
+        if (b->plans[i].K > k) rows.push_back(i);
+      for (size_t c0 = 0; c0 < rows.size(); c0 += 64) {
+        const int cnt = (int)std::min<size_t>(64, rows.size() - c0);
+        G2tRowTile rt;
+        memset(&rt, 0, sizeof(rt));
+        rt.prime = k;
+        rt.mt = (((b->plans[rows[c0]].N + 1) / 2 + 63) / 64) * 64;
+        rt.rows = 2 * cnt;
+        rt.x_off = b->g2t_x_elems;
+        rt.y_off = g2t_y_words;
+        b->g2t_x_elems += (int64_t)(rt.mt / 64) * 32768;
+        g2t_y_words += (int64_t)128 * rt.mt;
+        const int rti = (int)g2t_rts.size();
+        g2t_rts.push_back(rt);
+        for (int sl = 0; sl < cnt; ++sl) {
+          G2tTask t;
+          t.pair = b->dev_index[rows[c0 + sl]];
+          t.prime = k;
+          t.rt = rti;
+          t.slot = sl;
+          g2t_tasks.push_back(t);
+          gc.t_maxM = std::max(gc.t_maxM, (b->plans[rows[c0 + sl]].N + 1) / 2);
+        }
+        g2t_tiles = std::max(g2t_tiles, rt.mt / 32);
+      }
+    }
+    g2t_kmax = std::max(g2t_kmax, kmax);
+    std::vector<int> ord;
+    for (int r = rt0; r < (int)g2t_rts.size(); ++r) ord.push_back(r);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return g2t_rts[x].mt > g2t_rts[y].mt; });
+    for (int r : ord)
+      for (int t0 = g2t_rts[r].mt - 64; t0 >= 0; t0 -= 64) g2t_items.push_back(G2tItem{r, t0});
+    gc.t_ntask = (int)((int64_t)g2t_tasks.size() - gc.t_task_off);
+    gc.t_nitem = (int)((int64_t)g2t_items.size() - gc.t_item_off);
+    gc.count = gc.t_ntask;
+    b->g2cls.push_back(gc);
   }
   for (int lg = RS_NTT_LGMAX; lg > 0; --lg) {
     if (!bhatK[lg]) continue;
@@ -630,7 +729,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     int cmaxN = 0;
     for (int i : byN) {
       const PairPlan &p = b->plans[i];
-      if (g2lg[i]) continue;
+      if (g2lg[i] || g2t_lg[i]) continue;
       const int npair = (((p.N + 1) / 2 + RS_CONV_R - 1) / RS_CONV_R + 1) / 2;  // output-block pairs
       const int rounds = (npair + 255) / 256;
       const int warps = (npair + 32 * rounds - 1) / (32 * rounds);
@@ -692,11 +791,14 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                             (b->nyun > 0) +
                             (b->ng3b > 0) +
                             (b->ng3 > 0);
+  for (const auto &gc : b->g2cls)
+    if (gc.tensor) b->info.kernel_launches += 4;  // five launches per tensor-core class
 
   int rc = RS_OK;
   if (!order.empty()) rc = rs_ensure_tables(ctx, maxK, maxM, maxDx);
   for (int lg = 1; lg <= RS_NTT_LGMAX && rc == RS_OK; ++lg)
     if (bhatK[lg]) rc = rs_ensure_bhat(ctx, lg, bhatK[lg]);
+  if (rc == RS_OK && g2t_kmax > 0) rc = rs_ensure_g2t_btile(ctx, g2t_kmax, g2t_tiles);
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;
@@ -716,7 +818,10 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                o_st = carve(ST_COUNT * sizeof(unsigned long long)), o_cy = carve(b->cy_words * 8),
                o_g3d = carve(g3d.size() * sizeof(int2)), o_yt = carve(yun.size() * sizeof(int2)),
                o_yo = carve((size_t)b->nyun * b->yun_ostride * 4), o_yw = carve((size_t)b->nyun * 8 * b->yun_wstride * 4),
-               o_g3b = carve(g3b.size() * sizeof(int4)), o_fail = carve(b->schur ? b->img_words * sizeof(int2) : 0);
+               o_g3b = carve(g3b.size() * sizeof(int4)), o_fail = carve(b->schur ? b->img_words * sizeof(int2) : 0),
+               o_tt = carve(g2t_tasks.size() * sizeof(G2tTask)), o_trt = carve(g2t_rts.size() * sizeof(G2tRowTile)),
+               o_tit = carve(g2t_items.size() * sizeof(G2tItem)), o_tx = carve(b->g2t_x_elems * sizeof(uint16_t)),
+               o_ty = carve(g2t_y_words * 4);
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
     b->arena = nullptr;
@@ -743,6 +848,20 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_yun_work = (uint32_t *)(base + o_yw);
   b->d_g3b = (int4 *)(base + o_g3b);
   b->d_fail = b->schur ? (int2 *)(base + o_fail) : nullptr;
+  b->d_g2t_tasks = (G2tTask *)(base + o_tt);
+  b->d_g2t_rts = (G2tRowTile *)(base + o_trt);
+  b->d_g2t_items = (G2tItem *)(base + o_tit);
+  b->d_g2t_x = (uint16_t *)(base + o_tx);
+  b->d_g2t_y = (uint32_t *)(base + o_ty);
+  // Tensor-core operand digits: rows and inputs beyond each pair's points
+  // stay zero for the batch's life (the kernels write only inputs < M).
+  if (b->g2t_x_elems) {
+    e = cudaMemsetAsync(b->d_g2t_x, 0, b->g2t_x_elems * sizeof(uint16_t), b->stream);
+    if (e != cudaSuccess) {
+      rs_free_batch(b);
+      return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core operands: ") + cudaGetErrorString(e));
+    }
+  }
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
     b->h_in = opt.h_in;
@@ -773,7 +892,10 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                           {b->d_g3, g3.data(), g3.size() * sizeof(int2)},
                           {b->d_g3d, g3d.data(), g3d.size() * sizeof(int2)},
                           {b->d_yun_tasks, yun.data(), yun.size() * sizeof(int2)},
-                          {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)}};
+                          {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)},
+                          {b->d_g2t_tasks, g2t_tasks.data(), g2t_tasks.size() * sizeof(G2tTask)},
+                          {b->d_g2t_rts, g2t_rts.data(), g2t_rts.size() * sizeof(G2tRowTile)},
+                          {b->d_g2t_items, g2t_items.data(), g2t_items.size() * sizeof(G2tItem)}};
   size_t static_bytes = 0;
   for (const Piece &pc : pieces) static_bytes += (pc.bytes + 15) & ~(size_t)15;
   const bool pinned_static = !b->own_host && (size_t)opt.h_in_words * 4 >= (size_t)b->in_words * 4 + static_bytes;
@@ -800,6 +922,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       cudaError_t e2 = g2n_prepare();
       if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
       ctx->g2n_ready = e2 == cudaSuccess;
+    }
+    if (rc == RS_OK && g2t_kmax > 0 && !ctx->g2t_ready) {
+      cudaError_t e2 = g2t_prepare();
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
+      ctx->g2t_ready = e2 == cudaSuccess;
     }
     if (rc == RS_OK && !b->g2cls.empty() && !ctx->g2_ready) {
       cudaError_t e2 = g2_prepare(b->g2smem);
@@ -894,6 +1021,8 @@ static int enqueue(rs_batch *b, bool capturing) {
   }
   RS_CUDA(ctx, cudaMemsetAsync(b->d_counters, 0, 16 * sizeof(int32_t), s));
   RS_CUDA(ctx, cudaMemsetAsync(b->d_stats, 0, ST_COUNT * sizeof(unsigned long long), s));
+  if (!b->opt.images_only && b->out_words > b->status_off)
+    RS_CUDA(ctx, cudaMemsetAsync(b->d_out + b->status_off, 0, sizeof(uint32_t), s));
   if (timing) RS_CUDA(ctx, record(b->ev[0], s, capturing));
   if (b->schur) {  // Schur variant of G1 over every tile, then the elimination fallback
     G1sArgs a;
@@ -950,8 +1079,44 @@ static int enqueue(rs_batch *b, bool capturing) {
     std::lock_guard<std::mutex> lock(ctx->tab_mu);
     for (int l = 0; l <= RS_NTT_LGMAX; ++l) bhat[l] = ctx->bhat[l];
   }
+  uint16_t *g2t_bt = nullptr;
+  int g2t_tiles = 0;
+  {
+    std::lock_guard<std::mutex> lock(ctx->tab_mu);
+    g2t_bt = ctx->g2t_bt;
+    g2t_tiles = ctx->g2t_tiles;
+  }
   int gi = 0;
   for (const auto &gc : b->g2cls) {
+    if (gc.tensor) {
+      G2tArgs at;
+      at.pairs = b->d_pairs;
+      at.tasks = b->d_g2t_tasks + gc.t_task_off;
+      at.rts = b->d_g2t_rts;
+      at.items = b->d_g2t_items + gc.t_item_off;
+      at.mods = ctx->d_mods;
+      at.num = b->d_num;
+      at.den = b->d_den;
+      at.coef = b->d_num;
+      at.finv = tab.finv;
+      at.gtab = tab.gtab;
+      at.hq = tab.hq;
+      at.tab_stride = tab.N;
+      at.btile = g2t_bt;
+      at.bt_tiles = g2t_tiles;
+      at.x = b->d_g2t_x;
+      at.y = b->d_g2t_y;
+      at.err = reinterpret_cast<int32_t *>(b->d_out + b->status_off);
+      const int j = (int)b->classes.size() + gi;
+      cudaError_t fe = cudaSuccess;
+      cudaStream_t si = branch_begin(b, 1, gi, s, &fe);
+      RS_CUDA(ctx, fe);
+      RS_CUDA(ctx, launch_g2t(gc.t_ntask, gc.t_nitem, gc.t_maxM, at, si));
+      branch_end(b, 1, j, si, &fe);
+      RS_CUDA(ctx, fe);
+      ++gi;
+      continue;
+    }
     if (gc.lg < 0) {
       G2sArgs as;
       as.pairs = b->d_pairs;
@@ -1117,9 +1282,17 @@ static const uint32_t *result_shape(rs_batch *b, int i, int *deg, int *limbs) {
   return b->h_out + b->descs[d].out_off;
 }
 
+// The device status word copied back with the results: non-zero when a
+// bounded wait of the tensor-core interpolation ran out in the last run.
+static int device_status(rs_batch *b) {
+  if (b->opt.images_only || b->out_words <= b->status_off || !b->h_out) return RS_OK;
+  return b->h_out[b->status_off] ? RS_ERR_TIMEOUT : RS_OK;
+}
+
 int rs_unpack_one(rs_batch *b, int i, std::vector<uint32_t> &words, int *deg, int *limbs) {
   const PairPlan &p = b->plans[i];
   if (p.status != RS_OK) return p.status;
+  if (device_status(b) != RS_OK) return RS_ERR_TIMEOUT;
   const uint32_t *w = result_shape(b, i, deg, limbs);
   words.assign((size_t)(*deg + 1) * *limbs, 0u);
   for (int j = 0; j <= *deg; ++j)
@@ -1148,6 +1321,10 @@ static int unpack_pair(rs_batch *b, int i, rs_upoly &o) {
 int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status) {
   rs_ctx *ctx = b->ctx;
   const int n = b->n;
+  if (device_status(b) != RS_OK) {
+    for (int i = 0; i < n && status; ++i) status[i] = RS_ERR_TIMEOUT;
+    return rs_fail(ctx, RS_ERR_TIMEOUT, "tensor-core interpolation: a bounded device wait ran out");
+  }
   std::vector<int> rcs(n, RS_OK);
   // Large outputs are trimmed and copied by several host threads, each
   // taking a contiguous range of pairs of about equal size.
@@ -1242,7 +1419,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
     rs_config_default(&c);
   if (c.tile_points != 0 && c.tile_points != 32 && c.tile_points != 64 && c.tile_points != 128)
     return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
-  if (c.g2_form < 0 || c.g2_form > 3) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1, 2 or 3");
+  if (c.g2_form < 0 || c.g2_form > 4) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1, 2, 3 or 4");
   if (c.univariate < 0 || c.univariate > 1) return rs_fail(nullptr, RS_ERR_ARG, "univariate must be 0 or 1");
   int dev = c.device;
   int ndev = 0;
@@ -1316,6 +1493,8 @@ int rs_destroy(rs_ctx *ctx) {
     for (uint32_t *bh : ctx->bhat)
       if (bh) cudaFree(bh);
     for (void *bh : ctx->bhat_retired) cudaFree(bh);
+    if (ctx->g2t_bt) cudaFree(ctx->g2t_bt);
+    for (void *bt : ctx->g2t_retired) cudaFree(bt);
     void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw};
     for (void *p : dev)
       if (p) cudaFree(p);

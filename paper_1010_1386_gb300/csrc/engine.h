@@ -79,6 +79,13 @@ struct rs_ctx {
   int bhat_K[RS_NTT_LGMAX + 1] = {};
   std::vector<void *> bhat_retired;
   bool g2n_ready = false;
+  // Tensor-core G2: the Toeplitz digit tiles of the first g2t_K primes,
+  // g2t_tiles per prime (guarded by tab_mu; replaced tables are kept until
+  // the context is destroyed, as graphs may still read them).
+  uint16_t *g2t_bt = nullptr;
+  int g2t_K = 0, g2t_tiles = 0;
+  std::vector<void *> g2t_retired;
+  bool g2t_ready = false;
 };
 
 struct RsClassLaunch {
@@ -93,7 +100,10 @@ struct RsClassLaunch {
 };
 
 struct RsG2Class {
-  int lg = 0;  // > 0: transform-based G2 of length 2^lg (256 threads); 0: direct convolutions
+  int lg = 0;  // > 0: transform-based (or tensor-core) G2 of length group 2^lg; 0: direct convolutions
+  bool tensor = false;  // tensor-core products over row tiles (kernels_g2t.cu)
+  int64_t t_task_off = 0, t_item_off = 0;  // first task / work item of the class in the batch lists
+  int t_ntask = 0, t_nitem = 0, t_maxM = 0;
   int threads = 256;
   int64_t off = 0;  // first task of the class in the G2 task list
   int count = 0;
@@ -113,7 +123,7 @@ struct RsBatchOpts {
   bool tune = true;     // time G1 choices for classes missing from the tuner cache
   bool timing = false;  // record stage events even when the context does not time
   int g1_threads = 0;   // > 0: force this tile width (and opt.persistent) for every class
-  int g2_force = -1;    // 0: direct G2 for every pair, 1: transforms wherever possible, -1: choose
+  int g2_force = -1;    // 0: direct G2 for every pair, 1: transforms, 2: tensor cores wherever possible, -1: choose
   int yun_maxm = 0;     // > 0: square-free factorisation of R mod every prime after G2 (up to this multiplicity)
 };
 
@@ -136,6 +146,7 @@ struct rs_batch {
   int2 *d_fail = nullptr;
   int64_t in_words = 0, img_words = 0, out_words = 0;
   int64_t shape_off = 0;  // word offset of the per-pair result shapes in the output buffer
+  int64_t status_off = 0; // word offset of the device status word (0 = every bounded wait completed)
   int ng2 = 0, ng3 = 0, g2_threads = 256;
   int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int g3_jt = 32;                    // coefficients per CRT digit tile (32 or 16)
@@ -147,6 +158,13 @@ struct rs_batch {
   int2 *d_yun_tasks = nullptr;
   uint32_t *d_yun_out = nullptr, *d_yun_work = nullptr;
   int4 *d_g3b = nullptr;
+  // Tensor-core G2: tasks, row tiles, work items, operand digits and products.
+  G2tTask *d_g2t_tasks = nullptr;
+  G2tRowTile *d_g2t_rts = nullptr;
+  G2tItem *d_g2t_items = nullptr;
+  uint16_t *d_g2t_x = nullptr;
+  uint32_t *d_g2t_y = nullptr;
+  int64_t g2t_x_elems = 0;
   int64_t *d_cy = nullptr;
   size_t g2smem = 0;
   void *arena = nullptr;  // one device allocation carved into the buffers below
@@ -177,6 +195,9 @@ int64_t rs_input_words(const rs_bipoly &p);
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx);
 // Transformed interpolation kernels of length 2^lg for at least K primes.
 int rs_ensure_bhat(rs_ctx *ctx, int lg, int K);
+// Toeplitz digit tiles of the tensor-core G2 for at least K primes and
+// `tiles` diagonal offsets per prime (the point tables must cover K first).
+int rs_ensure_g2t_btile(rs_ctx *ctx, int K, int tiles);
 // log2 of the G2 transform length for N points (2^lg >= 2N - 1), 0 when
 // above the transform limit; model cost of a form (0 direct, 1 transforms).
 int rs_g2_len(int N);

@@ -1,0 +1,554 @@
+// G2 on the tensor cores.  Paper, Section 4.1: R^{(y)} is interpolated over
+// Z_p from its images; on the geometric points x_i = q^i the Vandermonde solve
+// factors into two convolutions with the chirp sequence b_t of prime p (the
+// derivation is in kernels_g23.cu).  For one prime every pair of a batch
+// convolves with the same b, so the convolutions of all pairs are one matrix
+// product Y = X T with the lower-triangular Toeplitz matrix T[s][t] = b_{t-s}:
+// rows are (pair, part) for the even part E and the odd part O of each pair,
+// columns are output indices.  This file computes those products exactly on
+// tcgen05 tensor cores.
+//
+// Exactness.  Residues enter as signed representatives |v| < 2^30 and are
+// split into four balanced base-256 digits v = sum_i d_i 256^i, d_0..d_2 in
+// [-128, 127], |d_3| <= 64; each digit is exact in bf16.  The product of two
+// residues is the sum over digit pairs (i, j) of d_i e_j 256^(i+j): seven
+// digit-weight classes s = i + j.  One MMA multiplies the i-th digit tile of X
+// (128 rows x 16 inputs) by all four digit tiles of T laid side by side
+// (16 inputs x 4 x 32 outputs) and accumulates into TMEM columns starting at
+// class i, so class s of every output lands in its own fp32 column block.  A
+// class sums at most 4 x 64 products of magnitude <= 2^14 per 64 inputs, so
+// every partial sum is an integer below 2^22 in magnitude: exact in fp32.
+// After each 64 inputs the classes are read out, recombined with weights
+// 256^s mod p into an int64 per output (|sum| < 2^54 per 64 inputs, < 2^61 for
+// up to 8192 inputs), and the upper class columns are cleared.  The final
+// Montgomery reduction gives exactly the residue the direct convolution
+// computes (sum_s x_s b_{t-s} R^{-1} mod p, both operands in Montgomery form).
+//
+// Data movement.  Operands live in global memory already in the tensor
+// cores' shared-memory layout (no swizzle, K-major 8 x 16-byte core matrices,
+// 128 bytes between core matrices along K, 512 bytes between 8-row groups), so
+// every stage is a plain bulk copy (cp.async.bulk) completing on an mbarrier:
+//   X of a row tile: [64-input chunk][32-input stage][digit i][row/8][in/8][row%8][in%8];
+//   T of a prime: one 16 KB tile per diagonal offset D = t0 - s0 (a multiple
+//     of 32, from -32): [half h][(4 digits x 32 outputs)/8][in/8][n%8][in%8].
+// One thread block per work item (row tile, 64 outputs t0..t0+63): warp 8
+// loads 96 KB chunks into two buffers and issues the MMAs; warps 0-3 and 4-7
+// drain the two accumulator halves (outputs t0..t0+31 and t0+32..t0+63), so
+// one half's read-out overlaps the other half's MMAs.  Every wait is bounded
+// (about a second); a wait that runs out sets the error word and the block
+// drains its copies and MMAs, frees its tensor memory and returns.
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rs.h"
+#include "blockinv.cuh"
+#include "rs_internal.cuh"
+
+namespace {
+
+constexpr int kRows = 128;                     // MMA M: 64 pairs x {E, O}
+constexpr int kHalfT = 32;                     // outputs per accumulator half
+constexpr int kStageS = 32;                    // inputs per stage
+constexpr int kChunkS = 64;                    // inputs per exact accumulation
+constexpr int kAStageBytes = 4 * kRows * kStageS * 2;     // 32 KB: four digit tiles
+constexpr int kBStageBytes = 2 * 4 * kHalfT * kStageS * 2;  // 16 KB: two halves
+constexpr int kAChunkBytes = 2 * kAStageBytes;
+constexpr int kBufBytes = kAChunkBytes + 2 * kBStageBytes;  // 96 KB
+constexpr int kGemmSmem = 2 * kBufBytes;
+constexpr int kHalfCols = 7 * kHalfT;          // TMEM columns of one half: 7 classes x 32
+constexpr int kThreads = 288;
+constexpr uint64_t kWaitNs = 1000000000ull;    // a wait gives up after a second
+// kind::f16 instruction descriptor: fp32 accumulator (bits 4-5 = 1), bf16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N = 128 (bits 17-22: N / 8),
+// M = 128 (bits 24-28: M / 16).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  Gives up when another
+// thread of the block gave up (abort), or after kWaitNs: then it raises the
+// block's abort flag and the error word.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, int32_t *err, bool watch = true) {
+  uint64_t t0 = 0;
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (watch && *abort) return false;
+      const uint64_t now = globaltimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > kWaitNs) {
+        *abort = 1;
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start address / 16 (bits 0-13), leading
+// byte offset / 16 (bits 16-29: 128 B between core matrices along K), stride
+// byte offset / 16 (bits 32-45: 512 B between 8-row groups), descriptor
+// version 1 (bit 46), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(512 >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+#define RS_V32(v)                                                                                                 \
+  v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11], v[12], v[13], v[14], v[15], v[16], \
+      v[17], v[18], v[19], v[20], v[21], v[22], v[23], v[24], v[25], v[26], v[27], v[28], v[29], v[30], v[31]
+#define RS_O32(v)                                                                                           \
+  "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),           \
+      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
+      "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),         \
+      "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),          \
+      "=r"(v[30]), "=r"(v[31])
+#define RS_IO32(v)                                                                                          \
+  "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),           \
+      "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), \
+      "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]),         \
+      "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),          \
+      "+r"(v[30]), "+r"(v[31])
+#define RS_P32                                                                                                  \
+  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, " \
+  "%23, %24, %25, %26, %27, %28, %29, %30, %31}"
+
+// 32 consecutive TMEM columns of this warp's 32 lanes (one per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " RS_P32 ", [%32];" : RS_O32(v) : "r"(taddr));
+}
+
+// Completes the loads above; the registers pass through so that no use of
+// them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : RS_IO32(v)::"memory");
+}
+
+__device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// An fp32 integer |c| <= 2^22 -> int32: c + 1.5 * 2^23 lies in [2^23, 2^24]
+// where the spacing is 1, so its bit pattern is 0x4B400000 + c.
+__device__ __forceinline__ int32_t dec(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
+__device__ __forceinline__ int32_t signed_rep_t(uint32_t v, uint32_t p) {
+  return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
+}
+
+// Balanced base-256 digits of |v| < 2^30 as bf16 bit patterns (a digit has at
+// most 8 significant bits, so the top half of its fp32 pattern is exact).
+__device__ __forceinline__ void digits4(int32_t v, uint32_t (&bits)[4]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int32_t d = (int32_t)(int8_t)(v & 0xff);
+    bits[i] = __float_as_uint((float)d) >> 16;
+    v = (v - d) >> 8;
+  }
+  bits[3] = __float_as_uint((float)v) >> 16;
+}
+
+// Element offset of (row, input s, digit 0) in a row tile's operand layout;
+// digit i is 4096 elements further.  s0 a multiple of 8 addresses 8 inputs.
+__device__ __forceinline__ int64_t xoff(int row, int s) {
+  return (int64_t)(s >> 6) * 32768 + ((s >> 5) & 1) * 16384 + (row >> 3) * 256 + ((s & 31) >> 3) * 64 +
+         (row & 7) * 8 + (s & 7);
+}
+
+// The digits of 8 consecutive inputs s0..s0+7 of one row: four 16-byte stores.
+__device__ __forceinline__ void store_digits8(uint16_t *x, int row, int s0, const int32_t (&v)[8]) {
+  uint32_t w[4][4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    uint32_t lo[4], hi[4];
+    digits4(v[e], lo);
+    digits4(v[e + 1], hi);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) w[i][e >> 1] = lo[i] | (hi[i] << 16);
+  }
+  uint16_t *p = x + xoff(row, s0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<uint4 *>(p + i * 4096) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+}
+
+__device__ __forceinline__ int64_t fold64_t(int64_t s, uint32_t c32) { return rs_fold64(s, c32); }
+
+__device__ __forceinline__ uint32_t finish64_t(int64_t s, const ModP &m) {
+  const uint64_t t = (uint64_t)(s + ((int64_t)m.p << 22));  // |s| < 2^53: 0 <= t < 2^54 < p 2^32
+  return redc(t, m.p, m.pinv);
+}
+
+// ------------------------------------------------------------- products
+//
+// Block for item (rt, t0): Y[row][t] = sum_{s <= t} X[row][s] b_{t-s} mod p
+// for t in [t0, t0 + 64), over the 64-input chunks c = 0 .. t0 / 64.  Chunk c,
+// stage u (u = 0, 1) covers inputs s0 = 64 c + 32 u .. s0 + 31 and uses the
+// Toeplitz tile of diagonal offset t0 - s0, index (t0 - s0) / 32 + 1.
+__global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t bar[10];  // full[2], empty[2], accfull[2], accfree[2], drain
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  const G2tItem it = a.items[blockIdx.x];
+  const G2tRowTile rt = a.rts[it.rt];
+  const ModP m = a.mods[rt.prime];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nc = it.t0 / kChunkS + 1;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t b_full = smem_u32(&bar[0]), b_empty = smem_u32(&bar[2]);
+  const uint32_t b_accfull = smem_u32(&bar[4]), b_accfree = smem_u32(&bar[6]), b_drain = smem_u32(&bar[8]);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(b_full + 8 * i, 1);
+      mbar_init(b_empty + 8 * i, 1);
+      mbar_init(b_accfull + 8 * i, 1);
+      mbar_init(b_accfree + 8 * i, 4);  // one arrival per draining warp
+    }
+    mbar_init(b_drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {  // 512 columns: two halves of 7 x 32
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_slot;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      const uint8_t *xa = reinterpret_cast<const uint8_t *>(a.x + rt.x_off);
+      const uint8_t *bt = reinterpret_cast<const uint8_t *>(a.btile + (size_t)rt.prime * a.bt_tiles * 8192);
+      auto load = [&](int c, int buf) {
+        const uint32_t dst = sbase + buf * kBufBytes, fb = b_full + 8 * buf;
+        const int d0 = (it.t0 - kChunkS * c) / kStageS + 1;  // tile of stage 0; stage 1 takes d0 - 1
+        mbar_expect_tx(fb, kBufBytes);
+        bulk_load(dst, xa + (size_t)c * kAChunkBytes, kAChunkBytes, fb);
+        bulk_load(dst + kAChunkBytes, bt + (size_t)d0 * kBStageBytes, kBStageBytes, fb);
+        bulk_load(dst + kAChunkBytes + kBStageBytes, bt + (size_t)(d0 - 1) * kBStageBytes, kBStageBytes, fb);
+      };
+      int loaded = 1, landed = 0;  // chunks whose copies were issued / waited for
+      load(0, 0);
+      for (int c = 0; c < nc; ++c) {
+        const int buf = c & 1;
+        if (!mbar_wait(b_full + 8 * buf, (c >> 1) & 1, &abort_flag, a.err)) break;
+        landed = c + 1;
+        const uint32_t abase = sbase + buf * kBufBytes, bbase = abase + kAChunkBytes;
+        bool ok = true;
+        for (int h = 0; h < 2; ++h) {
+          if (!mbar_wait(b_accfree + 8 * h, c & 1, &abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const uint64_t ad = sdesc(abase + u * kAStageBytes + i * 8192 + ks * 256);
+                const uint64_t bd = sdesc(bbase + u * kBStageBytes + h * 8192 + ks * 256);
+                tc_mma(tbase + h * kHalfCols + i * kHalfT, ad, bd, (u | ks | i) != 0);
+              }
+          tc_commit(b_accfull + 8 * h);
+        }
+        if (!ok) break;
+        tc_commit(b_empty + 8 * buf);
+        if (c + 1 < nc) {
+          // buffer buf ^ 1 held chunk c - 1: its MMAs must be done
+          if (c >= 1 && !mbar_wait(b_empty + 8 * (buf ^ 1), ((c - 1) >> 1) & 1, &abort_flag, a.err)) break;
+          load(c + 1, buf ^ 1);
+          loaded = c + 2;
+        }
+      }
+      // Drain: every MMA this thread issued, and copies still in flight.
+      tc_commit(b_drain);
+      mbar_wait(b_drain, 0, &abort_flag, a.err, false);
+      for (int c = landed; c < loaded; ++c) mbar_wait(b_full + 8 * (c & 1), (c >> 1) & 1, &abort_flag, a.err, false);
+    }
+    __syncwarp();
+  } else {
+    // Warps 0-3 drain half 0 (outputs t0 .. t0 + 31), warps 4-7 half 1; a
+    // warp reads the TMEM lanes of its quarter: rows 32 q .. 32 q + 31.
+    const int h = warp >> 2, q = warp & 3, row = 32 * q + lane;
+    const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16) + h * kHalfCols;
+    const uint32_t c32 = m.r1;                                             // 2^32 mod p < 2^21
+    const int32_t w48 = (int32_t)(((uint64_t)c32 << 16) % m.p);           // 2^48 mod p
+    // Classes 4..6 start cleared; classes 0..3 are written by each chunk's first MMA.
+#pragma unroll
+    for (int z = 0; z < 3; ++z) tmem_zero32(tl + 128 + 32 * z);
+    tmem_wait_st();
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b_accfree + 8 * h);
+    int64_t acc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc[t] = 0;
+    bool ok = true;
+    for (int c = 0; c < nc; ++c) {
+      if (!mbar_wait(b_accfull + 8 * h, c & 1, &abort_flag, a.err)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t v0[32], v1[32];
+      tmem_ld32(tl + 0, v0);
+      tmem_ld32(tl + 32, v1);
+      tmem_wait_ld(v0);
+      tmem_wait_ld(v1);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] += (int64_t)(dec(v0[t]) + dec(v1[t]) * 256);
+      tmem_ld32(tl + 64, v0);
+      tmem_ld32(tl + 96, v1);
+      tmem_wait_ld(v0);
+      tmem_wait_ld(v1);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] += (int64_t)(dec(v0[t]) + dec(v1[t]) * 256) * 65536;
+      tmem_ld32(tl + 128, v0);
+      tmem_ld32(tl + 160, v1);
+      tmem_wait_ld(v0);
+      tmem_wait_ld(v1);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] = rs_mac_s32(acc[t], dec(v0[t]) + dec(v1[t]) * 256, (int32_t)c32);
+      tmem_ld32(tl + 192, v0);
+      tmem_wait_ld(v0);
+#pragma unroll
+      for (int t = 0; t < 32; ++t) acc[t] = rs_mac_s32(acc[t], dec(v0[t]), w48);
+      if (c + 1 < nc) {
+#pragma unroll
+        for (int z = 0; z < 3; ++z) tmem_zero32(tl + 128 + 32 * z);
+        tmem_wait_st();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_accfree + 8 * h);
+    }
+    if (ok && row < rt.rows) {
+      uint32_t *y = a.y + rt.y_off + (size_t)row * rt.mt + it.t0 + kHalfT * h;
+#pragma unroll
+      for (int t = 0; t < 32; t += 4) {
+        uint4 w;
+        w.x = finish64_t(fold64_t(acc[t], c32), m);
+        w.y = finish64_t(fold64_t(acc[t + 1], c32), m);
+        w.z = finish64_t(fold64_t(acc[t + 2], c32), m);
+        w.w = finish64_t(fold64_t(acc[t + 3], c32), m);
+        *reinterpret_cast<uint4 *>(y + t) = w;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+  }
+}
+
+// ------------------------------------------------- element-wise steps
+
+// Images -> operand digits.  One block per (pair, prime): the same fractions
+// as the direct form (z+ +- z-, over the paired denominators inverted
+// together), scaled by 1 / (2 F_i) for E and by 1 / (2 q^i F_i) for O.
+// Shared memory: 4 M words.
+__global__ void g2t_prep_kernel(G2tArgs a) {
+  extern __shared__ __align__(16) uint32_t sw[];
+  __shared__ uint32_t scratch[128];
+  const G2tTask tk = a.tasks[blockIdx.x];
+  const PairDesc pd = a.pairs[tk.pair];
+  const ModP m = a.mods[tk.prime];
+  const int NI = pd.NI, M = NI >> 1, T = blockDim.x, tid = threadIdx.x;
+  const size_t base = (size_t)pd.img_off + (size_t)tk.prime * NI;
+  const size_t tb = (size_t)tk.prime * a.tab_stride;
+  const uint32_t *finv = a.finv + tb, *hq = a.hq + tb;
+  uint32_t *dens = sw, *inv = sw + M;
+  int32_t *xe = reinterpret_cast<int32_t *>(sw + 2 * M), *xo = xe + M;
+  for (int i = tid; i < M; i += T) dens[i] = mmul(a.den[base + 2 * i], a.den[base + 2 * i + 1], m);
+  __syncthreads();
+  batch_invert(dens, inv, M, m, scratch);
+  __syncthreads();
+  for (int i = tid; i < M; i += T) {
+    const uint32_t np = a.num[base + 2 * i], dp = a.den[base + 2 * i];
+    const uint32_t nm = a.num[base + 2 * i + 1], dm = a.den[base + 2 * i + 1];
+    const uint32_t e = mmul(mmul2(np, dm, nm, dp, m), inv[i], m);             // z+ + z-
+    const uint32_t o = mmul(mmul2(np, dm, mneg(nm, m.p), dp, m), inv[i], m);  // z+ - z-
+    xe[i] = signed_rep_t(mmul(mmul(e, hq[0], m), finv[i], m), m.p);
+    xo[i] = signed_rep_t(mmul(mmul(o, hq[i], m), finv[i], m), m.p);
+  }
+  __syncthreads();
+  uint16_t *x = a.x + a.rts[tk.rt].x_off;
+  const int ng = (M + 7) >> 3;
+  for (int w = tid; w < 2 * ng; w += T) {
+    const int part = w >= ng, g = w - part * ng;
+    const int32_t *src = part ? xo : xe;
+    int32_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = 8 * g + e < M ? src[8 * g + e] : 0;
+    store_digits8(x, 2 * tk.slot + part, 8 * g, v);
+  }
+}
+
+// First products -> reversed operand: X'[s] = Y[D - s] Q^{-C(D-s,2)} F_{D-s}
+// for s <= D = M - 1 (the Newton coefficients times F, reversed).
+__global__ void g2t_mid_kernel(G2tArgs a) {
+  const G2tTask tk = a.tasks[blockIdx.x];
+  const PairDesc pd = a.pairs[tk.pair];
+  const ModP m = a.mods[tk.prime];
+  const G2tRowTile rt = a.rts[tk.rt];
+  const int M = pd.NI >> 1, D = M - 1;
+  const uint32_t *gt = a.gtab + (size_t)tk.prime * a.tab_stride;
+  const int ng = (M + 7) >> 3;
+  for (int w = threadIdx.x; w < 2 * ng; w += blockDim.x) {
+    const int part = w >= ng, g = w - part * ng, row = 2 * tk.slot + part;
+    const uint32_t *y = a.y + rt.y_off + (size_t)row * rt.mt;
+    int32_t v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int s = 8 * g + e;
+      v[e] = s < M ? signed_rep_t(mmul(y[D - s], gt[D - s], m), m.p) : 0;
+    }
+    store_digits8(a.x + rt.x_off, row, 8 * g, v);
+  }
+}
+
+// Second products -> coefficients: R_{2i + part} = Y'[D - i] / F_i (plain).
+__global__ void g2t_post_kernel(G2tArgs a) {
+  const G2tTask tk = a.tasks[blockIdx.x];
+  const PairDesc pd = a.pairs[tk.pair];
+  const ModP m = a.mods[tk.prime];
+  const G2tRowTile rt = a.rts[tk.rt];
+  const int N = pd.N, M = pd.NI >> 1, D = M - 1;
+  const size_t base = (size_t)pd.img_off + (size_t)tk.prime * pd.NI;
+  const uint32_t *finv = a.finv + (size_t)tk.prime * a.tab_stride;
+  const uint32_t *y0 = a.y + rt.y_off + (size_t)(2 * tk.slot) * rt.mt;
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    const int i = c >> 1, part = c & 1;
+    a.coef[base + c] = from_mont(mmul(y0[(size_t)part * rt.mt + D - i], finv[i], m), m);
+  }
+}
+
+// Toeplitz digit tiles: tile d of prime k holds T[s][t] = b_{D + t - s},
+// D = 32 (d - 1), for inputs s < 32 and outputs t < 64 (two halves of 32),
+// b_u = 0 for u < 0 or u >= nvalid.  One thread per 16-byte row segment.
+__global__ void g2t_btile_kernel(const int32_t *btab, int tab_stride, int nvalid, int K, int ntiles,
+                                 uint16_t *out) {
+  const int64_t total = (int64_t)K * ntiles * 1024;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < total; v += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(v / ((int64_t)ntiles * 1024));
+    const int rem = (int)(v - (int64_t)k * ntiles * 1024);
+    const int d = rem >> 10, w = rem & 1023;
+    const int h = w >> 9, ngp = (w >> 5) & 15, kc = (w >> 3) & 3, r = w & 7;
+    const int n = ngp * 8 + r, j = n >> 5, tt = n & 31;
+    const int u0 = 32 * (d - 1) + 32 * h + tt - 8 * kc;  // input e of the segment reads b_{u0 - e}
+    uint32_t word[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      uint32_t lo[4], hi[4];
+      const int ua = u0 - e, ub = u0 - e - 1;
+      digits4(ua >= 0 && ua < nvalid ? btab[(size_t)k * tab_stride + ua] : 0, lo);
+      digits4(ub >= 0 && ub < nvalid ? btab[(size_t)k * tab_stride + ub] : 0, hi);
+      const uint32_t l = j == 0 ? lo[0] : j == 1 ? lo[1] : j == 2 ? lo[2] : lo[3];
+      const uint32_t u = j == 0 ? hi[0] : j == 1 ? hi[1] : j == 2 ? hi[2] : hi[3];
+      word[e >> 1] = l | (u << 16);
+    }
+    *reinterpret_cast<uint4 *>(out + v * 8) = make_uint4(word[0], word[1], word[2], word[3]);
+  }
+}
+
+}  // namespace
+
+cudaError_t g2t_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(g2t_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(g2t_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * RS_G2T_MAX_M * 4);
+  return e;
+}
+
+cudaError_t launch_g2t_btile(const int32_t *btab, int tab_stride, int nvalid, int K, int ntiles, uint16_t *out,
+                             cudaStream_t s) {
+  const int64_t total = (int64_t)K * ntiles * 1024;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 65535);
+  g2t_btile_kernel<<<blocks, 256, 0, s>>>(btab, tab_stride, nvalid, K, ntiles, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g2t(int ntasks, int nitems, int maxM, const G2tArgs &a, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  g2t_prep_kernel<<<ntasks, 256, (size_t)4 * maxM * 4, s>>>(a);
+  g2t_gemm_kernel<<<nitems, kThreads, kGemmSmem, s>>>(a);
+  g2t_mid_kernel<<<ntasks, 256, 0, s>>>(a);
+  g2t_gemm_kernel<<<nitems, kThreads, kGemmSmem, s>>>(a);
+  g2t_post_kernel<<<ntasks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}

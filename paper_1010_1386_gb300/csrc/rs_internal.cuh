@@ -113,6 +113,47 @@ struct G2Args {
   int32_t tab_stride;
 };
 
+// Tensor-core G2 (kernels_g2t.cu).  For one prime, the rows of a row tile
+// are 64 (pair, prime) tasks x {E, O}; their inputs are zero beyond each
+// pair's point-pair count M, and the tile's length mt (a multiple of 64)
+// covers its largest M.
+struct G2tRowTile {
+  int64_t x_off;  // element offset of the tile's operand digits (64 KB per 64 inputs)
+  int64_t y_off;  // word offset of the tile's products, [128 rows][mt]
+  int32_t prime;
+  int32_t mt;
+  int32_t rows;   // rows in use (2 x tasks)
+  int32_t pad;
+};
+
+struct G2tItem {  // one block: outputs t0 .. t0 + 63 of a row tile
+  int32_t rt;
+  int32_t t0;
+};
+
+struct G2tTask {  // one (pair, prime): rows 2 slot (E) and 2 slot + 1 (O) of row tile rt
+  int32_t pair, prime, rt, slot;
+};
+
+struct G2tArgs {
+  const PairDesc *pairs;
+  const G2tTask *tasks;
+  const G2tRowTile *rts;
+  const G2tItem *items;
+  const ModP *mods;
+  const uint32_t *num, *den;
+  uint32_t *coef;             // out: R mod p (plain), may alias num
+  const uint32_t *finv, *gtab, *hq;  // as in G2Args
+  int32_t tab_stride;
+  const uint16_t *btile;      // [prime][bt_tiles][8192] Toeplitz digit tiles (bf16 patterns)
+  int32_t bt_tiles;           // tiles per prime: diagonal offsets -32, 0, 32, ...
+  uint16_t *x;                // operand digits of every row tile
+  uint32_t *y;                // products of every row tile
+  int32_t *err;               // set to 1 by a block whose bounded wait ran out
+};
+
+#define RS_G2T_MAX_M 4096  // point pairs per (pair, prime) the tensor-core form takes
+
 // The three NTT primes P0 < P1 < P2 of the transform-based G2 (each
 // c 2^k + 1 with k >= 25, in (2^30, 2^31)) and their Garner constants.
 struct NttConst {
@@ -181,6 +222,14 @@ cudaError_t launch_g2(int threads, int blocks, size_t smem, const G2Args &a, cud
 cudaError_t g2_prepare(size_t smem);
 cudaError_t g2n_prepare();
 cudaError_t launch_g2n(int blocks, size_t smem, const G2nArgs &a, cudaStream_t s);
+// Tensor-core G2: kernel attributes once; the Toeplitz digit tiles of K
+// primes (ntiles per prime, entries t < nvalid of btab); the five launches of
+// one class (images -> E/O digits, products, reversed scaled digits,
+// products, coefficients), maxM its largest point-pair count.
+cudaError_t g2t_prepare();
+cudaError_t launch_g2t_btile(const int32_t *btab, int tab_stride, int nvalid, int K, int ntiles, uint16_t *out,
+                             cudaStream_t s);
+cudaError_t launch_g2t(int ntasks, int nitems, int maxM, const G2tArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
 // CRT digits by tiles of jt (32 or 16) coefficients (tasks step by jt), any
