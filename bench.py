@@ -572,7 +572,7 @@ def batch_main(args, world, rank, local, dist):
                      "classes": [{"stage": "G1" if e["kind"] == 0 else "G2", "cap": e["cap"],
                                   "lg_points": e["lg_points"], "lg_images": e["lg_images"],
                                   "choice": (e["choice"] if e["kind"] == 0 else
-                                             ("transforms" if e["choice"] else "direct")),
+                                             ["direct", "transforms", "tensor cores"][e["choice"]]),
                                   "persistent": e["persistent"],
                                   "gain": (e["ms_default"] / e["ms_best"]) if e["ms_best"] else None}
                                  for e in tuned]},

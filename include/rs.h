@@ -307,12 +307,15 @@ int rs_images(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, int32_t nprim
  * candidates, times their G1 launches with CUDA events (median of three
  * after one warm-up) and caches the fastest; the built-in default is kept
  * unless another candidate is more than 2% faster.  The interpolation stage
- * (G2) has one more free choice per pair: direct convolutions or
- * number-theoretic transforms (for D + 1 <= 4096).  Pairs are grouped by
- * transform length 2^lg; for a group missing from the cache the tuner times
- * the whole path on a sample with each form and keeps the faster G2 (the
- * instruction-count model's choice unless the other is more than 2%
- * faster).  The server never tunes; it uses cached choices, so warm the
+ * (G2) has one more free choice per pair: direct convolutions,
+ * number-theoretic transforms, or exact products on the tensor cores of
+ * every pair of a prime at once (the last two for D + 1 <= 8192).  Pairs are
+ * grouped by transform length 2^lg; for a group missing from the cache the
+ * tuner times the whole path with each form (on the whole group up to 2^25
+ * images, else on a stride sample) and keeps the fastest G2 (the
+ * instruction-count model's choice between the first two unless another is
+ * more than 2% faster).  The groups that chose the tensor cores share one
+ * set of row tiles.  The server never tunes; it uses cached choices, so warm the
  * cache with rs_autotune first.
  * --------------------------------------------------------------------- */
 enum { RS_TUNE_G1 = 0, RS_TUNE_G2 = 1 };
@@ -323,7 +326,8 @@ typedef struct {
   int32_t sms, cap, lg_points, lg_images;  /* the class; for RS_TUNE_G2 cap is 0 and lg_points
                                               is log2 of the transform length */
   int32_t choice, persistent;              /* RS_TUNE_G1: tile points and schedule;
-                                              RS_TUNE_G2: 1 = transforms, 0 = direct (persistent 0) */
+                                              RS_TUNE_G2: 0 = direct, 1 = transforms, 2 = tensor
+                                              cores (persistent 0) */
   float ms_best, ms_default;               /* stage time of the choice and of the default on the
                                               tuning sample (0 when loaded without timings) */
 } rs_tune_entry;

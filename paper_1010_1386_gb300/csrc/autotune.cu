@@ -1,9 +1,9 @@
 // Tuner of the G1 launch (tile width and schedule) and of the G2 form
-// (direct convolutions or number-theoretic transforms) per workload class,
-// with a process-wide cache and its text file form.  The G1 candidates change
-// only how the (pair, prime, point) work list is cut into blocks and handed
-// to SMs, and both G2 forms compute the same residues, so every result is
-// the same under each choice.
+// (direct convolutions, number-theoretic transforms or tensor-core products)
+// per workload class, with a process-wide cache and its text file form.  The
+// G1 candidates change only how the (pair, prime, point) work list is cut
+// into blocks and handed to SMs, and every G2 form computes the same
+// residues exactly, so every result is the same under each choice.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -24,6 +24,7 @@ std::map<int64_t, RsG1Choice> g_cache;
 constexpr int64_t kSampleImages = int64_t(1) << 22;  // tuning sample bound
 constexpr int kRuns = 3;                             // timed runs per candidate (after one warm-up)
 constexpr float kKeepDefault = 1.02f;                // another choice must beat the default by 2%
+constexpr int64_t kWholeGroupImages = int64_t(1) << 25;  // G2 forms: groups timed whole up to this
 
 int ilog2(int64_t v) {
   int r = 0;
@@ -53,7 +54,7 @@ bool valid_entry(const rs_tune_entry &e) {
     return common && e.cap >= 8 && e.cap <= 72 && e.cap % 8 == 0 &&
            (e.choice == 32 || e.choice == 64 || e.choice == 128) && (e.persistent == 0 || e.persistent == 1);
   if (e.kind == RS_TUNE_G2)
-    return common && e.cap == 0 && e.lg_points >= 1 && e.lg_points <= RS_NTT_LGMAX && (e.choice == 0 || e.choice == 1) &&
+    return common && e.cap == 0 && e.lg_points >= 1 && e.lg_points <= RS_NTT_LGMAX && (e.choice >= 0 && e.choice <= 2) &&
            e.persistent == 0;
   return false;
 }
@@ -197,7 +198,12 @@ int rs_tune_g2(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::v
                const std::vector<int> &members, int64_t key, int model_form, int *form) {
   int64_t total = 0;
   for (int i : members) total += (int64_t)plans[i].K * plans[i].N;
-  const int64_t stride = std::max<int64_t>(1, (total + kSampleImages - 1) / kSampleImages);
+  // The tensor-core form multiplies all pairs of a prime at once, so a
+  // strided sample (fewer pairs per prime) would understate it: groups up to
+  // kWholeGroupImages are timed whole.
+  const int64_t stride = total <= kWholeGroupImages
+                             ? 1
+                             : std::max<int64_t>(1, (total + kSampleImages - 1) / kSampleImages);
   std::vector<rs_bipoly> F, G;
   std::vector<PairPlan> P;
   for (size_t s = 0; s < members.size(); s += (size_t)stride) {
@@ -205,13 +211,14 @@ int rs_tune_g2(rs_ctx *ctx, const rs_bipoly *f, const rs_bipoly *g, const std::v
     G.push_back(g[members[s]]);
     P.push_back(plans[members[s]]);
   }
-  float ms[2] = {0.f, 0.f};
-  for (int fm = 0; fm < 2; ++fm) {
+  float ms[3] = {0.f, 0.f, 0.f};  // direct, transforms, tensor cores
+  for (int fm = 0; fm < 3; ++fm) {
     const int rc = time_g2_form(ctx, F, G, P, fm, &ms[fm]);
     if (rc != RS_OK) return rc;
   }
   int best = model_form;
-  if (ms[1 - model_form] * kKeepDefault < ms[model_form]) best = 1 - model_form;
+  for (int fm = 0; fm < 3; ++fm)
+    if (ms[fm] * kKeepDefault < ms[best]) best = fm;
   RsG1Choice c;
   c.threads = best;
   c.persistent = 0;

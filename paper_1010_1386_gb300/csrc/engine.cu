@@ -640,8 +640,9 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       }
     }
   }
-  // Tensor-core classes, one per length group: for every prime k, the
-  // group's pairs with K > k in decreasing point count, 64 to a row tile
+  // One tensor-core class over every pair whose length group chose that
+  // form: for every prime k, the pairs with K > k in decreasing point count
+  // (so a tile's rows have similar lengths), 64 to a row tile
   // (rows 2 slot, 2 slot + 1: even and odd part); a tile's length is its
   // first pair's point-pair count rounded up to 64.  Work items: every 64
   // outputs of every tile, tiles by decreasing length, outputs from the top
@@ -653,13 +654,13 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   int64_t g2t_y_words = 0;
   int g2t_kmax = 0, g2t_tiles = 0;
   b->g2t_x_elems = 0;
-  for (int lg = RS_NTT_LGMAX; lg > 0 && !images_only && !g2tri; --lg) {
-    std::vector<int> mem;
-    for (int i : byN)
-      if (g2t_lg[i] == lg) mem.push_back(i);
-    if (mem.empty()) continue;
+  std::vector<int> g2t_mem;
+  for (int i : byN)
+    if (g2t_lg[i] > 0) g2t_mem.push_back(i);
+  if (!images_only && !g2tri && !g2t_mem.empty()) {
+    const std::vector<int> &mem = g2t_mem;
     RsG2Class gc;
-    gc.lg = lg;
+    gc.lg = g2t_lg[mem[0]];
     gc.tensor = true;
     gc.t_task_off = (int64_t)g2t_tasks.size();
     gc.t_item_off = (int64_t)g2t_items.size();

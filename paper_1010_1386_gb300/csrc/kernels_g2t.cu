@@ -31,8 +31,10 @@
 //   X of a row tile: [64-input chunk][32-input stage][digit i][row/8][in/8][row%8][in%8];
 //   T of a prime: one 16 KB tile per diagonal offset D = t0 - s0 (a multiple
 //     of 32, from -32): [half h][(4 digits x 32 outputs)/8][in/8][n%8][in%8].
-// One thread block per work item (row tile, 64 outputs t0..t0+63): warp 8
-// loads 96 KB chunks into two buffers and issues the MMAs; warps 0-3 and 4-7
+// One thread block per work item (row tile, 64 outputs t0..t0+63): in the
+// third warpgroup warp 9 loads 96 KB chunks into two buffers and warp 8
+// issues the MMAs (its issue blocks while the tensor pipe's queue is full,
+// so the copies have a warp of their own); warps 0-3 and 4-7
 // drain the two accumulator halves (outputs t0..t0+31 and t0+32..t0+63), so
 // one half's read-out overlaps the other half's MMAs.  Every wait is bounded
 // (about a second); a wait that runs out sets the error word and the block
@@ -57,7 +59,7 @@ constexpr int kAChunkBytes = 2 * kAStageBytes;
 constexpr int kBufBytes = kAChunkBytes + 2 * kBStageBytes;  // 96 KB
 constexpr int kGemmSmem = 2 * kBufBytes;
 constexpr int kHalfCols = 7 * kHalfT;          // TMEM columns of one half: 7 classes x 32
-constexpr int kThreads = 288;
+constexpr int kThreads = 384;  // warpgroups 0, 1: accumulator halves; 2: warp 8 issues, warp 9 loads
 constexpr uint64_t kWaitNs = 1000000000ull;    // a wait gives up after a second
 // kind::f16 instruction descriptor: fp32 accumulator (bits 4-5 = 1), bf16 A
 // and B (bits 7-9, 10-12 = 1), both K-major, N = 128 (bits 17-22: N / 8),
@@ -151,34 +153,23 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-#define RS_V32(v)                                                                                                 \
-  v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], v[8], v[9], v[10], v[11], v[12], v[13], v[14], v[15], v[16], \
-      v[17], v[18], v[19], v[20], v[21], v[22], v[23], v[24], v[25], v[26], v[27], v[28], v[29], v[30], v[31]
-#define RS_O32(v)                                                                                           \
-  "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),           \
-      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
-      "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),         \
-      "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),          \
-      "=r"(v[30]), "=r"(v[31])
-#define RS_IO32(v)                                                                                          \
-  "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),           \
-      "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), \
-      "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]),         \
-      "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]),          \
-      "+r"(v[30]), "+r"(v[31])
-#define RS_P32                                                                                                  \
-  "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, " \
-  "%23, %24, %25, %26, %27, %28, %29, %30, %31}"
 
-// 32 consecutive TMEM columns of this warp's 32 lanes (one per thread).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 " RS_P32 ", [%32];" : RS_O32(v) : "r"(taddr));
+// 16 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
 }
 
-// Completes the loads above; the registers pass through so that no use of
-// them is scheduled before the wait.
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" : RS_IO32(v)::"memory");
+// Orders later uses of 16 loaded registers after a tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_hold16(uint32_t *v) {
+  asm volatile(""
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                 "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                 "+r"(v[15])::"memory");
 }
 
 __device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
@@ -192,11 +183,22 @@ __device__ __forceinline__ void tmem_zero32(uint32_t taddr) {
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// An fp32 integer |c| <= 2^22 -> int32: c + 1.5 * 2^23 lies in [2^23, 2^24]
-// where the spacing is 1, so its bit pattern is 0x4B400000 + c.
-__device__ __forceinline__ int32_t dec(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
+// Read-out of the digit-weight classes.  With digits |d_0..d_2| <= 128 and
+// |d_3| <= 64, one input adds at most 2^14, 2^15, 3 2^14, 3 2^14, 2^15, 2^14,
+// 2^12 to classes 0..6, so over 64 inputs |c_s| <= 2^20, 2^21, 3 2^20,
+// 3 2^20, 2^21, 2^20, 2^18.  For an fp32 integer c and a magic constant
+// m = 1.5 2^23 + delta with |c + delta| <= 2^22, c + m lies in [2^23, 2^24],
+// where the spacing is 1: its bit pattern is 0x4B400000 + delta + c.  With
+// delta = 0 for even classes and delta = -0xB4000 for odd ones (within the
+// bounds above), the 32-bit combination b_even + 256 b_odd equals
+// c_even + 256 c_odd + 2^31 exactly (|c_even + 256 c_odd| < 2^30), so each
+// class costs one FADD and each pair one IMAD; the constant biases are
+// removed once per output at the end.
+constexpr float kMagEven = 12582912.0f;           // 1.5 2^23
+constexpr float kMagOdd = 12582912.0f - 737280.0f;  // 1.5 2^23 - 0xB4000
+constexpr uint32_t kBias6 = 0x4B400000u;           // class 6 pattern offset
+
+__device__ __forceinline__ uint32_t mag(uint32_t v, float m) { return __float_as_uint(__uint_as_float(v) + m); }
 
 __device__ __forceinline__ int32_t signed_rep_t(uint32_t v, uint32_t p) {
   return v > (p >> 1) ? (int32_t)v - (int32_t)p : (int32_t)v;
@@ -285,24 +287,39 @@ __global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
   tc_fence_after();
   const uint32_t tbase = tmem_slot;
 
-  if (warp == 8) {
-    if (lane == 0) {
+  // Register split (launch: 168 per thread, 64,512 in all): the control
+  // warpgroup gives back down to 88, the two draining warpgroups take 208
+  // each (2 x 128 x 208 + 128 x 88 = 64,512; per SMSP 208 + 208 + 88 per
+  // lane, within its 16,384).
+  if (warp >= 8) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 88;" ::: "memory");
+    if (warp == 9 && lane == 0) {
+      // Producer: chunk c goes into buffer c & 1 once the MMAs of chunk c - 2
+      // (the buffer's previous contents) have completed.
       const uint8_t *xa = reinterpret_cast<const uint8_t *>(a.x + rt.x_off);
       const uint8_t *bt = reinterpret_cast<const uint8_t *>(a.btile + (size_t)rt.prime * a.bt_tiles * 8192);
-      auto load = [&](int c, int buf) {
+      int issued = 0;
+      for (int c = 0; c < nc; ++c) {
+        const int buf = c & 1;
+        if (c >= 2 && !mbar_wait(b_empty + 8 * buf, ((c - 2) >> 1) & 1, &abort_flag, a.err)) break;
         const uint32_t dst = sbase + buf * kBufBytes, fb = b_full + 8 * buf;
         const int d0 = (it.t0 - kChunkS * c) / kStageS + 1;  // tile of stage 0; stage 1 takes d0 - 1
         mbar_expect_tx(fb, kBufBytes);
         bulk_load(dst, xa + (size_t)c * kAChunkBytes, kAChunkBytes, fb);
         bulk_load(dst + kAChunkBytes, bt + (size_t)d0 * kBStageBytes, kBStageBytes, fb);
         bulk_load(dst + kAChunkBytes + kBStageBytes, bt + (size_t)(d0 - 1) * kBStageBytes, kBStageBytes, fb);
-      };
-      int loaded = 1, landed = 0;  // chunks whose copies were issued / waited for
-      load(0, 0);
+        issued = c + 1;
+      }
+      // The last copies into each buffer (no later phase follows them) must
+      // have landed before the block exits.
+      for (int c = issued > 2 ? issued - 2 : 0; c < issued; ++c)
+        mbar_wait(b_full + 8 * (c & 1), (c >> 1) & 1, &abort_flag, a.err, false);
+    }
+    if (warp == 8 && lane == 0) {
+      // MMA issuer.
       for (int c = 0; c < nc; ++c) {
         const int buf = c & 1;
         if (!mbar_wait(b_full + 8 * buf, (c >> 1) & 1, &abort_flag, a.err)) break;
-        landed = c + 1;
         const uint32_t abase = sbase + buf * kBufBytes, bbase = abase + kAChunkBytes;
         bool ok = true;
         for (int h = 0; h < 2; ++h) {
@@ -325,26 +342,20 @@ __global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
         }
         if (!ok) break;
         tc_commit(b_empty + 8 * buf);
-        if (c + 1 < nc) {
-          // buffer buf ^ 1 held chunk c - 1: its MMAs must be done
-          if (c >= 1 && !mbar_wait(b_empty + 8 * (buf ^ 1), ((c - 1) >> 1) & 1, &abort_flag, a.err)) break;
-          load(c + 1, buf ^ 1);
-          loaded = c + 2;
-        }
       }
-      // Drain: every MMA this thread issued, and copies still in flight.
+      // Drain every MMA this thread issued.
       tc_commit(b_drain);
       mbar_wait(b_drain, 0, &abort_flag, a.err, false);
-      for (int c = landed; c < loaded; ++c) mbar_wait(b_full + 8 * (c & 1), (c >> 1) & 1, &abort_flag, a.err, false);
     }
     __syncwarp();
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 208;" ::: "memory");
     // Warps 0-3 drain half 0 (outputs t0 .. t0 + 31), warps 4-7 half 1; a
     // warp reads the TMEM lanes of its quarter: rows 32 q .. 32 q + 31.
     const int h = warp >> 2, q = warp & 3, row = 32 * q + lane;
     const uint32_t tl = tbase + ((uint32_t)(32 * q) << 16) + h * kHalfCols;
     const uint32_t c32 = m.r1;                                             // 2^32 mod p < 2^21
-    const int32_t w48 = (int32_t)(((uint64_t)c32 << 16) % m.p);           // 2^48 mod p
+    const uint32_t w48 = (uint32_t)(((uint64_t)c32 << 16) % m.p);          // 2^48 mod p
     // Classes 4..6 start cleared; classes 0..3 are written by each chunk's first MMA.
 #pragma unroll
     for (int z = 0; z < 3; ++z) tmem_zero32(tl + 128 + 32 * z);
@@ -352,7 +363,9 @@ __global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(b_accfree + 8 * h);
-    int64_t acc[32];
+    // acc = sum over chunks of u + 2^16 w + c32 hh + w48 b6 (mod 2^64), each
+    // term carrying its constant bias; |true sum| < 2^60.
+    uint64_t acc[32];
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0;
     bool ok = true;
@@ -362,48 +375,50 @@ __global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
         break;
       }
       tc_fence_after();
-      uint32_t v0[32], v1[32];
-      tmem_ld32(tl + 0, v0);
-      tmem_ld32(tl + 32, v1);
-      tmem_wait_ld(v0);
-      tmem_wait_ld(v1);
 #pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] += (int64_t)(dec(v0[t]) + dec(v1[t]) * 256);
-      tmem_ld32(tl + 64, v0);
-      tmem_ld32(tl + 96, v1);
-      tmem_wait_ld(v0);
-      tmem_wait_ld(v1);
+      for (int grp = 0; grp < 2; ++grp) {
+        uint32_t v[7][16];
 #pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] += (int64_t)(dec(v0[t]) + dec(v1[t]) * 256) * 65536;
-      tmem_ld32(tl + 128, v0);
-      tmem_ld32(tl + 160, v1);
-      tmem_wait_ld(v0);
-      tmem_wait_ld(v1);
+        for (int k = 0; k < 7; ++k) tmem_ld16(tl + 32 * k + 16 * grp, v[k]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] = rs_mac_s32(acc[t], dec(v0[t]) + dec(v1[t]) * 256, (int32_t)c32);
-      tmem_ld32(tl + 192, v0);
-      tmem_wait_ld(v0);
+        for (int k = 0; k < 7; ++k) tmem_hold16(v[k]);
+        if (grp == 1) {  // every class of the chunk is in registers: free the accumulator half
+          if (c + 1 < nc) {
 #pragma unroll
-      for (int t = 0; t < 32; ++t) acc[t] = rs_mac_s32(acc[t], dec(v0[t]), w48);
-      if (c + 1 < nc) {
+            for (int z = 0; z < 3; ++z) tmem_zero32(tl + 128 + 32 * z);
+            tmem_wait_st();
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(b_accfree + 8 * h);
+        }
 #pragma unroll
-        for (int z = 0; z < 3; ++z) tmem_zero32(tl + 128 + 32 * z);
-        tmem_wait_st();
+        for (int t = 0; t < 16; ++t) {
+          const uint32_t u = mag(v[0][t], kMagEven) + 256u * mag(v[1][t], kMagOdd);
+          const uint32_t w = mag(v[2][t], kMagEven) + 256u * mag(v[3][t], kMagOdd);
+          const uint32_t hh = mag(v[4][t], kMagEven) + 256u * mag(v[5][t], kMagOdd);
+          const uint32_t b6 = mag(v[6][t], kMagEven);
+          uint64_t x = acc[16 * grp + t] + u;
+          x += (uint64_t)w << 16;
+          x += (uint64_t)hh * c32;
+          x += (uint64_t)b6 * w48;
+          acc[16 * grp + t] = x;
+        }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(b_accfree + 8 * h);
     }
     if (ok && row < rt.rows) {
+      const uint64_t bias =
+          (uint64_t)nc * ((1ull << 31) + (1ull << 47) + (1ull << 31) * c32 + (uint64_t)kBias6 * w48);
       uint32_t *y = a.y + rt.y_off + (size_t)row * rt.mt + it.t0 + kHalfT * h;
 #pragma unroll
       for (int t = 0; t < 32; t += 4) {
-        uint4 w;
-        w.x = finish64_t(fold64_t(acc[t], c32), m);
-        w.y = finish64_t(fold64_t(acc[t + 1], c32), m);
-        w.z = finish64_t(fold64_t(acc[t + 2], c32), m);
-        w.w = finish64_t(fold64_t(acc[t + 3], c32), m);
-        *reinterpret_cast<uint4 *>(y + t) = w;
+        uint4 o;
+        o.x = finish64_t(fold64_t((int64_t)(acc[t] - bias), c32), m);
+        o.y = finish64_t(fold64_t((int64_t)(acc[t + 1] - bias), c32), m);
+        o.z = finish64_t(fold64_t((int64_t)(acc[t + 2] - bias), c32), m);
+        o.w = finish64_t(fold64_t((int64_t)(acc[t + 3] - bias), c32), m);
+        *reinterpret_cast<uint4 *>(y + t) = o;
       }
     }
   }

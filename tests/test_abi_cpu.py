@@ -241,7 +241,7 @@ def test_autotune_cache_file_roundtrip(lib, tmp_path):
     bad_lines = ["0 152 40 10 21 48 1 1 1",      # tile width not 32/64/128
                  "0 152 44 10 21 64 1 1 1",      # capacity not a multiple of 8
                  "0 152 40 10 21 64 2 1 1",      # schedule not 0/1
-                 "1 152 0 12 22 2 0 1 1",        # G2 form not 0/1
+                 "1 152 0 12 22 3 0 1 1",        # G2 form not 0/1/2
                  "1 152 8 12 22 1 0 1 1",        # G2 entry with a capacity
                  "2 152 40 10 21 64 1 1 1",      # unknown kind
                  "0 152 40 10 21 64 1 1",        # a field missing
