@@ -1022,7 +1022,7 @@ static int enqueue(rs_batch *b, bool capturing) {
   }
   RS_CUDA(ctx, cudaMemsetAsync(b->d_counters, 0, 16 * sizeof(int32_t), s));
   RS_CUDA(ctx, cudaMemsetAsync(b->d_stats, 0, ST_COUNT * sizeof(unsigned long long), s));
-  if (!b->opt.images_only && b->out_words > b->status_off)
+  if (b->g2t_x_elems > 0)  // the status word only tensor-core G2 blocks write
     RS_CUDA(ctx, cudaMemsetAsync(b->d_out + b->status_off, 0, sizeof(uint32_t), s));
   if (timing) RS_CUDA(ctx, record(b->ev[0], s, capturing));
   if (b->schur) {  // Schur variant of G1 over every tile, then the elimination fallback
@@ -1286,7 +1286,7 @@ static const uint32_t *result_shape(rs_batch *b, int i, int *deg, int *limbs) {
 // The device status word copied back with the results: non-zero when a
 // bounded wait of the tensor-core interpolation ran out in the last run.
 static int device_status(rs_batch *b) {
-  if (b->opt.images_only || b->out_words <= b->status_off || !b->h_out) return RS_OK;
+  if (b->g2t_x_elems == 0 || b->out_words <= b->status_off || !b->h_out) return RS_OK;
   return b->h_out[b->status_off] ? RS_ERR_TIMEOUT : RS_OK;
 }
 
