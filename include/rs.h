@@ -108,6 +108,14 @@ typedef struct {
   const char *autotune_cache;  /* tuner cache file merged at rs_create (a missing file is not an
                                   error) and rewritten at rs_destroy; NULL = none.  The string
                                   is copied. */
+  int32_t crt_form;          /* Chinese remaindering digits: 0 = by the batch's shape (one thread
+                                per coefficient when there are at least 1024 coefficients per SM;
+                                else the tensor cores when some pair has at least 128 primes and
+                                the batch has 128-coefficient tiles for half the SMs, or some pair
+                                has at least 1024 primes; else tiles on the CUDA cores), 1 = CUDA
+                                cores only, 2 = tensor cores whenever the batch does not take one
+                                thread per coefficient */
+  int32_t reserved;          /* 0 */
 } rs_config;
 
 typedef struct rs_ctx rs_ctx;

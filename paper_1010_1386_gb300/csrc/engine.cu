@@ -247,6 +247,27 @@ int rs_ensure_g2t_btile(rs_ctx *ctx, int K, int tiles) {
   return RS_OK;
 }
 
+int rs_ensure_g3m_wtiles(rs_ctx *ctx, int KB) {
+  std::lock_guard<std::mutex> lock(ctx->tab_mu);
+  if (ctx->g3m_KB >= KB) return RS_OK;
+  const RsTables &t = ctx->tab;
+  if (t.K < 64 * (KB - 1))
+    return rs_fail(ctx, RS_ERR_STATE, "tensor-core CRT tables: CRT tables not built for these primes");
+  DevGuard dg(ctx->device);
+  uint16_t *nw = nullptr;
+  cudaError_t e = cudaMalloc(&nw, (size_t)std::max<int64_t>(1, g3m_wtile_elems(KB)) * sizeof(uint16_t));
+  if (e == cudaSuccess) e = launch_g3m_wtiles(t.wtab, t.K, KB, nw, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (nw) cudaFree(nw);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core CRT tables: ") + cudaGetErrorString(e));
+  }
+  if (ctx->g3m_wt) ctx->g3m_retired.push_back(ctx->g3m_wt);
+  ctx->g3m_wt = nw;
+  ctx->g3m_KB = KB;
+  return RS_OK;
+}
+
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   std::lock_guard<std::mutex> lock(ctx->tab_mu);
   const int need_c = N + 128 + dx + 1;
@@ -364,6 +385,7 @@ void rs_batch_sizes(const std::vector<PairPlan> &plans, const rs_bipoly *f, cons
     const int64_t mt = (((p.N + 1) / 2 + 63) / 64) * 64;
     t_items += (int64_t)p.K * (mt / 64);
     t_bytes += (int64_t)p.K * mt * 2 * (4 * 2 + 4);  // two rows: four bf16 digits and one product per input
+    t_bytes += (int64_t)((p.N + 127) / 128) * (((p.K + 63) / 64) * 65536 + 8);  // tensor-core CRT digit rows
     g3 += (p.N + 127) / 128;
     g3d += (p.N + 31) / 32;  // digit tiles
     g3b += (p.N + 127) / 128 * chunks;
@@ -759,6 +781,16 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     }
     b->g3_jt = nt32 < 2 * (int64_t)ctx->sms ? 16 : 32;
     b->g3_perthread = ncoef >= (int64_t)RS_G3P_MIN_COEF_PER_SM * ctx->sms;
+    // Otherwise the digits go to the tensor cores when a pair has enough
+    // primes for the per-block products to matter (two 64-prime blocks) and
+    // the 128-coefficient tiles fill half the SMs, or a pair has so many
+    // primes that the products dominate; with few tiles and a few hundred
+    // primes the CUDA-core tiles of 16 coefficients spread the work wider.
+    int64_t nt128 = 0;
+    for (int i : order) nt128 += (b->plans[i].N + 127) / 128;
+    b->g3_tensor = !b->g3_perthread && !images_only && ctx->cfg.crt_form != 1 &&
+                   (ctx->cfg.crt_form == 2 ||
+                    (maxK >= RS_G3M_MIN_K && (2 * nt128 >= ctx->sms || maxK >= RS_G3M_WIDE_K)));
   }
   for (int i : order) {
     const PairPlan &p = b->plans[i];
@@ -778,6 +810,16 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     }
     b->yun_wstride = ((int64_t)maxNp + 3) & ~(int64_t)3;
     b->yun_ostride = ((int64_t)maxNp + 2 * opt.yun_maxm + 2 + 3) & ~(int64_t)3;
+  }
+  // Tensor-core CRT digits: each task (128 coefficients of a pair) owns its
+  // operand digit rows, one 64 KB chunk per 64 of the pair's primes.
+  std::vector<int64_t> g3m_xoff;
+  b->g3m_x_elems = 0;
+  if (b->g3_tensor) {
+    for (const int2 &t : g3) {
+      g3m_xoff.push_back(b->g3m_x_elems);
+      b->g3m_x_elems += g3m_tile_elems(b->descs[t.x].K);
+    }
   }
   b->nyun = (int)yun.size();
   b->ng2 = images_only ? 0 : (int)g2.size();
@@ -800,6 +842,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   for (int lg = 1; lg <= RS_NTT_LGMAX && rc == RS_OK; ++lg)
     if (bhatK[lg]) rc = rs_ensure_bhat(ctx, lg, bhatK[lg]);
   if (rc == RS_OK && g2t_kmax > 0) rc = rs_ensure_g2t_btile(ctx, g2t_kmax, g2t_tiles);
+  if (rc == RS_OK && b->g3_tensor) rc = rs_ensure_g3m_wtiles(ctx, (maxK + 63) / 64);
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;
@@ -822,7 +865,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                o_g3b = carve(g3b.size() * sizeof(int4)), o_fail = carve(b->schur ? b->img_words * sizeof(int2) : 0),
                o_tt = carve(g2t_tasks.size() * sizeof(G2tTask)), o_trt = carve(g2t_rts.size() * sizeof(G2tRowTile)),
                o_tit = carve(g2t_items.size() * sizeof(G2tItem)), o_tx = carve(b->g2t_x_elems * sizeof(uint16_t)),
-               o_ty = carve(g2t_y_words * 4);
+               o_ty = carve(g2t_y_words * 4), o_g3mx = carve(b->g3m_x_elems * sizeof(uint16_t)),
+               o_g3mo = carve(g3m_xoff.size() * sizeof(int64_t));
   cudaError_t e = opt.stream_ordered ? cudaMallocAsync(&b->arena, off, b->stream) : cudaMalloc(&b->arena, off);
   if (e != cudaSuccess) {
     b->arena = nullptr;
@@ -854,14 +898,16 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   b->d_g2t_items = (G2tItem *)(base + o_tit);
   b->d_g2t_x = (uint16_t *)(base + o_tx);
   b->d_g2t_y = (uint32_t *)(base + o_ty);
+  b->d_g3m_x = (uint16_t *)(base + o_g3mx);
+  b->d_g3m_xoff = (int64_t *)(base + o_g3mo);
   // Tensor-core operand digits: rows and inputs beyond each pair's points
   // stay zero for the batch's life (the kernels write only inputs < M).
-  if (b->g2t_x_elems) {
+  if (b->g3m_x_elems) e = cudaMemsetAsync(b->d_g3m_x, 0, b->g3m_x_elems * sizeof(uint16_t), b->stream);
+  if (e == cudaSuccess && b->g2t_x_elems)
     e = cudaMemsetAsync(b->d_g2t_x, 0, b->g2t_x_elems * sizeof(uint16_t), b->stream);
-    if (e != cudaSuccess) {
-      rs_free_batch(b);
-      return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core operands: ") + cudaGetErrorString(e));
-    }
+  if (e != cudaSuccess) {
+    rs_free_batch(b);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core operands: ") + cudaGetErrorString(e));
   }
 
   if (opt.h_in && opt.h_in_words >= b->in_words && opt.h_out && opt.h_out_words >= b->out_words) {
@@ -896,7 +942,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
                           {b->d_g3b, g3b.data(), g3b.size() * sizeof(int4)},
                           {b->d_g2t_tasks, g2t_tasks.data(), g2t_tasks.size() * sizeof(G2tTask)},
                           {b->d_g2t_rts, g2t_rts.data(), g2t_rts.size() * sizeof(G2tRowTile)},
-                          {b->d_g2t_items, g2t_items.data(), g2t_items.size() * sizeof(G2tItem)}};
+                          {b->d_g2t_items, g2t_items.data(), g2t_items.size() * sizeof(G2tItem)},
+                          {b->d_g3m_xoff, g3m_xoff.data(), g3m_xoff.size() * sizeof(int64_t)}};
   size_t static_bytes = 0;
   for (const Piece &pc : pieces) static_bytes += (pc.bytes + 15) & ~(size_t)15;
   const bool pinned_static = !b->own_host && (size_t)opt.h_in_words * 4 >= (size_t)b->in_words * 4 + static_bytes;
@@ -923,6 +970,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       cudaError_t e2 = g2n_prepare();
       if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G2 set-up: ") + cudaGetErrorString(e2));
       ctx->g2n_ready = e2 == cudaSuccess;
+    }
+    if (rc == RS_OK && b->g3_tensor && !ctx->g3m_ready) {
+      cudaError_t e2 = g3m_prepare();
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
+      ctx->g3m_ready = e2 == cudaSuccess;
     }
     if (rc == RS_OK && g2t_kmax > 0 && !ctx->g2t_ready) {
       cudaError_t e2 = g2t_prepare();
@@ -1022,7 +1074,7 @@ static int enqueue(rs_batch *b, bool capturing) {
   }
   RS_CUDA(ctx, cudaMemsetAsync(b->d_counters, 0, 16 * sizeof(int32_t), s));
   RS_CUDA(ctx, cudaMemsetAsync(b->d_stats, 0, ST_COUNT * sizeof(unsigned long long), s));
-  if (b->g2t_x_elems > 0)  // the status word only tensor-core G2 blocks write
+  if (b->g2t_x_elems > 0 || b->g3_tensor)  // the status word only the tensor-core kernels write
     RS_CUDA(ctx, cudaMemsetAsync(b->d_out + b->status_off, 0, sizeof(uint32_t), s));
   if (timing) RS_CUDA(ctx, record(b->ev[0], s, capturing));
   if (b->schur) {  // Schur variant of G1 over every tile, then the elimination fallback
@@ -1223,10 +1275,27 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.shape = reinterpret_cast<int32_t *>(b->d_out + b->shape_off);
     RS_CUDA(ctx, cudaMemsetAsync(a3.shape, 0, b->descs.size() * 2 * sizeof(int32_t), s));
     a3.kmax = b->kmax;
-    if (b->g3_perthread)
+    if (b->g3_perthread) {
       RS_CUDA(ctx, launch_g3p(b->ng3, a3, b->d_g3, s));
-    else
+    } else if (b->g3_tensor) {
+      G3mArgs am;
+      am.pairs = b->d_pairs;
+      am.tasks = b->d_g3;
+      am.mods = ctx->d_mods;
+      am.crt = ctx->d_crt;
+      am.wtab = tab.wtab;
+      {
+        std::lock_guard<std::mutex> lock(ctx->tab_mu);
+        am.wtiles = ctx->g3m_wt;
+      }
+      am.coef = b->d_num;
+      am.xdig = b->d_g3m_x;
+      am.xoff = b->d_g3m_xoff;
+      am.err = reinterpret_cast<int32_t *>(b->d_out + b->status_off);
+      RS_CUDA(ctx, launch_g3m(b->ng3, am, s));
+    } else {
       RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
+    }
     RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));
@@ -1286,7 +1355,7 @@ static const uint32_t *result_shape(rs_batch *b, int i, int *deg, int *limbs) {
 // The device status word copied back with the results: non-zero when a
 // bounded wait of the tensor-core interpolation ran out in the last run.
 static int device_status(rs_batch *b) {
-  if (b->g2t_x_elems == 0 || b->out_words <= b->status_off || !b->h_out) return RS_OK;
+  if ((b->g2t_x_elems == 0 && !b->g3_tensor) || b->out_words <= b->status_off || !b->h_out) return RS_OK;
   return b->h_out[b->status_off] ? RS_ERR_TIMEOUT : RS_OK;
 }
 
@@ -1324,7 +1393,7 @@ int rs_unpack(rs_batch *b, rs_upoly *out, int32_t *status) {
   const int n = b->n;
   if (device_status(b) != RS_OK) {
     for (int i = 0; i < n && status; ++i) status[i] = RS_ERR_TIMEOUT;
-    return rs_fail(ctx, RS_ERR_TIMEOUT, "tensor-core interpolation: a bounded device wait ran out");
+    return rs_fail(ctx, RS_ERR_TIMEOUT, "tensor-core kernels: a bounded device wait ran out");
   }
   std::vector<int> rcs(n, RS_OK);
   // Large outputs are trimmed and copied by several host threads, each
@@ -1422,6 +1491,7 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
     return rs_fail(nullptr, RS_ERR_ARG, "tile_points must be 0, 32, 64 or 128");
   if (c.g2_form < 0 || c.g2_form > 4) return rs_fail(nullptr, RS_ERR_ARG, "g2_form must be 0, 1, 2, 3 or 4");
   if (c.univariate < 0 || c.univariate > 1) return rs_fail(nullptr, RS_ERR_ARG, "univariate must be 0 or 1");
+  if (c.crt_form < 0 || c.crt_form > 2) return rs_fail(nullptr, RS_ERR_ARG, "crt_form must be 0, 1 or 2");
   int dev = c.device;
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -1496,6 +1566,8 @@ int rs_destroy(rs_ctx *ctx) {
     for (void *bh : ctx->bhat_retired) cudaFree(bh);
     if (ctx->g2t_bt) cudaFree(ctx->g2t_bt);
     for (void *bt : ctx->g2t_retired) cudaFree(bt);
+    if (ctx->g3m_wt) cudaFree(ctx->g3m_wt);
+    for (void *wt : ctx->g3m_retired) cudaFree(wt);
     void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw};
     for (void *p : dev)
       if (p) cudaFree(p);

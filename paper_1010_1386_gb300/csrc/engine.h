@@ -86,6 +86,12 @@ struct rs_ctx {
   int g2t_K = 0, g2t_tiles = 0;
   std::vector<void *> g2t_retired;
   bool g2t_ready = false;
+  // Tensor-core CRT digits: W digit tiles of the digit blocks kb < g3m_KB
+  // (same lifetime rules as above).
+  uint16_t *g3m_wt = nullptr;
+  int g3m_KB = 0;
+  std::vector<void *> g3m_retired;
+  bool g3m_ready = false;
 };
 
 struct RsClassLaunch {
@@ -151,6 +157,10 @@ struct rs_batch {
   int ng3d = 0, ng3b = 0, kmax = 0;  // CRT digit tiles, limb chunks, largest K
   int g3_jt = 32;                    // coefficients per CRT digit tile (32 or 16)
   bool g3_perthread = false;         // CRT digits with one thread per coefficient
+  bool g3_tensor = false;            // CRT digits on the tensor cores (kernels_g3m.cu)
+  int64_t g3m_x_elems = 0;           // their operand digits
+  uint16_t *d_g3m_x = nullptr;
+  int64_t *d_g3m_xoff = nullptr;
   int64_t xl_words = 0, cy_words = 0;
   int2 *d_g3d = nullptr;
   int nyun = 0;                         // square-free tasks (pair, prime)
@@ -198,6 +208,8 @@ int rs_ensure_bhat(rs_ctx *ctx, int lg, int K);
 // Toeplitz digit tiles of the tensor-core G2 for at least K primes and
 // `tiles` diagonal offsets per prime (the point tables must cover K first).
 int rs_ensure_g2t_btile(rs_ctx *ctx, int K, int tiles);
+// W digit tiles of the tensor-core CRT digits for digit blocks kb < KB.
+int rs_ensure_g3m_wtiles(rs_ctx *ctx, int KB);
 // log2 of the G2 transform length for N points (2^lg >= 2N - 1), 0 when
 // above the transform limit; model cost of a form (0 direct, 1 transforms).
 int rs_g2_len(int N);

@@ -154,6 +154,28 @@ struct G2tArgs {
 
 #define RS_G2T_MAX_M 4096  // point pairs per (pair, prime) the tensor-core form takes
 
+#ifndef RS_G3M_MIN_K
+#define RS_G3M_MIN_K 128  // largest prime count from which a batch's digits take the tensor cores
+#endif
+#ifndef RS_G3M_WIDE_K
+#define RS_G3M_WIDE_K 1024  // ... and from which they do so even with few coefficient tiles
+#endif
+
+// Tensor-core CRT digits (kernels_g3m.cu): one block per 128 coefficients of
+// one pair (the output kernel's tasks), over 64-prime digit blocks.
+struct G3mArgs {
+  const PairDesc *pairs;
+  const int2 *tasks;        // (pair, first coefficient), coefficients in steps of 128
+  const ModP *mods;
+  const uint32_t *crt;      // (p_0 ... p_{k-1})^{-1} mod p_k, Montgomery form
+  const int32_t *wtab;      // triangular W[k][l] (signed Montgomery), as for the other digit kernels
+  const uint16_t *wtiles;   // W digit tiles per (block, chunk)
+  uint32_t *coef;           // in: R mod p_k (plain); overwritten by the digits
+  uint16_t *xdig;           // operand digits of every tile (zeroed once)
+  const int64_t *xoff;      // per task: element offset of its operand digits
+  int32_t *err;             // status word (a bounded wait ran out)
+};
+
 // The three NTT primes P0 < P1 < P2 of the transform-based G2 (each
 // c 2^k + 1 with k >= 25, in (2^30, 2^31)) and their Garner constants.
 struct NttConst {
@@ -230,6 +252,13 @@ cudaError_t g2t_prepare();
 cudaError_t launch_g2t_btile(const int32_t *btab, int tab_stride, int nvalid, int K, int ntiles, uint16_t *out,
                              cudaStream_t s);
 cudaError_t launch_g2t(int ntasks, int nitems, int maxM, const G2tArgs &a, cudaStream_t s);
+// Tensor-core CRT digits: kernel attributes; the W digit tiles of blocks
+// kb < KB (g3m_wtile_elems(KB) elements); per-tile operand size for K primes.
+cudaError_t g3m_prepare();
+int64_t g3m_wtile_elems(int KB);
+int64_t g3m_tile_elems(int K);
+cudaError_t launch_g3m_wtiles(const int32_t *wtab, int K, int KB, uint16_t *out, cudaStream_t s);
+cudaError_t launch_g3m(int ntiles, const G3mArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
 // CRT digits by tiles of jt (32 or 16) coefficients (tasks step by jt), any

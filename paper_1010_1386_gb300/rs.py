@@ -39,7 +39,8 @@ class rs_config(ctypes.Structure):
     _fields_ = [("device", c_int32), ("tile_points", c_int32), ("use_graphs", c_int32),
                 ("persistent", c_int32), ("timing", c_int32), ("autotune", c_int32),
                 ("g2_form", c_int32), ("univariate", c_int32),
-                ("mem_limit_bytes", c_int64), ("autotune_cache", c_char_p)]
+                ("mem_limit_bytes", c_int64), ("autotune_cache", c_char_p),
+                ("crt_form", c_int32), ("reserved", c_int32)]
 
 
 class rs_tune_entry(ctypes.Structure):
@@ -261,10 +262,12 @@ class Context:
     """One librs context (device memory, stream, prime tables) on one GPU."""
 
     def __init__(self, device=-1, tile_points=0, use_graphs=True, persistent=True, timing=False,
-                 mem_limit_bytes=0, autotune=True, autotune_cache=None, g2_form=0, univariate="prs"):
+                 mem_limit_bytes=0, autotune=True, autotune_cache=None, g2_form=0, univariate="prs",
+                 crt_form=0):
         """univariate: "prs" (division-free remainder sequence, one thread per
         image) or "schur" (Schur algorithm on displacement generators, one
-        warp per image)."""
+        warp per image); crt_form: rs_config.crt_form (0 by batch shape, 1
+        CUDA cores only, 2 tensor cores where possible)."""
         lib = load()
         cfg = rs_config()
         _check(lib.rs_config_default(ctypes.byref(cfg)))
@@ -273,6 +276,7 @@ class Context:
         cfg.mem_limit_bytes = mem_limit_bytes
         cfg.autotune = int(autotune)
         cfg.g2_form = int(g2_form)
+        cfg.crt_form = int(crt_form)
         if univariate not in ("prs", "schur"):
             raise ValueError("univariate must be 'prs' or 'schur'")
         cfg.univariate = 1 if univariate == "schur" else 0

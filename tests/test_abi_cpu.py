@@ -264,8 +264,9 @@ def test_config_layout(lib):
     assert (cfg.device, cfg.tile_points, cfg.use_graphs, cfg.persistent, cfg.timing, cfg.autotune) == \
         (-1, 0, 1, 1, 0, 1)
     assert cfg.mem_limit_bytes == 0 and cfg.autotune_cache is None
-    assert cfg.g2_form == 0
+    assert cfg.g2_form == 0 and cfg.crt_form == 0
     assert rs.rs_config.mem_limit_bytes.offset == 32 and rs.rs_config.autotune_cache.offset == 40
+    assert rs.rs_config.crt_form.offset == 48 and ctypes.sizeof(rs.rs_config) == 56
 
 
 def test_info_struct_layouts(tmp_path):
