@@ -357,6 +357,16 @@ int rs_autotune_load(const char *path);
 /* Empty the cache.  Host only. */
 int rs_autotune_clear(void);
 
+/* Test hook (failure detection without a GPU fault): while `on` is non-zero
+ * the copy warps of the tensor-core kernels (G2 products, CRT digits) of
+ * this context issue no copies, so the MMA and read-out warps' bounded
+ * mbarrier waits run out after about a second; each block then drains,
+ * frees its tensor memory and sets the status word, and the run's results
+ * fail with RS_ERR_TIMEOUT.  The context stays usable; turning the hook off
+ * restores normal runs (captured graphs read the flag from device memory).
+ * Never needed in normal use.  Synchronises the context's stream. */
+int rs_test_stall_tensor_cores(rs_ctx *ctx, int32_t on);
+
 /* ---------------------------------------------------------------------
  * Serving: a continuous-batching request server inside a context.
  * Each request is one resultant Res_y(f, g).  Submission plans the request

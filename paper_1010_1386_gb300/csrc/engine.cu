@@ -1160,6 +1160,7 @@ static int enqueue(rs_batch *b, bool capturing) {
       at.x = b->d_g2t_x;
       at.y = b->d_g2t_y;
       at.err = reinterpret_cast<int32_t *>(b->d_out + b->status_off);
+      at.stall = ctx->d_stall;
       const int j = (int)b->classes.size() + gi;
       cudaError_t fe = cudaSuccess;
       cudaStream_t si = branch_begin(b, 1, gi, s, &fe);
@@ -1292,6 +1293,7 @@ static int enqueue(rs_batch *b, bool capturing) {
       am.xdig = b->d_g3m_x;
       am.xoff = b->d_g3m_xoff;
       am.err = reinterpret_cast<int32_t *>(b->d_out + b->status_off);
+      am.stall = ctx->d_stall;
       RS_CUDA(ctx, launch_g3m(b->ng3, am, s));
     } else {
       RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
@@ -1469,6 +1471,15 @@ const char *rs_error_string(int code) {
 
 const char *rs_last_error(const rs_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
+int rs_test_stall_tensor_cores(rs_ctx *ctx, int32_t on) {
+  if (!ctx) return rs_fail(nullptr, RS_ERR_ARG, "ctx is NULL");
+  DevGuard dg(ctx->device);
+  const int32_t v = on ? 1 : 0;
+  RS_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  RS_CUDA(ctx, cudaMemcpy(ctx->d_stall, &v, sizeof(v), cudaMemcpyHostToDevice));
+  return RS_OK;
+}
+
 int rs_config_default(rs_config *cfg) {
   if (!cfg) return rs_fail(nullptr, RS_ERR_ARG, "cfg is NULL");
   memset(cfg, 0, sizeof(*cfg));
@@ -1529,6 +1540,8 @@ int rs_create(rs_ctx **out, const rs_config *cfg) {
   chk(cudaMalloc(&ctx->d_vtab, (size_t)np * RS_VT_STRIDE * 4), "cudaMalloc");
   chk(cudaMalloc(&ctx->d_crt, np * 4), "cudaMalloc");
   chk(cudaMalloc(&ctx->d_qbase, np * 4), "cudaMalloc");
+  chk(cudaMalloc(&ctx->d_stall, sizeof(int32_t)), "cudaMalloc");
+  if (rc == RS_OK) chk(cudaMemset(ctx->d_stall, 0, sizeof(int32_t)), "cudaMemset");
   if (rc == RS_OK) chk(cudaMemcpy(ctx->d_primes, ctx->primes.data(), np * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
   if (rc == RS_OK)
     chk(launch_init_primes(ctx->d_primes, np, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->stream),
@@ -1568,7 +1581,7 @@ int rs_destroy(rs_ctx *ctx) {
     for (void *bt : ctx->g2t_retired) cudaFree(bt);
     if (ctx->g3m_wt) cudaFree(ctx->g3m_wt);
     for (void *wt : ctx->g3m_retired) cudaFree(wt);
-    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw};
+    void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw, ctx->d_stall};
     for (void *p : dev)
       if (p) cudaFree(p);
     for (auto ss : ctx->side)

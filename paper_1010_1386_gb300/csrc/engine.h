@@ -50,6 +50,7 @@ struct rs_ctx {
   std::vector<uint32_t> primes;
   std::vector<double> log2p;
   uint32_t *d_primes = nullptr;
+  int32_t *d_stall = nullptr;  // test hook read by the tensor-core kernels' copy warps (0 = normal)
   ModP *d_mods = nullptr;
   uint32_t *d_vtab = nullptr;
   uint32_t *d_crt = nullptr;

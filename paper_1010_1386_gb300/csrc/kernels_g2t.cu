@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(kThreads, 1) g2t_gemm_kernel(G2tArgs a) {
       const uint8_t *xa = reinterpret_cast<const uint8_t *>(a.x + rt.x_off);
       const uint8_t *bt = reinterpret_cast<const uint8_t *>(a.btile + (size_t)rt.prime * a.bt_tiles * 8192);
       int issued = 0;
-      for (int c = 0; c < nc; ++c) {
+      const int ncopy = *a.stall ? 0 : nc;  // test hook: no copies, so every consumer's wait runs out
+      for (int c = 0; c < ncopy; ++c) {
         const int buf = c & 1;
         if (c >= 2 && !mbar_wait(b_empty + 8 * buf, ((c - 2) >> 1) & 1, &abort_flag, a.err)) break;
         const uint32_t dst = sbase + buf * kBufBytes, fb = b_full + 8 * buf;

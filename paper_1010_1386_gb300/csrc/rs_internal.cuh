@@ -150,6 +150,7 @@ struct G2tArgs {
   uint16_t *x;                // operand digits of every row tile
   uint32_t *y;                // products of every row tile
   int32_t *err;               // set to 1 by a block whose bounded wait ran out
+  const int32_t *stall;       // test hook: non-zero = the copy warp issues nothing
 };
 
 #define RS_G2T_MAX_M 4096  // point pairs per (pair, prime) the tensor-core form takes
@@ -174,6 +175,7 @@ struct G3mArgs {
   uint16_t *xdig;           // operand digits of every tile (zeroed once)
   const int64_t *xoff;      // per task: element offset of its operand digits
   int32_t *err;             // status word (a bounded wait ran out)
+  const int32_t *stall;     // test hook: non-zero = the copy warp issues nothing
 };
 
 // The three NTT primes P0 < P1 < P2 of the transform-based G2 (each

@@ -129,6 +129,7 @@ _SIGS = {
     "rs_autotune_save": (c_int32, [c_char_p]),
     "rs_autotune_load": (c_int32, [c_char_p]),
     "rs_autotune_clear": (c_int32, []),
+    "rs_test_stall_tensor_cores": (c_int32, [c_void_p, c_int32]),
 }
 
 _lib = None
@@ -307,6 +308,11 @@ class Context:
         s = c_void_p()
         _check(self.lib.rs_stream(self.h, ctypes.byref(s)), self.h)
         return s.value or 0
+
+    def stall_tensor_cores(self, on):
+        """Test hook: rs_test_stall_tensor_cores (the tensor-core kernels'
+        bounded waits run out; runs fail with RS_ERR_TIMEOUT)."""
+        _check(self.lib.rs_test_stall_tensor_cores(self.h, int(bool(on))))
 
     def resultant_y(self, f, g):
         """Res_y(f, g) as a list of Python ints (coefficient of x^i at i)."""
