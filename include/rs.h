@@ -114,7 +114,8 @@ typedef struct {
                                 the batch has 128-coefficient tiles for half the SMs, or some pair
                                 has at least 1024 primes; else tiles on the CUDA cores), 1 = CUDA
                                 cores only, 2 = tensor cores whenever the batch does not take one
-                                thread per coefficient */
+                                thread per coefficient.  With tensor-core digits the limbs
+                                sum_k v_k P_k are a tensor-core product too. */
   int32_t reserved;          /* 0 */
 } rs_config;
 

@@ -24,8 +24,8 @@ def _units():
     for cap in G1_CAPS:
         units.append(("kernels_g1.cu", f"g1_c{cap}.o", [f"-DRS_G1_CAP={cap}"]))
     for src in ("g1_dispatch.cu", "kernels_g23.cu", "kernels_g3.cu", "engine.cu", "server.cu", "noalloc.cu",
-                "autotune.cu", "kernels_g2ntt.cu", "kernels_g2t.cu", "kernels_g3m.cu", "kernels_yun.cu",
-                "kernels_schur.cu", "probe.cu"):
+                "autotune.cu", "kernels_g2ntt.cu", "kernels_g2t.cu", "kernels_g3m.cu", "kernels_g3l.cu",
+                "kernels_yun.cu", "kernels_schur.cu", "probe.cu"):
         units.append((src, src.rsplit(".", 1)[0] + ".o", []))
     units.append(("planner.cpp", "planner.o", ["-x", "cu"]))
     units.append(("squarefree.cpp", "squarefree.o", ["-x", "cu"]))

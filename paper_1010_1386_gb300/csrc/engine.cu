@@ -268,6 +268,43 @@ int rs_ensure_g3m_wtiles(rs_ctx *ctx, int KB) {
   return RS_OK;
 }
 
+// Chunk c's prefix products reach byte 2 nh[k] (balanced digits of P_k, k
+// its last prime's row) and, shifted by up to three digits, column
+// 2 nh[k] + 3: units 0 .. (2 nh[k] + 3) / 256 get a block each.
+int rs_ensure_g3l_tiles(rs_ctx *ctx, int KB) {
+  std::lock_guard<std::mutex> lock(ctx->tab_mu);
+  if (ctx->g3l_KB >= KB) return RS_OK;
+  const RsTables &t = ctx->tab;
+  if (t.K < 64 * (KB - 1) || (int)t.h_nh.size() < t.K + 1)
+    return rs_fail(ctx, RS_ERR_STATE, "tensor-core CRT limb tables: CRT tables not built for these primes");
+  std::vector<int32_t> cbase(KB + 1, 0);
+  for (int c = 0; c < KB; ++c) {
+    const int klast = std::min(64 * c + 63, t.K);
+    cbase[c + 1] = cbase[c] + (2 * t.h_nh[klast] + 3) / 256 + 1;
+  }
+  DevGuard dg(ctx->device);
+  uint16_t *nw = nullptr;
+  int32_t *ncb = nullptr;
+  cudaError_t e = cudaMalloc(&nw, (size_t)cbase[KB] * g3l_block_elems() * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ncb, cbase.size() * sizeof(int32_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ncb, cbase.data(), cbase.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_g3l_btiles(t.p16, t.poff, t.K, ncb, KB, cbase[KB], nw, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    if (nw) cudaFree(nw);
+    if (ncb) cudaFree(ncb);
+    return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core CRT limb tables: ") + cudaGetErrorString(e));
+  }
+  if (ctx->g3l_bt) ctx->g3m_retired.push_back(ctx->g3l_bt);
+  if (ctx->g3l_cbase) ctx->g3m_retired.push_back(ctx->g3l_cbase);
+  ctx->g3l_bt = nw;
+  ctx->g3l_cbase = ncb;
+  ctx->h_g3l_cbase = cbase;
+  ctx->g3l_KB = KB;
+  return RS_OK;
+}
+
 int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
   std::lock_guard<std::mutex> lock(ctx->tab_mu);
   const int need_c = N + 128 + dx + 1;
@@ -336,6 +373,7 @@ int rs_ensure_tables(rs_ctx *ctx, int K, int N, int dx) {
     free_tables(nt);
     return rs_fail(ctx, rs_cuda_code(e), std::string("point tables: ") + cudaGetErrorString(e));
   }
+  nt.h_nh = nh;
   if (t.finv) ctx->retired.push_back(t);
   t = nt;
   return RS_OK;
@@ -843,6 +881,34 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
     if (bhatK[lg]) rc = rs_ensure_bhat(ctx, lg, bhatK[lg]);
   if (rc == RS_OK && g2t_kmax > 0) rc = rs_ensure_g2t_btile(ctx, g2t_kmax, g2t_tiles);
   if (rc == RS_OK && b->g3_tensor) rc = rs_ensure_g3m_wtiles(ctx, (maxK + 63) / 64);
+  if (rc == RS_OK && b->g3_tensor) rc = rs_ensure_g3l_tiles(ctx, (maxK + 63) / 64);
+  if (rc == RS_OK && b->g3_tensor) {
+    // The limbs then come from the tensor cores too: one task per (digit
+    // task, unit of 64 limbs) instead of the limb chunks, with the chunks
+    // from the first whose prefix products reach the unit; the longest first.
+    std::vector<int32_t> cb;
+    {
+      std::lock_guard<std::mutex> lock(ctx->tab_mu);
+      cb = ctx->h_g3l_cbase;
+    }
+    const int KBt = (int)cb.size() - 1;
+    std::vector<std::pair<int, int4>> lt;
+    for (size_t ti = 0; ti < g3.size(); ++ti) {
+      const PairDesc &pd = b->descs[g3[ti].x];
+      const int KBp = (pd.K + 63) / 64, units = (pd.Lout + 63) / 64;
+      int lo = 0;
+      for (int u = 0; u < units; ++u) {
+        while (lo < KBt && cb[lo + 1] - cb[lo] - 1 < u) ++lo;
+        lt.push_back({KBp > lo ? KBp - lo : 0, make_int4((int)ti, u, lo, 0)});
+      }
+    }
+    std::stable_sort(lt.begin(), lt.end(), [](const std::pair<int, int4> &x, const std::pair<int, int4> &y) {
+      return x.first > y.first;
+    });
+    g3b.clear();
+    for (const auto &x : lt) g3b.push_back(x.second);
+    b->ng3b = (int)g3b.size();
+  }
   if (rc != RS_OK) {
     rs_free_batch(b);
     return rc;
@@ -975,6 +1041,11 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
       cudaError_t e2 = g3m_prepare();
       if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
       ctx->g3m_ready = e2 == cudaSuccess;
+    }
+    if (rc == RS_OK && b->g3_tensor && !ctx->g3l_ready) {
+      cudaError_t e2 = g3l_prepare();
+      if (e2 != cudaSuccess) rc = rs_fail(ctx, RS_ERR_CUDA, std::string("G3 set-up: ") + cudaGetErrorString(e2));
+      ctx->g3l_ready = e2 == cudaSuccess;
     }
     if (rc == RS_OK && g2t_kmax > 0 && !ctx->g2t_ready) {
       cudaError_t e2 = g2t_prepare();
@@ -1276,6 +1347,7 @@ static int enqueue(rs_batch *b, bool capturing) {
     a3.shape = reinterpret_cast<int32_t *>(b->d_out + b->shape_off);
     RS_CUDA(ctx, cudaMemsetAsync(a3.shape, 0, b->descs.size() * 2 * sizeof(int32_t), s));
     a3.kmax = b->kmax;
+    a3.signed_digits = b->g3_tensor ? 1 : 0;
     if (b->g3_perthread) {
       RS_CUDA(ctx, launch_g3p(b->ng3, a3, b->d_g3, s));
     } else if (b->g3_tensor) {
@@ -1295,10 +1367,27 @@ static int enqueue(rs_batch *b, bool capturing) {
       am.err = reinterpret_cast<int32_t *>(b->d_out + b->status_off);
       am.stall = ctx->d_stall;
       RS_CUDA(ctx, launch_g3m(b->ng3, am, s));
+      G3lArgs al;
+      al.pairs = b->d_pairs;
+      al.tasks = b->d_g3;
+      al.ltasks = b->d_g3b;
+      al.xdig = b->d_g3m_x;
+      al.xoff = b->d_g3m_xoff;
+      {
+        std::lock_guard<std::mutex> lock(ctx->tab_mu);
+        al.btiles = ctx->g3l_bt;
+        al.cbase = ctx->g3l_cbase;
+      }
+      al.xl = b->d_xl;
+      al.carry = b->d_cy;
+      al.err = am.err;
+      al.stall = ctx->d_stall;
+      RS_CUDA(ctx, launch_g3l(b->ng3b, al, s));
     } else {
       RS_CUDA(ctx, launch_g3t(b->ng3d, a3, b->d_g3d, s, b->g3_jt));
     }
-    RS_CUDA(ctx, launch_g3bc(b->ng3b, b->ng3, a3, b->d_g3, s));
+    // the output kernel; the limb chunks unless the tensor cores formed the limbs
+    RS_CUDA(ctx, launch_g3bc(b->g3_tensor ? 0 : b->ng3b, b->ng3, a3, b->d_g3, s));
   }
   if (timing) RS_CUDA(ctx, record(b->ev[3], s, capturing));
   return RS_OK;
@@ -1580,6 +1669,8 @@ int rs_destroy(rs_ctx *ctx) {
     if (ctx->g2t_bt) cudaFree(ctx->g2t_bt);
     for (void *bt : ctx->g2t_retired) cudaFree(bt);
     if (ctx->g3m_wt) cudaFree(ctx->g3m_wt);
+    if (ctx->g3l_bt) cudaFree(ctx->g3l_bt);
+    if (ctx->g3l_cbase) cudaFree(ctx->g3l_cbase);
     for (void *wt : ctx->g3m_retired) cudaFree(wt);
     void *dev[] = {ctx->d_primes, ctx->d_mods, ctx->d_vtab, ctx->d_crt, ctx->d_qbase, ctx->d_ntt_tw, ctx->d_stall};
     for (void *p : dev)

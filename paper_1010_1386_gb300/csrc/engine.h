@@ -39,6 +39,7 @@ struct RsTables {
   uint16_t *p16 = nullptr;   // prefix products in 16-bit digits
   int32_t *poff = nullptr;   // K + 1 row offsets into p16
   int32_t *nh = nullptr;     // digits per prefix product
+  std::vector<int32_t> h_nh;  // the same counts on the host
 };
 
 struct rs_ctx {
@@ -93,6 +94,14 @@ struct rs_ctx {
   int g3m_KB = 0;
   std::vector<void *> g3m_retired;
   bool g3m_ready = false;
+  // Tensor-core CRT limbs: prefix-product tiles of the chunks c < g3l_KB,
+  // block g3l_cbase[c] + u for the units u that chunk c reaches (host and
+  // device copies of cbase; same lifetime rules, kept in g3m_retired).
+  uint16_t *g3l_bt = nullptr;
+  int32_t *g3l_cbase = nullptr;
+  std::vector<int32_t> h_g3l_cbase;
+  int g3l_KB = 0;
+  bool g3l_ready = false;
 };
 
 struct RsClassLaunch {
@@ -211,6 +220,7 @@ int rs_ensure_bhat(rs_ctx *ctx, int lg, int K);
 int rs_ensure_g2t_btile(rs_ctx *ctx, int K, int tiles);
 // W digit tiles of the tensor-core CRT digits for digit blocks kb < KB.
 int rs_ensure_g3m_wtiles(rs_ctx *ctx, int KB);
+int rs_ensure_g3l_tiles(rs_ctx *ctx, int KB);
 // log2 of the G2 transform length for N points (2^lg >= 2N - 1), 0 when
 // above the transform limit; model cost of a form (0 direct, 1 transforms).
 int rs_g2_len(int N);

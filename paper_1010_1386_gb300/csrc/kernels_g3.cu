@@ -374,7 +374,8 @@ __global__ void __launch_bounds__(128) g3b_kernel(G3Args a) {
 
 // Carries and output: one thread per coefficient adds the chunk carries to
 // the chunk limbs and subtracts floor(P / 2), P = p_0 ... p_{K-1} (the offset
-// digits added sum_k (p_k - 1)/2 P_k = (P - 1)/2), giving the symmetric
+// digits added sum_k (p_k - 1)/2 P_k = (P - 1)/2; limbs summed from the
+// signed digits already have the symmetric value), giving the symmetric
 // representative in two's complement; only the Lout low limbs are formed,
 // which is exact because the result fits in them.  Each chunk's 16 limbs of
 // the block's 128 coefficients are staged in shared memory and written back
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
   const uint32_t *xl = a.xl + pd.xl_off + j;
   const int p0 = __ldg(a.poff + pd.K);
   const uint32_t *PK = reinterpret_cast<const uint32_t *>(a.p16 + p0);  // P's 32-bit limbs
-  const int plen = (__ldg(a.poff + pd.K + 1) - p0) / 2;
+  // limbs from the signed digits (tensor-core limb kernel) need no offset: P = 0 here
+  const int plen = a.signed_digits ? 0 : (__ldg(a.poff + pd.K + 1) - p0) / 2;
   uint32_t *o = a.out + pd.out_off;
   int64_t r = 0;
   int last_nz = -1, last_nf = -1;  // last limb != 0, last limb != 0xffffffff

@@ -15,9 +15,9 @@
 // except that each output column k is reduced modulo its own prime p_k.
 // The 64 digits of the block then follow on the CUDA cores from the triangle
 // of W inside the block (warps 0-3: the first 32, then warps 4-7: the last
-// 32), are written over the residues (for the limb kernel, as before) and,
-// as bf16 digits in the tensor cores' layout, to the tile's operand buffer,
-// from which later blocks copy them.
+// 32), are written over the residues and, as bf16 digits in the tensor
+// cores' layout, to the tile's operand buffer, from which later blocks (and
+// the tensor-core limb kernel) copy them.
 //
 // Operands: the tile's digit rows
 //   [64-digit chunk][32-digit stage][digit i][row/8][l/8][row%8][l%8]
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) g3m_kernel(G3mArgs a) {
           const int kk = kHalf * h + t;
           if (kk < bk && j < N) col[base + (size_t)kk * S] = (uint32_t)drow[kk];
         }
-        if (kb + 1 < KB) {
+        {  // every block, the last too: the limb kernel reads them all
 #pragma unroll
           for (int e8 = 0; e8 < 4; ++e8) {
             int32_t v8[8];

@@ -178,6 +178,24 @@ struct G3mArgs {
   const int32_t *stall;     // test hook: non-zero = the copy warp issues nothing
 };
 
+// Tensor-core CRT limbs (kernels_g3l.cu): one block per (128 coefficients of
+// a pair, unit of 64 output limbs), over the 64-prime chunks whose prefix
+// products reach the unit; reads the digit rows the tensor-core digit kernel
+// wrote and writes limb chunks and carries for the output kernel.
+struct G3lArgs {
+  const PairDesc *pairs;
+  const int2 *tasks;        // the digit kernel's tasks: (pair, first coefficient)
+  const int4 *ltasks;       // (digit task, unit, first chunk, -) per block
+  const uint16_t *xdig;     // operand digits of every digit task
+  const int64_t *xoff;      // per digit task: element offset of its operand digits
+  const uint16_t *btiles;   // prefix-product tiles, block cbase[c] + u per (chunk c, unit u)
+  const int32_t *cbase;     // per chunk: its first table block
+  uint32_t *xl;             // out: limbs [16 chunk + w][N] per pair
+  int64_t *carry;           // out: chunk carries [chunk][N] per pair
+  int32_t *err;             // status word (a bounded wait ran out)
+  const int32_t *stall;     // test hook: non-zero = the copy warp issues nothing
+};
+
 // The three NTT primes P0 < P1 < P2 of the transform-based G2 (each
 // c 2^k + 1 with k >= 25, in (2^30, 2^31)) and their Garner constants.
 struct NttConst {
@@ -236,6 +254,7 @@ struct G3Args {
   uint32_t *out;           // out: [coefficient][limb]
   int32_t *shape;          // out: per pair (1 + degree, limbs needed), zeroed before the launch
   int32_t kmax;            // largest K of the batch
+  int32_t signed_digits = 0;  // 1: the limbs come from the signed digits (no floor(P / 2) to remove)
 };
 
 // Launchers (kernels_*.cu).  Each returns the cudaGetLastError() of its launch.
@@ -261,6 +280,11 @@ int64_t g3m_wtile_elems(int KB);
 int64_t g3m_tile_elems(int K);
 cudaError_t launch_g3m_wtiles(const int32_t *wtab, int K, int KB, uint16_t *out, cudaStream_t s);
 cudaError_t launch_g3m(int ntiles, const G3mArgs &a, cudaStream_t s);
+cudaError_t g3l_prepare();
+int64_t g3l_block_elems();  // bf16 elements of one (chunk, unit) block of prefix-product tiles
+cudaError_t launch_g3l_btiles(const uint16_t *p16, const int32_t *poff, int K, const int32_t *cbase, int KB,
+                              int64_t nblocks, uint16_t *out, cudaStream_t s);
+cudaError_t launch_g3l(int ntasks, const G3lArgs &a, cudaStream_t s);
 cudaError_t launch_bhat(const int32_t *btab, int tab_stride, int nb, int K, int lg, const uint2 *tw,
                         const NttConst &nc, uint32_t *bhat, cudaStream_t s);
 // CRT digits by tiles of jt (32 or 16) coefficients (tasks step by jt), any

@@ -1,15 +1,18 @@
-"""Parity of the tensor-core CRT digits (rs_config.crt_form = 2).
+"""Parity of the tensor-core CRT (rs_config.crt_form = 2): digits and limbs.
 
 Garner's mixed-radix digits of a block of 64 primes take the contribution of
 every earlier digit as one exact product on the tensor cores (bf16 digits of
 the earlier digits and of W, fp32 accumulation read out every 64 digits,
 each column reduced modulo its own prime), then the block's own triangle on
-the CUDA cores.  Compared with the CUDA-core digit kernels bit for bit and
-with the oracles: prime counts on both sides of the 64-prime block
-boundaries (one block only, exactly 64, 65, 128, 129, several hundred),
-coefficient counts that leave the last 128-coefficient tile ragged, and the
-dense degree-15 shift workload at k = 512 against O2's digests.  Expected
-values never come from the GPU.
+the CUDA cores.  The limbs sum_k v_k P_k are a second exact product: the
+signed digits against the balanced bytes of the prefix products, by units
+of 256 byte columns, with the fp32 columns carry-saved between windows.
+Compared with the CUDA-core CRT kernels bit for bit and with the oracles:
+prime counts on both sides of the 64-prime block boundaries (one block
+only, exactly 64, 65, 128, 129, several hundred), coefficient counts that
+leave the last 128-coefficient tile ragged, several tiles with many primes,
+and the dense degree-15 shift workload at k = 512 against O2's digests.
+Expected values never come from the GPU.
 """
 import random
 
@@ -88,3 +91,26 @@ def test_shift_workload_full_size_exact():
     with rs.Context(device=0, crt_form=TENSOR) as c:
         got = c.resultant_batch(pairs)
     assert_full_size("shift_15_dense_512", got, pairs)
+
+
+def test_many_coefficient_tiles_and_limb_units():
+    """Pairs with 129 to 289 coefficients (two or three 128-row tiles, the
+    last ragged) and 235 to about 2,500 primes (up to 40 chunks: many
+    carry-saved windows, up to 39 units of 64 limbs): the tensor-core CRT
+    against the CUDA-core one, every coefficient, and sampled values against
+    the oracle."""
+    rng = random.Random(54)
+    pairs = []
+    for bits, dx, dy in ((900, 6, 11), (2500, 8, 8), (300, 12, 12), (3000, 10, 13)):
+        pairs.append((rand_bipoly(rng, dx, dy, bits=bits), rand_bipoly(rng, dx, dy, bits=bits)))
+    shapes = [rs.result_bound(f, g) for f, g in pairs]
+    assert any(b["deg"] + 1 > 256 for b in shapes) and all(b["deg"] + 1 > 128 for b in shapes), shapes
+    assert max(b["primes"] for b in shapes) > 2048, shapes
+    got = {}
+    for form in (CUDA_CORES, TENSOR):
+        with rs.Context(device=0, crt_form=form) as c:
+            got[form] = c.resultant_batch(pairs)
+    assert got[TENSOR] == got[CUDA_CORES]
+    rng2 = random.Random(55)
+    for (f, g), R in zip(pairs, got[TENSOR]):
+        check_sampled_31(f, g, R, rng2, samples=2)
