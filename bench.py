@@ -514,16 +514,27 @@ def batch_main(args, world, rank, local, dist):
         b.run()
         b.results(raw=True)
     barrier(dist, local)
-    t = time.perf_counter()
-    for s in range(e2e_steps):
-        b = pipe[s % depth]
-        if s >= depth:
-            b.results(raw=True)  # step s - depth: its results before the batch is reused
-        b.upload(pairs)
-        b.run()
-    for s in range(max(0, e2e_steps - depth), e2e_steps):
-        pipe[s % depth].results(raw=True)
-    pipe_ms = 1e3 * (time.perf_counter() - t) / e2e_steps
+    # GPU span of the loop: the first step's stream from its first upload to
+    # the last step's stream after its last run (the events wait on nothing
+    # else, so the span counts the device time of the overlapped steps).
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks_e2e:  # the pipelined loop keeps the GPU busy for longer
+        t = time.perf_counter()
+        for s in range(e2e_steps):
+            b = pipe[s % depth]
+            if s >= depth:
+                b.results(raw=True)  # step s - depth: its results before the batch is reused
+            if s == 0:
+                g0.record(streams[0])
+            b.upload(pairs)
+            b.run()
+            if s == e2e_steps - 1:
+                g1.record(streams[s % depth])
+        for s in range(max(0, e2e_steps - depth), e2e_steps):
+            pipe[s % depth].results(raw=True)
+        pipe_ms = 1e3 * (time.perf_counter() - t) / e2e_steps
+    torch.cuda.synchronize(local)
+    pipe_gpu_ms = g0.elapsed_time(g1) / e2e_steps
     e2e_val = world * npairs / (max_over_ranks(dist, local, pipe_ms) * 1e-3)
     for b in pipe:
         b.close()
@@ -566,6 +577,8 @@ def batch_main(args, world, rank, local, dist):
                 "d2h_bytes_per_step": info["output_bytes"],
                 "form": "pipelined: three prepared batches on three streams rotate (a step's result "
                         "copy and trim just before its batch is reused), %d steps" % e2e_steps,
+                "clocks": clocks_e2e.summary(),
+                "gpu_ms_per_step": pipe_gpu_ms,
                 "sequential": {"value": e2e_seq, "unit": "resultants/s",
                                "form": "one prepared batch: upload, run, results, step after step"}},
         "autotune": {"build_s": t_tune,
