@@ -254,16 +254,21 @@ int rs_ensure_g3m_wtiles(rs_ctx *ctx, int KB) {
   if (t.K < 64 * (KB - 1))
     return rs_fail(ctx, RS_ERR_STATE, "tensor-core CRT tables: CRT tables not built for these primes");
   DevGuard dg(ctx->device);
-  uint16_t *nw = nullptr;
+  uint16_t *nw = nullptr, *nr = nullptr;
   cudaError_t e = cudaMalloc(&nw, (size_t)std::max<int64_t>(1, g3m_wtile_elems(KB)) * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&nr, (size_t)std::max<int64_t>(1, g3m_rtile_elems(KB)) * sizeof(uint16_t));
   if (e == cudaSuccess) e = launch_g3m_wtiles(t.wtab, t.K, KB, nw, ctx->stream);
+  if (e == cudaSuccess) e = launch_g3m_rtiles(t.wtab, t.K, KB, nr, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     if (nw) cudaFree(nw);
+    if (nr) cudaFree(nr);
     return rs_fail(ctx, rs_cuda_code(e), std::string("tensor-core CRT tables: ") + cudaGetErrorString(e));
   }
   if (ctx->g3m_wt) ctx->g3m_retired.push_back(ctx->g3m_wt);
+  if (ctx->g3m_rt) ctx->g3m_retired.push_back(ctx->g3m_rt);
   ctx->g3m_wt = nw;
+  ctx->g3m_rt = nr;
   ctx->g3m_KB = KB;
   return RS_OK;
 }
@@ -1360,6 +1365,7 @@ static int enqueue(rs_batch *b, bool capturing) {
       {
         std::lock_guard<std::mutex> lock(ctx->tab_mu);
         am.wtiles = ctx->g3m_wt;
+        am.rtiles = ctx->g3m_rt;
       }
       am.coef = b->d_num;
       am.xdig = b->d_g3m_x;
@@ -1669,6 +1675,7 @@ int rs_destroy(rs_ctx *ctx) {
     if (ctx->g2t_bt) cudaFree(ctx->g2t_bt);
     for (void *bt : ctx->g2t_retired) cudaFree(bt);
     if (ctx->g3m_wt) cudaFree(ctx->g3m_wt);
+    if (ctx->g3m_rt) cudaFree(ctx->g3m_rt);
     if (ctx->g3l_bt) cudaFree(ctx->g3l_bt);
     if (ctx->g3l_cbase) cudaFree(ctx->g3l_cbase);
     for (void *wt : ctx->g3m_retired) cudaFree(wt);

@@ -91,6 +91,7 @@ struct rs_ctx {
   // Tensor-core CRT digits: W digit tiles of the digit blocks kb < g3m_KB
   // (same lifetime rules as above).
   uint16_t *g3m_wt = nullptr;
+  uint16_t *g3m_rt = nullptr;  // per block: the rect digit tile (W of its last 32 primes on its first 32)
   int g3m_KB = 0;
   std::vector<void *> g3m_retired;
   bool g3m_ready = false;

@@ -171,6 +171,7 @@ struct G3mArgs {
   const uint32_t *crt;      // (p_0 ... p_{k-1})^{-1} mod p_k, Montgomery form
   const int32_t *wtab;      // triangular W[k][l] (signed Montgomery), as for the other digit kernels
   const uint16_t *wtiles;   // W digit tiles per (block, chunk)
+  const uint16_t *rtiles;   // per block: W of its last 32 primes against its first 32, as digits
   uint32_t *coef;           // in: R mod p_k (plain); overwritten by the digits
   uint16_t *xdig;           // operand digits of every tile (zeroed once)
   const int64_t *xoff;      // per task: element offset of its operand digits
@@ -279,6 +280,8 @@ cudaError_t g3m_prepare();
 int64_t g3m_wtile_elems(int KB);
 int64_t g3m_tile_elems(int K);
 cudaError_t launch_g3m_wtiles(const int32_t *wtab, int K, int KB, uint16_t *out, cudaStream_t s);
+int64_t g3m_rtile_elems(int KB);
+cudaError_t launch_g3m_rtiles(const int32_t *wtab, int K, int KB, uint16_t *out, cudaStream_t s);
 cudaError_t launch_g3m(int ntiles, const G3mArgs &a, cudaStream_t s);
 cudaError_t g3l_prepare();
 int64_t g3l_block_elems();  // bf16 elements of one (chunk, unit) block of prefix-product tiles
