@@ -822,9 +822,9 @@ def measure_batch(ctx, pairs, steps, warmup, stream, flush, e2e_steps=0):
 
 def other_configs(ctx, local, steps, flush, stream):
     """Compact records of the other configurations, on the same GPU right
-    after the headline workload: configs[1] (one dense degree-30 pair, with
-    its end-to-end rate), the coprime non-generic batch of 32 (configs[3]'s
-    non-zero variant) and the serving stream of configs[4] (10,000 requests
+    after the headline workload: the single dense degree-30 pair (with its
+    end-to-end rate), the coprime non-generic batch of 32 (g = (pq)_y, the
+    non-zero variant of f = p q^2, g = f_y) and the serving stream (10,000 requests
     at 0.8 of the measured saturation rate)."""
     from paper_1010_1386_gb300 import inputs
     out = {}
@@ -850,7 +850,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-per-instance", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
-                    help="batch workload: skip the compact records of configs[1], [3'] and [4]")
+                    help="batch workload: skip the compact records of the single degree-30 pair, "
+                         "the coprime non-generic batch and the serving stream")
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write profiles/g1_traffic.json from an ncu --csv log of the G1 launches and exit")
     ap.add_argument("--record-command", default="", help="the ncu command that wrote CSV (stored with it)")

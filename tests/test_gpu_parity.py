@@ -1,9 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Small inputs are compared coefficient by coefficient with the exact oracle
-O1; every instance of the full-size workloads (configs[1], all 512 pairs of
-configs[2], all 32 pairs of configs[3] and its coprime variant, the first
-512 requests of configs[4]) is compared coefficient by coefficient with the
+O1; every instance of the full-size workloads (the single dense degree-30
+pair, all 512 pairs of the batch, all 32 pairs of the non-generic batch
+f = p q^2, g = f_y and of its coprime variant, the first 512 requests of the
+serving stream) is compared coefficient by coefficient with the
 independent modular oracle O2 through the stored digests of its exact
 results (tests/golden/full_size.json).  Sampled modular images are checked
 against det S(x_i) mod p at the library's own points.  Expected values never
@@ -158,7 +159,7 @@ def test_images_against_oracle(ctx):
 # ---------------------------------------------------------- full-size configs
 
 def test_single_dense30_full_size(ctx):
-    """configs[1] (dense total degree 30, signed 32-bit): every coefficient
+    """The single pair of dense total degree 30 (signed 32-bit): every coefficient
     against the oracle O2, the planner's bounds, and sampled images against
     the result reduced at the library's own points."""
     [(f, g)] = inputs.workload_single(1)
@@ -174,7 +175,7 @@ def test_single_dense30_full_size(ctx):
 
 
 def test_batch_full_size_exact(ctx):
-    """configs[2], all 512 pairs in one batch: every coefficient of every
+    """The 512-pair batch, all pairs in one batch: every coefficient of every
     resultant against the oracle O2, and the degree bound."""
     pairs = inputs.workload_batch(2, n=512)
     got = ctx.resultant_batch(pairs)
