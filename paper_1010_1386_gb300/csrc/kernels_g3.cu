@@ -401,15 +401,28 @@ __global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
   int64_t r = 0;
   int last_nz = -1, last_nf = -1;  // last limb != 0, last limb != 0xffffffff
   uint32_t top_nz = 0u, top_nf = 0u, top = 0u;
+  // A chunk's loads (its limbs, P's limbs, its carry) are independent of the
+  // carry chain: chunk c + 1's are issued before chunk c's chain and stores,
+  // so a chunk does not wait a memory latency after the previous one.
+  auto load = [&](int c, uint32_t (&x)[16], uint32_t (&pkv)[17], int64_t &cyv) {
+#pragma unroll
+    for (int w = 0; w < 16; ++w) x[w] = xl[(size_t)(16 * c + w) * N];
+#pragma unroll
+    for (int w = 0; w < 17; ++w) pkv[w] = 16 * c + w < plen ? __ldg(PK + 16 * c + w) : 0u;
+    cyv = a.carry[pd.cy_off + (size_t)c * N + j];
+  };
+  uint32_t xw[16], pk[17];
+  int64_t cy = 0;
+  if (live && C > 0) load(0, xw, pk, cy);
   for (int c = 0; c < C; ++c) {
+    uint32_t xn[16], pn[17];
+    int64_t cn = 0;
+#pragma unroll
+    for (int w = 0; w < 16; ++w) xn[w] = 0u;
+#pragma unroll
+    for (int w = 0; w < 17; ++w) pn[w] = 0u;
+    if (live && c + 1 < C) load(c + 1, xn, pn, cn);
     if (live) {
-      // every load of the chunk first (they are independent), then the carry chain
-      uint32_t xw[16], pk[17];
-#pragma unroll
-      for (int w = 0; w < 16; ++w) xw[w] = xl[(size_t)(16 * c + w) * N];
-#pragma unroll
-      for (int w = 0; w < 17; ++w) pk[w] = 16 * c + w < plen ? __ldg(PK + 16 * c + w) : 0u;
-      const int64_t cy = a.carry[pd.cy_off + (size_t)c * N + j];
 #pragma unroll
       for (int w = 0; w < 16; ++w) {
         const int l = 16 * c + w;
@@ -440,6 +453,11 @@ __global__ void __launch_bounds__(128) g3c_kernel(G3Args a) {
       if (j0 + jj < N && w < nl) o[(size_t)(j0 + jj) * L + 16 * c + w] = T[jj * 17 + w];
     }
     __syncthreads();
+#pragma unroll
+    for (int w = 0; w < 16; ++w) xw[w] = xn[w];
+#pragma unroll
+    for (int w = 0; w < 17; ++w) pk[w] = pn[w];
+    cy = cn;
   }
   if (!live) return;
   // fewest limbs whose two's-complement value is this coefficient
