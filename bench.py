@@ -847,7 +847,9 @@ def other_configs(ctx, local, steps, flush, stream):
     """Compact records of the other configurations, on the same GPU right
     after the headline workload: the single dense degree-30 pair (with its
     end-to-end rate), the coprime non-generic batch of 32 (g = (pq)_y, the
-    non-zero variant of f = p q^2, g = f_y) and the serving stream (10,000 requests
+    non-zero variant of f = p q^2, g = f_y), both projections of the dense
+    degree-15 shift workload at k = 2048 (about 2,000 primes per resultant;
+    with its end-to-end rate) and the serving stream (10,000 requests
     at 0.8 of the measured saturation rate)."""
     from paper_1010_1386_gb300 import inputs
     out = {}
@@ -855,6 +857,9 @@ def other_configs(ctx, local, steps, flush, stream):
                                              e2e_steps=20)
     out["c3p_nongeneric_coprime_32"] = measure_batch(ctx, inputs.workload_nongeneric(3, n=32, coprime=True),
                                                      max(3, min(steps, 5)), 2, stream, flush)
+    base = inputs.workload_shift(5, 15, False, 2048)
+    shift = base + [(inputs.swap_xy(f), inputs.swap_xy(g)) for f, g in base]
+    out["shift_dense15_k2048"] = measure_batch(ctx, shift, max(3, min(steps, 10)), 3, stream, flush, e2e_steps=10)
     srv = measure_serving(local, 10000, 0.8, 3, 256)
     out["c4_serving_10000"] = {k: srv[k] for k in ("value", "unit", "latency_ms", "saturation",
                                                    "arrival_rate_per_s", "load_vs_saturation", "wall_s")}
@@ -874,7 +879,8 @@ def main():
     ap.add_argument("--no-per-instance", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="batch workload: skip the compact records of the single degree-30 pair, "
-                         "the coprime non-generic batch and the serving stream")
+                         "the coprime non-generic batch, the k = 2048 shift workload and the "
+                         "serving stream")
     ap.add_argument("--record-traffic", default=None, metavar="CSV",
                     help="write profiles/g1_traffic.json from an ncu --csv log of the G1 launches and exit")
     ap.add_argument("--record-command", default="", help="the ncu command that wrote CSV (stored with it)")
