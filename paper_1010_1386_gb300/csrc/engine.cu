@@ -638,7 +638,8 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
   // length instead (256 threads, shared memory 3 N + 2^lg words).
   // The form is chosen per transform-length group: forced by the context or
   // the options, else the tuner's cached choice (timed now when missing and
-  // allowed; groups with lg < 9 keep the model's choice), else the model.
+  // allowed; groups with lg < 7, under 64 point pairs, keep the model's
+  // choice), else the model.
   std::vector<int> g2lg(n, 0), g2t_lg(n, 0);  // transform / tensor-core length group per pair
   int bhatK[RS_NTT_LGMAX + 1] = {};
   const bool g2tri = ctx->cfg.g2_form == 3;  // triangular factorisation of the Vandermonde system
@@ -681,7 +682,7 @@ int rs_build_batch(rs_ctx *ctx, int n, const rs_bipoly *f, const rs_bipoly *g,
         form = ctx->cfg.g2_form == 2 ? 1 : ctx->cfg.g2_form == 4 ? 2 : 0;
       } else if (opt.g2_force >= 0) {
         form = opt.g2_force;
-      } else if (lg >= 9) {
+      } else if (lg >= 7) {
         const int64_t key = rs_tune_key_g2(ctx->sms, lg, images);
         RsG1Choice c;
         if (rs_tune_find(key, &c)) {
