@@ -573,7 +573,9 @@ def batch_main(args, world, rank, local, dist):
                       "univariate": ("Schur algorithm on displacement generators, one warp per image"
                                      if args.univariate == "schur" else
                                      "division-free remainder sequence, one thread per image"),
-                      "interpolation": {"auto": "convolutions (direct or transforms per pair)",
+                      "interpolation": {"auto": "convolutions per length group: direct, transforms or all pairs of "
+                                                "a prime as one exact tensor-core product (bf16 digits, fp32 "
+                                                "accumulation), as the tuner chose",
                                         "direct": "direct convolutions", "transforms": "transforms",
                                         "triangular": "triangular factorisation of the Vandermonde "
                                                       "system (Bjorck-Pereyra stages)",
